@@ -1,0 +1,354 @@
+"""Benchmark of the D3Q19 sweep on GB300: MLUPS and fraction of the HBM roofline.
+
+Workload (one "step" = one Sweep = ghost exchange + fused stream/collide over
+every Block): a body-force channel of 256^3 cells split into 4x4x4 Blocks of
+64^3 with the on-device ghost-layer exchange, periodic along x and z, resting
+walls at -y/+y, BGK tau = 0.8, force 1e-6 along x, FP32 storage and arithmetic.
+Synthetic input (the state starts at rest, as in the paper's runs).  The two
+PDF buffers (2 x 1.4 GB) are far larger than L2, so no flush is needed.
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (the path has no data
+exchange between GPUs); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, B, TAU, FORCE = 256, 64, 0.8, 1e-6
+BYTES_PER_LUP = {0: 19 * 4 * 2 + 1, 1: 19 * 2 * 2 + 1, 2: 19 * 2 * 2 + 1, 3: 19 * 8 * 2 + 1}
+WORKLOAD = ("D3Q19 body-force channel 256^3, 4x4x4 Blocks of 64^3 with on-device ghost "
+            "exchange, periodic x/z, no-slip y walls, BGK tau=0.8, F=1e-6 (configs[1])")
+METRIC = "MLUPS"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        smax = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[2] > 0.3 * max(x[2] for x in rows)] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _oracle_sample(seconds, warm_steps=0):
+    """The FP64 oracle on a bounded sample of the workload (a 64^3 channel with
+    the same boundaries and physics), stepped until `seconds` have passed."""
+    import oracle
+
+    oracle.build()
+    n = 64
+    p = oracle.Problem(dims=(n, n, n), tau=TAU, periodic=(1, 0, 1), force=(FORCE, 0, 0))
+    f = oracle.zeros(p)
+    if warm_steps:
+        f = oracle.run(p, f, warm_steps)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        f = oracle.step(p, f)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and steps >= 3:
+            break
+    return n**3 * steps / el / 1e6, steps, el
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    n = 64
+    p = oracle.Problem(dims=(n, n, n), tau=TAU, periodic=(1, 0, 1), force=(FORCE, 0, 0))
+    # each step: one oracle time step of a 64^3 block of the channel; the run
+    # stays within a few minutes for the default step counts
+    per_step_budget = 120.0 / max(1, args.steps + args.warmup)
+    f = oracle.zeros(p)
+    t_one = time.perf_counter()
+    f = oracle.step(p, f)
+    t_one = time.perf_counter() - t_one
+    cells = n**3
+    if t_one > per_step_budget:
+        # shrink the sample along z so the whole run stays bounded
+        nz = max(1, int(n * per_step_budget / t_one))
+        p = oracle.Problem(dims=(n, n, nz), tau=TAU, periodic=(1, 0, 1), force=(FORCE, 0, 0))
+        f = oracle.zeros(p)
+        cells = n * n * nz
+    for _ in range(args.warmup):
+        f = oracle.step(p, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.step(p, f)
+    el = time.perf_counter() - t0
+    v = cells * args.steps / el / 1e6
+    sample = f"64x64x{cells // 4096} channel block per step, FP64 C oracle, single thread"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+           "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_1007_1388_gb300 import build
+
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    import paper_1007_1388_gb300 as L
+    from paper_1007_1388_gb300 import workloads as W
+
+    L.use_torch_allocator()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def make(storage=L.LBM_F32, coll=L.LBM_BGK, **extra):
+        p = L.make_params(collision=coll, force=(FORCE, 0, 0), storage=storage,
+                          **W.channel_bc(), **extra)
+        return L.lbm_create((N, N, N), (B, B, B), TAU, None, p)
+
+    ctx = make()
+    info = L.lbm_get_info(ctx)
+    cells = info.cells
+    stream = ctx.stream  # the torch stream the library enqueues on
+
+    # ---- warm-up, then the timed region: K steps, per-launch events live
+    L.lbm_step(ctx, args.warmup)
+    L.lbm_profile_enable(ctx, True)
+    L.lbm_profile_read(ctx)  # clear
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev) as clk:
+        e0.record(stream)
+        L.lbm_step(ctx, args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    prof = L.lbm_profile_read(ctx)
+    L.lbm_profile_enable(ctx, False)
+    ms_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e6
+
+    # ---- graph-replay timing of the same step (information)
+    barrier()
+    e0.record(stream)
+    L.lbm_step(ctx, args.steps)
+    e1.record(stream)
+    barrier()
+    graph_mlups = cells * args.steps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+
+    peak, peak_kind = _peaks()
+    sweep_ms = prof.sweep_ms / max(1, prof.sweep_launches)
+    xch_ms = prof.exchange_ms / max(1, prof.exchange_launches)
+    alg_bytes = BYTES_PER_LUP[0] * cells
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    traffic = _ncu_traffic("sweep_f32_channel256")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": peak_kind, "kernel": "lbm::sweep_kernel<F32,BGK,forced>",
+                "bytes_per_lup": BYTES_PER_LUP[0], "sweep_ms": sweep_ms,
+                "exchange_ms": xch_ms, "exchange_pdfs": info.exchange_pdfs}
+
+    # ---- e2e: through the C ABI with pinned host buffers, copies included
+    e2e = None
+    if not args.skip_e2e:
+        rho_h = torch.ones(cells, dtype=torch.float32).pin_memory()
+        u_h = torch.zeros(3 * cells, dtype=torch.float32).pin_memory()
+        rho_o = torch.empty(cells, dtype=torch.float32).pin_memory()
+        u_o = torch.empty(3 * cells, dtype=torch.float32).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        L.lbm_init_equilibrium(ctx, rho_h, u_h)             # H2D of the initial fields
+        L.lbm_run_to_residual(ctx, 0.0, 10, args.steps)     # residual D2H every 10 steps
+        L.lbm_macroscopic(ctx, rho_o, u_o)                  # D2H of the final fields
+        barrier()
+        el = time.perf_counter() - t0
+        checks = (args.steps + 9) // 10
+        e2e = {"value": ws * cells * args.steps / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 16 * cells / args.steps,
+               "d2h_bytes_per_step": (16 * cells + 8 * R_K_HOST * checks) / args.steps,
+               "calls": "lbm_init_equilibrium + lbm_run_to_residual(check_every=10) + lbm_macroscopic"}
+    ctx.destroy()
+
+    # ---- storage variants and TRT on the same workload (information)
+    variants = {}
+    if not args.skip_variants:
+        vsteps = max(50, min(args.steps, 500))
+        for name, kw in [("trt_f32", dict(coll=L.LBM_TRT)),
+                         ("bgk_f16s", dict(storage=L.LBM_F16S, storage_scale=256.0)),
+                         ("bgk_bf16s", dict(storage=L.LBM_BF16S)),
+                         ("bgk_f64", dict(storage=L.LBM_F64))]:
+            c = make(**kw)
+            L.lbm_step(c, 5)
+            L.lbm_profile_enable(c, True)
+            L.lbm_profile_read(c)
+            barrier()
+            e0.record(stream)
+            L.lbm_step(c, vsteps)
+            e1.record(stream)
+            barrier()
+            pr = L.lbm_profile_read(c)
+            st = kw.get("storage", 0)
+            sw = pr.sweep_ms / max(1, pr.sweep_launches)
+            variants[name] = {
+                "mlups": cells * vsteps / (e0.elapsed_time(e1) * 1e-3) / 1e6,
+                "sweep_gbs": BYTES_PER_LUP[st] * cells / (sw * 1e-3) / 1e9,
+                "frac": BYTES_PER_LUP[st] * cells / (sw * 1e-3) / 1e9 / peak,
+                "bytes_per_lup": BYTES_PER_LUP[st]}
+            c.destroy()
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        v, steps, el = _oracle_sample(args.cpu_seconds)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"64^3 block of the same channel, {steps} FP64 steps in {el:.1f} s, "
+                         "single-threaded C"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "cells": cells, "blocks": info.blocks,
+                          "tile": list(info.tile), "parallelism": f"replicas x{ws}",
+                          "l2": "inputs larger than L2 (2 x 1.4 GB PDF buffers), no flush"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": int(prof.sweep_launches + prof.exchange_launches),
+               "clocks": clk.summary(), "graph_mlups": graph_mlups, "variants": variants}
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+R_K_HOST = 8  # doubles per instance read back by one residual check
+
+
+def _ncu_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d[name]
+        from paper_1007_1388_gb300 import build
+
+        if ent.get("kernel_hash") != build.kernel_hash():
+            return None
+        return ent["dram_bytes_per_launch_full"]
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-variants", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

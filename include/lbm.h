@@ -1,0 +1,259 @@
+/*
+ * lbm.h - C ABI of the GB300 D3Q19 lattice Boltzmann library (liblbm.so).
+ *
+ * The library runs the data-parallel hot path of the patch/block lattice
+ * Boltzmann scheme of Feichtinger et al. on one GPU: the fused pull
+ * stream-and-collide sweep (Sec. 2.1, Eq. (1)-(2); GPU kernel design of
+ * Sec. 3.2) with half-way bounce-back and moving walls read from a per-cell
+ * flag field (Sec. 2.1), and the ghost-layer exchange between the Blocks of
+ * one Patch (Sec. 4.2, Sec. 4.4), done entirely in device memory.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an lbm_status (0 = LBM_OK); no C++ exception
+ *    crosses this boundary.  lbm_last_error() gives a readable message.
+ *  - The library owns all device memory of a context (allocated through the
+ *    allocator installed with lbm_set_allocator, cudaMalloc by default) and
+ *    enqueues all work on the context's stream (lbm_params.stream, or a
+ *    stream it creates).  The caller owns every host buffer and every device
+ *    buffer it passes in.
+ *  - "host" pointers are ordinary CPU memory (pageable or pinned); "device"
+ *    pointers are CUDA device memory of the current device.  Entry points
+ *    taking host pointers synchronise the context stream before returning;
+ *    entry points taking device pointers (suffix _device) only enqueue.
+ *  - A context is used by one host thread at a time.
+ *  - Cell fields are laid out with x fastest: cell (x,y,z) of a domain of
+ *    nx*ny*nz interior cells has index c = (z*ny + y)*nx + x.  PDF arrays
+ *    are direction-major: f[q*N + c].  Velocity arrays are component-major:
+ *    u[a*N + c].  For a batch context the instances are concatenated in
+ *    order, each with its own N_k and this layout inside its slice
+ *    (PDF slice 19*N_k values, velocity slice 3*N_k values).
+ *
+ * D3Q19 directions (Sec. 2.1: 19 PDFs per cell, weights 1/3, 1/18, 1/36):
+ *    q :  0   1   2   3   4   5   6   7   8   9  10  11  12  13  14  15  16  17  18
+ *   ex :  0  +1  -1   0   0   0   0  +1  -1  +1  -1  +1  -1  +1  -1   0   0   0   0
+ *   ey :  0   0   0  +1  -1   0   0  +1  -1  -1  +1   0   0   0   0  +1  -1  +1  -1
+ *   ez :  0   0   0   0   0  +1  -1   0   0   0   0  +1  -1  -1  +1  +1  -1  -1  +1
+ * opposite(q) = q+1 for odd q, q-1 for even q > 0, and 0 for q = 0.
+ *
+ * PDFs are exchanged in their shifted form f~_q = f_q - w_q rho0 (Sec. 2.1),
+ * so a fluid at rest with density rho0 has f~ = 0.  The stored state after a
+ * step holds post-collision values; rho = rho0 + sum_q f~_q and
+ * u = (sum_q e_q f~_q - F/2)/rho0 recover the density and velocity that the
+ * last collision of each cell used.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_Q 19
+
+/* Status codes. */
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,    /* an argument is out of its documented range */
+    LBM_ENOMEM = -2,    /* the allocator returned NULL */
+    LBM_ECUDA = -3,     /* a CUDA call failed (message in lbm_last_error) */
+    LBM_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    LBM_ENUMERIC = -5   /* a NaN or Inf was found where the call checks for it */
+} lbm_status;
+
+/* Per-cell flag values (one uint8 per interior cell). */
+enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_MOVING = 2 };
+/* Collision operators: single relaxation time of Eq. (1), or two relaxation times. */
+enum { LBM_BGK = 0, LBM_TRT = 1 };
+/* PDF storage formats.  Arithmetic is FP32 for the first three and FP64 for
+ * LBM_F64.  F16S/BF16S store the shifted PDF f~ (times storage_scale) in
+ * IEEE half / bfloat16, rounded to nearest even. */
+enum { LBM_F32 = 0, LBM_F16S = 1, LBM_BF16S = 2, LBM_F64 = 3 };
+
+typedef struct {
+    int collision;        /* LBM_BGK (default) or LBM_TRT */
+    double magic;         /* TRT Lambda = (tau - 1/2)(1/omega_minus - 1/2); default 3/16 */
+    double rho0;          /* reference density; default 1 */
+    double force[3];      /* body force density F (Guo forcing); default 0 */
+    double wall_u[3];     /* velocity of every LBM_MOVING wall or cell; default 0 */
+    int periodic[3];      /* 1 = periodic along x / y / z; default 0 */
+    int face_bc[6];       /* wall kind beyond the -x,+x,-y,+y,-z,+z faces of a
+                             non-periodic axis: LBM_NOSLIP (default) or LBM_MOVING.
+                             Edge and corner cells of the wall shell shared by two
+                             walls rest (LBM_NOSLIP). */
+    int storage;          /* LBM_F32 (default), LBM_F16S, LBM_BF16S, LBM_F64 */
+    double storage_scale; /* power of two multiplying f~ in F16S/BF16S storage; default 1 */
+    void *stream;         /* cudaStream_t to enqueue on; NULL = the library creates one */
+    int tile[3];          /* sweep tile: threads along x, rows along y, cells per thread
+                             along z; {0,0,0} = the library's default (or lbm_autotune) */
+    int graph_steps;      /* steps per captured CUDA graph; 0 = automatic, -1 = no graphs */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fills *p with the defaults listed above. */
+void lbm_default_params(lbm_params *p);
+
+/*
+ * lbm_create - one Patch (Sec. 4.2) of dims[0]*dims[1]*dims[2] interior
+ * cells split into a Cartesian grid of Blocks of block_dims cells each.
+ *   dims, block_dims : host int[3]; dims[a] must be a positive multiple of
+ *                      block_dims[a] (else LBM_EINVAL).
+ *   tau              : relaxation time, > 1/2 (else LBM_EINVAL); omega = 1/tau.
+ *   flags            : host uint8[nx*ny*nz] with LBM_FLUID/NOSLIP/MOVING, x fastest,
+ *                      copied; NULL = all fluid.
+ *   p                : host, may be NULL for defaults.
+ *   out              : receives the context; NULL on failure.
+ * Every Block carries a one-cell ghost shell.  Along periodic axes the
+ * ghost cells are images of the opposite boundary (filled by the exchange);
+ * beyond non-periodic faces they are walls of kind face_bc.  The state starts
+ * at rest: f~ = 0 in every cell (Sec. 2.1 initialisation).
+ */
+int lbm_create(const int dims[3], const int block_dims[3], double tau, const uint8_t *flags,
+               const lbm_params *p, lbm_ctx **out);
+
+/*
+ * lbm_batch_create - n independent instances (each one single-Block Patch)
+ * in one context, advanced together by one sweep launch per step.
+ *   dims  : host int[n*3], the interior size of each instance.
+ *   tau   : host double[n], one relaxation time per instance (> 1/2).
+ *   flags : host array of n pointers to uint8[nx_k*ny_k*nz_k]; the array or
+ *           any entry may be NULL (all fluid).
+ *   p     : boundary kinds, force, storage etc. shared by all instances.
+ */
+int lbm_batch_create(int n, const int *dims, const double *tau, const uint8_t *const *flags,
+                     const lbm_params *p, lbm_ctx **out);
+
+/* Releases every resource of the context (NULL is ignored). */
+void lbm_destroy(lbm_ctx *ctx);
+
+/*
+ * lbm_step - advance n >= 0 time steps.  Each step is one Sweep (Sec. 4):
+ * the communication step (ghost exchange in device memory) then the work
+ * step (fused pull stream + bounce-back + collide, Eq. (1)).  Enqueued on
+ * the context stream; device errors surface at the next synchronising call.
+ */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/* Blocks until all enqueued work of the context has finished. */
+int lbm_synchronize(lbm_ctx *ctx);
+
+/*
+ * lbm_macroscopic - density and velocity of every interior cell of the
+ * current state (Sec. 2.1 moments): rho = rho0 + sum f~, u = (sum e f~ - F/2)/rho0.
+ * Solid cells report rho0 and 0.  rho: float[N], u: float[3*N].
+ * The host variant synchronises; the _device variant writes caller-owned
+ * device arrays asynchronously on the context stream.
+ */
+int lbm_macroscopic(lbm_ctx *ctx, float *rho, float *u);
+int lbm_macroscopic_device(lbm_ctx *ctx, float *rho, float *u);
+
+/*
+ * lbm_get_pdfs / lbm_set_pdfs - the shifted PDFs f~ of the current state as
+ * host double[19*N] (checkpoint / restart and parity interface).  Solid
+ * cells read as 0; values written into solid cells are ignored.  With
+ * F16S/BF16S storage, set rounds to the storage format.
+ */
+int lbm_get_pdfs(lbm_ctx *ctx, double *f);
+int lbm_set_pdfs(lbm_ctx *ctx, const double *f);
+
+/*
+ * lbm_init_equilibrium - sets every fluid cell to f~eq(rho - rho0, u) of
+ * Eq. (2) (warm start from given fields).  rho: float[N], u: float[3*N].
+ */
+int lbm_init_equilibrium(lbm_ctx *ctx, const float *rho, const float *u);
+int lbm_init_equilibrium_device(lbm_ctx *ctx, const float *rho, const float *u);
+
+/*
+ * lbm_invariants - FP64 sums over fluid cells of the current state:
+ * mass = sum (rho0 + sum f~), momentum = sum (sum e f~ - F/2), and the number
+ * of cells holding a NaN or Inf (nonfinite may be NULL).  Host outputs.
+ * per_instance != NULL receives 5 doubles per instance
+ * {mass, mom_x, mom_y, mom_z, nonfinite}.  Deterministic for a given context.
+ */
+int lbm_invariants(lbm_ctx *ctx, double *mass, double mom[3], double *nonfinite,
+                   double *per_instance);
+
+/*
+ * lbm_residual - one-step velocity residual r = ||u_n - u_{n-1}||_2 / ||u_n||_2
+ * over fluid cells (FP64), between the current state and the one before the
+ * last step.  r = 0 when both norms vanish.  per_instance != NULL receives one
+ * residual per instance.  LBM_EINVAL if no step has been taken since the
+ * state was last set.
+ */
+int lbm_residual(lbm_ctx *ctx, double *r, double *per_instance);
+
+/*
+ * lbm_run_to_residual - steps in chunks of check_every until the residual
+ * falls below tol or max_steps is reached.  *steps receives the steps taken
+ * and *r the last residual.  Returns LBM_ENUMERIC if a NaN appears.
+ */
+int lbm_run_to_residual(lbm_ctx *ctx, double tol, int check_every, long long max_steps,
+                        long long *steps, double *r);
+
+/* Sizes of a context. */
+typedef struct {
+    long long cells;          /* interior cells over all Blocks / instances */
+    long long fluid_cells;    /* interior fluid cells */
+    long long stored_cells;   /* cells per PDF buffer including ghost shells and padding */
+    int blocks;               /* Blocks (patch) or instances (batch) */
+    int instances;
+    int storage;
+    int bytes_per_pdf;
+    long long exchange_pdfs;  /* PDFs copied by one ghost exchange */
+    long long device_bytes;   /* device memory held by the context */
+    int tile[3];              /* sweep tile in use */
+    long long tiles;          /* sweep work items (CTAs) per step */
+} lbm_info;
+int lbm_get_info(lbm_ctx *ctx, lbm_info *info);
+
+/*
+ * Timing of individual launches, for roofline accounting.  While enabled,
+ * lbm_step launches without graphs and records a CUDA event pair around
+ * every exchange and sweep launch on the context stream.  lbm_profile_read
+ * synchronises, returns the accumulated device times in milliseconds and
+ * the launch counts, and clears them.
+ */
+typedef struct {
+    double sweep_ms;
+    long long sweep_launches;
+    double exchange_ms;
+    long long exchange_launches;
+} lbm_profile;
+int lbm_profile_enable(lbm_ctx *ctx, int on);
+int lbm_profile_read(lbm_ctx *ctx, lbm_profile *out);
+
+/*
+ * lbm_autotune - times each candidate sweep tile on the context's own data
+ * (sweeps from the current state into the scratch buffer, which leaves the
+ * simulation state unchanged) and keeps the fastest.  cache_path (may be
+ * NULL) names a JSON-lines file: a matching entry is reused instead of
+ * timing, a new result is appended.  best (may be NULL) receives the tile.
+ */
+int lbm_autotune(lbm_ctx *ctx, const char *cache_path, int best[3]);
+
+/* Device memory hooks: alloc(bytes, stream, user) returns a device pointer or
+ * NULL; release(ptr, bytes, stream, user) frees it.  Passing NULL restores
+ * cudaMalloc/cudaFree.  Applies to contexts created afterwards. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *user);
+
+/* The direction table above: e int[57] (q-major triples), w double[19],
+ * opp int[19].  Host only, needs no GPU. */
+int lbm_directions(int *e, double *w, int *opp);
+
+/* Message of the last failure on ctx, or of the calling thread's last failed
+ * lbm_create / lbm_batch_create when ctx is NULL.  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Library version string, e.g. "lbm 0.1 sm_103a". */
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,1117 @@
+// Host runtime of liblbm.so: contexts, the Patch/Block manager, the ghost
+// exchange plan, CUDA-graph replay of time steps, launch timing, the tile
+// autotuner and the C ABI of include/lbm.h.
+//
+// A context holds one Patch split into Blocks (Sec. 4.2), or a batch of
+// independent single-Block instances.  All Blocks of all instances live in
+// two device buffers (src / dst, Sec. 2.1 two-grid pull scheme), each Block
+// with a one-cell ghost shell.  One time step is one Sweep (Sec. 4): the
+// communication step (exchange kernel, device memory only; the local
+// "buffer swap" of Sec. 4.4 becomes a direct ghost-layer copy) followed by the
+// work step (sweep kernel over every Block in one launch).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <memory>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+// ------------------------------------------------------------ allocator
+struct Allocator {
+    lbm_alloc_fn alloc = nullptr;
+    lbm_free_fn release = nullptr;
+    void *user = nullptr;
+};
+Allocator g_alloc;
+thread_local std::string g_create_error;
+
+struct DevMem {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    // configuration
+    lbm_params p{};
+    int ninst = 0;
+    std::vector<int> idims;        // 3 per instance
+    std::vector<double> itau;
+    int storage = LBM_F32;
+    int elem = 4;
+    bool forced = false;
+    // geometry (host copies)
+    std::vector<BlockGeom> blocks;
+    std::vector<Tile> tiles;
+    std::vector<long long> inst_tile_begin;
+    std::vector<XDesc> xdesc;
+    std::vector<XWork> xwork;
+    std::vector<long long> inst_out_base;
+    long long cells = 0, fluid = 0, stored = 0, exchange_pdfs = 0;
+    int tile[3] = {64, 4, 4};
+    int grid = 0;  // 0 = one CTA per tile
+    // device
+    Allocator alloc;
+    std::vector<DevMem> owned;
+    void *buf[2] = {nullptr, nullptr};
+    uint8_t *d_flags = nullptr;
+    BlockGeom *d_blocks = nullptr;
+    Tile *d_tiles = nullptr;
+    XDesc *d_xdesc = nullptr;
+    XWork *d_xwork = nullptr;
+    void *d_consts = nullptr;
+    long long *d_inst_begin = nullptr;
+    double *d_partial = nullptr;
+    double *d_red = nullptr;
+    size_t partial_cap = 0;
+    long long device_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // state
+    int cur = 0;
+    bool have_prev = false;
+    // graphs: graph[par] runs graph_steps steps starting from buffer par
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_steps = 0;
+    // launch timing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;   // 3 per profiled step
+    std::vector<char> ev_has_x;
+    size_t ev_used = 0;
+    double acc_sweep_ms = 0, acc_x_ms = 0;
+    long long acc_sweeps = 0, acc_x = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_ctx *c, int code, const char *fmt, ...)
+{
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+void *dev_alloc(lbm_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (c->alloc.alloc) {
+        p = c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free(lbm_ctx *c, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (c->alloc.release)
+        c->alloc.release(p, bytes, (void *)c->stream, c->alloc.user);
+    else if (!c->alloc.alloc)
+        cudaFree(p);
+}
+
+// Allocation owned by the context until lbm_destroy.
+template <typename P>
+int own(lbm_ctx *c, P **out, size_t bytes)
+{
+    void *p = dev_alloc(c, bytes);
+    if (!p) return fail(c, LBM_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    c->owned.push_back({p, bytes});
+    c->device_bytes += (long long)bytes;
+    *out = static_cast<P *>(p);
+    return LBM_OK;
+}
+
+// Releases one allocation made with own() (no-op for NULL).
+void disown(lbm_ctx *c, void *p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < c->owned.size(); ++i)
+        if (c->owned[i].ptr == p) {
+            dev_free(c, p, c->owned[i].bytes);
+            c->device_bytes -= (long long)c->owned[i].bytes;
+            c->owned.erase(c->owned.begin() + long(i));
+            return;
+        }
+}
+
+// Scoped temporary device buffer.
+struct Temp {
+    lbm_ctx *c;
+    void *p = nullptr;
+    size_t bytes = 0;
+    Temp(lbm_ctx *c_, size_t b) : c(c_), bytes(b) { p = dev_alloc(c, b); }
+    ~Temp() { dev_free(c, p, bytes); }
+};
+
+template <typename T>
+int upload(lbm_ctx *c, T **dst, const std::vector<T> &v)
+{
+    int rc = own(c, dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+    if (rc) return rc;
+    if (!v.empty())
+        CK(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, c->stream),
+           "upload");
+    return LBM_OK;
+}
+
+int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// What lies at instance position (X,Y,Z): periodic axes wrap; beyond one
+// non-periodic face is that face's wall; beyond two or more (an edge or
+// corner of the wall shell) is a resting wall.
+uint8_t classify(const lbm_params &p, const int N[3], const uint8_t *flags, long long X, long long Y,
+                 long long Z)
+{
+    long long pos[3] = {X, Y, Z};
+    int beyond = 0, face = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (pos[a] >= 0 && pos[a] < N[a]) continue;
+        if (p.periodic[a]) {
+            pos[a] = ((pos[a] % N[a]) + N[a]) % N[a];
+        } else {
+            ++beyond;
+            face = 2 * a + (pos[a] < 0 ? 0 : 1);
+        }
+    }
+    if (beyond >= 2) return F_NOSLIP;
+    if (beyond == 1) return uint8_t(p.face_bc[face]);
+    if (!flags) return F_FLUID;
+    return flags[(pos[2] * N[1] + pos[1]) * N[0] + pos[0]];
+}
+
+void build_tiles(lbm_ctx *c, const int t[3], std::vector<Tile> &tiles, std::vector<long long> &begin)
+{
+    tiles.clear();
+    begin.assign(c->ninst + 1, 0);
+    int inst = -1;
+    for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+        const BlockGeom &b = c->blocks[bi];
+        while (inst < b.inst) begin[++inst] = (long long)tiles.size();
+        for (int z = 0; z < b.nz; z += t[2])
+            for (int y = 0; y < b.ny; y += t[1])
+                for (int x = 0; x < b.nx; x += t[0]) tiles.push_back({int(bi), x, y, z});
+    }
+    while (inst < c->ninst) begin[++inst] = (long long)tiles.size();
+}
+
+// Instance description used while building a context.
+struct InstSpec {
+    int dims[3];
+    int bdims[3];
+    double tau;
+    const uint8_t *flags;
+};
+
+int validate_params(const lbm_params &p)
+{
+    if (p.collision != LBM_BGK && p.collision != LBM_TRT) return 0;
+    if (p.storage < LBM_F32 || p.storage > LBM_F64) return 0;
+    if (!(p.rho0 > 0) || !std::isfinite(p.rho0)) return 0;
+    if (p.collision == LBM_TRT && !(p.magic > 0)) return 0;
+    for (int f = 0; f < 6; ++f)
+        if (p.face_bc[f] != LBM_NOSLIP && p.face_bc[f] != LBM_MOVING) return 0;
+    double s = p.storage_scale;
+    int e2 = 0;
+    if (!(s > 0) || !std::isfinite(s) || std::frexp(s, &e2) != 0.5) return 0;  // power of two
+    return 1;
+}
+
+template <typename T>
+std::vector<char> make_consts(const lbm_ctx *c)
+{
+    std::vector<char> raw(sizeof(CollideConsts<T>) * c->ninst);
+    const lbm_params &p = c->p;
+    const double s = (c->storage == LBM_F16S || c->storage == LBM_BF16S) ? p.storage_scale : 1.0;
+    for (int k = 0; k < c->ninst; ++k) {
+        CollideConsts<T> cc{};
+        const double tau = c->itau[k];
+        const double wp = 1.0 / tau;
+        const double wm = p.collision == LBM_TRT ? 1.0 / (0.5 + p.magic / (tau - 0.5)) : wp;
+        cc.rho0s = T(s * p.rho0);
+        cc.ufac = T(1.0 / (s * p.rho0));
+        for (int a = 0; a < 3; ++a) {
+            cc.uoff[a] = T(p.force[a] / (2.0 * p.rho0));
+            cc.Fs[a] = T(s * p.force[a]);
+        }
+        cc.omega_p = T(wp);
+        cc.omega_m = T(wm);
+        cc.cp = T(1.0 - 0.5 * wp);
+        cc.cm = T(1.0 - 0.5 * wm);
+        for (int q = 0; q < Q; ++q) {
+            const double eu = ex(q) * p.wall_u[0] + ey(q) * p.wall_u[1] + ez(q) * p.wall_u[2];
+            cc.bbw[q] = T(s * 6.0 * wq(q) * p.rho0 * eu);
+        }
+        cc.inv_s = T(1.0 / s);
+        cc.rho0 = T(p.rho0);
+        std::memcpy(raw.data() + sizeof(cc) * k, &cc, sizeof(cc));
+    }
+    return raw;
+}
+
+void invalidate_graphs(lbm_ctx *c)
+{
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
+}
+
+int set_tiles(lbm_ctx *c, const int t[3], int grid)
+{
+    std::vector<Tile> tiles;
+    std::vector<long long> begin;
+    build_tiles(c, t, tiles, begin);
+    Tile *dt = nullptr;
+    long long *db = nullptr;
+    int rc = upload(c, &dt, tiles);
+    if (rc) return rc;
+    rc = upload(c, &db, begin);
+    if (rc) return rc;
+    size_t need = sizeof(double) * R_K * std::max<size_t>(tiles.size(), 1);
+    if (need > c->partial_cap) {
+        CK(cudaStreamSynchronize(c->stream), "set_tiles");
+        disown(c, c->d_partial);
+        c->d_partial = nullptr;
+        c->partial_cap = 0;
+        rc = own(c, &c->d_partial, need);
+        if (rc) return rc;
+        c->partial_cap = need;
+    }
+    CK(cudaStreamSynchronize(c->stream), "set_tiles");
+    disown(c, c->d_tiles);
+    disown(c, c->d_inst_begin);
+    c->tiles.swap(tiles);
+    c->inst_tile_begin.swap(begin);
+    c->d_tiles = dt;
+    c->d_inst_begin = db;
+    for (int a = 0; a < 3; ++a) c->tile[a] = t[a];
+    c->grid = grid;
+    invalidate_graphs(c);
+    return LBM_OK;
+}
+
+int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
+{
+    const lbm_params &p = c->p;
+    c->ninst = int(inst.size());
+    c->storage = p.storage;
+    c->elem = p.storage == LBM_F32 ? 4 : (p.storage == LBM_F64 ? 8 : 2);
+    c->forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
+    const int align = 16 / c->elem;  // cells per 16 bytes
+
+    if (p.stream) {
+        c->stream = static_cast<cudaStream_t>(p.stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        c->own_stream = true;
+    }
+
+    // ---- blocks and flags
+    std::vector<uint8_t> hflags;
+    long long pdf_base = 0, cell_base = 0, out_base = 0;
+    for (int k = 0; k < c->ninst; ++k) {
+        const InstSpec &s = inst[k];
+        c->idims.insert(c->idims.end(), s.dims, s.dims + 3);
+        c->itau.push_back(s.tau);
+        c->inst_out_base.push_back(out_base);
+        const int nb[3] = {s.dims[0] / s.bdims[0], s.dims[1] / s.bdims[1], s.dims[2] / s.bdims[2]};
+        const int first_block = int(c->blocks.size());
+        for (int bz = 0; bz < nb[2]; ++bz)
+            for (int by = 0; by < nb[1]; ++by)
+                for (int bx = 0; bx < nb[0]; ++bx) {
+                    BlockGeom b{};
+                    b.nx = s.bdims[0];
+                    b.ny = s.bdims[1];
+                    b.nz = s.bdims[2];
+                    b.ox = align;
+                    b.px = round_up(b.ox + b.nx + 1, align);
+                    b.py = b.ny + 2;
+                    b.G = (long long)b.px * b.py * (b.nz + 2);
+                    if ((long long)Q * b.G >= (1ll << 31))
+                        return fail(c, LBM_EINVAL,
+                                    "block of %dx%dx%d cells is too large for 32-bit plane "
+                                    "offsets; split the domain into more blocks",
+                                    b.nx, b.ny, b.nz);
+                    b.pdf_base = pdf_base;
+                    b.cell_base = cell_base;
+                    b.inst = k;
+                    b.gx = bx * b.nx;
+                    b.gy = by * b.ny;
+                    b.gz = bz * b.nz;
+                    b.out_base = out_base;
+                    b.NX = s.dims[0];
+                    b.NY = s.dims[1];
+                    b.NZ = s.dims[2];
+                    pdf_base += (long long)Q * b.G;
+                    cell_base += b.G;
+                    // flags of every stored cell (interior, ghost shell, padding)
+                    std::vector<uint8_t> f(size_t(b.G), F_NOSLIP);
+                    for (int z = -1; z <= b.nz; ++z)
+                        for (int y = -1; y <= b.ny; ++y)
+                            for (int x = -1; x <= b.nx; ++x) {
+                                const long long cidx =
+                                    ((long long)(z + 1) * b.py + (y + 1)) * b.px + (x + b.ox);
+                                uint8_t v = classify(p, s.dims, s.flags, b.gx + x, b.gy + y, b.gz + z);
+                                if (v > F_MOVING)
+                                    return fail(c, LBM_EINVAL, "flag value %d is not LBM_FLUID/NOSLIP/MOVING",
+                                                int(v));
+                                f[cidx] = v;
+                            }
+                    const long long pxy = (long long)b.px * b.py;
+                    for (int z = 0; z < b.nz; ++z)
+                        for (int y = 0; y < b.ny; ++y)
+                            for (int x = 0; x < b.nx; ++x) {
+                                const long long cidx = (z + 1) * pxy + (long long)(y + 1) * b.px + (x + b.ox);
+                                if (f[cidx] != F_FLUID) continue;
+                                ++c->fluid;
+                                for (int q = 1; q < Q; ++q)
+                                    if (f[cidx - (ex(q) + ey(q) * (long long)b.px + ez(q) * pxy)] & F_KIND) {
+                                        f[cidx] |= F_NEAR;
+                                        break;
+                                    }
+                            }
+                    hflags.insert(hflags.end(), f.begin(), f.end());
+                    c->blocks.push_back(b);
+                }
+        // ---- ghost exchange plan: faces and edges with a neighbour block
+        for (int bz = 0; bz < nb[2]; ++bz)
+            for (int by = 0; by < nb[1]; ++by)
+                for (int bx = 0; bx < nb[0]; ++bx) {
+                    const int me = first_block + (bz * nb[1] + by) * nb[0] + bx;
+                    const int bpos[3] = {bx, by, bz};
+                    for (int n0 = -1; n0 <= 1; ++n0)
+                        for (int n1 = -1; n1 <= 1; ++n1)
+                            for (int n2 = -1; n2 <= 1; ++n2) {
+                                const int n[3] = {n0, n1, n2};
+                                const int nnz = (n0 != 0) + (n1 != 0) + (n2 != 0);
+                                if (nnz == 0 || nnz == 3) continue;  // no corner links in D3Q19
+                                int npos[3];
+                                bool ok = true;
+                                for (int a = 0; a < 3; ++a) {
+                                    npos[a] = bpos[a] + n[a];
+                                    if (npos[a] < 0 || npos[a] >= nb[a]) {
+                                        if (!p.periodic[a]) ok = false;
+                                        npos[a] = (npos[a] + nb[a]) % nb[a];
+                                    }
+                                }
+                                if (!ok) continue;
+                                XDesc d{};
+                                d.dst_block = me;
+                                d.src_block = first_block + (npos[2] * nb[1] + npos[1]) * nb[0] + npos[0];
+                                const int bd[3] = {s.bdims[0], s.bdims[1], s.bdims[2]};
+                                int start[3], len[3], shift[3];
+                                for (int a = 0; a < 3; ++a) {
+                                    start[a] = n[a] < 0 ? -1 : (n[a] > 0 ? bd[a] : 0);
+                                    len[a] = n[a] == 0 ? bd[a] : 1;
+                                    shift[a] = -n[a] * bd[a];
+                                }
+                                d.x0 = start[0];
+                                d.y0 = start[1];
+                                d.z0 = start[2];
+                                d.lx = len[0];
+                                d.ly = len[1];
+                                d.lz = len[2];
+                                d.sx = shift[0];
+                                d.sy = shift[1];
+                                d.sz = shift[2];
+                                d.ncell = len[0] * len[1] * len[2];
+                                d.ndir = 0;
+                                for (int q = 1; q < Q; ++q) {
+                                    const int e[3] = {ex(q), ey(q), ez(q)};
+                                    bool into = true;
+                                    for (int a = 0; a < 3; ++a)
+                                        if (n[a] != 0 && e[a] != -n[a]) into = false;
+                                    if (into) d.dir[d.ndir++] = q;
+                                }
+                                const int id = int(c->xdesc.size());
+                                c->xdesc.push_back(d);
+                                const long long items = (long long)d.ncell * d.ndir;
+                                c->exchange_pdfs += items;
+                                for (long long f0 = 0; f0 < items; f0 += 256)
+                                    c->xwork.push_back({id, int(f0)});
+                            }
+                }
+        out_base += (long long)s.dims[0] * s.dims[1] * s.dims[2];
+    }
+    c->cells = out_base;
+    c->stored = cell_base;
+
+    // ---- device memory
+    const size_t buf_bytes = size_t(pdf_base) * c->elem;
+    int rc;
+    if ((rc = own(c, &c->buf[0], buf_bytes))) return rc;
+    if ((rc = own(c, &c->buf[1], buf_bytes))) return rc;
+    CK(cudaMemsetAsync(c->buf[0], 0, buf_bytes, c->stream), "memset");
+    CK(cudaMemsetAsync(c->buf[1], 0, buf_bytes, c->stream), "memset");
+    if ((rc = upload(c, &c->d_flags, hflags))) return rc;
+    if ((rc = upload(c, &c->d_blocks, c->blocks))) return rc;
+    if ((rc = upload(c, &c->d_xdesc, c->xdesc))) return rc;
+    if ((rc = upload(c, &c->d_xwork, c->xwork))) return rc;
+    std::vector<char> consts =
+        c->storage == LBM_F64 ? make_consts<double>(c) : make_consts<float>(c);
+    if ((rc = upload(c, reinterpret_cast<char **>(&c->d_consts), consts))) return rc;
+    if ((rc = own(c, &c->d_red, sizeof(double) * R_K * c->ninst))) return rc;
+
+    int t[3] = {p.tile[0], p.tile[1], p.tile[2]};
+    if (t[0] <= 0 || t[1] <= 0 || t[2] <= 0) {
+        // default: a warp-multiple along x covering the block width, 256 threads
+        int maxnx = 0;
+        for (const BlockGeom &b : c->blocks) maxnx = std::max(maxnx, b.nx);
+        t[0] = std::min(128, round_up(std::max(maxnx, 1), 32));
+        t[1] = std::max(1, 256 / t[0]);
+        t[2] = 4;
+    }
+    if (t[0] * t[1] > 256 || t[0] % 32 != 0)
+        return fail(c, LBM_EINVAL, "tile %dx%d: threads along x must be a multiple of 32 and "
+                    "tile[0]*tile[1] <= 256", t[0], t[1]);
+    if ((rc = set_tiles(c, t, 0))) return rc;
+
+    // graph length: enough work per replay to hide launch overhead
+    if (p.graph_steps < 0) {
+        c->graph_steps = 0;
+    } else if (p.graph_steps > 0) {
+        c->graph_steps = p.graph_steps + (p.graph_steps & 1);
+    } else {
+        long long per = std::max<long long>(c->cells, 1);
+        long long g = (4ll << 20) / per;
+        g = std::max(2ll, std::min(100ll, g + (g & 1)));
+        c->graph_steps = int(g);
+    }
+    CK(cudaStreamSynchronize(c->stream), "create");
+    return LBM_OK;
+}
+
+// ---- launches
+SweepArgs sweep_args(const lbm_ctx *c, int from)
+{
+    SweepArgs a{};
+    a.tiles = c->d_tiles;
+    a.ntiles = (long long)c->tiles.size();
+    a.blocks = c->d_blocks;
+    a.consts = c->d_consts;
+    a.flags = c->d_flags;
+    a.src = c->buf[from];
+    a.dst = c->buf[from ^ 1];
+    a.tx = c->tile[0];
+    a.ty = c->tile[1];
+    a.tz = c->tile[2];
+    a.collision = c->p.collision;
+    a.forced = c->forced ? 1 : 0;
+    a.storage = c->storage;
+    a.grid = c->grid;
+    return a;
+}
+
+FieldArgs field_args(const lbm_ctx *c)
+{
+    FieldArgs a{};
+    a.tiles = c->d_tiles;
+    a.ntiles = (long long)c->tiles.size();
+    a.blocks = c->d_blocks;
+    a.consts = c->d_consts;
+    a.flags = c->d_flags;
+    a.tx = c->tile[0];
+    a.ty = c->tile[1];
+    a.tz = c->tile[2];
+    a.storage = c->storage;
+    return a;
+}
+
+cudaError_t enqueue_exchange(const lbm_ctx *c, int which)
+{
+    ExchangeArgs x{};
+    x.desc = c->d_xdesc;
+    x.work = c->d_xwork;
+    x.nwork = int(c->xwork.size());
+    x.blocks = c->d_blocks;
+    x.buf = c->buf[which];
+    x.elem_bytes = c->elem;
+    return launch_exchange(x, c->stream);
+}
+
+// One step from buffer `from` (exchange on it, sweep into the other).
+cudaError_t enqueue_step(const lbm_ctx *c, int from)
+{
+    cudaError_t e = enqueue_exchange(c, from);
+    if (e != cudaSuccess) return e;
+    return launch_sweep(sweep_args(c, from), c->stream);
+}
+
+int ensure_event(lbm_ctx *c, size_t idx)
+{
+    while (c->ev.size() <= idx) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e), "cudaEventCreate");
+        c->ev.push_back(e);
+    }
+    return LBM_OK;
+}
+
+int direct_steps(lbm_ctx *c, int n)
+{
+    for (int s = 0; s < n; ++s) {
+        if (c->profiling) {
+            size_t base = c->ev_used;
+            int rc = ensure_event(c, base + 2);
+            if (rc) return rc;
+            const bool has_x = !c->xwork.empty();
+            CK(cudaEventRecord(c->ev[base], c->stream), "cudaEventRecord");
+            CK(enqueue_exchange(c, c->cur), "exchange launch");
+            CK(cudaEventRecord(c->ev[base + 1], c->stream), "cudaEventRecord");
+            CK(launch_sweep(sweep_args(c, c->cur), c->stream), "sweep launch");
+            CK(cudaEventRecord(c->ev[base + 2], c->stream), "cudaEventRecord");
+            c->ev_has_x.push_back(has_x ? 1 : 0);
+            c->ev_used += 3;
+        } else {
+            CK(enqueue_step(c, c->cur), "step launch");
+        }
+        c->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+int ensure_graph(lbm_ctx *c, int par)
+{
+    if (c->graph[par]) return LBM_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int from = par;
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < c->graph_steps && le == cudaSuccess; ++s) {
+        le = enqueue_step(c, from);
+        from ^= 1;
+    }
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, le, "launch during capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(c, ee, "end capture");
+    cudaError_t ie = cudaGraphInstantiate(&c->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        c->graph[par] = nullptr;
+        return cuda_fail(c, ie, "graph instantiate");
+    }
+    return LBM_OK;
+}
+
+int reduce(lbm_ctx *c, bool with_prev, std::vector<double> &out)
+{
+    FieldArgs a = field_args(c);
+    CK(launch_reduce(a, c->buf[c->cur], with_prev ? c->buf[c->cur ^ 1] : nullptr, c->d_partial,
+                     c->d_inst_begin, c->ninst, c->d_red, c->stream),
+       "reduce launch");
+    out.assign(size_t(R_K) * c->ninst, 0.0);
+    CK(cudaMemcpyAsync(out.data(), c->d_red, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
+                       c->stream),
+       "reduce D2H");
+    CK(cudaStreamSynchronize(c->stream), "reduce sync");
+    return LBM_OK;
+}
+
+std::string tune_key(const lbm_ctx *c)
+{
+    std::ostringstream k;
+    cudaDeviceProp prop{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    k << prop.name << "|st" << c->storage << "|c" << c->p.collision << "|f" << int(c->forced)
+      << "|n" << c->blocks.size();
+    // the block shapes (sorted) describe the work
+    std::vector<std::string> shapes;
+    for (const BlockGeom &b : c->blocks) {
+        std::ostringstream s;
+        s << b.nx << "x" << b.ny << "x" << b.nz;
+        shapes.push_back(s.str());
+    }
+    std::sort(shapes.begin(), shapes.end());
+    size_t h = 1469598103934665603ull;
+    for (auto &s : shapes)
+        for (char ch : s) h = (h ^ size_t(uint8_t(ch))) * 1099511628211ull;
+    k << "|h" << std::hex << h;
+    return k.str();
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void lbm_default_params(lbm_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->collision = LBM_BGK;
+    p->magic = 3.0 / 16.0;
+    p->rho0 = 1.0;
+    for (int f = 0; f < 6; ++f) p->face_bc[f] = LBM_NOSLIP;
+    p->storage = LBM_F32;
+    p->storage_scale = 1.0;
+    p->stream = nullptr;
+    p->graph_steps = 0;
+}
+
+static int create_common(const std::vector<InstSpec> &inst, const lbm_params *pin, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    lbm_params p;
+    if (pin)
+        p = *pin;
+    else
+        lbm_default_params(&p);
+    if (!validate_params(p))
+        return fail(nullptr, LBM_EINVAL, "invalid lbm_params (collision, storage, rho0, magic, "
+                    "face_bc or storage_scale out of range)");
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "out of host memory");
+    c->p = p;
+    c->alloc = g_alloc;
+    int rc;
+    try {
+        rc = build_context(c, inst);
+    } catch (const std::bad_alloc &) {
+        rc = fail(c, LBM_ENOMEM, "out of host memory");
+    }
+    if (rc != LBM_OK) {
+        g_create_error = c->err;
+        lbm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_create(const int dims[3], const int block_dims[3], double tau, const uint8_t *flags,
+               const lbm_params *p, lbm_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (!dims || !block_dims) return fail(nullptr, LBM_EINVAL, "dims and block_dims are required");
+    InstSpec s{};
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] <= 0 || block_dims[a] <= 0 || dims[a] % block_dims[a] != 0)
+            return fail(nullptr, LBM_EINVAL,
+                        "dims[%d]=%d must be a positive multiple of block_dims[%d]=%d", a, dims[a],
+                        a, block_dims[a]);
+        s.dims[a] = dims[a];
+        s.bdims[a] = block_dims[a];
+    }
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, LBM_EINVAL, "tau must be > 1/2");
+    s.tau = tau;
+    s.flags = flags;
+    return create_common({s}, p, out);
+}
+
+int lbm_batch_create(int n, const int *dims, const double *tau, const uint8_t *const *flags,
+                     const lbm_params *p, lbm_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (n <= 0 || !dims || !tau) return fail(nullptr, LBM_EINVAL, "n > 0, dims and tau are required");
+    std::vector<InstSpec> inst(n);
+    for (int k = 0; k < n; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            if (dims[3 * k + a] <= 0)
+                return fail(nullptr, LBM_EINVAL, "instance %d: dims must be positive", k);
+            inst[k].dims[a] = inst[k].bdims[a] = dims[3 * k + a];
+        }
+        if (!(tau[k] > 0.5) || !std::isfinite(tau[k]))
+            return fail(nullptr, LBM_EINVAL, "instance %d: tau must be > 1/2", k);
+        inst[k].tau = tau[k];
+        inst[k].flags = flags ? flags[k] : nullptr;
+    }
+    return create_common(inst, p, out);
+}
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    invalidate_graphs(c);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (auto it = c->owned.rbegin(); it != c->owned.rend(); ++it) dev_free(c, it->ptr, it->bytes);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int lbm_step(lbm_ctx *c, int n)
+{
+    if (!c || n < 0) return fail(c, LBM_EINVAL, "lbm_step: bad arguments");
+    if (n == 0) return LBM_OK;
+    int rc;
+    if (c->profiling || c->graph_steps == 0) {
+        rc = direct_steps(c, n);
+    } else {
+        rc = LBM_OK;
+        while (n >= c->graph_steps && rc == LBM_OK) {
+            rc = ensure_graph(c, c->cur);
+            if (rc) break;
+            CK(cudaGraphLaunch(c->graph[c->cur], c->stream), "cudaGraphLaunch");
+            n -= c->graph_steps;  // even: parity unchanged
+        }
+        if (rc == LBM_OK && n > 0) rc = direct_steps(c, n);
+    }
+    if (rc == LBM_OK) c->have_prev = true;
+    return rc;
+}
+
+int lbm_synchronize(lbm_ctx *c)
+{
+    if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
+    CK(cudaStreamSynchronize(c->stream), "lbm_synchronize");
+    return LBM_OK;
+}
+
+int lbm_macroscopic_device(lbm_ctx *c, float *rho, float *u)
+{
+    if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_macroscopic_device: NULL argument");
+    CK(launch_macroscopic(field_args(c), c->buf[c->cur], rho, u, c->stream), "macroscopic launch");
+    return LBM_OK;
+}
+
+int lbm_macroscopic(lbm_ctx *c, float *rho, float *u)
+{
+    if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_macroscopic: NULL argument");
+    const size_t n = size_t(c->cells);
+    Temp t(c, sizeof(float) * 4 * n);
+    if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes", t.bytes);
+    float *dr = static_cast<float *>(t.p), *du = dr + n;
+    int rc = lbm_macroscopic_device(c, dr, du);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(rho, dr, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream), "D2H rho");
+    CK(cudaMemcpyAsync(u, du, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream), "D2H u");
+    CK(cudaStreamSynchronize(c->stream), "lbm_macroscopic");
+    return LBM_OK;
+}
+
+int lbm_get_pdfs(lbm_ctx *c, double *f)
+{
+    if (!c || !f) return fail(c, LBM_EINVAL, "lbm_get_pdfs: NULL argument");
+    const size_t n = size_t(c->cells) * Q;
+    Temp t(c, sizeof(double) * n);
+    if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes", t.bytes);
+    CK(launch_get_pdfs(field_args(c), c->buf[c->cur], static_cast<double *>(t.p), c->stream),
+       "get_pdfs launch");
+    CK(cudaMemcpyAsync(f, t.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "D2H pdfs");
+    CK(cudaStreamSynchronize(c->stream), "lbm_get_pdfs");
+    return LBM_OK;
+}
+
+int lbm_set_pdfs(lbm_ctx *c, const double *f)
+{
+    if (!c || !f) return fail(c, LBM_EINVAL, "lbm_set_pdfs: NULL argument");
+    const size_t n = size_t(c->cells) * Q;
+    Temp t(c, sizeof(double) * n);
+    if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes", t.bytes);
+    CK(cudaMemcpyAsync(t.p, f, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "H2D pdfs");
+    CK(launch_set_pdfs(field_args(c), c->buf[c->cur], static_cast<const double *>(t.p), c->stream),
+       "set_pdfs launch");
+    CK(cudaStreamSynchronize(c->stream), "lbm_set_pdfs");
+    c->have_prev = false;
+    return LBM_OK;
+}
+
+int lbm_init_equilibrium_device(lbm_ctx *c, const float *rho, const float *u)
+{
+    if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_init_equilibrium_device: NULL argument");
+    CK(launch_init_equilibrium(field_args(c), c->buf[c->cur], rho, u, c->stream), "init launch");
+    c->have_prev = false;
+    return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_ctx *c, const float *rho, const float *u)
+{
+    if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_init_equilibrium: NULL argument");
+    const size_t n = size_t(c->cells);
+    Temp t(c, sizeof(float) * 4 * n);
+    if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes", t.bytes);
+    float *dr = static_cast<float *>(t.p), *du = dr + n;
+    CK(cudaMemcpyAsync(dr, rho, sizeof(float) * n, cudaMemcpyHostToDevice, c->stream), "H2D rho");
+    CK(cudaMemcpyAsync(du, u, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, c->stream), "H2D u");
+    int rc = lbm_init_equilibrium_device(c, dr, du);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream), "lbm_init_equilibrium");
+    return LBM_OK;
+}
+
+int lbm_invariants(lbm_ctx *c, double *mass, double mom[3], double *nonfinite, double *per_instance)
+{
+    if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
+    std::vector<double> r;
+    int rc = reduce(c, false, r);
+    if (rc) return rc;
+    const lbm_params &p = c->p;
+    double M = 0, J[3] = {0, 0, 0}, bad = 0;
+    for (int k = 0; k < c->ninst; ++k) {
+        const double *v = &r[size_t(R_K) * k];
+        const double m = v[R_NFLUID] * p.rho0 + v[R_DRHO];
+        const double j[3] = {v[R_JX] - v[R_NFLUID] * 0.5 * p.force[0],
+                             v[R_JY] - v[R_NFLUID] * 0.5 * p.force[1],
+                             v[R_JZ] - v[R_NFLUID] * 0.5 * p.force[2]};
+        M += m;
+        for (int a = 0; a < 3; ++a) J[a] += j[a];
+        bad += v[R_NONFINITE];
+        if (per_instance) {
+            per_instance[5 * k] = m;
+            for (int a = 0; a < 3; ++a) per_instance[5 * k + 1 + a] = j[a];
+            per_instance[5 * k + 4] = v[R_NONFINITE];
+        }
+    }
+    if (mass) *mass = M;
+    if (mom)
+        for (int a = 0; a < 3; ++a) mom[a] = J[a];
+    if (nonfinite) *nonfinite = bad;
+    return LBM_OK;
+}
+
+int lbm_residual(lbm_ctx *c, double *res, double *per_instance)
+{
+    if (!c || !res) return fail(c, LBM_EINVAL, "lbm_residual: NULL argument");
+    if (!c->have_prev)
+        return fail(c, LBM_EINVAL, "lbm_residual: no step has been taken since the state was set");
+    std::vector<double> r;
+    int rc = reduce(c, true, r);
+    if (rc) return rc;
+    double num = 0, den = 0;
+    auto ratio = [](double a, double b) {
+        if (b == 0.0) return a == 0.0 ? 0.0 : INFINITY;
+        return std::sqrt(a) / std::sqrt(b);
+    };
+    for (int k = 0; k < c->ninst; ++k) {
+        const double *v = &r[size_t(R_K) * k];
+        num += v[R_DU2];
+        den += v[R_U2];
+        if (per_instance) per_instance[k] = ratio(v[R_DU2], v[R_U2]);
+    }
+    *res = ratio(num, den);
+    return LBM_OK;
+}
+
+int lbm_run_to_residual(lbm_ctx *c, double tol, int check_every, long long max_steps,
+                        long long *steps, double *res)
+{
+    if (!c || check_every <= 0 || max_steps < 0)
+        return fail(c, LBM_EINVAL, "lbm_run_to_residual: bad arguments");
+    long long done = 0;
+    double r = INFINITY;
+    while (done < max_steps) {
+        const int n = int(std::min<long long>(check_every, max_steps - done));
+        int rc = lbm_step(c, n);
+        if (rc) return rc;
+        done += n;
+        rc = lbm_residual(c, &r, nullptr);
+        if (rc) return rc;
+        if (std::isnan(r)) {
+            if (steps) *steps = done;
+            if (res) *res = r;
+            return fail(c, LBM_ENUMERIC, "residual is NaN after %lld steps", done);
+        }
+        if (r < tol) break;
+    }
+    if (steps) *steps = done;
+    if (res) *res = r;
+    return LBM_OK;
+}
+
+int lbm_get_info(lbm_ctx *c, lbm_info *info)
+{
+    if (!c || !info) return fail(c, LBM_EINVAL, "lbm_get_info: NULL argument");
+    info->cells = c->cells;
+    info->fluid_cells = c->fluid;
+    info->stored_cells = c->stored;
+    info->blocks = int(c->blocks.size());
+    info->instances = c->ninst;
+    info->storage = c->storage;
+    info->bytes_per_pdf = c->elem;
+    info->exchange_pdfs = c->exchange_pdfs;
+    info->device_bytes = c->device_bytes;
+    for (int a = 0; a < 3; ++a) info->tile[a] = c->tile[a];
+    info->tiles = (long long)c->tiles.size();
+    return LBM_OK;
+}
+
+int lbm_profile_enable(lbm_ctx *c, int on)
+{
+    if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
+    c->profiling = on != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx *c, lbm_profile *out)
+{
+    if (!c || !out) return fail(c, LBM_EINVAL, "lbm_profile_read: NULL argument");
+    CK(cudaStreamSynchronize(c->stream), "profile sync");
+    for (size_t s = 0; s * 3 < c->ev_used; ++s) {
+        float x = 0.f, w = 0.f;
+        CK(cudaEventElapsedTime(&x, c->ev[3 * s], c->ev[3 * s + 1]), "elapsed");
+        CK(cudaEventElapsedTime(&w, c->ev[3 * s + 1], c->ev[3 * s + 2]), "elapsed");
+        if (c->ev_has_x[s]) {
+            c->acc_x_ms += x;
+            ++c->acc_x;
+        }
+        c->acc_sweep_ms += w;
+        ++c->acc_sweeps;
+    }
+    c->ev_used = 0;
+    c->ev_has_x.clear();
+    out->sweep_ms = c->acc_sweep_ms;
+    out->sweep_launches = c->acc_sweeps;
+    out->exchange_ms = c->acc_x_ms;
+    out->exchange_launches = c->acc_x;
+    c->acc_sweep_ms = c->acc_x_ms = 0;
+    c->acc_sweeps = c->acc_x = 0;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
+{
+    if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
+    const std::string key = tune_key(c);
+    int best[4] = {c->tile[0], c->tile[1], c->tile[2], c->grid};
+    bool cached = false;
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line;
+        const std::string needle = "\"key\": \"" + key + "\"";
+        while (std::getline(in, line)) {
+            if (line.find(needle) == std::string::npos) continue;
+            size_t t = line.find("\"tile\": [");
+            int v[4];
+            if (t != std::string::npos &&
+                std::sscanf(line.c_str() + t, "\"tile\": [%d, %d, %d, %d]", &v[0], &v[1], &v[2], &v[3]) == 4) {
+                std::memcpy(best, v, sizeof v);
+                cached = true;
+            }
+        }
+    }
+    if (!cached) {
+        int maxnx = 0;
+        for (const BlockGeom &b : c->blocks) maxnx = std::max(maxnx, b.nx);
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        std::vector<std::array<int, 4>> cand;
+        for (int tx : {32, 64, 128, 256}) {
+            if (tx > std::max(32, round_up(maxnx, 32))) continue;
+            for (int th : {128, 256}) {
+                if (th < tx) continue;
+                for (int tz : {1, 2, 4, 8, 16}) cand.push_back({tx, th / tx, tz, 0});
+            }
+        }
+        // persistent variants of the default tile
+        for (int m : {4, 8, 16}) cand.push_back({c->tile[0], c->tile[1], c->tile[2], m * sms});
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0), "event");
+        CK(cudaEventCreate(&e1), "event");
+        float best_ms = 1e30f;
+        const int reps = 5;
+        for (auto &cd : cand) {
+            int t[3] = {cd[0], cd[1], cd[2]};
+            int rc = set_tiles(c, t, cd[3] ? int(std::min<long long>(cd[3], 1ll << 30)) : 0);
+            if (rc) return rc;
+            SweepArgs a = sweep_args(c, c->cur);
+            CK(launch_sweep(a, c->stream), "tune");
+            CK(cudaEventRecord(e0, c->stream), "event");
+            for (int r = 0; r < reps; ++r) CK(launch_sweep(a, c->stream), "tune");
+            CK(cudaEventRecord(e1, c->stream), "event");
+            CK(cudaEventSynchronize(e1), "tune sync");
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            if (ms < best_ms) {
+                best_ms = ms;
+                best[0] = cd[0];
+                best[1] = cd[1];
+                best[2] = cd[2];
+                best[3] = cd[3];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cache_path) {
+            std::ofstream o(cache_path, std::ios::app);
+            o << "{\"key\": \"" << key << "\", \"tile\": [" << best[0] << ", " << best[1] << ", "
+              << best[2] << ", " << best[3] << "], \"ms_per_sweep\": " << best_ms / reps << "}\n";
+        }
+    }
+    int t[3] = {best[0], best[1], best[2]};
+    int rc = set_tiles(c, t, best[3]);
+    if (rc) return rc;
+    c->have_prev = false;  // the scratch buffer was overwritten
+    if (best_out)
+        for (int a = 0; a < 3; ++a) best_out[a] = best[a];
+    CK(cudaStreamSynchronize(c->stream), "autotune");
+    return LBM_OK;
+}
+
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *user)
+{
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(nullptr, LBM_EINVAL, "alloc and release must both be given or both be NULL");
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.user = user;
+    return LBM_OK;
+}
+
+int lbm_directions(int *e, double *w, int *o)
+{
+    for (int q = 0; q < Q; ++q) {
+        if (e) {
+            e[3 * q] = ex(q);
+            e[3 * q + 1] = ey(q);
+            e[3 * q + 2] = ez(q);
+        }
+        if (w) w[q] = wq(q);
+        if (o) o[q] = opp(q);
+    }
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c)
+{
+    if (c) return c->err.c_str();
+    return g_create_error.c_str();
+}
+
+const char *lbm_version(void) { return "lbm 0.1 sm_103a"; }
+
+}  // extern "C"

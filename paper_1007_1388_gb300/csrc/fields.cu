@@ -1,0 +1,416 @@
+// Kernels around the sweep: the ghost-layer exchange between Blocks, the
+// moment (macroscopic) output, equilibrium initialisation, PDF conversion
+// for checkpoints, and the FP64 invariant / residual reductions.
+#include <cstdio>
+
+#include "device_common.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- exchange
+// The communication step of a Sweep (Sec. 4, Sec. 4.4): every ghost cell of
+// a Block that some interior cell pulls from receives, for the directions
+// pointing into the Block, the post-collision PDF of the matching boundary
+// cell of the neighbouring Block (or of the Block itself across a periodic
+// boundary).  Faces carry 5 directions, edges 1; D3Q19 has no corner links.
+// The copy reads interior cells and writes ghost cells of the same buffer,
+// so it needs no second buffer and no ordering between work items.
+template <typename E>
+__global__ void __launch_bounds__(256) exchange_kernel(const __grid_constant__ ExchangeArgs a)
+{
+    const XWork w = a.work[blockIdx.x];
+    const XDesc &d = a.desc[w.desc];
+    const int item = w.first + int(threadIdx.x);
+    if (item >= d.ncell * d.ndir) return;
+    const int k = item / d.ncell;
+    const int cell = item - k * d.ncell;
+    const int cx = cell % d.lx;
+    const int cy = (cell / d.lx) % d.ly;
+    const int cz = cell / (d.lx * d.ly);
+    const int x = d.x0 + cx, y = d.y0 + cy, z = d.z0 + cz;
+    const BlockGeom &bd = a.blocks[d.dst_block];
+    const BlockGeom &bs = a.blocks[d.src_block];
+    const int q = d.dir[k];
+    const long long di = bd.pdf_base + (long long)q * bd.G +
+                         ((long long)(z + 1) * bd.py + (y + 1)) * bd.px + (x + bd.ox);
+    const long long si = bs.pdf_base + (long long)q * bs.G +
+                         ((long long)(z + d.sz + 1) * bs.py + (y + d.sy + 1)) * bs.px +
+                         (x + d.sx + bs.ox);
+    E *buf = static_cast<E *>(a.buf);
+    buf[di] = buf[si];
+}
+
+cudaError_t launch_exchange(const ExchangeArgs &a, cudaStream_t s)
+{
+    if (a.nwork == 0) return cudaSuccess;
+    switch (a.elem_bytes) {
+    case 2: exchange_kernel<uint16_t><<<a.nwork, 256, 0, s>>>(a); break;
+    case 4: exchange_kernel<uint32_t><<<a.nwork, 256, 0, s>>>(a); break;
+    case 8: exchange_kernel<unsigned long long><<<a.nwork, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- per-cell helpers
+struct CellPos {
+    const BlockGeom *b;
+    int x, y, z;   // interior coordinates inside the block
+    int c;         // stored cell index inside the block
+    long long o;   // cell index inside the instance's output slice
+};
+
+// Iterates the cells of the tiles (same tiling as the sweep), calling fn for
+// every interior cell.
+template <typename Fn>
+__device__ __forceinline__ void for_each_cell(const FieldArgs &a, Fn fn)
+{
+    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const Tile tile = a.tiles[t];
+        const BlockGeom &b = a.blocks[tile.block];
+        const int x = tile.x0 + int(threadIdx.x);
+        const int y = tile.y0 + int(threadIdx.y);
+        if (x >= b.nx || y >= b.ny) continue;
+        const int zend = min(tile.z0 + a.tz, b.nz);
+        const int pxy = b.px * b.py;
+        for (int z = tile.z0; z < zend; ++z) {
+            CellPos p;
+            p.b = &b;
+            p.x = x;
+            p.y = y;
+            p.z = z;
+            p.c = (z + 1) * pxy + (y + 1) * b.px + (x + b.ox);
+            p.o = ((long long)(b.gz + z) * b.NY + (b.gy + y)) * b.NX + (b.gx + x);
+            fn(p);
+        }
+    }
+}
+
+__device__ __forceinline__ long long inst_cells(const BlockGeom &b)
+{
+    return (long long)b.NX * b.NY * b.NZ;
+}
+
+// ------------------------------------------------------------ macroscopic
+// Moments of the stored post-collision state (Sec. 2.1): rho = rho0 + sum f~,
+// u = (sum e f~ - F/2)/rho0, which is the velocity the last collision used.
+template <int ST>
+__global__ void __launch_bounds__(256) macro_kernel(const __grid_constant__ FieldArgs a,
+                                                    const void *buf, float *rho, float *u)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    for_each_cell(a, [&](const CellPos &p) {
+        const BlockGeom &b = *p.b;
+        const CollideConsts<T> &P = cs[b.inst];
+        const long long N = inst_cells(b);
+        float *r = rho + b.out_base;
+        float *v = u + 3 * b.out_base;
+        if (a.flags[b.cell_base + p.c] & F_KIND) {
+            r[p.o] = float(P.rho0);
+            v[p.o] = v[N + p.o] = v[2 * N + p.o] = 0.f;
+            return;
+        }
+        const S *g = static_cast<const S *>(buf) + b.pdf_base + p.c;
+        T d = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const T gq = Tr::to_t(g[(long long)q * b.G]);
+            d += gq;
+            jx += T(ex(q)) * gq;
+            jy += T(ey(q)) * gq;
+            jz += T(ez(q)) * gq;
+        }
+        r[p.o] = float(P.rho0 + d * P.inv_s);
+        v[p.o] = float(jx * P.ufac - P.uoff[0]);
+        v[N + p.o] = float(jy * P.ufac - P.uoff[1]);
+        v[2 * N + p.o] = float(jz * P.ufac - P.uoff[2]);
+    });
+}
+
+// ------------------------------------------------------ init equilibrium
+// f~ = f~eq(rho - rho0, u) of Eq. (2) in every fluid cell, 0 in solid cells.
+template <int ST>
+__global__ void __launch_bounds__(256) init_eq_kernel(const __grid_constant__ FieldArgs a, void *buf,
+                                                      const float *rho, const float *u)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    for_each_cell(a, [&](const CellPos &p) {
+        const BlockGeom &b = *p.b;
+        const CollideConsts<T> &P = cs[b.inst];
+        const long long N = inst_cells(b);
+        S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
+        if (a.flags[b.cell_base + p.c] & F_KIND) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) g[(long long)q * b.G] = Tr::from_t(T(0));
+            return;
+        }
+        const float *r = rho + b.out_base;
+        const float *v = u + 3 * b.out_base;
+        const T s = T(1) / P.inv_s;
+        const T drho_s = (T(r[p.o]) - P.rho0) * s;
+        const T ux = v[p.o], uy = v[N + p.o], uz = v[2 * N + p.o];
+        const T usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const T eu = T(ex(q)) * ux + T(ey(q)) * uy + T(ez(q)) * uz;
+            const T feq = T(wq(q)) * (drho_s + P.rho0s * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
+            g[(long long)q * b.G] = Tr::from_t(feq);
+        }
+    });
+}
+
+// ------------------------------------------------------------ PDF in/out
+template <int ST>
+__global__ void __launch_bounds__(256) get_pdfs_kernel(const __grid_constant__ FieldArgs a,
+                                                       const void *buf, double *f)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    for_each_cell(a, [&](const CellPos &p) {
+        const BlockGeom &b = *p.b;
+        const double inv_s = double(cs[b.inst].inv_s);
+        const long long N = inst_cells(b);
+        double *out = f + (long long)Q * b.out_base;
+        const bool solid = a.flags[b.cell_base + p.c] & F_KIND;
+        const S *g = static_cast<const S *>(buf) + b.pdf_base + p.c;
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            out[q * N + p.o] = solid ? 0.0 : double(Tr::to_t(g[(long long)q * b.G])) * inv_s;
+    });
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) set_pdfs_kernel(const __grid_constant__ FieldArgs a, void *buf,
+                                                       const double *f)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    for_each_cell(a, [&](const CellPos &p) {
+        const BlockGeom &b = *p.b;
+        const double s = 1.0 / double(cs[b.inst].inv_s);
+        const long long N = inst_cells(b);
+        const double *in = f + (long long)Q * b.out_base;
+        const bool solid = a.flags[b.cell_base + p.c] & F_KIND;
+        S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            g[(long long)q * b.G] = Tr::from_t(solid ? T(0) : T(in[q * N + p.o] * s));
+    });
+}
+
+// ------------------------------------------------------------- reductions
+// FP64 sums over the fluid cells of each tile: drho, momentum (before the
+// -F/2 shift, which the host applies), fluid and non-finite cell counts,
+// and for the residual sum |u_cur - u_prev|^2 and sum |u_cur|^2.  One CTA
+// per tile writes R_K partials; a second kernel adds the partials of each
+// instance in a fixed order, so results are deterministic.
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) reduce_tiles_kernel(const __grid_constant__ FieldArgs a,
+                                                           const void *cur, const void *prev,
+                                                           double *partial)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    double acc[R_K];
+#pragma unroll
+    for (int k = 0; k < R_K; ++k) acc[k] = 0.0;
+
+    const long long t = blockIdx.x;
+    const Tile tile = a.tiles[t];
+    const BlockGeom &b = a.blocks[tile.block];
+    const int x = tile.x0 + int(threadIdx.x);
+    const int y = tile.y0 + int(threadIdx.y);
+    if (x < b.nx && y < b.ny) {
+        const CollideConsts<T> &P = cs[b.inst];
+        const double inv_s = double(P.inv_s), rho0 = double(P.rho0);
+        const double hF[3] = {double(P.uoff[0]) * rho0, double(P.uoff[1]) * rho0,
+                              double(P.uoff[2]) * rho0};
+        const int zend = min(tile.z0 + a.tz, b.nz);
+        const int pxy = b.px * b.py;
+        for (int z = tile.z0; z < zend; ++z) {
+            const int c = (z + 1) * pxy + (y + 1) * b.px + (x + b.ox);
+            if (a.flags[b.cell_base + c] & F_KIND) continue;
+            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
+            double d = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const double v = double(Tr::to_t(g[(long long)q * b.G])) * inv_s;
+                d += v;
+                j[0] += ex(q) * v;
+                j[1] += ey(q) * v;
+                j[2] += ez(q) * v;
+            }
+            acc[R_DRHO] += d;
+            acc[R_JX] += j[0];
+            acc[R_JY] += j[1];
+            acc[R_JZ] += j[2];
+            acc[R_NFLUID] += 1.0;
+            if (!isfinite(d + j[0] + j[1] + j[2])) acc[R_NONFINITE] += 1.0;
+            if (prev) {
+                const S *h = static_cast<const S *>(prev) + b.pdf_base + c;
+                double k3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const double v = double(Tr::to_t(h[(long long)q * b.G])) * inv_s;
+                    k3[0] += ex(q) * v;
+                    k3[1] += ey(q) * v;
+                    k3[2] += ez(q) * v;
+                }
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const double uc = (j[m] - hF[m]) / rho0;
+                    const double up = (k3[m] - hF[m]) / rho0;
+                    acc[R_DU2] += (uc - up) * (uc - up);
+                    acc[R_U2] += uc * uc;
+                }
+            }
+        }
+    }
+    __shared__ double red[8][R_K];
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < R_K; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (warp == 0 && lane < R_K) {
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += red[w][lane];
+        partial[t * R_K + lane] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) reduce_instances_kernel(const double *partial,
+                                                               const long long *begin, double *out)
+{
+    const int inst = blockIdx.x;
+    const long long t0 = begin[inst], t1 = begin[inst + 1];
+    __shared__ double red[8][R_K];
+    double acc[R_K];
+#pragma unroll
+    for (int k = 0; k < R_K; ++k) acc[k] = 0.0;
+    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < R_K; ++k) acc[k] += partial[t * R_K + k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < R_K; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < R_K) {
+        double v = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+        out[inst * R_K + threadIdx.x] = v;
+    }
+}
+
+// -------------------------------------------------------------- launchers
+static dim3 field_block(const FieldArgs &a) { return dim3(a.tx, a.ty, 1); }
+static unsigned field_grid(const FieldArgs &a) { return unsigned(a.ntiles); }
+
+#define LBM_DISPATCH_ST(st, call)                   \
+    switch (st) {                                   \
+    case 0: call(0); break;                         \
+    case 1: call(1); break;                         \
+    case 2: call(2); break;                         \
+    case 3: call(3); break;                         \
+    default: return cudaErrorInvalidValue;          \
+    }
+
+cudaError_t launch_macroscopic(const FieldArgs &a, const void *buf, float *rho, float *u,
+                               cudaStream_t s)
+{
+    if (a.ntiles == 0) return cudaSuccess;
+#define CALL(ST) macro_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, buf, rho, u)
+    LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_equilibrium(const FieldArgs &a, void *buf, const float *rho, const float *u,
+                                    cudaStream_t s)
+{
+    if (a.ntiles == 0) return cudaSuccess;
+#define CALL(ST) init_eq_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, buf, rho, u)
+    LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_pdfs(const FieldArgs &a, const void *buf, double *f, cudaStream_t s)
+{
+    if (a.ntiles == 0) return cudaSuccess;
+#define CALL(ST) get_pdfs_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, buf, f)
+    LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_pdfs(const FieldArgs &a, void *buf, const double *f, cudaStream_t s)
+{
+    if (a.ntiles == 0) return cudaSuccess;
+#define CALL(ST) set_pdfs_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, buf, f)
+    LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void *buf, size_t bytes, cudaStream_t s)
+{
+    return cudaMemsetAsync(buf, 0, bytes, s);
+}
+
+cudaError_t launch_reduce(const FieldArgs &a, const void *cur, const void *prev, double *partial,
+                          const long long *inst_tile_begin, int ninst, double *out, cudaStream_t s)
+{
+    if (a.tx * a.ty > 256) return cudaErrorInvalidValue;
+    if (a.ntiles > 0) {
+#define CALL(ST) reduce_tiles_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, cur, prev, partial)
+        LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    reduce_instances_kernel<<<ninst, 256, 0, s>>>(partial, inst_tile_begin, out);
+    return cudaGetLastError();
+}
+
+// Sweep dispatch over the storage formats (kernels live in sweep_*.cu).
+template <int ST> cudaError_t launch_sweep_st(const SweepArgs &, cudaStream_t);
+
+cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s)
+{
+    switch (a.storage) {
+    case 0: return launch_sweep_st<0>(a, s);
+    case 1: return launch_sweep_st<1>(a, s);
+    case 2: return launch_sweep_st<2>(a, s);
+    case 3: return launch_sweep_st<3>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,7 @@
+// Sweep kernels for storage format f32 (one translation unit per format
+// so that the build compiles them in parallel).
+#include "sweep_impl.cuh"
+
+namespace lbm {
+template cudaError_t launch_sweep_st<0>(const SweepArgs &, cudaStream_t);
+}

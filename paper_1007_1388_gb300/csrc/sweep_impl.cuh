@@ -1,0 +1,95 @@
+// The fused D3Q19 sweep: pull stream + half-way bounce-back + collide.
+//
+// One thread updates one cell per z step of its tile (Sec. 3.2: one GPU
+// thread per lattice cell, structure-of-arrays PDF layout, pull scheme so
+// that every store is aligned and coalesced).  For each fluid cell x the
+// kernel pulls g_q = src_q[x - e_q]; when x - e_q is a wall or a solid cell
+// it applies half-way bounce-back (Sec. 2.1) with the momentum-consistent
+// sign, g_q = src_opp(q)[x] + s 6 w_q rho0 (e_q . u_wall).  It then collides
+// (Eq. (1), BGK or TRT, optional Guo forcing) and stores dst_q[x].  Solid
+// cells are skipped.  The ghost shell of each Block has been filled by the
+// exchange kernel beforehand, so interior and boundary cells run the same
+// instruction sequence (which keeps multi-Block runs bitwise equal to a
+// single-Block run).
+#pragma once
+
+#include "device_common.cuh"
+
+namespace lbm {
+
+template <int ST, int COLL, bool FORCE>
+__global__ void __launch_bounds__(256, 3) sweep_kernel(const __grid_constant__ SweepArgs a)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *__restrict__ consts = static_cast<const CollideConsts<T> *>(a.consts);
+
+    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const Tile tile = a.tiles[t];
+        const BlockGeom &b = a.blocks[tile.block];
+        const int x = tile.x0 + int(threadIdx.x);
+        const int y = tile.y0 + int(threadIdx.y);
+        const int nx = b.nx, ny = b.ny;
+        if (x >= nx || y >= ny) continue;
+        const int zend = min(tile.z0 + a.tz, b.nz);
+        const int px = b.px;
+        const int pxy = px * b.py;
+        const int G = int(b.G);
+        const CollideConsts<T> *cc = consts + b.inst;
+        const Coll<T> P = load_coll<T>(cc);
+        const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
+        S *__restrict__ dst = static_cast<S *>(a.dst) + b.pdf_base;
+        const uint8_t *__restrict__ fl = a.flags + b.cell_base;
+
+        int c = (tile.z0 + 1) * pxy + (y + 1) * px + (x + b.ox);
+        for (int z = tile.z0; z < zend; ++z, c += pxy) {
+            const uint8_t flag = fl[c];
+            if (flag & F_KIND) continue;  // solid cells are not updated
+            T f[Q];
+            if (!(flag & F_NEAR)) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+                    f[q] = Tr::ld(src + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int n = c - (ex(q) + ey(q) * px + ez(q) * pxy);
+                    const uint8_t nf = fl[n];
+                    if (nf & F_KIND) {
+                        T v = Tr::ld(src + (opp(q) * G + c));
+                        if ((nf & F_KIND) == F_MOVING) v += __ldg(&cc->bbw[q]);
+                        f[q] = v;
+                    } else {
+                        f[q] = Tr::ld(src + (q * G + n));
+                    }
+                }
+            }
+            collide<T, COLL, FORCE>(f, P);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
+        }
+    }
+}
+
+template <int ST>
+cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
+{
+    dim3 block(a.tx, a.ty, 1);
+    const unsigned grid = unsigned(a.grid > 0 ? a.grid : a.ntiles);
+    if (grid == 0) return cudaSuccess;
+    if (a.collision == 0) {
+        if (a.forced)
+            sweep_kernel<ST, 0, true><<<grid, block, 0, s>>>(a);
+        else
+            sweep_kernel<ST, 0, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.forced)
+            sweep_kernel<ST, 1, true><<<grid, block, 0, s>>>(a);
+        else
+            sweep_kernel<ST, 1, false><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

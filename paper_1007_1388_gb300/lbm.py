@@ -1,0 +1,373 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own; every step of the lattice Boltzmann path runs in the
+library's CUDA kernels.  PyTorch supplies plumbing only: the device memory
+(through ``use_torch_allocator``) and the CUDA stream each context runs on.
+
+If liblbm.so has not been built, importing works but the first call raises
+``RuntimeError``: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import weakref
+
+import numpy as np
+
+Q = 19
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENUMERIC = 0, -1, -2, -3, -4, -5
+LBM_FLUID, LBM_NOSLIP, LBM_MOVING = 0, 1, 2
+LBM_BGK, LBM_TRT = 0, 1
+LBM_F32, LBM_F16S, LBM_BF16S, LBM_F64 = 0, 1, 2, 3
+STORAGE_NAMES = {LBM_F32: "f32", LBM_F16S: "f16s", LBM_BF16S: "bf16s", LBM_F64: "f64"}
+BYTES_PER_PDF = {LBM_F32: 4, LBM_F16S: 2, LBM_BF16S: 2, LBM_F64: 8}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("collision", ctypes.c_int),
+        ("magic", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("force", ctypes.c_double * 3),
+        ("wall_u", ctypes.c_double * 3),
+        ("periodic", ctypes.c_int * 3),
+        ("face_bc", ctypes.c_int * 6),
+        ("storage", ctypes.c_int),
+        ("storage_scale", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("tile", ctypes.c_int * 3),
+        ("graph_steps", ctypes.c_int),
+    ]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [
+        ("cells", ctypes.c_longlong),
+        ("fluid_cells", ctypes.c_longlong),
+        ("stored_cells", ctypes.c_longlong),
+        ("blocks", ctypes.c_int),
+        ("instances", ctypes.c_int),
+        ("storage", ctypes.c_int),
+        ("bytes_per_pdf", ctypes.c_int),
+        ("exchange_pdfs", ctypes.c_longlong),
+        ("device_bytes", ctypes.c_longlong),
+        ("tile", ctypes.c_int * 3),
+        ("tiles", ctypes.c_longlong),
+    ]
+
+
+class lbm_profile(ctypes.Structure):
+    _fields_ = [
+        ("sweep_ms", ctypes.c_double),
+        ("sweep_launches", ctypes.c_longlong),
+        ("exchange_ms", ctypes.c_double),
+        ("exchange_launches", ctypes.c_longlong),
+    ]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+# every symbol include/lbm.h declares, with its ctypes signature
+_P = ctypes.POINTER
+_vp, _i, _d, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+SIGNATURES = {
+    "lbm_default_params": ([_P(lbm_params)], None),
+    "lbm_create": ([_P(ctypes.c_int), _P(ctypes.c_int), _d, _vp, _P(lbm_params), _P(_vp)], _i),
+    "lbm_batch_create": ([_i, _P(ctypes.c_int), _P(_d), _P(_vp), _P(lbm_params), _P(_vp)], _i),
+    "lbm_destroy": ([_vp], None),
+    "lbm_step": ([_vp, _i], _i),
+    "lbm_synchronize": ([_vp], _i),
+    "lbm_macroscopic": ([_vp, _vp, _vp], _i),
+    "lbm_macroscopic_device": ([_vp, _vp, _vp], _i),
+    "lbm_get_pdfs": ([_vp, _vp], _i),
+    "lbm_set_pdfs": ([_vp, _vp], _i),
+    "lbm_init_equilibrium": ([_vp, _vp, _vp], _i),
+    "lbm_init_equilibrium_device": ([_vp, _vp, _vp], _i),
+    "lbm_invariants": ([_vp, _P(_d), _P(_d), _P(_d), _vp], _i),
+    "lbm_residual": ([_vp, _P(_d), _vp], _i),
+    "lbm_run_to_residual": ([_vp, _d, _i, _ll, _P(_ll), _P(_d)], _i),
+    "lbm_get_info": ([_vp, _P(lbm_info)], _i),
+    "lbm_profile_enable": ([_vp, _i], _i),
+    "lbm_profile_read": ([_vp, _P(lbm_profile)], _i),
+    "lbm_autotune": ([_vp, ctypes.c_char_p, _P(ctypes.c_int)], _i),
+    "lbm_set_allocator": ([ALLOC_FN, FREE_FN, _vp], _i),
+    "lbm_directions": ([_P(ctypes.c_int), _P(_d), _P(ctypes.c_int)], _i),
+    "lbm_last_error": ([_vp], ctypes.c_char_p),
+    "lbm_version": ([], ctypes.c_char_p),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        msg = lib().lbm_last_error(ctx.ptr if ctx is not None else None)
+        raise LBMError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch.Tensor
+
+
+# ---------------------------------------------------------------- allocator
+_torch_hooks = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _torch_hooks
+    import torch
+
+    if _torch_hooks is not None:
+        return
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0)
+        except Exception:  # out of memory -> NULL -> LBM_ENOMEM
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib().lbm_set_allocator(hooks[0], hooks[1], None))
+    _torch_hooks = hooks
+
+
+# ------------------------------------------------------------------ context
+class Ctx:
+    """Owner of one lbm_ctx*; destroyed by lbm_destroy or garbage collection."""
+
+    def __init__(self, ptr, cells, ninst, stream, inst_cells):
+        self.ptr = ptr
+        self.cells = cells
+        self.ninst = ninst
+        self.stream = stream  # keeps the torch stream alive
+        self.inst_cells = inst_cells
+        self._fin = weakref.finalize(self, lib().lbm_destroy, ptr)
+
+    def destroy(self):
+        self._fin()
+
+
+def lbm_default_params() -> lbm_params:
+    p = lbm_params()
+    lib().lbm_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(**kw) -> lbm_params:
+    """lbm_default_params() with the given fields replaced (lists for arrays)."""
+    p = lbm_default_params()
+    for k, v in kw.items():
+        if k in ("force", "wall_u", "periodic", "face_bc", "tile"):
+            getattr(p, k)[:] = list(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _stream_for(params):
+    """A torch stream for the context unless the caller set one."""
+    if params.stream:
+        return None
+    import torch
+
+    if not torch.cuda.is_available():
+        return None
+    s = torch.cuda.Stream()
+    params.stream = s.cuda_stream
+    return s
+
+
+def lbm_create(dims, block_dims, tau, flags=None, params=None) -> Ctx:
+    p = params if params is not None else lbm_default_params()
+    p = lbm_params.from_buffer_copy(p)
+    stream = _stream_for(p)
+    d = (ctypes.c_int * 3)(*[int(v) for v in dims])
+    b = (ctypes.c_int * 3)(*[int(v) for v in block_dims])
+    fl = None
+    if flags is not None:
+        fl = np.ascontiguousarray(flags, dtype=np.uint8).reshape(-1)
+        if fl.size != int(np.prod(dims)):
+            raise ValueError("flags must have nx*ny*nz entries")
+    out = ctypes.c_void_p()
+    _check(lib().lbm_create(d, b, float(tau), _ptr(fl), ctypes.byref(p), ctypes.byref(out)))
+    n = int(np.prod(dims))
+    return Ctx(out.value, n, 1, stream, [n])
+
+
+def lbm_batch_create(dims, tau, flags=None, params=None) -> Ctx:
+    dims = np.ascontiguousarray(dims, dtype=np.int32).reshape(-1, 3)
+    n = dims.shape[0]
+    tau = np.ascontiguousarray(tau, dtype=np.float64).reshape(n)
+    p = params if params is not None else lbm_default_params()
+    p = lbm_params.from_buffer_copy(p)
+    stream = _stream_for(p)
+    keep = []
+    fl_arr = None
+    if flags is not None:
+        fl_arr = (ctypes.c_void_p * n)()
+        for k in range(n):
+            if flags[k] is None:
+                fl_arr[k] = None
+                continue
+            a = np.ascontiguousarray(flags[k], dtype=np.uint8).reshape(-1)
+            if a.size != int(np.prod(dims[k])):
+                raise ValueError(f"flags[{k}] must have nx*ny*nz entries")
+            keep.append(a)
+            fl_arr[k] = a.ctypes.data
+    out = ctypes.c_void_p()
+    _check(lib().lbm_batch_create(n, dims.ctypes.data_as(_P(ctypes.c_int)),
+                                  tau.ctypes.data_as(_P(ctypes.c_double)), fl_arr,
+                                  ctypes.byref(p), ctypes.byref(out)))
+    inst_cells = [int(np.prod(d)) for d in dims]
+    return Ctx(out.value, sum(inst_cells), n, stream, inst_cells)
+
+
+def lbm_destroy(ctx: Ctx):
+    ctx.destroy()
+
+
+def lbm_step(ctx: Ctx, n: int = 1):
+    _check(lib().lbm_step(ctx.ptr, int(n)), ctx)
+
+
+def lbm_synchronize(ctx: Ctx):
+    _check(lib().lbm_synchronize(ctx.ptr), ctx)
+
+
+def lbm_macroscopic(ctx: Ctx, rho=None, u=None):
+    """Host variant: fills (or allocates) numpy rho[N], u[3N] float32."""
+    rho = np.empty(ctx.cells, np.float32) if rho is None else rho
+    u = np.empty(3 * ctx.cells, np.float32) if u is None else u
+    assert rho.dtype == np.float32 and rho.size == ctx.cells and rho.flags.c_contiguous
+    assert u.dtype == np.float32 and u.size == 3 * ctx.cells and u.flags.c_contiguous
+    _check(lib().lbm_macroscopic(ctx.ptr, _ptr(rho), _ptr(u)), ctx)
+    return rho, u
+
+
+def lbm_macroscopic_device(ctx: Ctx, rho, u):
+    """Device variant: rho, u are contiguous float32 CUDA tensors (N and 3N)."""
+    _check(lib().lbm_macroscopic_device(ctx.ptr, _ptr(rho), _ptr(u)), ctx)
+
+
+def lbm_get_pdfs(ctx: Ctx, f=None):
+    f = np.empty(Q * ctx.cells, np.float64) if f is None else f
+    assert f.dtype == np.float64 and f.size == Q * ctx.cells and f.flags.c_contiguous
+    _check(lib().lbm_get_pdfs(ctx.ptr, _ptr(f)), ctx)
+    return f
+
+
+def lbm_set_pdfs(ctx: Ctx, f):
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+    assert f.size == Q * ctx.cells
+    _check(lib().lbm_set_pdfs(ctx.ptr, _ptr(f)), ctx)
+
+
+def lbm_init_equilibrium(ctx: Ctx, rho, u):
+    rho = np.ascontiguousarray(rho, dtype=np.float32).reshape(-1)
+    u = np.ascontiguousarray(u, dtype=np.float32).reshape(-1)
+    assert rho.size == ctx.cells and u.size == 3 * ctx.cells
+    _check(lib().lbm_init_equilibrium(ctx.ptr, _ptr(rho), _ptr(u)), ctx)
+
+
+def lbm_init_equilibrium_device(ctx: Ctx, rho, u):
+    _check(lib().lbm_init_equilibrium_device(ctx.ptr, _ptr(rho), _ptr(u)), ctx)
+
+
+def lbm_invariants(ctx: Ctx, per_instance: bool = False):
+    """(mass, momentum[3], nonfinite) or, with per_instance, also a (ninst, 5) array."""
+    m, nf = ctypes.c_double(), ctypes.c_double()
+    mom = (ctypes.c_double * 3)()
+    per = np.zeros((ctx.ninst, 5)) if per_instance else None
+    _check(lib().lbm_invariants(ctx.ptr, ctypes.byref(m), mom, ctypes.byref(nf), _ptr(per)), ctx)
+    res = (m.value, np.array(mom[:]), nf.value)
+    return res + (per,) if per_instance else res
+
+
+def lbm_residual(ctx: Ctx, per_instance: bool = False):
+    r = ctypes.c_double()
+    per = np.zeros(ctx.ninst) if per_instance else None
+    _check(lib().lbm_residual(ctx.ptr, ctypes.byref(r), _ptr(per)), ctx)
+    return (r.value, per) if per_instance else r.value
+
+
+def lbm_run_to_residual(ctx: Ctx, tol: float, check_every: int = 10, max_steps: int = 10**6):
+    steps, r = ctypes.c_longlong(), ctypes.c_double()
+    _check(lib().lbm_run_to_residual(ctx.ptr, float(tol), int(check_every), int(max_steps),
+                                     ctypes.byref(steps), ctypes.byref(r)), ctx)
+    return steps.value, r.value
+
+
+def lbm_get_info(ctx: Ctx) -> lbm_info:
+    info = lbm_info()
+    _check(lib().lbm_get_info(ctx.ptr, ctypes.byref(info)), ctx)
+    return info
+
+
+def lbm_profile_enable(ctx: Ctx, on: bool = True):
+    _check(lib().lbm_profile_enable(ctx.ptr, 1 if on else 0), ctx)
+
+
+def lbm_profile_read(ctx: Ctx) -> lbm_profile:
+    prof = lbm_profile()
+    _check(lib().lbm_profile_read(ctx.ptr, ctypes.byref(prof)), ctx)
+    return prof
+
+
+def lbm_autotune(ctx: Ctx, cache_path: str | None = None):
+    best = (ctypes.c_int * 3)()
+    _check(lib().lbm_autotune(ctx.ptr, cache_path.encode() if cache_path else None, best), ctx)
+    return tuple(best)
+
+
+def lbm_directions():
+    e = (ctypes.c_int * (3 * Q))()
+    w = (ctypes.c_double * Q)()
+    o = (ctypes.c_int * Q)()
+    _check(lib().lbm_directions(e, w, o))
+    return np.array(e[:]).reshape(Q, 3), np.array(w[:]), np.array(o[:])
+
+
+def lbm_last_error(ctx: Ctx | None = None) -> str:
+    return lib().lbm_last_error(ctx.ptr if ctx is not None else None).decode()
+
+
+def lbm_version() -> str:
+    return lib().lbm_version().decode()
