@@ -190,12 +190,24 @@ def run_gpu(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
+    n, b = args.size, args.block
+
     def make(storage=L.LBM_F32, coll=L.LBM_BGK, **extra):
         p = L.make_params(collision=coll, force=(FORCE, 0, 0), storage=storage,
                           **W.channel_bc(), **extra)
-        return L.lbm_create((N, N, N), (B, B, B), TAU, None, p)
+        return L.lbm_create((n, n, n), (b, b, b), TAU, None, p)
 
-    ctx = make()
+    main_kw = {}
+    if args.storage:
+        main_kw["storage"] = {"f32": L.LBM_F32, "f16s": L.LBM_F16S, "bf16s": L.LBM_BF16S,
+                              "f64": L.LBM_F64}[args.storage]
+        if main_kw["storage"] == L.LBM_F16S:
+            main_kw["storage_scale"] = 256.0
+    if args.trt:
+        main_kw["coll"] = L.LBM_TRT
+    ctx = make(**main_kw)
+    if args.autotune:
+        L.lbm_autotune(ctx, None)
     info = L.lbm_get_info(ctx)
     cells = info.cells
     stream = ctx.stream  # the torch stream the library enqueues on
@@ -232,13 +244,14 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     sweep_ms = prof.sweep_ms / max(1, prof.sweep_launches)
     xch_ms = prof.exchange_ms / max(1, prof.exchange_launches)
-    alg_bytes = BYTES_PER_LUP[0] * cells
+    st_main = main_kw.get("storage", 0)
+    alg_bytes = BYTES_PER_LUP[st_main] * cells
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
     traffic = _ncu_traffic("sweep_f32_channel256")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": peak_kind, "kernel": "lbm::sweep_kernel<F32,BGK,forced>",
-                "bytes_per_lup": BYTES_PER_LUP[0], "sweep_ms": sweep_ms,
+                "peak_kind": peak_kind, "kernel": "lbm::sweep_kernel (forced)",
+                "bytes_per_lup": BYTES_PER_LUP[st_main], "sweep_ms": sweep_ms,
                 "exchange_ms": xch_ms, "exchange_pdfs": info.exchange_pdfs}
 
     # ---- e2e: through the C ABI with pinned host buffers, copies included
@@ -275,9 +288,9 @@ def run_gpu(args):
             L.lbm_profile_enable(c, True)
             L.lbm_profile_read(c)
             barrier()
-            e0.record(stream)
+            e0.record(c.stream)
             L.lbm_step(c, vsteps)
-            e1.record(stream)
+            e1.record(c.stream)
             barrier()
             pr = L.lbm_profile_read(c)
             st = kw.get("storage", 0)
@@ -342,6 +355,11 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--size", type=int, default=N, help="cells per axis (profiling runs use less)")
+    ap.add_argument("--block", type=int, default=B, help="cells per Block along each axis")
+    ap.add_argument("--storage", default="", help="f32 | f16s | bf16s | f64 (default f32)")
+    ap.add_argument("--trt", action="store_true", help="TRT instead of BGK")
+    ap.add_argument("--autotune", action="store_true", help="pick the sweep tile by timing")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

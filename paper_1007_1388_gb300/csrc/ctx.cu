@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <memory>
@@ -64,6 +65,7 @@ struct lbm_ctx {
     long long cells = 0, fluid = 0, stored = 0, exchange_pdfs = 0;
     int tile[3] = {64, 4, 4};
     int grid = 0;  // 0 = one CTA per tile
+    int minb = 3;  // register budget of the sweep (resident CTAs per SM)
     // device
     Allocator alloc;
     std::vector<DevMem> owned;
@@ -335,7 +337,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     c->storage = p.storage;
     c->elem = p.storage == LBM_F32 ? 4 : (p.storage == LBM_F64 ? 8 : 2);
     c->forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
-    const int align = 16 / c->elem;  // cells per 16 bytes
+    const int align = 32 / c->elem;  // cells per 32-byte DRAM sector
 
     if (p.stream) {
         c->stream = static_cast<cudaStream_t>(p.stream);
@@ -411,6 +413,25 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                     hflags.insert(hflags.end(), f.begin(), f.end());
                     c->blocks.push_back(b);
                 }
+        // ---- direct reads across x faces
+        for (int bz = 0; bz < nb[2]; ++bz)
+            for (int by = 0; by < nb[1]; ++by)
+                for (int bx = 0; bx < nb[0]; ++bx) {
+                    BlockGeom &b = c->blocks[first_block + (bz * nb[1] + by) * nb[0] + bx];
+                    for (int side = -1; side <= 1; side += 2) {
+                        int nbx = bx + side;
+                        if (nbx < 0 || nbx >= nb[0]) {
+                            if (!p.periodic[0]) continue;
+                            nbx = (nbx + nb[0]) % nb[0];
+                        }
+                        const BlockGeom &n = c->blocks[first_block + (bz * nb[1] + by) * nb[0] + nbx];
+                        const long long off = n.pdf_base - b.pdf_base - side * (long long)b.nx;
+                        if (side < 0)
+                            b.xm_off = off;
+                        else
+                            b.xp_off = off;
+                    }
+                }
         // ---- ghost exchange plan: faces and edges with a neighbour block
         for (int bz = 0; bz < nb[2]; ++bz)
             for (int by = 0; by < nb[1]; ++by)
@@ -423,6 +444,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                 const int n[3] = {n0, n1, n2};
                                 const int nnz = (n0 != 0) + (n1 != 0) + (n2 != 0);
                                 if (nnz == 0 || nnz == 3) continue;  // no corner links in D3Q19
+                                if (n0 != 0) continue;  // x faces: read directly by the sweep
                                 int npos[3];
                                 bool ok = true;
                                 for (int a = 0; a < 3; ++a) {
@@ -537,6 +559,7 @@ SweepArgs sweep_args(const lbm_ctx *c, int from)
     a.forced = c->forced ? 1 : 0;
     a.storage = c->storage;
     a.grid = c->grid;
+    a.minb = c->minb;
     return a;
 }
 
@@ -1006,7 +1029,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
 {
     if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
     const std::string key = tune_key(c);
-    int best[4] = {c->tile[0], c->tile[1], c->tile[2], c->grid};
+    int best[5] = {c->tile[0], c->tile[1], c->tile[2], c->grid, c->minb};
     bool cached = false;
     if (cache_path) {
         std::ifstream in(cache_path);
@@ -1015,30 +1038,34 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         while (std::getline(in, line)) {
             if (line.find(needle) == std::string::npos) continue;
             size_t t = line.find("\"tile\": [");
-            int v[4];
+            int v[5];
             if (t != std::string::npos &&
-                std::sscanf(line.c_str() + t, "\"tile\": [%d, %d, %d, %d]", &v[0], &v[1], &v[2], &v[3]) == 4) {
+                std::sscanf(line.c_str() + t, "\"tile\": [%d, %d, %d, %d, %d]", &v[0], &v[1], &v[2],
+                            &v[3], &v[4]) == 5) {
                 std::memcpy(best, v, sizeof v);
                 cached = true;
             }
         }
     }
     if (!cached) {
+        const char *ev = std::getenv("LBM_AUTOTUNE_VERBOSE");
+        const bool verbose = ev && ev[0] == '1';
         int maxnx = 0;
         for (const BlockGeom &b : c->blocks) maxnx = std::max(maxnx, b.nx);
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        std::vector<std::array<int, 4>> cand;
-        for (int tx : {32, 64, 128, 256}) {
-            if (tx > std::max(32, round_up(maxnx, 32))) continue;
-            for (int th : {128, 256}) {
-                if (th < tx) continue;
-                for (int tz : {1, 2, 4, 8, 16}) cand.push_back({tx, th / tx, tz, 0});
+        std::vector<std::array<int, 5>> cand;
+        for (int mb : {3, 4})
+            for (int tx : {32, 64, 128, 256}) {
+                if (tx > std::max(32, round_up(maxnx, 32))) continue;
+                for (int th : {128, 256}) {
+                    if (th < tx) continue;
+                    for (int tz : {1, 2, 4, 8, 16}) cand.push_back({tx, th / tx, tz, 0, mb});
+                }
             }
-        }
         // persistent variants of the default tile
-        for (int m : {4, 8, 16}) cand.push_back({c->tile[0], c->tile[1], c->tile[2], m * sms});
+        for (int m : {4, 8, 16}) cand.push_back({c->tile[0], c->tile[1], c->tile[2], m * sms, c->minb});
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");
@@ -1048,6 +1075,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
             int t[3] = {cd[0], cd[1], cd[2]};
             int rc = set_tiles(c, t, cd[3] ? int(std::min<long long>(cd[3], 1ll << 30)) : 0);
             if (rc) return rc;
+            c->minb = cd[4];
             SweepArgs a = sweep_args(c, c->cur);
             CK(launch_sweep(a, c->stream), "tune");
             CK(cudaEventRecord(e0, c->stream), "event");
@@ -1056,12 +1084,16 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
             CK(cudaEventSynchronize(e1), "tune sync");
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            if (verbose)
+                std::fprintf(stderr, "lbm_autotune: tile %d %d %d grid %d minb %d: %.4f ms/sweep\n",
+                             cd[0], cd[1], cd[2], cd[3], cd[4], ms / reps);
             if (ms < best_ms) {
                 best_ms = ms;
                 best[0] = cd[0];
                 best[1] = cd[1];
                 best[2] = cd[2];
                 best[3] = cd[3];
+                best[4] = cd[4];
             }
         }
         cudaEventDestroy(e0);
@@ -1069,12 +1101,14 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         if (cache_path) {
             std::ofstream o(cache_path, std::ios::app);
             o << "{\"key\": \"" << key << "\", \"tile\": [" << best[0] << ", " << best[1] << ", "
-              << best[2] << ", " << best[3] << "], \"ms_per_sweep\": " << best_ms / reps << "}\n";
+              << best[2] << ", " << best[3] << ", " << best[4] << "], \"ms_per_sweep\": "
+              << best_ms / reps << "}\n";
         }
     }
     int t[3] = {best[0], best[1], best[2]};
     int rc = set_tiles(c, t, best[3]);
     if (rc) return rc;
+    c->minb = best[4];
     c->have_prev = false;  // the scratch buffer was overwritten
     if (best_out)
         for (int a = 0; a < 3; ++a) best_out[a] = best[a];

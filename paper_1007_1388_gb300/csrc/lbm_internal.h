@@ -31,13 +31,20 @@ enum : uint8_t {
 
 // One Block (or one batch instance) in device memory.  The Block stores
 // (nx+2)(ny+2)(nz+2) logical cells with x padded: row pitch px, the first
-// interior cell of a row at x index ox (so interior rows start 16-byte
-// aligned), ghost cells at ox-1 and ox+nx.  PDF plane q of the Block lives
-// at buf + pdf_base + q*G, flag byte of cell c at flags + cell_base + c.
+// interior cell of a row at x index ox (so interior rows start on a 32-byte
+// DRAM sector), ghost cells at ox-1 and ox+nx.  PDF plane q of the Block
+// lives at buf + pdf_base + q*G, flag byte of cell c at flags + cell_base + c.
+//
+// Across x faces the sweep reads the neighbouring Block's boundary column
+// directly (xm_off / xp_off: element offset from this Block's stored cell
+// x = ox-1 / ox+nx to the matching interior cell of the -x / +x neighbour,
+// 0 where the face is a wall), so the ghost exchange copies only the y and z
+// faces and the yz edges, which are contiguous rows in this layout.
 struct BlockGeom {
     long long pdf_base;   // elements
     long long cell_base;  // cells (flags)
     long long G;          // cells per plane = px*py*pz
+    long long xm_off, xp_off;
     int nx, ny, nz;       // interior cells
     int px, py;           // padded row pitch (cells), rows per plane (ny+2)
     int ox;               // x index of the first interior cell
@@ -97,6 +104,7 @@ struct SweepArgs {
     int forced;               // any instance has a nonzero force
     int storage;              // LBM_F32 .. LBM_F64
     int grid;                 // CTAs to launch (<= ntiles; persistent loop when smaller)
+    int minb;                 // register budget: 3 or 4 resident 256-thread CTAs per SM
 };
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
 

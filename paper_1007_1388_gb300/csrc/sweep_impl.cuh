@@ -17,8 +17,10 @@
 
 namespace lbm {
 
-template <int ST, int COLL, bool FORCE>
-__global__ void __launch_bounds__(256, 3) sweep_kernel(const __grid_constant__ SweepArgs a)
+// MINB = CTAs of 256 threads per SM the register allocation must allow
+// (3 -> 80 registers, 4 -> 64); chosen per context by the autotuner.
+template <int ST, int COLL, bool FORCE, int MINB>
+__global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     using Tr = Traits<ST>;
     using S = typename Tr::S;
@@ -39,6 +41,10 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const __grid_constant__ S
         const CollideConsts<T> *cc = consts + b.inst;
         const Coll<T> P = load_coll<T>(cc);
         const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
+        // directions with e_x = +1 pull from x-1, e_x = -1 from x+1: on the
+        // Block's first / last column those come from the x neighbour
+        const S *__restrict__ srcm = src + (x == 0 ? b.xm_off : 0ll);
+        const S *__restrict__ srcp = src + (x == nx - 1 ? b.xp_off : 0ll);
         S *__restrict__ dst = static_cast<S *>(a.dst) + b.pdf_base;
         const uint8_t *__restrict__ fl = a.flags + b.cell_base;
 
@@ -49,8 +55,10 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const __grid_constant__ S
             T f[Q];
             if (!(flag & F_NEAR)) {
 #pragma unroll
-                for (int q = 0; q < Q; ++q)
-                    f[q] = Tr::ld(src + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
+                for (int q = 0; q < Q; ++q) {
+                    const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+                    f[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
+                }
             } else {
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
@@ -61,7 +69,8 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const __grid_constant__ S
                         if ((nf & F_KIND) == F_MOVING) v += __ldg(&cc->bbw[q]);
                         f[q] = v;
                     } else {
-                        f[q] = Tr::ld(src + (q * G + n));
+                        const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+                        f[q] = Tr::ld(s + (q * G + n));
                     }
                 }
             }
@@ -72,23 +81,34 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel(const __grid_constant__ S
     }
 }
 
+template <int ST, int MINB>
+void launch_sweep_minb(const SweepArgs &a, unsigned grid, dim3 block, cudaStream_t s)
+{
+    if (a.collision == 0) {
+        if (a.forced)
+            sweep_kernel<ST, 0, true, MINB><<<grid, block, 0, s>>>(a);
+        else
+            sweep_kernel<ST, 0, false, MINB><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.forced)
+            sweep_kernel<ST, 1, true, MINB><<<grid, block, 0, s>>>(a);
+        else
+            sweep_kernel<ST, 1, false, MINB><<<grid, block, 0, s>>>(a);
+    }
+}
+
 template <int ST>
 cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
 {
     dim3 block(a.tx, a.ty, 1);
     const unsigned grid = unsigned(a.grid > 0 ? a.grid : a.ntiles);
     if (grid == 0) return cudaSuccess;
-    if (a.collision == 0) {
-        if (a.forced)
-            sweep_kernel<ST, 0, true><<<grid, block, 0, s>>>(a);
-        else
-            sweep_kernel<ST, 0, false><<<grid, block, 0, s>>>(a);
-    } else {
-        if (a.forced)
-            sweep_kernel<ST, 1, true><<<grid, block, 0, s>>>(a);
-        else
-            sweep_kernel<ST, 1, false><<<grid, block, 0, s>>>(a);
-    }
+    if (ST == 3)  // FP64 arithmetic needs the larger register budget
+        launch_sweep_minb<ST, 2>(a, grid, block, s);
+    else if (a.minb == 4)
+        launch_sweep_minb<ST, 4>(a, grid, block, s);
+    else
+        launch_sweep_minb<ST, 3>(a, grid, block, s);
     return cudaGetLastError();
 }
 

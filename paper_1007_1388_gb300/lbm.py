@@ -134,6 +134,20 @@ def _check(rc, ctx=None):
         raise LBMError(rc, msg.decode() if msg else "")
 
 
+def _host_buf(a, n, dtype):
+    """Checks a caller-given host buffer (numpy array or CPU torch tensor)."""
+    if isinstance(a, np.ndarray):
+        ok = a.dtype == dtype and a.size == n and a.flags.c_contiguous
+    else:
+        import torch
+
+        tdt = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        ok = (a.dtype == tdt and a.numel() == n and a.is_contiguous() and a.device.type == "cpu")
+    if not ok:
+        raise ValueError(f"host buffer must be a contiguous {np.dtype(dtype).name} array of {n} values")
+    return a
+
+
 def _ptr(a):
     """Address of a numpy array or torch tensor (host or device)."""
     if a is None:
@@ -274,10 +288,8 @@ def lbm_synchronize(ctx: Ctx):
 
 def lbm_macroscopic(ctx: Ctx, rho=None, u=None):
     """Host variant: fills (or allocates) numpy rho[N], u[3N] float32."""
-    rho = np.empty(ctx.cells, np.float32) if rho is None else rho
-    u = np.empty(3 * ctx.cells, np.float32) if u is None else u
-    assert rho.dtype == np.float32 and rho.size == ctx.cells and rho.flags.c_contiguous
-    assert u.dtype == np.float32 and u.size == 3 * ctx.cells and u.flags.c_contiguous
+    rho = _host_buf(np.empty(ctx.cells, np.float32) if rho is None else rho, ctx.cells, np.float32)
+    u = _host_buf(np.empty(3 * ctx.cells, np.float32) if u is None else u, 3 * ctx.cells, np.float32)
     _check(lib().lbm_macroscopic(ctx.ptr, _ptr(rho), _ptr(u)), ctx)
     return rho, u
 
@@ -288,8 +300,7 @@ def lbm_macroscopic_device(ctx: Ctx, rho, u):
 
 
 def lbm_get_pdfs(ctx: Ctx, f=None):
-    f = np.empty(Q * ctx.cells, np.float64) if f is None else f
-    assert f.dtype == np.float64 and f.size == Q * ctx.cells and f.flags.c_contiguous
+    f = _host_buf(np.empty(Q * ctx.cells, np.float64) if f is None else f, Q * ctx.cells, np.float64)
     _check(lib().lbm_get_pdfs(ctx.ptr, _ptr(f)), ctx)
     return f
 
@@ -301,9 +312,11 @@ def lbm_set_pdfs(ctx: Ctx, f):
 
 
 def lbm_init_equilibrium(ctx: Ctx, rho, u):
-    rho = np.ascontiguousarray(rho, dtype=np.float32).reshape(-1)
-    u = np.ascontiguousarray(u, dtype=np.float32).reshape(-1)
-    assert rho.size == ctx.cells and u.size == 3 * ctx.cells
+    if isinstance(rho, np.ndarray) or not hasattr(rho, "data_ptr"):
+        rho = np.ascontiguousarray(rho, dtype=np.float32).reshape(-1)
+        u = np.ascontiguousarray(u, dtype=np.float32).reshape(-1)
+    _host_buf(rho, ctx.cells, np.float32)
+    _host_buf(u, 3 * ctx.cells, np.float32)
     _check(lib().lbm_init_equilibrium(ctx.ptr, _ptr(rho), _ptr(u)), ctx)
 
 

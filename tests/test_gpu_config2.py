@@ -64,11 +64,11 @@ def test_channel_256_blocks_vs_single_and_analytic(L, coll):
     del fs
     rho, u = L.lbm_macroscopic(multi)
     ux = u[:N**3].reshape(N, N, N)
-    prof = ux.mean(axis=(0, 2))
+    # the flow is translation invariant along x and z, cell for cell bitwise
+    assert np.array_equal(ux, np.broadcast_to(ux[:1, :, :1], ux.shape))
+    prof = ux[0, :, 0].astype(np.float64)
     ua = _startup_profile(N, FORCE, (TAU - 0.5) / 3, STEPS)
     assert np.abs(prof - ua).max() <= 0.01 * ua.max()
-    # uniform along x and z (periodic, no obstacles)
-    assert np.abs(ux - prof[None, :, None]).max() <= 1e-6 * ua.max() + 1e-12
     # one more step: sampled cells against the oracle from the same state
     rng = np.random.default_rng(2000 + coll)
     cells = rng.choice(N**3, 4096, replace=False)

@@ -105,7 +105,8 @@ def test_one_step_from_random_state(L, seed):
     mr, jr = oracle.invariants(p, got)
     assert bad == 0
     assert abs(m - mr) <= 1e-12 * abs(mr)
-    assert np.abs(j - jr).max() <= 1e-12 * max(1.0, np.abs(jr).max())
+    # FP64 sums over ~1e5 cells in different orders: relative 1e-11
+    assert np.abs(j - jr).max() <= 1e-11 * max(1.0, np.abs(jr).max())
     r = L.lbm_residual(ctx)
     assert abs(r - oracle.residual(p, f0, got)) <= 1e-10 * r
     # moments of the stored state
@@ -203,7 +204,8 @@ def test_set_get_roundtrip_rounds_as_documented(L, storage):
     if storage == 0:
         exp = f.astype(np.float32).astype(np.float64)
     elif storage == 1:
-        exp = (f * scale).astype(np.float16).astype(np.float64) / scale
+        # the kernel rounds to FP32 first, then to the storage format
+        exp = (f * scale).astype(np.float32).astype(np.float16).astype(np.float64) / scale
     elif storage == 2:
         exp = _bf16_round((f * scale).astype(np.float32)) / scale
     else:
@@ -265,7 +267,8 @@ def test_batch_of_uneven_instances_matches_oracle(L):
         ref = oracle.run(p, oracle.zeros(p), 30)
         assert np.abs(fk - ref).max() <= TOL_MULTISTEP, k
         m, j = oracle.invariants(p, fk)
-        assert abs(per[k, 0] - m) <= 1e-12 * m and np.abs(per[k, 1:4] - j).max() <= 1e-12
+        assert abs(per[k, 0] - m) <= 1e-12 * m
+        assert np.abs(per[k, 1:4] - j).max() <= 1e-11 * max(1.0, np.abs(j).max())
     ctx.destroy()
 
 
@@ -307,7 +310,7 @@ def test_edge_cases(L):
     assert ei.value.code == L.LBM_EINVAL
 
 
-def test_init_equilibrium_and_run_to_residual(L):
+def test_init_equilibrium_from_random_fields(L):
     rng = np.random.default_rng(12)
     dims = (8, 12, 6)
     kw = dict(force=(1e-5, 0, 0), collision=1, **W.channel_bc())
@@ -318,6 +321,20 @@ def test_init_equilibrium_and_run_to_residual(L):
     p = _orc_problem(dims, 0.8, None, kw)
     ref = oracle.init_equilibrium(p, rho.astype(np.float64), u.astype(np.float64))
     assert np.abs(_state(L, ctx, dims) - ref).max() <= 1e-9
+    # random velocity noise on an even periodic grid excites a non-decaying
+    # period-2 (staggered) mode of the discrete scheme: the oracle shows the
+    # same one-step residual, which therefore never falls
+    L.lbm_step(ctx, 500)
+    f = oracle.run(p, ref, 499)
+    r_ref = oracle.residual(p, f, oracle.step(p, f))
+    assert abs(L.lbm_residual(ctx) - r_ref) <= 1e-4 * r_ref
+    ctx.destroy()
+
+
+def test_run_to_residual_from_smooth_start(L):
+    dims = (8, 12, 6)
+    kw = dict(force=(1e-5, 0, 0), collision=1, **W.channel_bc())
+    ctx = L.lbm_create(dims, (8, 6, 6), 0.8, None, _gpu_params(L, **kw))
     steps, r = L.lbm_run_to_residual(ctx, 1e-6, 10, 20000)
     assert r < 1e-6 and steps % 10 == 0
     _, uu = L.lbm_macroscopic(ctx)
