@@ -245,6 +245,31 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *user);
  * opp int[19].  Host only, needs no GPU. */
 int lbm_directions(int *e, double *w, int *opp);
 
+/*
+ * lbm_invariants_noalloc - the FP64 sums of lbm_invariants for callers that
+ * cannot allocate device memory.  The paper has no counterpart; it exists for
+ * callers that run where cudaMalloc is not allowed or not safe (while another
+ * component captures a CUDA graph, inside a framework's allocator callback,
+ * or when a caching allocator already holds all device memory).
+ *   f       : device, float[19*n_cells], shifted PDFs, direction-major
+ *             (f[q*n_cells + c]); caller-owned.
+ *   flags   : device, uint8[n_cells] (LBM_FLUID = 0 is summed), or NULL = all fluid.
+ *   rho0, force : as in lbm_params; mass = sum (rho0 + sum f~),
+ *             momentum = sum (sum e f~ - F/2) over fluid cells.
+ *   out     : device-accessible double[5] = {mass, mom_x, mom_y, mom_z, nonfinite}.
+ *   stream  : cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Allocates nothing: partial sums go to a fixed file-scope device array of
+ * 2 MiB (32768 partials of 2048 cells), which every GPU that loads the
+ * library holds until the process exits.  n_cells above 67108864 returns
+ * LBM_EINVAL.  The first call on a device looks the array up with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call reuses the same array, so calls that overlap on the GPU (other
+ * streams, other threads) race; every slot a call reads it writes first.
+ * Asynchronous: out is valid once the stream has reached the call.
+ */
+int lbm_invariants_noalloc(const float *f, const uint8_t *flags, long long n_cells, double rho0,
+                           const double force[3], double *out, void *stream);
+
 /* Message of the last failure on ctx, or of the calling thread's last failed
  * lbm_create / lbm_batch_create when ctx is NULL.  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);

@@ -697,6 +697,9 @@ std::string tune_key(const lbm_ctx *c)
 
 }  // namespace
 
+// Message reported by lbm_last_error(NULL) for entry points without a context.
+void lbm::set_global_error(const char *msg) { g_create_error = msg ? msg : ""; }
+
 // =================================================================== C ABI
 extern "C" {
 

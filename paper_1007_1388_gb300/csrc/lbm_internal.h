@@ -87,6 +87,9 @@ struct XDesc {
     int ncell;             // lx*ly*lz
 };
 
+// Sets the calling thread's message for lbm_last_error(NULL).
+void set_global_error(const char *msg);
+
 // Reduction outputs per tile / instance.
 enum { R_DRHO = 0, R_JX, R_JY, R_JZ, R_NFLUID, R_NONFINITE, R_DU2, R_U2, R_K };
 

@@ -98,6 +98,7 @@ SIGNATURES = {
     "lbm_autotune": ([_vp, ctypes.c_char_p, _P(ctypes.c_int)], _i),
     "lbm_set_allocator": ([ALLOC_FN, FREE_FN, _vp], _i),
     "lbm_directions": ([_P(ctypes.c_int), _P(_d), _P(ctypes.c_int)], _i),
+    "lbm_invariants_noalloc": ([_vp, _vp, _ll, _d, _P(_d), _vp, _vp], _i),
     "lbm_last_error": ([_vp], ctypes.c_char_p),
     "lbm_version": ([], ctypes.c_char_p),
 }
@@ -376,6 +377,21 @@ def lbm_directions():
     o = (ctypes.c_int * Q)()
     _check(lib().lbm_directions(e, w, o))
     return np.array(e[:]).reshape(Q, 3), np.array(w[:]), np.array(o[:])
+
+
+def lbm_invariants_noalloc(f, flags, n_cells: int, rho0: float, force, out, stream=None):
+    """Allocation-free FP64 invariants of a caller-owned device PDF array.
+
+    f: CUDA float32 tensor of 19*n_cells (direction-major); flags: CUDA uint8
+    tensor of n_cells or None; out: CUDA float64 tensor of 5; stream: a
+    torch.cuda.Stream (default: the current stream).  Enqueues only.
+    """
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    F = (ctypes.c_double * 3)(*[float(v) for v in force])
+    _check(lib().lbm_invariants_noalloc(_ptr(f), _ptr(flags), int(n_cells), float(rho0), F,
+                                        _ptr(out), s.cuda_stream))
 
 
 def lbm_last_error(ctx: Ctx | None = None) -> str:
