@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "lbm.h"
 #include "lbm_internal.h"
 
@@ -66,6 +68,14 @@ struct lbm_ctx {
     int tile[3] = {64, 4, 4};
     int grid = 0;  // 0 = one CTA per tile
     int minb = 3;  // register budget of the sweep (resident CTAs per SM)
+    // kernel choice and the TMA sweep's launch state
+    int kernel = LBM_KERNEL_REGISTER;
+    TmaMaps maps{};
+    int tma_zchunk = 8;
+    int tma_grid = 0;
+    int exchange_mode = LBM_EXCHANGE_FUSED;
+    bool ghosts_stale = false;  // state set from outside: refresh ghost layers before the next sweep
+    int *d_err = nullptr;       // device error word written by timed-out waits
     // device
     Allocator alloc;
     std::vector<DevMem> owned;
@@ -250,6 +260,8 @@ int validate_params(const lbm_params &p)
     for (int f = 0; f < 6; ++f)
         if (p.face_bc[f] != LBM_NOSLIP && p.face_bc[f] != LBM_MOVING) return 0;
     double s = p.storage_scale;
+    if (p.exchange_mode != LBM_EXCHANGE_FUSED && p.exchange_mode != LBM_EXCHANGE_KERNEL) return 0;
+    if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_TMA) return 0;
     int e2 = 0;
     if (!(s > 0) || !std::isfinite(s) || std::frexp(s, &e2) != 0.5) return 0;  // power of two
     return 1;
@@ -330,6 +342,85 @@ int set_tiles(lbm_ctx *c, const int t[3], int grid)
     return LBM_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, fetched through the runtime (no
+// link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+int encode_map(lbm_ctx *c, CUtensorMap *m, CUtensorMapDataType dt, void *base, int esize,
+               const BlockGeom &b, long long planes, int boxw, int boxh)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    cuuint64_t dims[4] = {cuuint64_t(b.px), cuuint64_t(b.py), cuuint64_t(b.nz + 2), cuuint64_t(planes)};
+    cuuint64_t strides[3] = {cuuint64_t(b.px) * esize, cuuint64_t(b.px) * b.py * esize,
+                             cuuint64_t(b.G) * esize};
+    cuuint32_t box[4] = {cuuint32_t(boxw), cuuint32_t(boxh), 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+    return LBM_OK;
+}
+
+// Whether the TMA sweep applies: one Patch of equal Blocks, 32/64/128 cells
+// wide, a row count divisible by the strip height, FP32/F16S/BF16S.
+bool tma_applicable(const lbm_ctx *c)
+{
+    if (c->ninst != 1 || c->storage == LBM_F64 || c->blocks.empty()) return false;
+    const BlockGeom &b0 = c->blocks[0];
+    if (b0.nx != 32 && b0.nx != 64 && b0.nx != 128) return false;
+    if (b0.ny % (256 / b0.nx) != 0) return false;
+    for (const BlockGeom &b : c->blocks)
+        if (b.nx != b0.nx || b.ny != b0.ny || b.nz != b0.nz) return false;
+    return true;
+}
+
+int setup_tma(lbm_ctx *c)
+{
+    const BlockGeom &b = c->blocks[0];
+    const int tx = b.nx, ty = 256 / b.nx, A = 16 / c->elem;
+    const CUtensorMapDataType dt = c->storage == LBM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : c->storage == LBM_F16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const long long planes = (long long)Q * (long long)c->blocks.size();
+    // every Block has the same geometry, so Block k's plane q is plane 19k+q
+    for (size_t k = 0; k < c->blocks.size(); ++k)
+        if (c->blocks[k].pdf_base != (long long)k * Q * b.G)
+            return fail(c, LBM_EINVAL, "TMA sweep: Blocks are not laid out uniformly");
+    int rc;
+    for (int par = 0; par < 2; ++par) {
+        if ((rc = encode_map(c, &c->maps.box_a[par], dt, c->buf[par], c->elem, b, planes, tx, ty))) return rc;
+        if ((rc = encode_map(c, &c->maps.box_b[par], dt, c->buf[par], c->elem, b, planes, tx + A, ty))) return rc;
+        if ((rc = encode_map(c, &c->maps.halo[par], dt, c->buf[par], c->elem, b, planes, A, ty))) return rc;
+    }
+    if ((rc = encode_map(c, &c->maps.flags, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->d_flags, 1, b,
+                         (long long)c->blocks.size(), tx, ty)))
+        return rc;
+    int occ = 0, dev = 0, sms = 1;
+    CK(tma_occupancy(c->storage, tx, c->p.collision, c->forced ? 1 : 0, &occ), "TMA occupancy");
+    if (occ < 1) return fail(c, LBM_ECUDA, "TMA sweep does not fit on an SM");
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    c->tma_grid = occ * sms;
+    c->kernel = LBM_KERNEL_TMA;
+    return LBM_OK;
+}
+
 int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
 {
     const lbm_params &p = c->p;
@@ -337,7 +428,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     c->storage = p.storage;
     c->elem = p.storage == LBM_F32 ? 4 : (p.storage == LBM_F64 ? 8 : 2);
     c->forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
-    const int align = 32 / c->elem;  // cells per 32-byte DRAM sector
+    c->exchange_mode = p.exchange_mode;
 
     if (p.stream) {
         c->stream = static_cast<cudaStream_t>(p.stream);
@@ -360,11 +451,12 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
             for (int by = 0; by < nb[1]; ++by)
                 for (int bx = 0; bx < nb[0]; ++bx) {
                     BlockGeom b{};
+                    b.xm_block = b.xp_block = -1;
                     b.nx = s.bdims[0];
                     b.ny = s.bdims[1];
                     b.nz = s.bdims[2];
-                    b.ox = align;
-                    b.px = round_up(b.ox + b.nx + 1, align);
+                    b.ox = OX;
+                    b.px = round_up(OX + b.nx + 1, 16);
                     b.py = b.ny + 2;
                     b.G = (long long)b.px * b.py * (b.nz + 2);
                     if ((long long)Q * b.G >= (1ll << 31))
@@ -424,12 +516,40 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                             if (!p.periodic[0]) continue;
                             nbx = (nbx + nb[0]) % nb[0];
                         }
-                        const BlockGeom &n = c->blocks[first_block + (bz * nb[1] + by) * nb[0] + nbx];
+                        const int nid = first_block + (bz * nb[1] + by) * nb[0] + nbx;
+                        const BlockGeom &n = c->blocks[nid];
                         const long long off = n.pdf_base - b.pdf_base - side * (long long)b.nx;
-                        if (side < 0)
+                        if (side < 0) {
                             b.xm_off = off;
-                        else
+                            b.xm_block = nid;
+                        } else {
                             b.xp_off = off;
+                            b.xp_block = nid;
+                        }
+                    }
+                    // fused ghost writes: faces -y,+y,-z,+z then edges
+                    // (-y,-z),(+y,-z),(-y,+z),(+y,+z)
+                    const int dyz[8][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1},
+                                           {-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
+                    const long long px = b.px, pxy = (long long)b.px * b.py;
+                    for (int k = 0; k < 8; ++k) {
+                        int ny_ = by + dyz[k][0], nz_ = bz + dyz[k][1];
+                        bool ok = true;
+                        if (ny_ < 0 || ny_ >= nb[1]) {
+                            if (!p.periodic[1]) ok = false;
+                            ny_ = (ny_ + nb[1]) % nb[1];
+                        }
+                        if (nz_ < 0 || nz_ >= nb[2]) {
+                            if (!p.periodic[2]) ok = false;
+                            nz_ = (nz_ + nb[2]) % nb[2];
+                        }
+                        if (!ok) continue;
+                        const BlockGeom &n = c->blocks[first_block + (nz_ * nb[1] + ny_) * nb[0] + bx];
+                        // our boundary cell seen from the neighbour lies one
+                        // Block length the other way
+                        b.push_off[k] = n.pdf_base - b.pdf_base - dyz[k][0] * b.ny * px -
+                                        dyz[k][1] * (long long)b.nz * pxy;
+                        b.push_mask |= 1 << k;
                     }
                 }
         // ---- ghost exchange plan: faces and edges with a neighbour block
@@ -511,6 +631,8 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
         c->storage == LBM_F64 ? make_consts<double>(c) : make_consts<float>(c);
     if ((rc = upload(c, reinterpret_cast<char **>(&c->d_consts), consts))) return rc;
     if ((rc = own(c, &c->d_red, sizeof(double) * R_K * c->ninst))) return rc;
+    if ((rc = own(c, &c->d_err, sizeof(int)))) return rc;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
 
     int t[3] = {p.tile[0], p.tile[1], p.tile[2]};
     if (t[0] <= 0 || t[1] <= 0 || t[2] <= 0) {
@@ -525,6 +647,12 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
         return fail(c, LBM_EINVAL, "tile %dx%d: threads along x must be a multiple of 32 and "
                     "tile[0]*tile[1] <= 256", t[0], t[1]);
     if ((rc = set_tiles(c, t, 0))) return rc;
+    if (p.kernel != LBM_KERNEL_REGISTER && tma_applicable(c)) {
+        if ((rc = setup_tma(c))) return rc;
+    } else if (p.kernel == LBM_KERNEL_TMA) {
+        return fail(c, LBM_EINVAL, "the TMA sweep needs one Patch of equal Blocks 32, 64 or 128 "
+                    "cells wide with rows divisible by 256/width, and F32/F16S/BF16S storage");
+    }
 
     // graph length: enough work per replay to hide launch overhead
     if (p.graph_steps < 0) {
@@ -590,12 +718,64 @@ cudaError_t enqueue_exchange(const lbm_ctx *c, int which)
     return launch_exchange(x, c->stream);
 }
 
-// One step from buffer `from` (exchange on it, sweep into the other).
+// Bound of every mbarrier wait of the TMA sweep, in SM clock cycles (about
+// one second at the GB300's 2 GHz boost clock).
+constexpr long long kWaitCycles = 2000000000ll;
+
+// The work step from buffer `from` into the other.  With the fused exchange
+// the sweep also writes the boundary PDFs into the neighbours' ghost layers.
+cudaError_t enqueue_sweep(const lbm_ctx *c, int from)
+{
+    SweepArgs a = sweep_args(c, from);
+    a.push = c->exchange_mode == LBM_EXCHANGE_FUSED ? 1 : 0;
+    if (c->kernel != LBM_KERNEL_TMA) return launch_sweep(a, c->stream);
+    const BlockGeom &b = c->blocks[0];
+    TmaSweepArgs t{};
+    t.a = a;
+    t.nx = b.nx;
+    t.ny = b.ny;
+    t.nz = b.nz;
+    t.px = b.px;
+    t.py = b.py;
+    t.ngy = b.ny / (256 / b.nx);
+    t.zchunk = c->tma_zchunk;
+    t.nzc = (b.nz + c->tma_zchunk - 1) / c->tma_zchunk;
+    t.nitems = (long long)c->blocks.size() * t.ngy * t.nzc;
+    t.parity = from;
+    t.drop_stage = (c->p.debug_flags & LBM_DEBUG_DROP_STAGE) ? 3 : -1;
+    t.wait_cycles = kWaitCycles;
+    t.err = c->d_err;
+    const int grid = int(std::min<long long>(t.nitems, c->tma_grid));
+    return launch_sweep_tma(t, c->maps, grid, c->stream);
+}
+
+bool exchange_each_step(const lbm_ctx *c)
+{
+    return c->exchange_mode == LBM_EXCHANGE_KERNEL && !c->xwork.empty();
+}
+
+// One step from buffer `from` (communication step, then the work step).
 cudaError_t enqueue_step(const lbm_ctx *c, int from)
 {
-    cudaError_t e = enqueue_exchange(c, from);
-    if (e != cudaSuccess) return e;
-    return launch_sweep(sweep_args(c, from), c->stream);
+    if (exchange_each_step(c)) {
+        cudaError_t e = enqueue_exchange(c, from);
+        if (e != cudaSuccess) return e;
+    }
+    return enqueue_sweep(c, from);
+}
+
+// Reads and clears the device error word (synchronises the stream).
+int check_device_error(lbm_ctx *c)
+{
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "error word");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (h == 0) return LBM_OK;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return fail(c, LBM_ETIMEOUT, "a bounded wait of the TMA sweep expired (%s); the state is undefined",
+                h == 1 ? "staged data never arrived" : h == 2 ? "a stage was never released"
+                                                                : "copies in flight at exit");
 }
 
 int ensure_event(lbm_ctx *c, size_t idx)
@@ -615,11 +795,11 @@ int direct_steps(lbm_ctx *c, int n)
             size_t base = c->ev_used;
             int rc = ensure_event(c, base + 2);
             if (rc) return rc;
-            const bool has_x = !c->xwork.empty();
+            const bool has_x = exchange_each_step(c);
             CK(cudaEventRecord(c->ev[base], c->stream), "cudaEventRecord");
-            CK(enqueue_exchange(c, c->cur), "exchange launch");
+            if (has_x) CK(enqueue_exchange(c, c->cur), "exchange launch");
             CK(cudaEventRecord(c->ev[base + 1], c->stream), "cudaEventRecord");
-            CK(launch_sweep(sweep_args(c, c->cur), c->stream), "sweep launch");
+            CK(enqueue_sweep(c, c->cur), "sweep launch");
             CK(cudaEventRecord(c->ev[base + 2], c->stream), "cudaEventRecord");
             c->ev_has_x.push_back(has_x ? 1 : 0);
             c->ev_used += 3;
@@ -659,6 +839,8 @@ int ensure_graph(lbm_ctx *c, int par)
 
 int reduce(lbm_ctx *c, bool with_prev, std::vector<double> &out)
 {
+    int rc0 = check_device_error(c);
+    if (rc0) return rc0;
     FieldArgs a = field_args(c);
     CK(launch_reduce(a, c->buf[c->cur], with_prev ? c->buf[c->cur ^ 1] : nullptr, c->d_partial,
                      c->d_inst_begin, c->ninst, c->d_red, c->stream),
@@ -803,6 +985,11 @@ int lbm_step(lbm_ctx *c, int n)
 {
     if (!c || n < 0) return fail(c, LBM_EINVAL, "lbm_step: bad arguments");
     if (n == 0) return LBM_OK;
+    if (c->ghosts_stale) {
+        // the state was set from outside: fill the ghost layers once
+        if (!c->xwork.empty()) CK(enqueue_exchange(c, c->cur), "exchange launch");
+        c->ghosts_stale = false;
+    }
     int rc;
     if (c->profiling || c->graph_steps == 0) {
         rc = direct_steps(c, n);
@@ -824,7 +1011,7 @@ int lbm_synchronize(lbm_ctx *c)
 {
     if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
     CK(cudaStreamSynchronize(c->stream), "lbm_synchronize");
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 int lbm_macroscopic_device(lbm_ctx *c, float *rho, float *u)
@@ -846,7 +1033,7 @@ int lbm_macroscopic(lbm_ctx *c, float *rho, float *u)
     CK(cudaMemcpyAsync(rho, dr, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream), "D2H rho");
     CK(cudaMemcpyAsync(u, du, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, c->stream), "D2H u");
     CK(cudaStreamSynchronize(c->stream), "lbm_macroscopic");
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 int lbm_get_pdfs(lbm_ctx *c, double *f)
@@ -859,7 +1046,7 @@ int lbm_get_pdfs(lbm_ctx *c, double *f)
        "get_pdfs launch");
     CK(cudaMemcpyAsync(f, t.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "D2H pdfs");
     CK(cudaStreamSynchronize(c->stream), "lbm_get_pdfs");
-    return LBM_OK;
+    return check_device_error(c);
 }
 
 int lbm_set_pdfs(lbm_ctx *c, const double *f)
@@ -873,6 +1060,7 @@ int lbm_set_pdfs(lbm_ctx *c, const double *f)
        "set_pdfs launch");
     CK(cudaStreamSynchronize(c->stream), "lbm_set_pdfs");
     c->have_prev = false;
+    c->ghosts_stale = true;
     return LBM_OK;
 }
 
@@ -881,6 +1069,7 @@ int lbm_init_equilibrium_device(lbm_ctx *c, const float *rho, const float *u)
     if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_init_equilibrium_device: NULL argument");
     CK(launch_init_equilibrium(field_args(c), c->buf[c->cur], rho, u, c->stream), "init launch");
     c->have_prev = false;
+    c->ghosts_stale = true;
     return LBM_OK;
 }
 
@@ -992,6 +1181,17 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info)
     info->device_bytes = c->device_bytes;
     for (int a = 0; a < 3; ++a) info->tile[a] = c->tile[a];
     info->tiles = (long long)c->tiles.size();
+    info->kernel = c->kernel;
+    info->exchange_mode = c->exchange_mode;
+    info->stages = c->kernel == LBM_KERNEL_TMA ? tma_stages(c->storage) : 0;
+    info->sweep_ctas = c->kernel == LBM_KERNEL_TMA ? c->tma_grid
+                       : c->grid > 0                ? c->grid
+                                                    : int(c->tiles.size());
+    if (c->kernel == LBM_KERNEL_TMA) {
+        info->tile[0] = c->blocks[0].nx;
+        info->tile[1] = 256 / c->blocks[0].nx;
+        info->tile[2] = c->tma_zchunk;
+    }
     return LBM_OK;
 }
 
@@ -1031,8 +1231,12 @@ int lbm_profile_read(lbm_ctx *c, lbm_profile *out)
 int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
 {
     if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
-    const std::string key = tune_key(c);
-    int best[5] = {c->tile[0], c->tile[1], c->tile[2], c->grid, c->minb};
+    const bool tma_ok = c->kernel == LBM_KERNEL_TMA || (c->tma_grid > 0);
+    const std::string key = tune_key(c) + (tma_ok ? "|tma" : "");
+    // configuration: kind (0 register sweep, 1 TMA sweep), tx, ty, tz, grid, minb, zchunk
+    using Cfg = std::array<int, 7>;
+    Cfg best = {c->kernel == LBM_KERNEL_TMA ? 1 : 0, c->tile[0], c->tile[1], c->tile[2],
+                c->grid, c->minb, c->tma_zchunk};
     bool cached = false;
     if (cache_path) {
         std::ifstream in(cache_path);
@@ -1040,16 +1244,25 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         const std::string needle = "\"key\": \"" + key + "\"";
         while (std::getline(in, line)) {
             if (line.find(needle) == std::string::npos) continue;
-            size_t t = line.find("\"tile\": [");
-            int v[5];
+            size_t t = line.find("\"cfg\": [");
+            Cfg v;
             if (t != std::string::npos &&
-                std::sscanf(line.c_str() + t, "\"tile\": [%d, %d, %d, %d, %d]", &v[0], &v[1], &v[2],
-                            &v[3], &v[4]) == 5) {
-                std::memcpy(best, v, sizeof v);
+                std::sscanf(line.c_str() + t, "\"cfg\": [%d, %d, %d, %d, %d, %d, %d]", &v[0], &v[1],
+                            &v[2], &v[3], &v[4], &v[5], &v[6]) == 7) {
+                best = v;
                 cached = true;
             }
         }
     }
+    auto apply = [&](const Cfg &cd) -> int {
+        int t[3] = {cd[1], cd[2], cd[3]};
+        int rc = set_tiles(c, t, cd[4]);
+        if (rc) return rc;
+        c->minb = cd[5];
+        c->tma_zchunk = cd[6];
+        c->kernel = cd[0] ? LBM_KERNEL_TMA : LBM_KERNEL_REGISTER;
+        return LBM_OK;
+    };
     if (!cached) {
         const char *ev = std::getenv("LBM_AUTOTUNE_VERBOSE");
         const bool verbose = ev && ev[0] == '1';
@@ -1058,63 +1271,60 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        std::vector<std::array<int, 5>> cand;
+        std::vector<Cfg> cand;
+        const int zc0 = c->tma_zchunk;
+        if (tma_ok)
+            for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, c->tile[0], c->tile[1], c->tile[2], c->grid, c->minb, zc});
         for (int mb : {3, 4})
             for (int tx : {32, 64, 128, 256}) {
                 if (tx > std::max(32, round_up(maxnx, 32))) continue;
                 for (int th : {128, 256}) {
                     if (th < tx) continue;
-                    for (int tz : {1, 2, 4, 8, 16}) cand.push_back({tx, th / tx, tz, 0, mb});
+                    for (int tz : {1, 2, 4, 8, 16}) cand.push_back({0, tx, th / tx, tz, 0, mb, zc0});
                 }
             }
         // persistent variants of the default tile
-        for (int m : {4, 8, 16}) cand.push_back({c->tile[0], c->tile[1], c->tile[2], m * sms, c->minb});
+        for (int m : {4, 8, 16}) cand.push_back({0, c->tile[0], c->tile[1], c->tile[2], m * sms, c->minb, zc0});
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");
         float best_ms = 1e30f;
         const int reps = 5;
-        for (auto &cd : cand) {
-            int t[3] = {cd[0], cd[1], cd[2]};
-            int rc = set_tiles(c, t, cd[3] ? int(std::min<long long>(cd[3], 1ll << 30)) : 0);
+        for (const Cfg &cd : cand) {
+            int rc = apply(cd);
             if (rc) return rc;
-            c->minb = cd[4];
-            SweepArgs a = sweep_args(c, c->cur);
-            CK(launch_sweep(a, c->stream), "tune");
+            CK(enqueue_sweep(c, c->cur), "tune");
             CK(cudaEventRecord(e0, c->stream), "event");
-            for (int r = 0; r < reps; ++r) CK(launch_sweep(a, c->stream), "tune");
+            for (int r = 0; r < reps; ++r) CK(enqueue_sweep(c, c->cur), "tune");
             CK(cudaEventRecord(e1, c->stream), "event");
             CK(cudaEventSynchronize(e1), "tune sync");
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
             if (verbose)
-                std::fprintf(stderr, "lbm_autotune: tile %d %d %d grid %d minb %d: %.4f ms/sweep\n",
-                             cd[0], cd[1], cd[2], cd[3], cd[4], ms / reps);
+                std::fprintf(stderr,
+                             "lbm_autotune: %s tile %d %d %d grid %d minb %d zchunk %d: %.4f ms/sweep\n",
+                             cd[0] ? "tma" : "reg", cd[1], cd[2], cd[3], cd[4], cd[5], cd[6], ms / reps);
             if (ms < best_ms) {
                 best_ms = ms;
-                best[0] = cd[0];
-                best[1] = cd[1];
-                best[2] = cd[2];
-                best[3] = cd[3];
-                best[4] = cd[4];
+                best = cd;
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        int rc = check_device_error(c);
+        if (rc) return rc;
         if (cache_path) {
             std::ofstream o(cache_path, std::ios::app);
-            o << "{\"key\": \"" << key << "\", \"tile\": [" << best[0] << ", " << best[1] << ", "
-              << best[2] << ", " << best[3] << ", " << best[4] << "], \"ms_per_sweep\": "
-              << best_ms / reps << "}\n";
+            o << "{\"key\": \"" << key << "\", \"cfg\": [" << best[0];
+            for (int k = 1; k < 7; ++k) o << ", " << best[k];
+            o << "], \"ms_per_sweep\": " << best_ms / reps << "}\n";
         }
     }
-    int t[3] = {best[0], best[1], best[2]};
-    int rc = set_tiles(c, t, best[3]);
+    int rc = apply(best);
     if (rc) return rc;
-    c->minb = best[4];
     c->have_prev = false;  // the scratch buffer was overwritten
     if (best_out)
-        for (int a = 0; a < 3; ++a) best_out[a] = best[a];
+        for (int a = 0; a < 3; ++a) best_out[a] = best[1 + a];
     CK(cudaStreamSynchronize(c->stream), "autotune");
     return LBM_OK;
 }

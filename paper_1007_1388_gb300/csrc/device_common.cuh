@@ -166,4 +166,29 @@ __device__ __forceinline__ void collide(T (&f)[Q], const Coll<T> &P)
     }
 }
 
+// Fused ghost-layer write (the communication step folded into the work step):
+// a cell on a y or z face of its Block also stores each PDF that leaves the
+// Block through that face into the ghost cell of the neighbour that pulls it
+// in the next step (5 PDFs per face cell, 1 per yz-edge cell).
+template <typename Tr, typename T>
+__device__ __forceinline__ void push_ghosts(typename Tr::S *__restrict__ dst, const BlockGeom &b,
+                                            int y, int z, int c, int G, const T (&f)[Q])
+{
+    const int m = b.push_mask;
+    const bool ylo = y == 0, yhi = y == b.ny - 1, zlo = z == 0, zhi = z == b.nz - 1;
+    if (!m || !(ylo || yhi || zlo || zhi)) return;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int o = q * G + c;
+        if (ey(q) < 0 && ylo && (m & 1)) Tr::st(dst + b.push_off[0] + o, f[q]);
+        if (ey(q) > 0 && yhi && (m & 2)) Tr::st(dst + b.push_off[1] + o, f[q]);
+        if (ez(q) < 0 && zlo && (m & 4)) Tr::st(dst + b.push_off[2] + o, f[q]);
+        if (ez(q) > 0 && zhi && (m & 8)) Tr::st(dst + b.push_off[3] + o, f[q]);
+        if (ey(q) < 0 && ez(q) < 0 && ylo && zlo && (m & 16)) Tr::st(dst + b.push_off[4] + o, f[q]);
+        if (ey(q) > 0 && ez(q) < 0 && yhi && zlo && (m & 32)) Tr::st(dst + b.push_off[5] + o, f[q]);
+        if (ey(q) < 0 && ez(q) > 0 && ylo && zhi && (m & 64)) Tr::st(dst + b.push_off[6] + o, f[q]);
+        if (ey(q) > 0 && ez(q) > 0 && yhi && zhi && (m & 128)) Tr::st(dst + b.push_off[7] + o, f[q]);
+    }
+}
+
 }  // namespace lbm

@@ -399,6 +399,38 @@ cudaError_t launch_reduce(const FieldArgs &a, const void *cur, const void *prev,
     return cudaGetLastError();
 }
 
+// TMA sweep dispatch (kernels live in sweep_tma_*.cu).
+template <int ST>
+cudaError_t launch_sweep_tma_st(const TmaSweepArgs &, const TmaMaps &, int, cudaStream_t, int *);
+
+cudaError_t launch_sweep_tma(const TmaSweepArgs &a, const TmaMaps &maps, int grid, cudaStream_t s)
+{
+    switch (a.a.storage) {
+    case 0: return launch_sweep_tma_st<0>(a, maps, grid, s, nullptr);
+    case 1: return launch_sweep_tma_st<1>(a, maps, grid, s, nullptr);
+    case 2: return launch_sweep_tma_st<2>(a, maps, grid, s, nullptr);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t tma_occupancy(int storage, int tx, int collision, int forced, int *ctas_per_sm)
+{
+    TmaSweepArgs a{};
+    a.a.storage = storage;
+    a.a.collision = collision;
+    a.a.forced = forced;
+    a.nx = tx;
+    TmaMaps maps{};
+    switch (storage) {
+    case 0: return launch_sweep_tma_st<0>(a, maps, 0, nullptr, ctas_per_sm);
+    case 1: return launch_sweep_tma_st<1>(a, maps, 0, nullptr, ctas_per_sm);
+    case 2: return launch_sweep_tma_st<2>(a, maps, 0, nullptr, ctas_per_sm);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+int tma_stages(int storage) { return storage == 0 ? 4 : 5; }
+
 // Sweep dispatch over the storage formats (kernels live in sweep_*.cu).
 template <int ST> cudaError_t launch_sweep_st(const SweepArgs &, cudaStream_t);
 

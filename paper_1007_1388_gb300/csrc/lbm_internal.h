@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (types only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -29,10 +30,15 @@ enum : uint8_t {
     F_NEAR = 4,   // fluid cell with at least one wall / solid neighbour
 };
 
+// Stored x index of the first interior cell of every row: 16 cells, so that
+// interior rows start on a 32-byte DRAM sector for every PDF type and the
+// one-byte flag rows start 16-byte aligned (a TMA requirement).
+constexpr int OX = 16;
+
 // One Block (or one batch instance) in device memory.  The Block stores
-// (nx+2)(ny+2)(nz+2) logical cells with x padded: row pitch px, the first
-// interior cell of a row at x index ox (so interior rows start on a 32-byte
-// DRAM sector), ghost cells at ox-1 and ox+nx.  PDF plane q of the Block
+// (nx+2)(ny+2)(nz+2) logical cells with x padded: row pitch px (a multiple of
+// 16 cells), the first interior cell of a row at x index ox = OX, ghost cells
+// at ox-1 and ox+nx.  PDF plane q of the Block
 // lives at buf + pdf_base + q*G, flag byte of cell c at flags + cell_base + c.
 //
 // Across x faces the sweep reads the neighbouring Block's boundary column
@@ -45,6 +51,13 @@ struct BlockGeom {
     long long cell_base;  // cells (flags)
     long long G;          // cells per plane = px*py*pz
     long long xm_off, xp_off;
+    // Fused ghost writes: element offset from this Block's stored cell to the
+    // ghost cell of the neighbour that pulls it, for the -y, +y, -z, +z faces
+    // and the (-y,-z), (+y,-z), (-y,+z), (+y,+z) edges; bit k of push_mask is
+    // set when neighbour k exists.
+    long long push_off[8];
+    int push_mask;
+    int xm_block, xp_block;  // -x / +x neighbour Block, -1 where the face is a wall
     int nx, ny, nz;       // interior cells
     int px, py;           // padded row pitch (cells), rows per plane (ny+2)
     int ox;               // x index of the first interior cell
@@ -108,7 +121,34 @@ struct SweepArgs {
     int storage;              // LBM_F32 .. LBM_F64
     int grid;                 // CTAs to launch (<= ntiles; persistent loop when smaller)
     int minb;                 // register budget: 3 or 4 resident 256-thread CTAs per SM
+    int push;                 // 1: write boundary PDFs into the neighbours' ghost layers
 };
+
+// TMA-staged sweep over a Patch whose Blocks all have nx = TX (32..256).
+struct TmaSweepArgs {
+    SweepArgs a;
+    int nx, ny, nz;           // Block interior size (uniform)
+    int px, py;               // stored pitch (uniform)
+    int ngy;                  // row groups of TY rows per Block
+    int zchunk, nzc;          // z slices per work item, work items along z per Block
+    long long nitems;         // Blocks * ngy * nzc
+    int parity;               // which tensor maps describe src
+    int drop_stage;           // failure-path test: skip this stage's loads (-1 = none)
+    long long wait_cycles;    // bound of every mbarrier wait
+    int *err;                 // device error word (set on a timed-out wait)
+};
+// Tensor maps of the TMA sweep: the PDF buffers viewed as a 4-D tensor
+// (x, y, z, 19 * Block + q), and the flag array as (x, y, z, Block).
+struct TmaMaps {
+    CUtensorMap box_a[2];  // per buffer: box {TX, TY, 1, 1} for directions with e_x = 0
+    CUtensorMap box_b[2];  // {TX + A, TY, 1, 1} for e_x = +-1 (A = 16 bytes of elements)
+    CUtensorMap halo[2];   // {A, TY, 1, 1}: boundary columns of the x-neighbour Blocks
+    CUtensorMap flags;     // uint8 {TX, TY, 1, 1}
+};
+// Returns cudaErrorNotSupported when the Block width has no instantiation.
+cudaError_t launch_sweep_tma(const TmaSweepArgs &a, const TmaMaps &maps, int grid, cudaStream_t s);
+int tma_stages(int storage);
+cudaError_t tma_occupancy(int storage, int tx, int collision, int forced, int *ctas_per_sm);
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
 
 // Exchange CTA work list: CTA k copies items [first, first + blockDim) of

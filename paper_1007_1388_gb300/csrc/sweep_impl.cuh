@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
             collide<T, COLL, FORCE>(f, P);
 #pragma unroll
             for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
+            if (a.push) push_ghosts<Tr>(dst, b, y, z, c, G, f);
         }
     }
 }

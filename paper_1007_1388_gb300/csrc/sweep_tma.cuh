@@ -1,0 +1,347 @@
+// TMA-staged D3Q19 sweep for Patches whose Blocks all have nx = TX cells
+// (TX = 32, 64 or 128).
+//
+// The register sweep is latency-bound: every pulled PDF in flight holds a
+// register, so the register file caps the bytes in flight per SM.  Here one
+// producer warp streams, per z slice of a TY-row strip of a Block, 19 boxes
+// (one per direction, shifted by -e_q) with cp.async.bulk.tensor into a ring
+// of shared-memory stages, plus the x-halo columns from the neighbouring
+// Blocks (direct reads across x faces, as in the register sweep) and the flag
+// row; eight consumer warps read one cell each from shared memory, apply
+// bounce-back, collide (Eq. (1)) and store with coalesced global stores.
+// Stages are handed over with mbarriers (full: transaction bytes landed;
+// empty: all consumer warps have read the stage).  Every wait is bounded by
+// a clock limit; a wait that expires writes an error word and the CTA leaves
+// after waiting (again bounded) for its own copies in flight.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of the given parity; false once `limit` SM clock
+// cycles have passed without it completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            int c3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared-memory layout of one stage: the 19 direction boxes (e_x = 0:
+// TX x TY elements; e_x = +-1: (TX + A) x TY), 10 x-halo boxes (A x TY;
+// slots 0..4 for the e_x = +1 directions 1,7,9,11,13 from the -x neighbour,
+// 5..9 for e_x = -1 directions 2,8,10,12,14 from the +x neighbour) and the
+// flag box (TX x TY bytes), each on a 128-byte boundary.
+template <int ST, int TX>
+struct TmaLayout {
+    using S = typename Traits<ST>::S;
+    static constexpr int E = int(sizeof(S));
+    static constexpr int A = 16 / E;
+    static constexpr int TY = 256 / TX;
+    static constexpr int BOXA = TX * TY * E;
+    static constexpr int BOXB = (TX + A) * TY * E;
+    static constexpr int HALO = A * TY * E;
+    static constexpr int FLAG = TX * TY;
+    __host__ __device__ static constexpr int r128(int v) { return (v + 127) / 128 * 128; }
+    static constexpr int RA = r128(BOXA), RB = r128(BOXB), RH = r128(HALO), RF = r128(FLAG);
+    __host__ __device__ static constexpr int box_off(int q)
+    {
+        int o = 0;
+        for (int k = 0; k < q; ++k) o += ex(k) == 0 ? RA : RB;
+        return o;
+    }
+    __host__ __device__ static constexpr int halo_slot(int q)
+    {
+        int k = 0;
+        for (int j = 1; j < q; ++j)
+            if (ex(j) == ex(q)) ++k;
+        return ex(q) > 0 ? k : 5 + k;
+    }
+    static constexpr int HALO0 = box_off(Q);
+    static constexpr int FLAGS = HALO0 + 10 * RH;
+    static constexpr int STAGE = FLAGS + RF;
+    static constexpr int STAGES = ST == 0 ? 4 : 5;
+    static constexpr int SMEM = STAGES * STAGE + 2 * STAGES * 8 + 128;
+    static constexpr int MINB = ST == 0 ? 2 : 3;  // resident CTAs the register budget allows
+    static constexpr uint32_t BYTES_CORE = 9 * BOXA + 10 * BOXB + FLAG;
+};
+
+template <int ST, int COLL, bool FORCE, int TX>
+__global__ void __launch_bounds__(288, TmaLayout<ST, TX>::MINB)
+    sweep_tma_kernel(const __grid_constant__ TmaSweepArgs ta, const __grid_constant__ TmaMaps maps)
+{
+    using Ly = TmaLayout<ST, TX>;
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    constexpr int TY = Ly::TY, A = Ly::A, STAGES = Ly::STAGES;
+    constexpr int NCW = 256 / 32;  // consumer warps
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * Ly::STAGE);
+    uint64_t *empty = full + STAGES;
+
+    const int tid = int(threadIdx.x);
+    const int warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    const SweepArgs &a = ta.a;
+    const long long lim = ta.wait_cycles;
+    const int per_blk = ta.ngy * ta.nzc;
+
+    if (warp == NCW) {
+        // ------------------------------------------------------ producer
+        const CUtensorMap *ma = &maps.box_a[ta.parity];
+        const CUtensorMap *mb = &maps.box_b[ta.parity];
+        const CUtensorMap *mh = &maps.halo[ta.parity];
+        const CUtensorMap *mf = &maps.flags;
+        int s = 0;
+        uint32_t ph = 0;
+        long long iter = 0;
+        // stages whose copies may still be in flight, for the exit drain
+        bool pending[STAGES];
+        uint32_t pend_ph[STAGES];
+        for (int k = 0; k < STAGES; ++k) pending[k] = false;
+        bool ok = true;
+        for (long long it = blockIdx.x; it < ta.nitems && ok; it += gridDim.x) {
+            const int blk = int(it / per_blk);
+            const int rem = int(it - (long long)blk * per_blk);
+            const int zc = rem / ta.ngy, yg = rem - zc * ta.ngy;
+            const BlockGeom &b = a.blocks[blk];
+            const int y0 = yg * TY;
+            const int z0 = zc * ta.zchunk, z1 = min(z0 + ta.zchunk, ta.nz);
+            const int hm = b.xm_block, hp = b.xp_block;
+            const uint32_t bytes =
+                Ly::BYTES_CORE + (hm >= 0 ? 5u * Ly::HALO : 0u) + (hp >= 0 ? 5u * Ly::HALO : 0u);
+            for (int z = z0; z < z1; ++z) {
+                if (!mbar_wait(&empty[s], ph ^ 1u, lim)) {
+                    if (lane == 0) atomicCAS(ta.err, 0, 2);
+                    ok = false;
+                    break;
+                }
+                unsigned char *st = smem + s * Ly::STAGE;
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes);
+                __syncwarp();
+                const bool drop = iter == ta.drop_stage;
+                if (!drop) {
+                    if (lane < Q) {
+                        const int q = lane;
+                        const int exq = ex(q);
+                        const int xs = exq > 0 ? OX - A : OX;
+                        tma_load_4d(st + Ly::box_off(q), exq == 0 ? ma : mb, xs, y0 + 1 - ey(q),
+                                    z + 1 - ez(q), blk * Q + q, &full[s]);
+                    } else if (lane < Q + 10) {
+                        // halo slot k: directions 1,7,9,11,13 (k < 5) / 2,8,10,12,14
+                        const int k = lane - Q;
+                        const int qq = k < 5 ? (k == 0 ? 1 : 5 + 2 * k) : (k == 5 ? 2 : 6 + 2 * (k - 5));
+                        const int nbk = k < 5 ? hm : hp;
+                        if (nbk >= 0)
+                            tma_load_4d(st + Ly::HALO0 + k * Ly::RH, mh, k < 5 ? OX + ta.nx - A : OX,
+                                        y0 + 1 - ey(qq), z + 1 - ez(qq), nbk * Q + qq, &full[s]);
+                    } else if (lane == Q + 10) {
+                        tma_load_4d(st + Ly::FLAGS, mf, OX, y0 + 1, z + 1, blk, &full[s]);
+                    }
+                }
+                pending[s] = !drop;
+                pend_ph[s] = ph;
+                ++iter;
+                if (++s == STAGES) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        // exit: every stage with copies issued must have landed before the
+        // CTA's shared memory goes away (bounded wait)
+        for (int k = 0; k < STAGES; ++k)
+            if (pending[k] && !mbar_wait(&full[k], pend_ph[k], lim) && lane == 0) atomicCAS(ta.err, 0, 3);
+        return;
+    }
+
+    // ------------------------------------------------------------ consumers
+    const CollideConsts<T> *__restrict__ consts = static_cast<const CollideConsts<T> *>(a.consts);
+    const int tx = tid % TX, ty = tid / TX;
+    const int px = ta.px, pxy = ta.px * ta.py;
+    int s = 0;
+    uint32_t ph = 0;
+    for (long long it = blockIdx.x; it < ta.nitems; it += gridDim.x) {
+        const int blk = int(it / per_blk);
+        const int rem = int(it - (long long)blk * per_blk);
+        const int zc = rem / ta.ngy, yg = rem - zc * ta.ngy;
+        const BlockGeom &b = a.blocks[blk];
+        const int y = yg * TY + ty;
+        const int z0 = zc * ta.zchunk, z1 = min(z0 + ta.zchunk, ta.nz);
+        const bool hm = b.xm_block >= 0, hp = b.xp_block >= 0;
+        const int G = int(b.G);
+        const CollideConsts<T> *cc = consts + b.inst;
+        const Coll<T> P = load_coll<T>(cc);
+        const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
+        S *__restrict__ dst = static_cast<S *>(a.dst) + b.pdf_base;
+        const uint8_t *__restrict__ fl = a.flags + b.cell_base;
+        for (int z = z0; z < z1; ++z) {
+            if (!mbar_wait(&full[s], ph, lim)) {
+                if (lane == 0) atomicCAS(ta.err, 0, 1);
+                return;
+            }
+            const unsigned char *st = smem + s * Ly::STAGE;
+            const uint8_t flag = st[Ly::FLAGS + ty * TX + tx];
+            T f[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const S *box = reinterpret_cast<const S *>(st + Ly::box_off(q));
+                S v;
+                if (ex(q) == 0) {
+                    v = box[ty * TX + tx];
+                } else if (ex(q) > 0) {
+                    v = box[ty * (TX + A) + tx - 1 + A];
+                    if (tx == 0 && hm)
+                        v = reinterpret_cast<const S *>(st + Ly::HALO0 + Ly::halo_slot(q) * Ly::RH)[ty * A + A - 1];
+                } else {
+                    v = box[ty * (TX + A) + tx + 1];
+                    if (tx == TX - 1 && hp)
+                        v = reinterpret_cast<const S *>(st + Ly::HALO0 + Ly::halo_slot(q) * Ly::RH)[ty * A];
+                }
+                f[q] = Tr::to_t(v);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == STAGES) {
+                s = 0;
+                ph ^= 1u;
+            }
+            if (flag & F_KIND) continue;  // solid cells are not updated
+            const int c = (z + 1) * pxy + (y + 1) * px + (OX + tx);
+            if (flag & F_NEAR) {
+                // half-way bounce-back where the source is a wall or solid
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const uint8_t nf = fl[c - (ex(q) + ey(q) * px + ez(q) * pxy)];
+                    if (nf & F_KIND) {
+                        T v = Tr::ld(src + (opp(q) * G + c));
+                        if ((nf & F_KIND) == F_MOVING) v += __ldg(&cc->bbw[q]);
+                        f[q] = v;
+                    }
+                }
+            }
+            collide<T, COLL, FORCE>(f, P);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
+            if (a.push) push_ghosts<Tr>(dst, b, y, z, c, G, f);
+        }
+    }
+}
+
+template <int ST, int COLL, bool FORCE, int TX>
+cudaError_t launch_tma_inst(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s)
+{
+    constexpr int smem = TmaLayout<ST, TX>::SMEM;
+    auto kern = sweep_tma_kernel<ST, COLL, FORCE, TX>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    kern<<<grid, 288, smem, s>>>(ta, maps);
+    return cudaGetLastError();
+}
+
+template <int ST, int COLL, bool FORCE, int TX>
+cudaError_t occupancy_tma_inst(int *n)
+{
+    constexpr int smem = TmaLayout<ST, TX>::SMEM;
+    auto kern = sweep_tma_kernel<ST, COLL, FORCE, TX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, 288, smem);
+}
+
+template <int ST>
+cudaError_t launch_sweep_tma_st(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s,
+                                int *occ)
+{
+    const int coll = ta.a.collision, forced = ta.a.forced;
+#define LBM_TMA_TX(TXV)                                                                              \
+    if (ta.nx == TXV) {                                                                             \
+        if (occ) {                                                                                  \
+            if (coll == 0)                                                                          \
+                return forced ? occupancy_tma_inst<ST, 0, true, TXV>(occ)                            \
+                              : occupancy_tma_inst<ST, 0, false, TXV>(occ);                          \
+            return forced ? occupancy_tma_inst<ST, 1, true, TXV>(occ)                                \
+                          : occupancy_tma_inst<ST, 1, false, TXV>(occ);                              \
+        }                                                                                           \
+        if (coll == 0)                                                                              \
+            return forced ? launch_tma_inst<ST, 0, true, TXV>(ta, maps, grid, s)                     \
+                          : launch_tma_inst<ST, 0, false, TXV>(ta, maps, grid, s);                   \
+        return forced ? launch_tma_inst<ST, 1, true, TXV>(ta, maps, grid, s)                         \
+                      : launch_tma_inst<ST, 1, false, TXV>(ta, maps, grid, s);                       \
+    }
+    LBM_TMA_TX(32)
+    LBM_TMA_TX(64)
+    LBM_TMA_TX(128)
+#undef LBM_TMA_TX
+    return cudaErrorNotSupported;
+}
+
+}  // namespace lbm
