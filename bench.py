@@ -193,7 +193,7 @@ def run_gpu(args):
     n, b = args.size, args.block
 
     def make(storage=L.LBM_F32, coll=L.LBM_BGK, **extra):
-        p = L.make_params(collision=coll, force=(FORCE, 0, 0), storage=storage,
+        p = L.make_params(collision=coll, force=(args.force, 0, 0), storage=storage,
                           **W.channel_bc(), **extra)
         return L.lbm_create((n, n, n), (b, b, b), TAU, None, p)
 
@@ -205,6 +205,8 @@ def run_gpu(args):
             main_kw["storage_scale"] = 256.0
     if args.trt:
         main_kw["coll"] = L.LBM_TRT
+    if args.kernel:
+        main_kw["kernel"] = {"auto": 0, "register": 1, "tma": 2}[args.kernel]
     ctx = make(**main_kw)
     if args.autotune:
         L.lbm_autotune(ctx, None)
@@ -360,6 +362,8 @@ def main():
     ap.add_argument("--storage", default="", help="f32 | f16s | bf16s | f64 (default f32)")
     ap.add_argument("--trt", action="store_true", help="TRT instead of BGK")
     ap.add_argument("--autotune", action="store_true", help="pick the sweep tile by timing")
+    ap.add_argument("--kernel", default="", help="auto | register | tma")
+    ap.add_argument("--force", type=float, default=FORCE, help="body force along x")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

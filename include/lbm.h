@@ -89,10 +89,6 @@ typedef struct {
     int tile[3];          /* sweep tile: threads along x, rows along y, cells per thread
                              along z; {0,0,0} = the library's default (or lbm_autotune) */
     int graph_steps;      /* steps per captured CUDA graph; 0 = automatic, -1 = no graphs */
-    int exchange_mode;    /* LBM_EXCHANGE_FUSED (default): the sweep writes each Block's
-                             boundary PDFs straight into its neighbours' ghost layers;
-                             LBM_EXCHANGE_KERNEL: a separate exchange launch per step
-                             (the pack/copy/unpack step of Sec. 4.4 as its own kernel) */
     int kernel;           /* LBM_KERNEL_AUTO (default): TMA-staged sweep where the Patch
                              allows it, else the register sweep; LBM_KERNEL_REGISTER;
                              LBM_KERNEL_TMA (LBM_EINVAL at create when not applicable) */
@@ -100,7 +96,6 @@ typedef struct {
                              load so its bounded waits expire (failure-path tests) */
 } lbm_params;
 
-enum { LBM_EXCHANGE_FUSED = 0, LBM_EXCHANGE_KERNEL = 1 };
 enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_REGISTER = 1, LBM_KERNEL_TMA = 2 };
 enum { LBM_DEBUG_DROP_STAGE = 1 };
 
@@ -223,7 +218,6 @@ typedef struct {
     int tile[3];              /* sweep tile in use */
     long long tiles;          /* sweep work items (CTAs) per step */
     int kernel;               /* LBM_KERNEL_REGISTER or LBM_KERNEL_TMA in use */
-    int exchange_mode;
     int sweep_ctas;           /* CTAs of one sweep launch */
     int stages;               /* pipeline depth of the TMA sweep (0 for the register sweep) */
 } lbm_info;

@@ -61,20 +61,17 @@ struct lbm_ctx {
     std::vector<BlockGeom> blocks;
     std::vector<Tile> tiles;
     std::vector<long long> inst_tile_begin;
-    std::vector<XDesc> xdesc;
-    std::vector<XWork> xwork;
+    std::vector<XSlab> xslabs;
     std::vector<long long> inst_out_base;
     long long cells = 0, fluid = 0, stored = 0, exchange_pdfs = 0;
     int tile[3] = {64, 4, 4};
     int grid = 0;  // 0 = one CTA per tile
-    int minb = 3;  // register budget of the sweep (resident CTAs per SM)
+    int minb = 2;  // register budget of the sweep (resident CTAs per SM)
     // kernel choice and the TMA sweep's launch state
     int kernel = LBM_KERNEL_REGISTER;
     TmaMaps maps{};
     int tma_zchunk = 8;
     int tma_grid = 0;
-    int exchange_mode = LBM_EXCHANGE_FUSED;
-    bool ghosts_stale = false;  // state set from outside: refresh ghost layers before the next sweep
     int *d_err = nullptr;       // device error word written by timed-out waits
     // device
     Allocator alloc;
@@ -83,8 +80,7 @@ struct lbm_ctx {
     uint8_t *d_flags = nullptr;
     BlockGeom *d_blocks = nullptr;
     Tile *d_tiles = nullptr;
-    XDesc *d_xdesc = nullptr;
-    XWork *d_xwork = nullptr;
+    XSlab *d_xslabs = nullptr;
     void *d_consts = nullptr;
     long long *d_inst_begin = nullptr;
     double *d_partial = nullptr;
@@ -205,6 +201,19 @@ int upload(lbm_ctx *c, T **dst, const std::vector<T> &v)
 
 int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
+// Cells per PDF plane: the stored cells padded so that the plane stride in
+// bytes is an odd multiple of `unit` bytes.  The 19 read and 19 write streams
+// of a sweep are one plane apart; a stride with a large power-of-two factor
+// lines them up on the same DRAM channels.
+long long plane_cells(long long cells, int elem)
+{
+    const long long unit = 256;
+    const long long per = std::max<long long>(unit / elem, 16);
+    long long k = (cells + per - 1) / per;
+    if ((k & 1) == 0) ++k;
+    return k * per;
+}
+
 // What lies at instance position (X,Y,Z): periodic axes wrap; beyond one
 // non-periodic face is that face's wall; beyond two or more (an edge or
 // corner of the wall shell) is a resting wall.
@@ -260,7 +269,6 @@ int validate_params(const lbm_params &p)
     for (int f = 0; f < 6; ++f)
         if (p.face_bc[f] != LBM_NOSLIP && p.face_bc[f] != LBM_MOVING) return 0;
     double s = p.storage_scale;
-    if (p.exchange_mode != LBM_EXCHANGE_FUSED && p.exchange_mode != LBM_EXCHANGE_KERNEL) return 0;
     if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_TMA) return 0;
     int e2 = 0;
     if (!(s > 0) || !std::isfinite(s) || std::frexp(s, &e2) != 0.5) return 0;  // power of two
@@ -286,14 +294,39 @@ std::vector<char> make_consts(const lbm_ctx *c)
         }
         cc.omega_p = T(wp);
         cc.omega_m = T(wm);
-        cc.cp = T(1.0 - 0.5 * wp);
-        cc.cm = T(1.0 - 0.5 * wm);
         for (int q = 0; q < Q; ++q) {
             const double eu = ex(q) * p.wall_u[0] + ey(q) * p.wall_u[1] + ez(q) * p.wall_u[2];
             cc.bbw[q] = T(s * 6.0 * wq(q) * p.rho0 * eu);
         }
         cc.inv_s = T(1.0 / s);
         cc.rho0 = T(p.rho0);
+        const double rho0s = s * p.rho0;
+        const double ap = (1.0 - 0.5 * wp) / wp, am = (1.0 - 0.5 * wm) / wm;
+        const double wc[2] = {1.0 / 18.0, 1.0 / 36.0};
+        cc.zero = T(0);
+        cc.nc15 = T(-1.5 * rho0s);
+        cc.c45 = T(4.5 * rho0s);
+        cc.c0a = T(wp / 3.0);
+        cc.c0b = T(1.0 - wp);
+        cc.hwp = T(0.5 * wp);
+        cc.hwm = T(0.5 * wm);
+        for (int a = 0; a < 3; ++a) {
+            const double Fs = s * p.force[a];
+            cc.Fs[a] = T(Fs);
+            cc.k9F[a] = T(9.0 * ap * Fs);
+            cc.nk3F[a] = T(-3.0 * ap * Fs);
+        }
+        for (int c2 = 0; c2 < 2; ++c2) {
+            cc.obw[c2] = T(wp * wc[c2]);
+            cc.oc3[c2] = T(wp * 3.0 * rho0s * wc[c2]);
+            cc.nwpw[c2] = T(-wp * wc[c2]);
+            cc.nwmc3[c2] = T(-wm * 3.0 * rho0s * wc[c2]);
+            for (int a = 0; a < 3; ++a) {
+                const double Fs = s * p.force[a];
+                cc.okF[c2][a] = T(wp * 3.0 * am * wc[c2] * Fs);
+                cc.nwmkF[c2][a] = T(-wm * 3.0 * am * wc[c2] * Fs);
+            }
+        }
         std::memcpy(raw.data() + sizeof(cc) * k, &cc, sizeof(cc));
     }
     return raw;
@@ -360,18 +393,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-int encode_map(lbm_ctx *c, CUtensorMap *m, CUtensorMapDataType dt, void *base, int esize,
-               const BlockGeom &b, long long planes, int boxw, int boxh)
+int encode_map(lbm_ctx *c, CUtensorMap *m, CUtensorMapDataType dt, void *base, int esize, int pitch,
+               long long plane, const BlockGeom &b, long long planes, int boxw, int boxh)
 {
     auto enc = tensor_map_encoder();
     if (!enc) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled is not available");
-    cuuint64_t dims[4] = {cuuint64_t(b.px), cuuint64_t(b.py), cuuint64_t(b.nz + 2), cuuint64_t(planes)};
-    cuuint64_t strides[3] = {cuuint64_t(b.px) * esize, cuuint64_t(b.px) * b.py * esize,
-                             cuuint64_t(b.G) * esize};
+    cuuint64_t dims[4] = {cuuint64_t(pitch), cuuint64_t(b.py), cuuint64_t(b.nz + 2), cuuint64_t(planes)};
+    cuuint64_t strides[3] = {cuuint64_t(pitch) * esize, cuuint64_t(pitch) * b.py * esize,
+                             cuuint64_t(plane) * esize};
     cuuint32_t box[4] = {cuuint32_t(boxw), cuuint32_t(boxh), 1, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(m, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(c, LBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
     return LBM_OK;
@@ -384,6 +417,7 @@ bool tma_applicable(const lbm_ctx *c)
     if (c->ninst != 1 || c->storage == LBM_F64 || c->blocks.empty()) return false;
     const BlockGeom &b0 = c->blocks[0];
     if (b0.nx != 32 && b0.nx != 64 && b0.nx != 128) return false;
+    if (b0.px != b0.nx) return false;
     if (b0.ny % (256 / b0.nx) != 0) return false;
     for (const BlockGeom &b : c->blocks)
         if (b.nx != b0.nx || b.ny != b0.ny || b.nz != b0.nz) return false;
@@ -403,12 +437,17 @@ int setup_tma(lbm_ctx *c)
         if (c->blocks[k].pdf_base != (long long)k * Q * b.G)
             return fail(c, LBM_EINVAL, "TMA sweep: Blocks are not laid out uniformly");
     int rc;
+    for (size_t k = 0; k < c->blocks.size(); ++k)
+        if (c->blocks[k].cell_base != (long long)k * b.Gf)
+            return fail(c, LBM_EINVAL, "TMA sweep: flag planes are not laid out uniformly");
     for (int par = 0; par < 2; ++par) {
-        if ((rc = encode_map(c, &c->maps.box_a[par], dt, c->buf[par], c->elem, b, planes, tx, ty))) return rc;
-        if ((rc = encode_map(c, &c->maps.box_b[par], dt, c->buf[par], c->elem, b, planes, tx + A, ty))) return rc;
-        if ((rc = encode_map(c, &c->maps.halo[par], dt, c->buf[par], c->elem, b, planes, A, ty))) return rc;
+        void *base = c->buf[par];
+        if ((rc = encode_map(c, &c->maps.box_a[par], dt, base, c->elem, b.px, b.G, b, planes, tx, ty))) return rc;
+        if ((rc = encode_map(c, &c->maps.box_b[par], dt, base, c->elem, b.px, b.G, b, planes, tx + A, ty)))
+            return rc;
+        if ((rc = encode_map(c, &c->maps.halo[par], dt, base, c->elem, b.px, b.G, b, planes, A, ty))) return rc;
     }
-    if ((rc = encode_map(c, &c->maps.flags, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->d_flags, 1, b,
+    if ((rc = encode_map(c, &c->maps.flags, CU_TENSOR_MAP_DATA_TYPE_UINT8, c->d_flags, 1, b.pxf, b.Gf, b,
                          (long long)c->blocks.size(), tx, ty)))
         return rc;
     int occ = 0, dev = 0, sms = 1;
@@ -428,7 +467,6 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     c->storage = p.storage;
     c->elem = p.storage == LBM_F32 ? 4 : (p.storage == LBM_F64 ? 8 : 2);
     c->forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
-    c->exchange_mode = p.exchange_mode;
 
     if (p.stream) {
         c->stream = static_cast<cudaStream_t>(p.stream);
@@ -455,10 +493,11 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                     b.nx = s.bdims[0];
                     b.ny = s.bdims[1];
                     b.nz = s.bdims[2];
-                    b.ox = OX;
-                    b.px = round_up(OX + b.nx + 1, 16);
+                    b.px = round_up(b.nx, 32 / c->elem);
+                    b.pxf = round_up(OXF + b.nx + 1, 16);
                     b.py = b.ny + 2;
-                    b.G = (long long)b.px * b.py * (b.nz + 2);
+                    b.G = plane_cells((long long)b.px * b.py * (b.nz + 2), c->elem);
+                    b.Gf = (long long)b.pxf * b.py * (b.nz + 2);
                     if ((long long)Q * b.G >= (1ll << 31))
                         return fail(c, LBM_EINVAL,
                                     "block of %dx%dx%d cells is too large for 32-bit plane "
@@ -475,29 +514,29 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                     b.NY = s.dims[1];
                     b.NZ = s.dims[2];
                     pdf_base += (long long)Q * b.G;
-                    cell_base += b.G;
+                    cell_base += b.Gf;
                     // flags of every stored cell (interior, ghost shell, padding)
-                    std::vector<uint8_t> f(size_t(b.G), F_NOSLIP);
+                    std::vector<uint8_t> f(size_t(b.Gf), F_NOSLIP);
                     for (int z = -1; z <= b.nz; ++z)
                         for (int y = -1; y <= b.ny; ++y)
                             for (int x = -1; x <= b.nx; ++x) {
                                 const long long cidx =
-                                    ((long long)(z + 1) * b.py + (y + 1)) * b.px + (x + b.ox);
+                                    ((long long)(z + 1) * b.py + (y + 1)) * b.pxf + (x + OXF);
                                 uint8_t v = classify(p, s.dims, s.flags, b.gx + x, b.gy + y, b.gz + z);
                                 if (v > F_MOVING)
                                     return fail(c, LBM_EINVAL, "flag value %d is not LBM_FLUID/NOSLIP/MOVING",
                                                 int(v));
                                 f[cidx] = v;
                             }
-                    const long long pxy = (long long)b.px * b.py;
+                    const long long pxy = (long long)b.pxf * b.py;
                     for (int z = 0; z < b.nz; ++z)
                         for (int y = 0; y < b.ny; ++y)
                             for (int x = 0; x < b.nx; ++x) {
-                                const long long cidx = (z + 1) * pxy + (long long)(y + 1) * b.px + (x + b.ox);
+                                const long long cidx = (z + 1) * pxy + (long long)(y + 1) * b.pxf + (x + OXF);
                                 if (f[cidx] != F_FLUID) continue;
                                 ++c->fluid;
                                 for (int q = 1; q < Q; ++q)
-                                    if (f[cidx - (ex(q) + ey(q) * (long long)b.px + ez(q) * pxy)] & F_KIND) {
+                                    if (f[cidx - (ex(q) + ey(q) * (long long)b.pxf + ez(q) * pxy)] & F_KIND) {
                                         f[cidx] |= F_NEAR;
                                         break;
                                     }
@@ -527,30 +566,6 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                             b.xp_block = nid;
                         }
                     }
-                    // fused ghost writes: faces -y,+y,-z,+z then edges
-                    // (-y,-z),(+y,-z),(-y,+z),(+y,+z)
-                    const int dyz[8][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1},
-                                           {-1, -1}, {1, -1}, {-1, 1}, {1, 1}};
-                    const long long px = b.px, pxy = (long long)b.px * b.py;
-                    for (int k = 0; k < 8; ++k) {
-                        int ny_ = by + dyz[k][0], nz_ = bz + dyz[k][1];
-                        bool ok = true;
-                        if (ny_ < 0 || ny_ >= nb[1]) {
-                            if (!p.periodic[1]) ok = false;
-                            ny_ = (ny_ + nb[1]) % nb[1];
-                        }
-                        if (nz_ < 0 || nz_ >= nb[2]) {
-                            if (!p.periodic[2]) ok = false;
-                            nz_ = (nz_ + nb[2]) % nb[2];
-                        }
-                        if (!ok) continue;
-                        const BlockGeom &n = c->blocks[first_block + (nz_ * nb[1] + ny_) * nb[0] + bx];
-                        // our boundary cell seen from the neighbour lies one
-                        // Block length the other way
-                        b.push_off[k] = n.pdf_base - b.pdf_base - dyz[k][0] * b.ny * px -
-                                        dyz[k][1] * (long long)b.nz * pxy;
-                        b.push_mask |= 1 << k;
-                    }
                 }
         // ---- ghost exchange plan: faces and edges with a neighbour block
         for (int bz = 0; bz < nb[2]; ++bz)
@@ -575,40 +590,41 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                     }
                                 }
                                 if (!ok) continue;
-                                XDesc d{};
-                                d.dst_block = me;
-                                d.src_block = first_block + (npos[2] * nb[1] + npos[1]) * nb[0] + npos[0];
-                                const int bd[3] = {s.bdims[0], s.bdims[1], s.bdims[2]};
-                                int start[3], len[3], shift[3];
-                                for (int a = 0; a < 3; ++a) {
-                                    start[a] = n[a] < 0 ? -1 : (n[a] > 0 ? bd[a] : 0);
-                                    len[a] = n[a] == 0 ? bd[a] : 1;
-                                    shift[a] = -n[a] * bd[a];
+                                // one slab per direction entering this Block
+                                // through the face / edge: the ghost rows of
+                                // `me`, copied from the neighbour's boundary rows
+                                const BlockGeom &bm = c->blocks[me];
+                                const BlockGeom &bs =
+                                    c->blocks[first_block + (npos[2] * nb[1] + npos[1]) * nb[0] + npos[0]];
+                                const int yg = n1 < 0 ? -1 : (n1 > 0 ? bm.ny : 0);
+                                const int zg = n2 < 0 ? -1 : (n2 > 0 ? bm.nz : 0);
+                                const int ys = yg - n1 * bm.ny, zs = zg - n2 * bm.nz;
+                                const long long pxy = (long long)bm.px * bm.py;
+                                XSlab sl{};
+                                sl.len = bm.px;  // whole rows (padding included) stay 32-byte aligned
+                                if (n1 != 0 && n2 == 0) {  // y face: one row per z
+                                    sl.rows = bm.nz;
+                                    sl.stride = pxy;
+                                } else if (n2 != 0 && n1 == 0) {  // z face: one row per y
+                                    sl.rows = bm.ny;
+                                    sl.stride = bm.px;
+                                } else {  // yz edge
+                                    sl.rows = 1;
+                                    sl.stride = 0;
                                 }
-                                d.x0 = start[0];
-                                d.y0 = start[1];
-                                d.z0 = start[2];
-                                d.lx = len[0];
-                                d.ly = len[1];
-                                d.lz = len[2];
-                                d.sx = shift[0];
-                                d.sy = shift[1];
-                                d.sz = shift[2];
-                                d.ncell = len[0] * len[1] * len[2];
-                                d.ndir = 0;
+                                const long long d0 = ((long long)(zg + 1) * bm.py + (yg + 1)) * bm.px;
+                                const long long s0 = ((long long)(zs + 1) * bm.py + (ys + 1)) * bm.px;
                                 for (int q = 1; q < Q; ++q) {
                                     const int e[3] = {ex(q), ey(q), ez(q)};
                                     bool into = true;
-                                    for (int a = 0; a < 3; ++a)
-                                        if (n[a] != 0 && e[a] != -n[a]) into = false;
-                                    if (into) d.dir[d.ndir++] = q;
+                                    for (int a2 = 0; a2 < 3; ++a2)
+                                        if (n[a2] != 0 && e[a2] != -n[a2]) into = false;
+                                    if (!into) continue;
+                                    sl.dst = bm.pdf_base + (long long)q * bm.G + d0;
+                                    sl.src = bs.pdf_base + (long long)q * bs.G + s0;
+                                    c->xslabs.push_back(sl);
+                                    c->exchange_pdfs += (long long)sl.rows * bm.nx;
                                 }
-                                const int id = int(c->xdesc.size());
-                                c->xdesc.push_back(d);
-                                const long long items = (long long)d.ncell * d.ndir;
-                                c->exchange_pdfs += items;
-                                for (long long f0 = 0; f0 < items; f0 += 256)
-                                    c->xwork.push_back({id, int(f0)});
                             }
                 }
         out_base += (long long)s.dims[0] * s.dims[1] * s.dims[2];
@@ -625,8 +641,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     CK(cudaMemsetAsync(c->buf[1], 0, buf_bytes, c->stream), "memset");
     if ((rc = upload(c, &c->d_flags, hflags))) return rc;
     if ((rc = upload(c, &c->d_blocks, c->blocks))) return rc;
-    if ((rc = upload(c, &c->d_xdesc, c->xdesc))) return rc;
-    if ((rc = upload(c, &c->d_xwork, c->xwork))) return rc;
+    if ((rc = upload(c, &c->d_xslabs, c->xslabs))) return rc;
     std::vector<char> consts =
         c->storage == LBM_F64 ? make_consts<double>(c) : make_consts<float>(c);
     if ((rc = upload(c, reinterpret_cast<char **>(&c->d_consts), consts))) return rc;
@@ -709,10 +724,8 @@ FieldArgs field_args(const lbm_ctx *c)
 cudaError_t enqueue_exchange(const lbm_ctx *c, int which)
 {
     ExchangeArgs x{};
-    x.desc = c->d_xdesc;
-    x.work = c->d_xwork;
-    x.nwork = int(c->xwork.size());
-    x.blocks = c->d_blocks;
+    x.slabs = c->d_xslabs;
+    x.nslabs = int(c->xslabs.size());
     x.buf = c->buf[which];
     x.elem_bytes = c->elem;
     return launch_exchange(x, c->stream);
@@ -722,12 +735,10 @@ cudaError_t enqueue_exchange(const lbm_ctx *c, int which)
 // one second at the GB300's 2 GHz boost clock).
 constexpr long long kWaitCycles = 2000000000ll;
 
-// The work step from buffer `from` into the other.  With the fused exchange
-// the sweep also writes the boundary PDFs into the neighbours' ghost layers.
+// The work step from buffer `from` into the other.
 cudaError_t enqueue_sweep(const lbm_ctx *c, int from)
 {
     SweepArgs a = sweep_args(c, from);
-    a.push = c->exchange_mode == LBM_EXCHANGE_FUSED ? 1 : 0;
     if (c->kernel != LBM_KERNEL_TMA) return launch_sweep(a, c->stream);
     const BlockGeom &b = c->blocks[0];
     TmaSweepArgs t{};
@@ -737,6 +748,7 @@ cudaError_t enqueue_sweep(const lbm_ctx *c, int from)
     t.nz = b.nz;
     t.px = b.px;
     t.py = b.py;
+    t.pxf = b.pxf;
     t.ngy = b.ny / (256 / b.nx);
     t.zchunk = c->tma_zchunk;
     t.nzc = (b.nz + c->tma_zchunk - 1) / c->tma_zchunk;
@@ -751,7 +763,7 @@ cudaError_t enqueue_sweep(const lbm_ctx *c, int from)
 
 bool exchange_each_step(const lbm_ctx *c)
 {
-    return c->exchange_mode == LBM_EXCHANGE_KERNEL && !c->xwork.empty();
+    return !c->xslabs.empty();
 }
 
 // One step from buffer `from` (communication step, then the work step).
@@ -985,11 +997,6 @@ int lbm_step(lbm_ctx *c, int n)
 {
     if (!c || n < 0) return fail(c, LBM_EINVAL, "lbm_step: bad arguments");
     if (n == 0) return LBM_OK;
-    if (c->ghosts_stale) {
-        // the state was set from outside: fill the ghost layers once
-        if (!c->xwork.empty()) CK(enqueue_exchange(c, c->cur), "exchange launch");
-        c->ghosts_stale = false;
-    }
     int rc;
     if (c->profiling || c->graph_steps == 0) {
         rc = direct_steps(c, n);
@@ -1060,7 +1067,6 @@ int lbm_set_pdfs(lbm_ctx *c, const double *f)
        "set_pdfs launch");
     CK(cudaStreamSynchronize(c->stream), "lbm_set_pdfs");
     c->have_prev = false;
-    c->ghosts_stale = true;
     return LBM_OK;
 }
 
@@ -1069,7 +1075,6 @@ int lbm_init_equilibrium_device(lbm_ctx *c, const float *rho, const float *u)
     if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_init_equilibrium_device: NULL argument");
     CK(launch_init_equilibrium(field_args(c), c->buf[c->cur], rho, u, c->stream), "init launch");
     c->have_prev = false;
-    c->ghosts_stale = true;
     return LBM_OK;
 }
 
@@ -1182,7 +1187,6 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info)
     for (int a = 0; a < 3; ++a) info->tile[a] = c->tile[a];
     info->tiles = (long long)c->tiles.size();
     info->kernel = c->kernel;
-    info->exchange_mode = c->exchange_mode;
     info->stages = c->kernel == LBM_KERNEL_TMA ? tma_stages(c->storage) : 0;
     info->sweep_ctas = c->kernel == LBM_KERNEL_TMA ? c->tma_grid
                        : c->grid > 0                ? c->grid
@@ -1275,7 +1279,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         const int zc0 = c->tma_zchunk;
         if (tma_ok)
             for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, c->tile[0], c->tile[1], c->tile[2], c->grid, c->minb, zc});
-        for (int mb : {3, 4})
+        for (int mb : {2, 3})
             for (int tx : {32, 64, 128, 256}) {
                 if (tx > std::max(32, round_up(maxnx, 32))) continue;
                 for (int th : {128, 256}) {

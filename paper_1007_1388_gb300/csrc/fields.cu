@@ -8,47 +8,33 @@
 namespace lbm {
 
 // ---------------------------------------------------------------- exchange
-// The communication step of a Sweep (Sec. 4, Sec. 4.4): every ghost cell of
-// a Block that some interior cell pulls from receives, for the directions
-// pointing into the Block, the post-collision PDF of the matching boundary
-// cell of the neighbouring Block (or of the Block itself across a periodic
-// boundary).  Faces carry 5 directions, edges 1; D3Q19 has no corner links.
-// The copy reads interior cells and writes ghost cells of the same buffer,
-// so it needs no second buffer and no ordering between work items.
-template <typename E>
+// The communication step of a Sweep (Sec. 4, Sec. 4.4): every ghost row of a
+// Block that some interior cell pulls from receives, for each direction
+// pointing into the Block, the post-collision PDFs of the matching boundary
+// row of the neighbouring Block (or of the Block itself across a periodic
+// boundary).  Only y and z faces and yz edges are copied: across x faces the
+// sweep reads the neighbour directly.  Each CTA copies one slab (one
+// direction plane of one face or edge) in 16-byte pieces; rows are 32-byte
+// aligned and padded to whole 32-byte units, so the copy is always vectorised.
+// It reads interior rows and writes ghost rows of the same buffer.
 __global__ void __launch_bounds__(256) exchange_kernel(const __grid_constant__ ExchangeArgs a)
 {
-    const XWork w = a.work[blockIdx.x];
-    const XDesc &d = a.desc[w.desc];
-    const int item = w.first + int(threadIdx.x);
-    if (item >= d.ncell * d.ndir) return;
-    const int k = item / d.ncell;
-    const int cell = item - k * d.ncell;
-    const int cx = cell % d.lx;
-    const int cy = (cell / d.lx) % d.ly;
-    const int cz = cell / (d.lx * d.ly);
-    const int x = d.x0 + cx, y = d.y0 + cy, z = d.z0 + cz;
-    const BlockGeom &bd = a.blocks[d.dst_block];
-    const BlockGeom &bs = a.blocks[d.src_block];
-    const int q = d.dir[k];
-    const long long di = bd.pdf_base + (long long)q * bd.G +
-                         ((long long)(z + 1) * bd.py + (y + 1)) * bd.px + (x + bd.ox);
-    const long long si = bs.pdf_base + (long long)q * bs.G +
-                         ((long long)(z + d.sz + 1) * bs.py + (y + d.sy + 1)) * bs.px +
-                         (x + d.sx + bs.ox);
-    E *buf = static_cast<E *>(a.buf);
-    buf[di] = buf[si];
+    const XSlab sl = a.slabs[blockIdx.x];
+    const int vrow = sl.len * a.elem_bytes / 16;  // 16-byte pieces per row
+    const int n = sl.rows * vrow;
+    char *buf = static_cast<char *>(a.buf);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int r = k / vrow, i = k - r * vrow;
+        const long long off = (long long)r * sl.stride * a.elem_bytes + (long long)i * 16;
+        const uint4 v = *reinterpret_cast<const uint4 *>(buf + sl.src * a.elem_bytes + off);
+        *reinterpret_cast<uint4 *>(buf + sl.dst * a.elem_bytes + off) = v;
+    }
 }
 
 cudaError_t launch_exchange(const ExchangeArgs &a, cudaStream_t s)
 {
-    if (a.nwork == 0) return cudaSuccess;
-    switch (a.elem_bytes) {
-    case 2: exchange_kernel<uint16_t><<<a.nwork, 256, 0, s>>>(a); break;
-    case 4: exchange_kernel<uint32_t><<<a.nwork, 256, 0, s>>>(a); break;
-    case 8: exchange_kernel<unsigned long long><<<a.nwork, 256, 0, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
-    }
+    if (a.nslabs == 0) return cudaSuccess;
+    exchange_kernel<<<a.nslabs, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -56,7 +42,8 @@ cudaError_t launch_exchange(const ExchangeArgs &a, cudaStream_t s)
 struct CellPos {
     const BlockGeom *b;
     int x, y, z;   // interior coordinates inside the block
-    int c;         // stored cell index inside the block
+    int c;         // PDF cell index inside the block
+    int cf;        // flag index inside the block
     long long o;   // cell index inside the instance's output slice
 };
 
@@ -73,13 +60,15 @@ __device__ __forceinline__ void for_each_cell(const FieldArgs &a, Fn fn)
         if (x >= b.nx || y >= b.ny) continue;
         const int zend = min(tile.z0 + a.tz, b.nz);
         const int pxy = b.px * b.py;
+        const int pxyf = b.pxf * b.py;
         for (int z = tile.z0; z < zend; ++z) {
             CellPos p;
             p.b = &b;
             p.x = x;
             p.y = y;
             p.z = z;
-            p.c = (z + 1) * pxy + (y + 1) * b.px + (x + b.ox);
+            p.c = (z + 1) * pxy + (y + 1) * b.px + x;
+            p.cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
             p.o = ((long long)(b.gz + z) * b.NY + (b.gy + y)) * b.NX + (b.gx + x);
             fn(p);
         }
@@ -108,7 +97,7 @@ __global__ void __launch_bounds__(256) macro_kernel(const __grid_constant__ Fiel
         const long long N = inst_cells(b);
         float *r = rho + b.out_base;
         float *v = u + 3 * b.out_base;
-        if (a.flags[b.cell_base + p.c] & F_KIND) {
+        if (a.flags[b.cell_base + p.cf] & F_KIND) {
             r[p.o] = float(P.rho0);
             v[p.o] = v[N + p.o] = v[2 * N + p.o] = 0.f;
             return;
@@ -145,7 +134,7 @@ __global__ void __launch_bounds__(256) init_eq_kernel(const __grid_constant__ Fi
         const CollideConsts<T> &P = cs[b.inst];
         const long long N = inst_cells(b);
         S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
-        if (a.flags[b.cell_base + p.c] & F_KIND) {
+        if (a.flags[b.cell_base + p.cf] & F_KIND) {
 #pragma unroll
             for (int q = 0; q < Q; ++q) g[(long long)q * b.G] = Tr::from_t(T(0));
             return;
@@ -179,7 +168,7 @@ __global__ void __launch_bounds__(256) get_pdfs_kernel(const __grid_constant__ F
         const double inv_s = double(cs[b.inst].inv_s);
         const long long N = inst_cells(b);
         double *out = f + (long long)Q * b.out_base;
-        const bool solid = a.flags[b.cell_base + p.c] & F_KIND;
+        const bool solid = a.flags[b.cell_base + p.cf] & F_KIND;
         const S *g = static_cast<const S *>(buf) + b.pdf_base + p.c;
 #pragma unroll
         for (int q = 0; q < Q; ++q)
@@ -200,7 +189,7 @@ __global__ void __launch_bounds__(256) set_pdfs_kernel(const __grid_constant__ F
         const double s = 1.0 / double(cs[b.inst].inv_s);
         const long long N = inst_cells(b);
         const double *in = f + (long long)Q * b.out_base;
-        const bool solid = a.flags[b.cell_base + p.c] & F_KIND;
+        const bool solid = a.flags[b.cell_base + p.cf] & F_KIND;
         S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
 #pragma unroll
         for (int q = 0; q < Q; ++q)
@@ -246,9 +235,11 @@ __global__ void __launch_bounds__(256) reduce_tiles_kernel(const __grid_constant
                               double(P.uoff[2]) * rho0};
         const int zend = min(tile.z0 + a.tz, b.nz);
         const int pxy = b.px * b.py;
+        const int pxyf = b.pxf * b.py;
         for (int z = tile.z0; z < zend; ++z) {
-            const int c = (z + 1) * pxy + (y + 1) * b.px + (x + b.ox);
-            if (a.flags[b.cell_base + c] & F_KIND) continue;
+            const int c = (z + 1) * pxy + (y + 1) * b.px + x;
+            const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
+            if (a.flags[b.cell_base + cf] & F_KIND) continue;
             const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
             double d = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll

@@ -30,37 +30,30 @@ enum : uint8_t {
     F_NEAR = 4,   // fluid cell with at least one wall / solid neighbour
 };
 
-// Stored x index of the first interior cell of every row: 16 cells, so that
-// interior rows start on a 32-byte DRAM sector for every PDF type and the
-// one-byte flag rows start 16-byte aligned (a TMA requirement).
-constexpr int OX = 16;
+// Layout of a Block.  PDF planes store (ny+2)(nz+2) rows of px cells: the
+// interior x range [0, nx) padded only up to a 32-byte multiple, plus one ghost
+// row on each y and z side.  There are no x ghost columns: across x faces the
+// sweep reads the neighbouring Block's boundary column directly, so a row is
+// exactly the data the sweep needs and the L2's 64-256-byte fetches carry no
+// padding.  The flag array keeps one ghost cell on every side (its interior x
+// starts at OXF = 16 so that flag rows are 16-byte aligned for TMA).
+constexpr int OXF = 16;
 
-// One Block (or one batch instance) in device memory.  The Block stores
-// (nx+2)(ny+2)(nz+2) logical cells with x padded: row pitch px (a multiple of
-// 16 cells), the first interior cell of a row at x index ox = OX, ghost cells
-// at ox-1 and ox+nx.  PDF plane q of the Block
-// lives at buf + pdf_base + q*G, flag byte of cell c at flags + cell_base + c.
-//
-// Across x faces the sweep reads the neighbouring Block's boundary column
-// directly (xm_off / xp_off: element offset from this Block's stored cell
-// x = ox-1 / ox+nx to the matching interior cell of the -x / +x neighbour,
-// 0 where the face is a wall), so the ghost exchange copies only the y and z
-// faces and the yz edges, which are contiguous rows in this layout.
+// PDF of cell (x,y,z) in direction q: buf[pdf_base + q*G + c] with
+// c = ((z+1)*py + y+1)*px + x; its flag: flags[cell_base + cf] with
+// cf = ((z+1)*py + y+1)*pxf + x + OXF.  xm_off / xp_off: element offset that
+// moves a pull across the -x / +x face into the neighbouring Block (0 where
+// the face is a wall; the flags then make the pull a bounce-back).
 struct BlockGeom {
     long long pdf_base;   // elements
-    long long cell_base;  // cells (flags)
-    long long G;          // cells per plane = px*py*pz
+    long long cell_base;  // flag bytes
+    long long G;          // PDF cells per plane = px*py*(nz+2)
+    long long Gf;         // flag cells = pxf*py*(nz+2)
     long long xm_off, xp_off;
-    // Fused ghost writes: element offset from this Block's stored cell to the
-    // ghost cell of the neighbour that pulls it, for the -y, +y, -z, +z faces
-    // and the (-y,-z), (+y,-z), (-y,+z), (+y,+z) edges; bit k of push_mask is
-    // set when neighbour k exists.
-    long long push_off[8];
-    int push_mask;
     int xm_block, xp_block;  // -x / +x neighbour Block, -1 where the face is a wall
     int nx, ny, nz;       // interior cells
-    int px, py;           // padded row pitch (cells), rows per plane (ny+2)
-    int ox;               // x index of the first interior cell
+    int px, py;           // PDF row pitch (cells), rows per plane (ny+2)
+    int pxf;              // flag row pitch (cells)
     int inst;             // instance this block belongs to
     int gx, gy, gz;       // origin of the block inside its instance
     long long out_base;   // first cell of the instance in the concatenated output
@@ -73,13 +66,28 @@ struct BlockGeom {
 //   drho_s = sum g,   u = (sum e g) * ufac + uoff  with ufac = 1/(s rho0), uoff = F/(2 rho0)
 //   feq_s  = w (drho_s + rho0s (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)),  rho0s = s rho0
 //   Guo source (scaled): cp w (9 (e.u)(e.Fs) - 3 u.Fs) + cm w 3 (e.Fs),  Fs = s F
+// Per-instance constants.  The first group serves the moment, conversion
+// and bounce-back kernels; the second the collision (collide.cuh), with the
+// Guo source folded into the equilibrium and the relaxation rates folded into
+// the coefficients:  a+ = (1 - omega+/2)/omega+,  a- = (1 - omega-/2)/omega-,
+// w_c = 1/18 (axis pairs, c = 0) or 1/36 (diagonal pairs, c = 1), and
+// omega = omega+ = omega- for BGK.
 template <typename T>
 struct CollideConsts {
-    T rho0s, ufac, uoff[3];
-    T omega_p, omega_m, cp, cm;
-    T Fs[3];
-    T bbw[Q];     // s * 6 w_q rho0 (e_q . u_wall)
+    T rho0s, ufac, uoff[3];   // rho0s = s rho0; u = j ufac + uoff, ufac = 1/(s rho0), uoff = F/(2 rho0)
+    T omega_p, omega_m;
+    T Fs[3];                  // s F
+    T bbw[Q];                 // s * 6 w_q rho0 (e_q . u_wall)
     T inv_s, rho0;
+    T zero;                   // 0
+    T nc15, c45;              // -1.5 rho0s, 4.5 rho0s
+    T k9F[3], nk3F[3];        // 9 a+ Fs, -3 a+ Fs
+    T c0a, c0b;               // omega+ / 3, 1 - omega+
+    T obw[2], oc3[2];         // BGK: omega w_c, omega 3 rho0s w_c
+    T okF[2][3];              // BGK: omega 3 a- w_c Fs
+    T hwp, hwm;               // TRT: omega+/2, omega-/2
+    T nwpw[2], nwmc3[2];      // TRT: -omega+ w_c, -omega- 3 rho0s w_c
+    T nwmkF[2][3];            // TRT: -omega- 3 a- w_c Fs
 };
 
 // Sweep work item: one CTA updates tx*ty*tz cells starting at (x0,y0,z0)
@@ -88,16 +96,14 @@ struct Tile {
     int block, x0, y0, z0;
 };
 
-// Ghost-exchange work item: copy, for every cell of a region of the ghost
-// shell of dst_block, the listed directions from the interior of src_block.
-struct XDesc {
-    int dst_block, src_block;
-    int x0, y0, z0;        // region start in interior coordinates (-1 or n for the ghost side)
-    int lx, ly, lz;        // region extent
-    int sx, sy, sz;        // source cell = region cell + (sx,sy,sz)
-    int ndir;
-    int dir[5];
-    int ncell;             // lx*ly*lz
+// Ghost-exchange work item: one direction plane of one face or edge of a
+// Block's ghost shell, a slab of `rows` rows of `len` contiguous elements
+// (stride `stride` elements between rows), copied from the neighbour's
+// matching boundary rows.  src / dst are element offsets into the buffer.
+struct XSlab {
+    long long src, dst;
+    long long stride;
+    int rows, len;
 };
 
 // Sets the calling thread's message for lbm_last_error(NULL).
@@ -120,15 +126,15 @@ struct SweepArgs {
     int forced;               // any instance has a nonzero force
     int storage;              // LBM_F32 .. LBM_F64
     int grid;                 // CTAs to launch (<= ntiles; persistent loop when smaller)
-    int minb;                 // register budget: 3 or 4 resident 256-thread CTAs per SM
-    int push;                 // 1: write boundary PDFs into the neighbours' ghost layers
+    int minb;                 // register budget: 2 or 3 resident 256-thread CTAs per SM
 };
 
 // TMA-staged sweep over a Patch whose Blocks all have nx = TX (32..256).
 struct TmaSweepArgs {
     SweepArgs a;
     int nx, ny, nz;           // Block interior size (uniform)
-    int px, py;               // stored pitch (uniform)
+    int px, py;               // PDF row pitch, rows per plane (uniform)
+    int pxf;                  // flag row pitch
     int ngy;                  // row groups of TY rows per Block
     int zchunk, nzc;          // z slices per work item, work items along z per Block
     long long nitems;         // Blocks * ngy * nzc
@@ -151,17 +157,9 @@ int tma_stages(int storage);
 cudaError_t tma_occupancy(int storage, int tx, int collision, int forced, int *ctas_per_sm);
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s);
 
-// Exchange CTA work list: CTA k copies items [first, first + blockDim) of
-// descriptor desc (items are direction-major, x fastest within a direction).
-struct XWork {
-    int desc;
-    int first;
-};
 struct ExchangeArgs {
-    const XDesc *desc;
-    const XWork *work;
-    int nwork;
-    const BlockGeom *blocks;
+    const XSlab *slabs;
+    int nslabs;
     void *buf;
     int elem_bytes;
 };

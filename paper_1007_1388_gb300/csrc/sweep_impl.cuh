@@ -1,16 +1,20 @@
-// The fused D3Q19 sweep: pull stream + half-way bounce-back + collide.
+// The fused D3Q19 sweep, register version: pull stream + half-way
+// bounce-back + collide, one cell per thread per z step of its tile.
 //
-// One thread updates one cell per z step of its tile (Sec. 3.2: one GPU
-// thread per lattice cell, structure-of-arrays PDF layout, pull scheme so
-// that every store is aligned and coalesced).  For each fluid cell x the
-// kernel pulls g_q = src_q[x - e_q]; when x - e_q is a wall or a solid cell
-// it applies half-way bounce-back (Sec. 2.1) with the momentum-consistent
-// sign, g_q = src_opp(q)[x] + s 6 w_q rho0 (e_q . u_wall).  It then collides
-// (Eq. (1), BGK or TRT, optional Guo forcing) and stores dst_q[x].  Solid
-// cells are skipped.  The ghost shell of each Block has been filled by the
-// exchange kernel beforehand, so interior and boundary cells run the same
-// instruction sequence (which keeps multi-Block runs bitwise equal to a
-// single-Block run).
+// Sec. 3.2: one GPU thread per lattice cell, structure-of-arrays PDFs, pull
+// scheme so that every store is aligned and coalesced.  For each fluid cell x
+// the kernel pulls g_q = src_q[x - e_q]; when x - e_q is a wall or a solid
+// cell it applies half-way bounce-back (Sec. 2.1) with the momentum-
+// consistent sign, g_q = src_opp(q)[x] + s 6 w_q rho0 (e_q . u_wall).  It
+// then collides (Eq. (1), BGK or TRT, Guo forcing; collide.cuh) and stores
+// dst_q[x].  Solid cells are skipped.  Across x faces the pull reads the
+// neighbouring Block's boundary column directly; the y/z ghost rows were
+// filled by the exchange, so every Block runs the same instruction sequence
+// (multi-Block runs are bitwise equal to single-Block runs).
+//
+// This version serves every geometry (batches of uneven instances, any Block
+// size, FP64); Patches of equal 32/64/128-wide Blocks use the TMA-staged
+// sweep, which gives bitwise equal results.
 #pragma once
 
 #include "device_common.cuh"
@@ -18,7 +22,7 @@
 namespace lbm {
 
 // MINB = CTAs of 256 threads per SM the register allocation must allow
-// (3 -> 80 registers, 4 -> 64); chosen per context by the autotuner.
+// (2 -> 128 registers, 3 -> 80); chosen per context by the autotuner.
 template <int ST, int COLL, bool FORCE, int MINB>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant__ SweepArgs a)
 {
@@ -39,7 +43,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         const int pxy = px * b.py;
         const int G = int(b.G);
         const CollideConsts<T> *cc = consts + b.inst;
-        const Coll<T> P = load_coll<T>(cc);
+        const CollKPtr<T> K{cc};
         const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
         // directions with e_x = +1 pull from x-1, e_x = -1 from x+1: on the
         // Block's first / last column those come from the x neighbour
@@ -48,9 +52,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         S *__restrict__ dst = static_cast<S *>(a.dst) + b.pdf_base;
         const uint8_t *__restrict__ fl = a.flags + b.cell_base;
 
-        int c = (tile.z0 + 1) * pxy + (y + 1) * px + (x + b.ox);
-        for (int z = tile.z0; z < zend; ++z, c += pxy) {
-            const uint8_t flag = fl[c];
+        const int pxf = b.pxf, pxyf = b.pxf * b.py;
+        int c = (tile.z0 + 1) * pxy + (y + 1) * px + x;
+        int cf = (tile.z0 + 1) * pxyf + (y + 1) * pxf + x + OXF;
+        for (int z = tile.z0; z < zend; ++z, c += pxy, cf += pxyf) {
+            const uint8_t flag = fl[cf];
             if (flag & F_KIND) continue;  // solid cells are not updated
             T f[Q];
             if (!(flag & F_NEAR)) {
@@ -63,10 +69,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const int n = c - (ex(q) + ey(q) * px + ez(q) * pxy);
-                    const uint8_t nf = fl[n];
+                    const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                     if (nf & F_KIND) {
                         T v = Tr::ld(src + (opp(q) * G + c));
-                        if ((nf & F_KIND) == F_MOVING) v += __ldg(&cc->bbw[q]);
+                        if ((nf & F_KIND) == F_MOVING) v = vadd(v, __ldg(&cc->bbw[q]));
                         f[q] = v;
                     } else {
                         const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
@@ -74,10 +80,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                     }
                 }
             }
-            collide<T, COLL, FORCE>(f, P);
+            collide_v<COLL, FORCE>(f, K);
 #pragma unroll
             for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
-            if (a.push) push_ghosts<Tr>(dst, b, y, z, c, G, f);
         }
     }
 }
@@ -104,10 +109,8 @@ cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
     dim3 block(a.tx, a.ty, 1);
     const unsigned grid = unsigned(a.grid > 0 ? a.grid : a.ntiles);
     if (grid == 0) return cudaSuccess;
-    if (ST == 3)  // FP64 arithmetic needs the larger register budget
+    if (ST == 3 || a.minb == 2)  // FP64 arithmetic needs the larger register budget
         launch_sweep_minb<ST, 2>(a, grid, block, s);
-    else if (a.minb == 4)
-        launch_sweep_minb<ST, 4>(a, grid, block, s);
     else
         launch_sweep_minb<ST, 3>(a, grid, block, s);
     return cudaGetLastError();

@@ -7,8 +7,10 @@
 // (one per direction, shifted by -e_q) with cp.async.bulk.tensor into a ring
 // of shared-memory stages, plus the x-halo columns from the neighbouring
 // Blocks (direct reads across x faces, as in the register sweep) and the flag
-// row; eight consumer warps read one cell each from shared memory, apply
-// bounce-back, collide (Eq. (1)) and store with coalesced global stores.
+// row; four consumer warps take two neighbouring cells per thread, read them
+// from shared memory, apply bounce-back, collide both at once with packed
+// FP32x2 arithmetic (collide.cuh; same rounding as the one-cell sweep) and
+// store them with 64-bit coalesced global stores.
 // Stages are handed over with mbarriers (full: transaction bytes landed;
 // empty: all consumer warps have read the stage).  Every wait is bounded by
 // a clock limit; a wait that expires writes an error word and the CTA leaves
@@ -90,6 +92,9 @@ struct TmaLayout {
     static constexpr int E = int(sizeof(S));
     static constexpr int A = 16 / E;
     static constexpr int TY = 256 / TX;
+    static constexpr int NCT = TX / 2 * TY;  // consumer threads (two cells each)
+    static constexpr int NCW = NCT / 32;     // consumer warps
+    static constexpr int THREADS = NCT + 32;
     static constexpr int BOXA = TX * TY * E;
     static constexpr int BOXB = (TX + A) * TY * E;
     static constexpr int HALO = A * TY * E;
@@ -112,22 +117,89 @@ struct TmaLayout {
     static constexpr int HALO0 = box_off(Q);
     static constexpr int FLAGS = HALO0 + 10 * RH;
     static constexpr int STAGE = FLAGS + RF;
-    static constexpr int STAGES = ST == 0 ? 4 : 5;
+    static constexpr int STAGES = ST == 0 ? 3 : 5;
     static constexpr int SMEM = STAGES * STAGE + 2 * STAGES * 8 + 128;
-    static constexpr int MINB = ST == 0 ? 2 : 3;  // resident CTAs the register budget allows
+    static constexpr int MINB = 3;  // resident CTAs the register budget allows
     static constexpr uint32_t BYTES_CORE = 9 * BOXA + 10 * BOXB + FLAG;
 };
 
+// Two neighbouring cells (x, x+1) of direction q from a staged box.
+template <int ST, int TX, int q>
+__device__ __forceinline__ F2 load_pair(const unsigned char *st, int ty, int x, bool hm, bool hp)
+{
+    using Ly = TmaLayout<ST, TX>;
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    constexpr int A = Ly::A;
+    const S *box = reinterpret_cast<const S *>(st + Ly::box_off(q));
+    float lo, hi;
+    if (ex(q) == 0) {
+        const S *p = box + ty * TX + x;  // even x: 4- or 8-byte aligned pair
+        if (ST == 0) {
+            const float2 v = *reinterpret_cast<const float2 *>(p);
+            lo = v.x;
+            hi = v.y;
+        } else if (ST == 1) {
+            const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+            lo = v.x;
+            hi = v.y;
+        } else {
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+            lo = v.x;
+            hi = v.y;
+        }
+    } else if (ex(q) > 0) {
+        const S *p = box + ty * (TX + A) + x - 1 + A;
+        lo = Tr::to_t(p[0]);
+        hi = Tr::to_t(p[1]);
+        if (x == 0 && hm)
+            lo = Tr::to_t(reinterpret_cast<const S *>(st + Ly::HALO0 + Ly::halo_slot(q) * Ly::RH)[ty * A + A - 1]);
+    } else {
+        const S *p = box + ty * (TX + A) + x + 1;
+        lo = Tr::to_t(p[0]);
+        hi = Tr::to_t(p[1]);
+        if (x == TX - 2 && hp)
+            hi = Tr::to_t(reinterpret_cast<const S *>(st + Ly::HALO0 + Ly::halo_slot(q) * Ly::RH)[ty * A]);
+    }
+    return f2_pack(lo, hi);
+}
+
+template <int ST>
+__device__ __forceinline__ void store_pair(typename Traits<ST>::S *p, F2 v, bool st_lo, bool st_hi)
+{
+    using Tr = Traits<ST>;
+    float lo, hi;
+    f2_unpack(v, lo, hi);
+    if (st_lo && st_hi) {
+        if (ST == 0)
+            *reinterpret_cast<unsigned long long *>(p) = v.r;
+        else if (ST == 1)
+            *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(lo, hi);
+        else
+            *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(lo, hi);
+    } else {
+        if (st_lo) Tr::st(p, lo);
+        if (st_hi) Tr::st(p + 1, hi);
+    }
+}
+
+template <int q, int ST, int TX>
+__device__ __forceinline__ void load_all(F2 (&f)[Q], const unsigned char *st, int ty, int x, bool hm,
+                                         bool hp)
+{
+    f[q] = load_pair<ST, TX, q>(st, ty, x, hm, hp);
+    if constexpr (q + 1 < Q) load_all<q + 1, ST, TX>(f, st, ty, x, hm, hp);
+}
+
 template <int ST, int COLL, bool FORCE, int TX>
-__global__ void __launch_bounds__(288, TmaLayout<ST, TX>::MINB)
+__global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>::MINB)
     sweep_tma_kernel(const __grid_constant__ TmaSweepArgs ta, const __grid_constant__ TmaMaps maps)
 {
     using Ly = TmaLayout<ST, TX>;
     using Tr = Traits<ST>;
     using S = typename Tr::S;
-    using T = typename Tr::T;
     constexpr int TY = Ly::TY, A = Ly::A, STAGES = Ly::STAGES;
-    constexpr int NCW = 256 / 32;  // consumer warps
+    constexpr int NCW = Ly::NCW;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem =
@@ -188,7 +260,9 @@ __global__ void __launch_bounds__(288, TmaLayout<ST, TX>::MINB)
                     if (lane < Q) {
                         const int q = lane;
                         const int exq = ex(q);
-                        const int xs = exq > 0 ? OX - A : OX;
+                        // e_x = +1 boxes start A cells left of the row (those
+                        // read as zeros: lane 0 takes the neighbour's halo)
+                        const int xs = exq > 0 ? -A : 0;
                         tma_load_4d(st + Ly::box_off(q), exq == 0 ? ma : mb, xs, y0 + 1 - ey(q),
                                     z + 1 - ez(q), blk * Q + q, &full[s]);
                     } else if (lane < Q + 10) {
@@ -197,10 +271,10 @@ __global__ void __launch_bounds__(288, TmaLayout<ST, TX>::MINB)
                         const int qq = k < 5 ? (k == 0 ? 1 : 5 + 2 * k) : (k == 5 ? 2 : 6 + 2 * (k - 5));
                         const int nbk = k < 5 ? hm : hp;
                         if (nbk >= 0)
-                            tma_load_4d(st + Ly::HALO0 + k * Ly::RH, mh, k < 5 ? OX + ta.nx - A : OX,
+                            tma_load_4d(st + Ly::HALO0 + k * Ly::RH, mh, k < 5 ? ta.nx - A : 0,
                                         y0 + 1 - ey(qq), z + 1 - ez(qq), nbk * Q + qq, &full[s]);
                     } else if (lane == Q + 10) {
-                        tma_load_4d(st + Ly::FLAGS, mf, OX, y0 + 1, z + 1, blk, &full[s]);
+                        tma_load_4d(st + Ly::FLAGS, mf, OXF, y0 + 1, z + 1, blk, &full[s]);
                     }
                 }
                 pending[s] = !drop;
@@ -220,9 +294,10 @@ __global__ void __launch_bounds__(288, TmaLayout<ST, TX>::MINB)
     }
 
     // ------------------------------------------------------------ consumers
-    const CollideConsts<T> *__restrict__ consts = static_cast<const CollideConsts<T> *>(a.consts);
-    const int tx = tid % TX, ty = tid / TX;
+    const CollideConsts<float> *__restrict__ consts = static_cast<const CollideConsts<float> *>(a.consts);
+    const int x = 2 * (tid % (TX / 2)), ty = tid / (TX / 2);
     const int px = ta.px, pxy = ta.px * ta.py;
+    const int pxf = ta.pxf, pxyf = ta.pxf * ta.py;
     int s = 0;
     uint32_t ph = 0;
     for (long long it = blockIdx.x; it < ta.nitems; it += gridDim.x) {
@@ -234,8 +309,8 @@ __global__ void __launch_bounds__(288, TmaLayout<ST, TX>::MINB)
         const int z0 = zc * ta.zchunk, z1 = min(z0 + ta.zchunk, ta.nz);
         const bool hm = b.xm_block >= 0, hp = b.xp_block >= 0;
         const int G = int(b.G);
-        const CollideConsts<T> *cc = consts + b.inst;
-        const Coll<T> P = load_coll<T>(cc);
+        const CollideConsts<float> *cc = consts + b.inst;
+        const CollK<float> K = load_collk<float>(cc);
         const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
         S *__restrict__ dst = static_cast<S *>(a.dst) + b.pdf_base;
         const uint8_t *__restrict__ fl = a.flags + b.cell_base;
@@ -245,49 +320,42 @@ __global__ void __launch_bounds__(288, TmaLayout<ST, TX>::MINB)
                 return;
             }
             const unsigned char *st = smem + s * Ly::STAGE;
-            const uint8_t flag = st[Ly::FLAGS + ty * TX + tx];
-            T f[Q];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const S *box = reinterpret_cast<const S *>(st + Ly::box_off(q));
-                S v;
-                if (ex(q) == 0) {
-                    v = box[ty * TX + tx];
-                } else if (ex(q) > 0) {
-                    v = box[ty * (TX + A) + tx - 1 + A];
-                    if (tx == 0 && hm)
-                        v = reinterpret_cast<const S *>(st + Ly::HALO0 + Ly::halo_slot(q) * Ly::RH)[ty * A + A - 1];
-                } else {
-                    v = box[ty * (TX + A) + tx + 1];
-                    if (tx == TX - 1 && hp)
-                        v = reinterpret_cast<const S *>(st + Ly::HALO0 + Ly::halo_slot(q) * Ly::RH)[ty * A];
-                }
-                f[q] = Tr::to_t(v);
-            }
+            const uint8_t fl0 = st[Ly::FLAGS + ty * TX + x], fl1 = st[Ly::FLAGS + ty * TX + x + 1];
+            F2 f[Q];
+            load_all<0, ST, TX>(f, st, ty, x, hm, hp);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             if (++s == STAGES) {
                 s = 0;
                 ph ^= 1u;
             }
-            if (flag & F_KIND) continue;  // solid cells are not updated
-            const int c = (z + 1) * pxy + (y + 1) * px + (OX + tx);
-            if (flag & F_NEAR) {
-                // half-way bounce-back where the source is a wall or solid
+            const bool solid0 = fl0 & F_KIND, solid1 = fl1 & F_KIND;
+            if (solid0 && solid1) continue;  // solid cells are not updated
+            const int c = (z + 1) * pxy + (y + 1) * px + x;
+            if ((fl0 | fl1) & F_NEAR) {
+                // half-way bounce-back, cell by cell, where the source is a wall or solid
+                const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const uint8_t nf = fl[c - (ex(q) + ey(q) * px + ez(q) * pxy)];
-                    if (nf & F_KIND) {
-                        T v = Tr::ld(src + (opp(q) * G + c));
-                        if ((nf & F_KIND) == F_MOVING) v += __ldg(&cc->bbw[q]);
-                        f[q] = v;
+                    float v[2];
+                    f2_unpack(f[q], v[0], v[1]);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const uint8_t own = k ? fl1 : fl0;
+                        if (!(own & F_NEAR)) continue;
+                        const uint8_t nf = fl[cf + k - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+                        if (nf & F_KIND) {
+                            float w = Tr::ld(src + (opp(q) * G + c + k));
+                            if ((nf & F_KIND) == F_MOVING) w = vadd(w, __ldg(&cc->bbw[q]));
+                            v[k] = w;
+                        }
                     }
+                    f[q] = f2_pack(v[0], v[1]);
                 }
             }
-            collide<T, COLL, FORCE>(f, P);
+            collide_v<COLL, FORCE>(f, K);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
-            if (a.push) push_ghosts<Tr>(dst, b, y, z, c, G, f);
+            for (int q = 0; q < Q; ++q) store_pair<ST>(dst + (q * G + c), f[q], !solid0, !solid1);
         }
     }
 }
@@ -303,7 +371,7 @@ cudaError_t launch_tma_inst(const TmaSweepArgs &ta, const TmaMaps &maps, int gri
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    kern<<<grid, 288, smem, s>>>(ta, maps);
+    kern<<<grid, TmaLayout<ST, TX>::THREADS, smem, s>>>(ta, maps);
     return cudaGetLastError();
 }
 
@@ -314,7 +382,7 @@ cudaError_t occupancy_tma_inst(int *n)
     auto kern = sweep_tma_kernel<ST, COLL, FORCE, TX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, 288, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, TmaLayout<ST, TX>::THREADS, smem);
 }
 
 template <int ST>

@@ -21,7 +21,6 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENUMERIC = 0, -1, -
 LBM_FLUID, LBM_NOSLIP, LBM_MOVING = 0, 1, 2
 LBM_BGK, LBM_TRT = 0, 1
 LBM_F32, LBM_F16S, LBM_BF16S, LBM_F64 = 0, 1, 2, 3
-LBM_EXCHANGE_FUSED, LBM_EXCHANGE_KERNEL = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_REGISTER, LBM_KERNEL_TMA = 0, 1, 2
 LBM_DEBUG_DROP_STAGE = 1
 STORAGE_NAMES = {LBM_F32: "f32", LBM_F16S: "f16s", LBM_BF16S: "bf16s", LBM_F64: "f64"}
@@ -45,7 +44,6 @@ class lbm_params(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("tile", ctypes.c_int * 3),
         ("graph_steps", ctypes.c_int),
-        ("exchange_mode", ctypes.c_int),
         ("kernel", ctypes.c_int),
         ("debug_flags", ctypes.c_int),
     ]
@@ -65,7 +63,6 @@ class lbm_info(ctypes.Structure):
         ("tile", ctypes.c_int * 3),
         ("tiles", ctypes.c_longlong),
         ("kernel", ctypes.c_int),
-        ("exchange_mode", ctypes.c_int),
         ("sweep_ctas", ctypes.c_int),
         ("stages", ctypes.c_int),
     ]

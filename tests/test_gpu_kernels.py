@@ -3,7 +3,6 @@
 - the TMA-staged sweep and the register sweep are bitwise equal (Block
   widths 32, 64 and 128; FP32, F16S and BF16S storage; BGK and TRT; forced;
   obstacles and moving walls);
-- the fused ghost writes and the separate exchange kernel are bitwise equal;
 - a TMA sweep whose staged data never arrives reports LBM_ETIMEOUT through
   its bounded waits instead of hanging, and the library stays usable.
 """
@@ -71,18 +70,6 @@ def test_tma_sweep_matches_oracle_and_walls_in_x(L):
     p = oracle.Problem(dims=dims, tau=0.8, flags=flags, **kw)
     ref = oracle.run(p, oracle.zeros(p), 30)
     assert np.abs(f.reshape(ref.shape) - ref).max() <= 1e-5
-
-
-@pytest.mark.parametrize("kernel", [1, 2])
-def test_fused_exchange_equals_exchange_kernel(L, kernel):
-    rng = np.random.default_rng(8)
-    dims = (128, 32, 30)
-    flags = W.random_flags(rng, dims, 0.05)
-    f0 = W.random_pdfs(rng, dims, 1e-2, flags)
-    kw = dict(collision=0, force=(1e-5, 0, 0), periodic=(1, 1, 1), kernel=kernel)
-    a, _ = _run(L, dims, (64, 8, 10), 0.9, flags, 20, f0, exchange_mode=L.LBM_EXCHANGE_FUSED, **kw)
-    b, _ = _run(L, dims, (64, 8, 10), 0.9, flags, 20, f0, exchange_mode=L.LBM_EXCHANGE_KERNEL, **kw)
-    assert np.array_equal(a, b)
 
 
 def test_tma_sweep_bounded_wait_reports_timeout(L):
