@@ -208,7 +208,8 @@ def run_gpu(args):
     if args.kernel:
         main_kw["kernel"] = {"auto": 0, "register": 1, "tma": 2}[args.kernel]
     ctx = make(**main_kw)
-    if args.autotune:
+    if not args.no_autotune:
+        # pick kernel, tile and register budget by timing on this GPU (outside the timed region)
         L.lbm_autotune(ctx, None)
     info = L.lbm_get_info(ctx)
     cells = info.cells
@@ -252,7 +253,8 @@ def run_gpu(args):
     traffic = _ncu_traffic("sweep_f32_channel256")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": peak_kind, "kernel": "lbm::sweep_kernel (forced)",
+                "peak_kind": peak_kind,
+                "kernel": "lbm::sweep_tma_kernel" if info.kernel == L.LBM_KERNEL_TMA else "lbm::sweep_kernel",
                 "bytes_per_lup": BYTES_PER_LUP[st_main], "sweep_ms": sweep_ms,
                 "exchange_ms": xch_ms, "exchange_pdfs": info.exchange_pdfs}
 
@@ -286,6 +288,7 @@ def run_gpu(args):
                          ("bgk_bf16s", dict(storage=L.LBM_BF16S)),
                          ("bgk_f64", dict(storage=L.LBM_F64))]:
             c = make(**kw)
+            L.lbm_autotune(c, None)
             L.lbm_step(c, 5)
             L.lbm_profile_enable(c, True)
             L.lbm_profile_read(c)
@@ -361,7 +364,7 @@ def main():
     ap.add_argument("--block", type=int, default=B, help="cells per Block along each axis")
     ap.add_argument("--storage", default="", help="f32 | f16s | bf16s | f64 (default f32)")
     ap.add_argument("--trt", action="store_true", help="TRT instead of BGK")
-    ap.add_argument("--autotune", action="store_true", help="pick the sweep tile by timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep configuration")
     ap.add_argument("--kernel", default="", help="auto | register | tma")
     ap.add_argument("--force", type=float, default=FORCE, help="body force along x")
     args = ap.parse_args()

@@ -113,6 +113,13 @@ struct CollKPtr {
     const CollideConsts<T> *__restrict__ p;
 };
 
+// Constants that are kernel parameters (one instance): read from the
+// parameter (constant) bank at their point of use, no registers held.
+template <typename T>
+struct CollKRef {
+    const CollideConsts<T> &p;
+};
+
 template <typename S, typename T>
 __device__ __forceinline__ CollK<S> load_collk(const CollideConsts<T> *__restrict__ c)
 {
@@ -150,12 +157,16 @@ __device__ __forceinline__ CollK<S> load_collk(const CollideConsts<T> *__restric
     template <typename S>                                                                            \
     __device__ __forceinline__ S k_##name(const CollK<S> &k) { return k.name; }                      \
     template <typename T>                                                                            \
-    __device__ __forceinline__ T k_##name(const CollKPtr<T> &k) { return __ldg(&k.p->name); }
+    __device__ __forceinline__ T k_##name(const CollKPtr<T> &k) { return __ldg(&k.p->name); }        \
+    template <typename T>                                                                            \
+    __device__ __forceinline__ T k_##name(const CollKRef<T> &k) { return k.p.name; }
 #define LBM_K1(name)                                                                                 \
     template <typename S>                                                                            \
     __device__ __forceinline__ S k_##name(const CollK<S> &k, int i) { return k.name[i]; }            \
     template <typename T>                                                                            \
-    __device__ __forceinline__ T k_##name(const CollKPtr<T> &k, int i) { return __ldg(&k.p->name[i]); }
+    __device__ __forceinline__ T k_##name(const CollKPtr<T> &k, int i) { return __ldg(&k.p->name[i]); } \
+    template <typename T>                                                                            \
+    __device__ __forceinline__ T k_##name(const CollKRef<T> &k, int i) { return k.p.name[i]; }
 #define LBM_K2(name)                                                                                 \
     template <typename S>                                                                            \
     __device__ __forceinline__ S k_##name(const CollK<S> &k, int i, int j) { return k.name[i][j]; }  \
@@ -163,7 +174,9 @@ __device__ __forceinline__ CollK<S> load_collk(const CollideConsts<T> *__restric
     __device__ __forceinline__ T k_##name(const CollKPtr<T> &k, int i, int j)                        \
     {                                                                                                \
         return __ldg(&k.p->name[i][j]);                                                              \
-    }
+    }                                                                                                \
+    template <typename T>                                                                            \
+    __device__ __forceinline__ T k_##name(const CollKRef<T> &k, int i, int j) { return k.p.name[i][j]; }
 LBM_K0(zero)
 LBM_K0(nc15)
 LBM_K0(c45)
@@ -238,20 +251,60 @@ template <int COLL, bool FORCE, typename V, typename KT>
 __device__ __forceinline__ void collide_v(V (&f)[Q], const KT &K)
 {
     using L = Lane<V>;
-    // moments from pair sums and differences
-    const V s1 = vadd(f[1], f[2]), s3 = vadd(f[3], f[4]), s5 = vadd(f[5], f[6]);
-    const V s7 = vadd(f[7], f[8]), s9 = vadd(f[9], f[10]), s11 = vadd(f[11], f[12]);
-    const V s13 = vadd(f[13], f[14]), s15 = vadd(f[15], f[16]), s17 = vadd(f[17], f[18]);
-    const V d1 = vsub(f[1], f[2]), d3 = vsub(f[3], f[4]), d5 = vsub(f[5], f[6]);
-    const V d7 = vsub(f[7], f[8]), d9 = vsub(f[9], f[10]), d11 = vsub(f[11], f[12]);
-    const V d13 = vsub(f[13], f[14]), d15 = vsub(f[15], f[16]), d17 = vsub(f[17], f[18]);
-    const V drho = vadd(vadd(vadd(vadd(f[0], s1), vadd(s3, s5)), vadd(vadd(s7, s9), vadd(s11, s13))),
-                        vadd(s15, s17));
-    // e_x: +1 for 1,7,9,11,13; e_y: +1 for 3,7,15,17 and -1 for 9;
-    // e_z: +1 for 5,11,15 and -1 for 13,17
-    const V jx = vadd(vadd(vadd(d1, d7), vadd(d9, d11)), d13);
-    const V jy = vadd(vsub(vadd(d3, d7), d9), vadd(d15, d17));
-    const V jz = vadd(vsub(vadd(d5, d11), d13), vsub(d15, d17));
+    // moments, accumulated pair by pair (sum and difference of each pair are
+    // used at once, so only the four accumulators stay live)
+    V drho, jx, jy, jz;
+    {
+        const V s = vadd(f[1], f[2]), d = vsub(f[1], f[2]);  // (+1, 0, 0)
+        drho = vadd(f[0], s);
+        jx = d;
+    }
+    {
+        const V s = vadd(f[3], f[4]), d = vsub(f[3], f[4]);  // (0, +1, 0)
+        drho = vadd(drho, s);
+        jy = d;
+    }
+    {
+        const V s = vadd(f[5], f[6]), d = vsub(f[5], f[6]);  // (0, 0, +1)
+        drho = vadd(drho, s);
+        jz = d;
+    }
+    {
+        const V s = vadd(f[7], f[8]), d = vsub(f[7], f[8]);  // (+1, +1, 0)
+        drho = vadd(drho, s);
+        jx = vadd(jx, d);
+        jy = vadd(jy, d);
+    }
+    {
+        const V s = vadd(f[9], f[10]), d = vsub(f[9], f[10]);  // (+1, -1, 0)
+        drho = vadd(drho, s);
+        jx = vadd(jx, d);
+        jy = vsub(jy, d);
+    }
+    {
+        const V s = vadd(f[11], f[12]), d = vsub(f[11], f[12]);  // (+1, 0, +1)
+        drho = vadd(drho, s);
+        jx = vadd(jx, d);
+        jz = vadd(jz, d);
+    }
+    {
+        const V s = vadd(f[13], f[14]), d = vsub(f[13], f[14]);  // (+1, 0, -1)
+        drho = vadd(drho, s);
+        jx = vadd(jx, d);
+        jz = vsub(jz, d);
+    }
+    {
+        const V s = vadd(f[15], f[16]), d = vsub(f[15], f[16]);  // (0, +1, +1)
+        drho = vadd(drho, s);
+        jy = vadd(jy, d);
+        jz = vadd(jz, d);
+    }
+    {
+        const V s = vadd(f[17], f[18]), d = vsub(f[17], f[18]);  // (0, +1, -1)
+        drho = vadd(drho, s);
+        jy = vadd(jy, d);
+        jz = vsub(jz, d);
+    }
     // u = j ufac + uoff (uoff = 0 without force; always an FMA, see above)
     const V ux = vfma(jx, L::c(k_ufac(K)), L::c(k_uoff(K, 0)));
     const V uy = vfma(jy, L::c(k_ufac(K)), L::c(k_uoff(K, 1)));

@@ -66,7 +66,8 @@ struct lbm_ctx {
     long long cells = 0, fluid = 0, stored = 0, exchange_pdfs = 0;
     int tile[3] = {64, 4, 4};
     int grid = 0;  // 0 = one CTA per tile
-    int minb = 2;  // register budget of the sweep (resident CTAs per SM)
+    int minb = 4;  // register budget of the sweep (resident CTAs per SM)
+    std::vector<char> h_consts;  // host copy of the per-instance CollideConsts
     // kernel choice and the TMA sweep's launch state
     int kernel = LBM_KERNEL_REGISTER;
     TmaMaps maps{};
@@ -644,6 +645,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     if ((rc = upload(c, &c->d_xslabs, c->xslabs))) return rc;
     std::vector<char> consts =
         c->storage == LBM_F64 ? make_consts<double>(c) : make_consts<float>(c);
+    c->h_consts = consts;
     if ((rc = upload(c, reinterpret_cast<char **>(&c->d_consts), consts))) return rc;
     if ((rc = own(c, &c->d_red, sizeof(double) * R_K * c->ninst))) return rc;
     if ((rc = own(c, &c->d_err, sizeof(int)))) return rc;
@@ -703,6 +705,13 @@ SweepArgs sweep_args(const lbm_ctx *c, int from)
     a.storage = c->storage;
     a.grid = c->grid;
     a.minb = c->minb;
+    a.unif = c->ninst == 1 ? 1 : 0;
+    if (a.unif) {
+        if (c->storage == LBM_F64)
+            std::memcpy(&a.kd, c->h_consts.data(), sizeof(a.kd));
+        else
+            std::memcpy(&a.kf, c->h_consts.data(), sizeof(a.kf));
+    }
     return a;
 }
 
@@ -1279,7 +1288,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         const int zc0 = c->tma_zchunk;
         if (tma_ok)
             for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, c->tile[0], c->tile[1], c->tile[2], c->grid, c->minb, zc});
-        for (int mb : {2, 3})
+        for (int mb : {3, 4})
             for (int tx : {32, 64, 128, 256}) {
                 if (tx > std::max(32, round_up(maxnx, 32))) continue;
                 for (int th : {128, 256}) {

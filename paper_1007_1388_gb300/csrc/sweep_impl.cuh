@@ -22,8 +22,26 @@
 namespace lbm {
 
 // MINB = CTAs of 256 threads per SM the register allocation must allow
-// (2 -> 128 registers, 3 -> 80); chosen per context by the autotuner.
-template <int ST, int COLL, bool FORCE, int MINB>
+// (3 -> 80 registers, 4 -> 64; FP64 uses 2 -> 128); chosen per context by
+// the autotuner.  Each thread updates exactly one cell: the tile's z slices
+// are the grid's y dimension.  (A per-thread loop over z made the compiler
+// keep 38 strength-reduced 64-bit load and store addresses live, which
+// spilled at these register budgets.)
+// UNIF: a single instance whose collision constants are kernel parameters.
+template <typename T>
+__device__ __forceinline__ const CollideConsts<T> &param_consts(const SweepArgs &a);
+template <>
+__device__ __forceinline__ const CollideConsts<float> &param_consts<float>(const SweepArgs &a)
+{
+    return a.kf;
+}
+template <>
+__device__ __forceinline__ const CollideConsts<double> &param_consts<double>(const SweepArgs &a)
+{
+    return a.kd;
+}
+
+template <int ST, int COLL, bool FORCE, int MINB, bool UNIF>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     using Tr = Traits<ST>;
@@ -38,12 +56,14 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         const int y = tile.y0 + int(threadIdx.y);
         const int nx = b.nx, ny = b.ny;
         if (x >= nx || y >= ny) continue;
-        const int zend = min(tile.z0 + a.tz, b.nz);
+        const int z = tile.z0 + int(blockIdx.y);
+        if (z >= b.nz) continue;
         const int px = b.px;
         const int pxy = px * b.py;
         const int G = int(b.G);
         const CollideConsts<T> *cc = consts + b.inst;
-        const CollKPtr<T> K{cc};
+        const CollKPtr<T> KP{cc};
+        const CollKRef<T> KR{param_consts<T>(a)};
         const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
         // directions with e_x = +1 pull from x-1, e_x = -1 from x+1: on the
         // Block's first / last column those come from the x neighbour
@@ -53,9 +73,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         const uint8_t *__restrict__ fl = a.flags + b.cell_base;
 
         const int pxf = b.pxf, pxyf = b.pxf * b.py;
-        int c = (tile.z0 + 1) * pxy + (y + 1) * px + x;
-        int cf = (tile.z0 + 1) * pxyf + (y + 1) * pxf + x + OXF;
-        for (int z = tile.z0; z < zend; ++z, c += pxy, cf += pxyf) {
+        const int c = (z + 1) * pxy + (y + 1) * px + x;
+        const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
+        {
             const uint8_t flag = fl[cf];
             if (flag & F_KIND) continue;  // solid cells are not updated
             T f[Q];
@@ -72,7 +92,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                     const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                     if (nf & F_KIND) {
                         T v = Tr::ld(src + (opp(q) * G + c));
-                        if ((nf & F_KIND) == F_MOVING) v = vadd(v, __ldg(&cc->bbw[q]));
+                        if ((nf & F_KIND) == F_MOVING)
+                            v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
                         f[q] = v;
                     } else {
                         const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
@@ -80,37 +101,52 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                     }
                 }
             }
-            collide_v<COLL, FORCE>(f, K);
+            if (UNIF)
+                collide_v<COLL, FORCE>(f, KR);
+            else
+                collide_v<COLL, FORCE>(f, KP);
 #pragma unroll
             for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
         }
     }
 }
 
-template <int ST, int MINB>
-void launch_sweep_minb(const SweepArgs &a, unsigned grid, dim3 block, cudaStream_t s)
+template <int ST, int MINB, bool UNIF>
+void launch_sweep_unif(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
     if (a.collision == 0) {
         if (a.forced)
-            sweep_kernel<ST, 0, true, MINB><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 0, true, MINB, UNIF><<<grid, block, 0, s>>>(a);
         else
-            sweep_kernel<ST, 0, false, MINB><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 0, false, MINB, UNIF><<<grid, block, 0, s>>>(a);
     } else {
         if (a.forced)
-            sweep_kernel<ST, 1, true, MINB><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 1, true, MINB, UNIF><<<grid, block, 0, s>>>(a);
         else
-            sweep_kernel<ST, 1, false, MINB><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 1, false, MINB, UNIF><<<grid, block, 0, s>>>(a);
     }
+}
+
+template <int ST, int MINB>
+void launch_sweep_minb(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (a.unif)
+        launch_sweep_unif<ST, MINB, true>(a, grid, block, s);
+    else
+        launch_sweep_unif<ST, MINB, false>(a, grid, block, s);
 }
 
 template <int ST>
 cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
 {
     dim3 block(a.tx, a.ty, 1);
-    const unsigned grid = unsigned(a.grid > 0 ? a.grid : a.ntiles);
-    if (grid == 0) return cudaSuccess;
-    if (ST == 3 || a.minb == 2)  // FP64 arithmetic needs the larger register budget
+    const unsigned gx = unsigned(a.grid > 0 ? a.grid : a.ntiles);
+    if (gx == 0) return cudaSuccess;
+    const dim3 grid(gx, unsigned(a.tz), 1);
+    if (ST == 3)  // FP64 arithmetic needs the larger register budget
         launch_sweep_minb<ST, 2>(a, grid, block, s);
+    else if (a.minb == 4)
+        launch_sweep_minb<ST, 4>(a, grid, block, s);
     else
         launch_sweep_minb<ST, 3>(a, grid, block, s);
     return cudaGetLastError();

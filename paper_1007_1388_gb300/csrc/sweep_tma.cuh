@@ -309,8 +309,7 @@ __global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>:
         const int z0 = zc * ta.zchunk, z1 = min(z0 + ta.zchunk, ta.nz);
         const bool hm = b.xm_block >= 0, hp = b.xp_block >= 0;
         const int G = int(b.G);
-        const CollideConsts<float> *cc = consts + b.inst;
-        const CollK<float> K = load_collk<float>(cc);
+        const CollKRef<float> K{ta.a.kf};  // one instance: constants are kernel parameters
         const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
         S *__restrict__ dst = static_cast<S *>(a.dst) + b.pdf_base;
         const uint8_t *__restrict__ fl = a.flags + b.cell_base;
@@ -346,7 +345,7 @@ __global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>:
                         const uint8_t nf = fl[cf + k - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                         if (nf & F_KIND) {
                             float w = Tr::ld(src + (opp(q) * G + c + k));
-                            if ((nf & F_KIND) == F_MOVING) w = vadd(w, __ldg(&cc->bbw[q]));
+                            if ((nf & F_KIND) == F_MOVING) w = vadd(w, ta.a.kf.bbw[q]);
                             v[k] = w;
                         }
                     }
