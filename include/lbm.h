@@ -89,8 +89,9 @@ typedef struct {
     int tile[3];          /* sweep tile: threads along x, rows along y, cells per thread
                              along z; {0,0,0} = the library's default (or lbm_autotune) */
     int graph_steps;      /* steps per captured CUDA graph; 0 = automatic, -1 = no graphs */
-    int kernel;           /* LBM_KERNEL_AUTO (default): TMA-staged sweep where the Patch
-                             allows it, else the register sweep; LBM_KERNEL_REGISTER;
+    int kernel;           /* LBM_KERNEL_AUTO (default): the register sweep, with the
+                             TMA-staged sweep prepared where the Patch allows it so
+                             that lbm_autotune can choose it; LBM_KERNEL_REGISTER;
                              LBM_KERNEL_TMA (LBM_EINVAL at create when not applicable) */
     int debug_flags;      /* 0; LBM_DEBUG_DROP_STAGE makes the TMA sweep skip one staged
                              load so its bounded waits expire (failure-path tests) */

@@ -43,12 +43,17 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def kernel_hash() -> str:
-    """Hash of every kernel source and header (ties profiles to the code they measured)."""
+SWEEP_SOURCES = ("sweep_impl.cuh", "collide.cuh", "device_common.cuh", "lbm_internal.h", "sweep_f32.cu",
+                 "sweep_f16s.cu", "sweep_bf16s.cu", "sweep_f64.cu")
+
+
+def kernel_hash(files=SWEEP_SOURCES) -> str:
+    """Hash of the sources that define the register sweep kernel (ties a
+    profile to the code it measured)."""
     import hashlib
 
     h = hashlib.sha256()
-    for path in sorted(_sources() + _headers()):
+    for path in sorted(os.path.join(CSRC, f) for f in files):
         h.update(os.path.basename(path).encode())
         with open(path, "rb") as f:
             h.update(f.read())

@@ -198,11 +198,18 @@ __global__ void __launch_bounds__(256) set_pdfs_kernel(const __grid_constant__ F
 }
 
 // ------------------------------------------------------------- reductions
-// FP64 sums over the fluid cells of each tile: drho, momentum (before the
-// -F/2 shift, which the host applies), fluid and non-finite cell counts,
-// and for the residual sum |u_cur - u_prev|^2 and sum |u_cur|^2.  One CTA
-// per tile writes R_K partials; a second kernel adds the partials of each
-// instance in a fixed order, so results are deterministic.
+// Sums over the fluid cells of each tile; one CTA per tile writes R_K
+// partials, a second kernel adds the partials of each instance in a fixed
+// order, so results are deterministic.
+//  - invariants (prev == NULL): drho, momentum (before the -F/2 shift, which
+//    the host applies), fluid and non-finite cell counts, every per-cell sum
+//    in FP64 so that mass conservation can be checked to roundoff;
+//  - residual (prev != NULL): sum |u_cur - u_prev|^2 and sum |u_cur|^2.  Each
+//    cell's velocity and its change (from the per-direction differences
+//    cur - prev, so the change keeps full relative precision) are formed in
+//    the arithmetic type of the sweep; the norms are accumulated in FP64.
+//    This keeps the check memory-bound: GB300's FP64 rate is far below its
+//    FP32 rate.
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -210,72 +217,8 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <int ST>
-__global__ void __launch_bounds__(256) reduce_tiles_kernel(const __grid_constant__ FieldArgs a,
-                                                           const void *cur, const void *prev,
-                                                           double *partial)
+__device__ __forceinline__ void block_partials(double (&acc)[R_K], double *out)
 {
-    using Tr = Traits<ST>;
-    using S = typename Tr::S;
-    using T = typename Tr::T;
-    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
-    double acc[R_K];
-#pragma unroll
-    for (int k = 0; k < R_K; ++k) acc[k] = 0.0;
-
-    const long long t = blockIdx.x;
-    const Tile tile = a.tiles[t];
-    const BlockGeom &b = a.blocks[tile.block];
-    const int x = tile.x0 + int(threadIdx.x);
-    const int y = tile.y0 + int(threadIdx.y);
-    if (x < b.nx && y < b.ny) {
-        const CollideConsts<T> &P = cs[b.inst];
-        const double inv_s = double(P.inv_s), rho0 = double(P.rho0);
-        const double hF[3] = {double(P.uoff[0]) * rho0, double(P.uoff[1]) * rho0,
-                              double(P.uoff[2]) * rho0};
-        const int zend = min(tile.z0 + a.tz, b.nz);
-        const int pxy = b.px * b.py;
-        const int pxyf = b.pxf * b.py;
-        for (int z = tile.z0; z < zend; ++z) {
-            const int c = (z + 1) * pxy + (y + 1) * b.px + x;
-            const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
-            if (a.flags[b.cell_base + cf] & F_KIND) continue;
-            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
-            double d = 0.0, j[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const double v = double(Tr::to_t(g[(long long)q * b.G])) * inv_s;
-                d += v;
-                j[0] += ex(q) * v;
-                j[1] += ey(q) * v;
-                j[2] += ez(q) * v;
-            }
-            acc[R_DRHO] += d;
-            acc[R_JX] += j[0];
-            acc[R_JY] += j[1];
-            acc[R_JZ] += j[2];
-            acc[R_NFLUID] += 1.0;
-            if (!isfinite(d + j[0] + j[1] + j[2])) acc[R_NONFINITE] += 1.0;
-            if (prev) {
-                const S *h = static_cast<const S *>(prev) + b.pdf_base + c;
-                double k3[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const double v = double(Tr::to_t(h[(long long)q * b.G])) * inv_s;
-                    k3[0] += ex(q) * v;
-                    k3[1] += ey(q) * v;
-                    k3[2] += ez(q) * v;
-                }
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const double uc = (j[m] - hF[m]) / rho0;
-                    const double up = (k3[m] - hF[m]) / rho0;
-                    acc[R_DU2] += (uc - up) * (uc - up);
-                    acc[R_U2] += uc * uc;
-                }
-            }
-        }
-    }
     __shared__ double red[8][R_K];
     const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
     const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
@@ -289,8 +232,109 @@ __global__ void __launch_bounds__(256) reduce_tiles_kernel(const __grid_constant
     if (warp == 0 && lane < R_K) {
         double v = 0.0;
         for (int w = 0; w < nwarps; ++w) v += red[w][lane];
-        partial[t * R_K + lane] = v;
+        out[lane] = v;
     }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) invariants_tiles_kernel(const __grid_constant__ FieldArgs a,
+                                                               const void *cur, double *partial)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    double acc[R_K];
+#pragma unroll
+    for (int k = 0; k < R_K; ++k) acc[k] = 0.0;
+    const long long t = blockIdx.x;
+    const Tile tile = a.tiles[t];
+    const BlockGeom &b = a.blocks[tile.block];
+    const int x = tile.x0 + int(threadIdx.x);
+    const int y = tile.y0 + int(threadIdx.y);
+    if (x < b.nx && y < b.ny) {
+        const double inv_s = double(cs[b.inst].inv_s);
+        const int zend = min(tile.z0 + a.tz, b.nz);
+        const int pxy = b.px * b.py, pxyf = b.pxf * b.py;
+        for (int z = tile.z0; z < zend; ++z) {
+            const int c = (z + 1) * pxy + (y + 1) * b.px + x;
+            const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
+            if (a.flags[b.cell_base + cf] & F_KIND) continue;
+            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
+            double d = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const double v = double(Tr::to_t(g[(long long)q * b.G])) * inv_s;
+                d += v;
+                if (ex(q)) j[0] += ex(q) > 0 ? v : -v;
+                if (ey(q)) j[1] += ey(q) > 0 ? v : -v;
+                if (ez(q)) j[2] += ez(q) > 0 ? v : -v;
+            }
+            acc[R_DRHO] += d;
+            acc[R_JX] += j[0];
+            acc[R_JY] += j[1];
+            acc[R_JZ] += j[2];
+            acc[R_NFLUID] += 1.0;
+            if (!isfinite(d + j[0] + j[1] + j[2])) acc[R_NONFINITE] += 1.0;
+        }
+    }
+    block_partials(acc, partial + t * R_K);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) residual_tiles_kernel(const __grid_constant__ FieldArgs a,
+                                                             const void *cur, const void *prev,
+                                                             double *partial)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    double acc[R_K];
+#pragma unroll
+    for (int k = 0; k < R_K; ++k) acc[k] = 0.0;
+    const long long t = blockIdx.x;
+    const Tile tile = a.tiles[t];
+    const BlockGeom &b = a.blocks[tile.block];
+    const int x = tile.x0 + int(threadIdx.x);
+    const int y = tile.y0 + int(threadIdx.y);
+    if (x < b.nx && y < b.ny) {
+        const CollideConsts<T> &P = cs[b.inst];
+        const T ufac = P.ufac, uo[3] = {P.uoff[0], P.uoff[1], P.uoff[2]};
+        const int zend = min(tile.z0 + a.tz, b.nz);
+        const int pxy = b.px * b.py, pxyf = b.pxf * b.py;
+        T du2 = T(0), u2 = T(0), nf = T(0), bad = T(0);  // over this thread's few cells
+        for (int z = tile.z0; z < zend; ++z) {
+            const int c = (z + 1) * pxy + (y + 1) * b.px + x;
+            const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
+            if (a.flags[b.cell_base + cf] & F_KIND) continue;
+            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
+            const S *h = static_cast<const S *>(prev) + b.pdf_base + c;
+            T j[3] = {T(0), T(0), T(0)}, dj[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const T v = Tr::to_t(g[(long long)q * b.G]);
+                const T dv = v - Tr::to_t(h[(long long)q * b.G]);
+                if (ex(q)) { j[0] += ex(q) > 0 ? v : -v; dj[0] += ex(q) > 0 ? dv : -dv; }
+                if (ey(q)) { j[1] += ey(q) > 0 ? v : -v; dj[1] += ey(q) > 0 ? dv : -dv; }
+                if (ez(q)) { j[2] += ez(q) > 0 ? v : -v; dj[2] += ez(q) > 0 ? dv : -dv; }
+            }
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const T u = j[m] * ufac - uo[m];
+                const T du = dj[m] * ufac;
+                u2 += u * u;
+                du2 += du * du;
+            }
+            nf += T(1);
+            if (!isfinite(j[0] + j[1] + j[2] + dj[0] + dj[1] + dj[2])) bad += T(1);
+        }
+        acc[R_DU2] = double(du2);
+        acc[R_U2] = double(u2);
+        acc[R_NFLUID] = double(nf);
+        acc[R_NONFINITE] = double(bad);
+    }
+    block_partials(acc, partial + t * R_K);
 }
 
 __global__ void __launch_bounds__(256) reduce_instances_kernel(const double *partial,
@@ -380,9 +424,15 @@ cudaError_t launch_reduce(const FieldArgs &a, const void *cur, const void *prev,
 {
     if (a.tx * a.ty > 256) return cudaErrorInvalidValue;
     if (a.ntiles > 0) {
-#define CALL(ST) reduce_tiles_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, cur, prev, partial)
-        LBM_DISPATCH_ST(a.storage, CALL)
+        if (prev) {
+#define CALL(ST) residual_tiles_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, cur, prev, partial)
+            LBM_DISPATCH_ST(a.storage, CALL)
 #undef CALL
+        } else {
+#define CALL(ST) invariants_tiles_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, cur, partial)
+            LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -107,8 +107,10 @@ def test_one_step_from_random_state(L, seed):
     assert abs(m - mr) <= 1e-12 * abs(mr)
     # FP64 sums over ~1e5 cells in different orders: relative 1e-11
     assert np.abs(j - jr).max() <= 1e-11 * max(1.0, np.abs(jr).max())
+    # the residual forms each cell's velocity and its change in FP32 (the
+    # norms accumulate in FP64): a few FP32 roundings, relative 1e-5
     r = L.lbm_residual(ctx)
-    assert abs(r - oracle.residual(p, f0, got)) <= 1e-10 * r
+    assert abs(r - oracle.residual(p, f0, got)) <= 1e-5 * r
     # moments of the stored state
     rho, u = L.lbm_macroscopic(ctx)
     rr, ur = oracle.macroscopic(p, got)
