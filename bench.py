@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 N, B, TAU, FORCE = 256, 64, 0.8, 1e-6
 BYTES_PER_LUP = {0: 19 * 4 * 2 + 1, 1: 19 * 2 * 2 + 1, 2: 19 * 2 * 2 + 1, 3: 19 * 8 * 2 + 1}
 WORKLOAD = ("D3Q19 body-force channel 256^3, 4x4x4 Blocks of 64^3 with on-device ghost "
-            "exchange, periodic x/z, no-slip y walls, BGK tau=0.8, F=1e-6 (configs[1])")
+            "exchange, periodic x/z, no-slip y walls, BGK tau=0.8, F=1e-6")
 METRIC = "MLUPS"
 
 
@@ -212,6 +212,7 @@ def run_gpu(args):
         # pick kernel, tile and register budget by timing on this GPU (outside the timed region)
         L.lbm_autotune(ctx, None)
     info = L.lbm_get_info(ctx)
+    sweep_cfg = list(L.lbm_get_sweep_config(ctx))
     cells = info.cells
     stream = ctx.stream  # the torch stream the library enqueues on
 
@@ -307,6 +308,10 @@ def run_gpu(args):
                 "bytes_per_lup": BYTES_PER_LUP[st]}
             c.destroy()
 
+    batch = None
+    if not args.skip_batch:
+        batch = _batch_variants(args, L, W, barrier, torch)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         v, steps, el = _oracle_sample(args.cpu_seconds)
@@ -320,11 +325,13 @@ def run_gpu(args):
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
                "config": {"workload": WORKLOAD, "cells": cells, "blocks": info.blocks,
-                          "tile": list(info.tile), "parallelism": f"replicas x{ws}",
+                          "tile": list(info.tile), "sweep_config": sweep_cfg,
+                          "parallelism": f"replicas x{ws}",
                           "l2": "inputs larger than L2 (2 x 1.4 GB PDF buffers), no flush"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(prof.sweep_launches + prof.exchange_launches),
-               "clocks": clk.summary(), "graph_mlups": graph_mlups, "variants": variants}
+               "clocks": clk.summary(), "graph_mlups": graph_mlups, "variants": variants,
+               "batch": batch}
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -332,6 +339,123 @@ def run_gpu(args):
 
 
 R_K_HOST = 8  # doubles per instance read back by one residual check
+
+BATCH_WORKLOAD = ("256 independent D3Q19 channels, per-axis sizes uniform in [16, 96], tau uniform "
+                  "in [0.55, 1.2], sphere packings (radius 2-6, porosity 0.7-0.9), seed 1234, "
+                  "BGK, F=1e-5 along x, walls at -y/+y")
+BATCH_FORCE = 1e-5
+
+
+def _batch_variants(args, L, W, barrier, torch):
+    """Batched launch over 256 uneven instances (one sweep launch per step, CUDA
+    graph, autotuned tiling) against the same instances as 256 separate
+    contexts on concurrent streams, FP32 and shifted-FP16 storage."""
+    inst = W.batch_instances(seed=1234, n=args.batch_instances)
+    dims = [d for d, _, _ in inst]
+    taus = [t for _, t, _ in inst]
+    flags = [f for _, _, f in inst]
+    steps = args.batch_steps
+    out = {"workload": BATCH_WORKLOAD, "instances": len(inst), "steps": steps}
+    for name, kw in [("f32", {}), ("f16s", dict(storage=L.LBM_F16S, storage_scale=256.0))]:
+        p = L.make_params(collision=L.LBM_BGK, force=(BATCH_FORCE, 0, 0), **W.channel_bc(), **kw)
+        ctx = L.lbm_batch_create(dims, taus, flags, p)
+        L.lbm_autotune(ctx, None)
+        info = L.lbm_get_info(ctx)
+        L.lbm_step(ctx, 10)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        L.lbm_step(ctx, steps)
+        e1.record(ctx.stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        res = {"mlups": info.cells * steps / (ms * 1e-3) / 1e6,
+               "mflups": info.fluid_cells * steps / (ms * 1e-3) / 1e6,
+               "ms_per_step": ms / steps, "cells": info.cells, "fluid_cells": info.fluid_cells,
+               "tile": list(info.tile), "sweep_ctas": info.sweep_ctas,
+               "sweep_config": list(L.lbm_get_sweep_config(ctx))}
+        L.lbm_profile_enable(ctx, True)
+        L.lbm_profile_read(ctx)
+        L.lbm_step(ctx, 20)
+        pr = L.lbm_profile_read(ctx)
+        L.lbm_profile_enable(ctx, False)
+        sw = pr.sweep_ms / max(1, pr.sweep_launches)
+        st = kw.get("storage", 0)
+        res["sweep_ms"] = sw
+        res["sweep_gbs"] = BYTES_PER_LUP[st] * info.cells / (sw * 1e-3) / 1e9
+        res["launches_per_step"] = (pr.sweep_launches + pr.exchange_launches) / 20
+        ctx.destroy()
+        # the same instances, one context (and stream) each
+        ctxs = [L.lbm_create(d, d, t, f, p) for d, t, f in inst]
+        for c in ctxs:
+            L.lbm_step(c, 10)
+        barrier()
+        t0 = time.perf_counter()
+        for c in ctxs:
+            L.lbm_step(c, steps)
+        barrier()
+        el = time.perf_counter() - t0
+        res["separate_mlups"] = info.cells * steps / el / 1e6
+        res["batched_over_separate"] = res["mlups"] / res["separate_mlups"]
+        for c in ctxs:
+            c.destroy()
+        out[name] = res
+    return out
+
+
+PRECISION_WORKLOAD = "D3Q19 lid-driven cavity 384^3, lid 0.05 along x on +y, BGK tau=0.55, 5000 steps"
+
+
+def run_precision_report(args):
+    """Storage precision at full size: u and rho of FP32, shifted FP16 (scale
+    256 and 1) and BF16 storage against FP64 storage of the same cavity, with
+    the MLUPS of each.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1007_1388_gb300 import build
+
+    build.build()
+    import paper_1007_1388_gb300 as L
+    from paper_1007_1388_gb300 import workloads as W
+
+    L.use_torch_allocator()
+    n, steps, b = args.report_size, args.report_steps, args.report_block
+    cases = [("f64", L.LBM_F64, 1.0), ("f32", L.LBM_F32, 1.0), ("f16s_scale256", L.LBM_F16S, 256.0),
+             ("f16s_scale1", L.LBM_F16S, 1.0), ("bf16s", L.LBM_BF16S, 1.0)]
+    out = {"report": "precision", "workload": PRECISION_WORKLOAD.replace("384", str(n), 1)
+           .replace("5000", str(steps)), "block": b}
+    ref = None
+    for name, st, scale in cases:
+        p = L.make_params(wall_u=(0.05, 0, 0), storage=st, storage_scale=scale, **W.cavity_bc())
+        ctx = L.lbm_create((n,) * 3, (b,) * 3, 0.55, None, p)
+        L.lbm_autotune(ctx, None)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        L.lbm_step(ctx, steps)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        m, _, nonfinite = L.lbm_invariants(ctx)
+        rho, u = L.lbm_macroscopic(ctx)
+        ctx.destroy()
+        rho = torch.from_numpy(rho).cuda().double()
+        u = torch.from_numpy(u).cuda().double()
+        row = {"mlups": n**3 * steps / (ms * 1e-3) / 1e6, "mass": m, "nonfinite": nonfinite}
+        if ref is None:
+            ref = (rho, u)
+            row["u_max"] = float(u.abs().max())
+        else:
+            du, dr = u - ref[1], rho - ref[0]
+            row.update(u_max_err=float(du.abs().max()), u_rms_err=float(du.square().mean().sqrt()),
+                       rho_max_err=float(dr.abs().max()), rho_rms_err=float(dr.square().mean().sqrt()))
+        out[name] = row
+        print(name, row, file=sys.stderr, flush=True)
+        del rho, u
+    print(json.dumps(out))
+    return 0
 
 
 def _ncu_traffic(name):
@@ -360,6 +484,14 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--report", default="", choices=["", "precision"],
+                    help="precision: storage-precision report on the 384^3 cavity (one JSON line)")
+    ap.add_argument("--report-size", type=int, default=384)
+    ap.add_argument("--report-steps", type=int, default=5000)
+    ap.add_argument("--report-block", type=int, default=128)
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--size", type=int, default=N, help="cells per axis (profiling runs use less)")
     ap.add_argument("--block", type=int, default=B, help="cells per Block along each axis")
     ap.add_argument("--storage", default="", help="f32 | f16s | bf16s | f64 (default f32)")
@@ -372,6 +504,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.report == "precision":
+        return run_precision_report(args)
     return run_gpu(args)
 
 

@@ -86,8 +86,10 @@ typedef struct {
     int storage;          /* LBM_F32 (default), LBM_F16S, LBM_BF16S, LBM_F64 */
     double storage_scale; /* power of two multiplying f~ in F16S/BF16S storage; default 1 */
     void *stream;         /* cudaStream_t to enqueue on; NULL = the library creates one */
-    int tile[3];          /* sweep tile: threads along x, rows along y, cells per thread
-                             along z; {0,0,0} = the library's default (or lbm_autotune) */
+    int tile[3];          /* sweep tile: threads along x (a multiple of 32), rows along
+                             y, z slices; {0,0,0} = the library's default: row tiles, or
+                             runs of 256 consecutive cells per CTA where a Block's width
+                             is not a multiple of 32 (lbm_autotune may change either) */
     int graph_steps;      /* steps per captured CUDA graph; 0 = automatic, -1 = no graphs */
     int kernel;           /* LBM_KERNEL_AUTO (default): the register sweep, with the
                              TMA-staged sweep prepared where the Patch allows it so
@@ -221,6 +223,10 @@ typedef struct {
     int kernel;               /* LBM_KERNEL_REGISTER or LBM_KERNEL_TMA in use */
     int sweep_ctas;           /* CTAs of one sweep launch */
     int stages;               /* pipeline depth of the TMA sweep (0 for the register sweep) */
+    int flat;                 /* > 0: the register sweep runs each Block as runs of this many
+                                 consecutive cells per CTA (tile[] is then {flat, 1, 1}) */
+    int mask;                 /* 1: the register sweep treats near-wall cells through
+                                 precomputed link masks under a warp vote */
 } lbm_info;
 int lbm_get_info(lbm_ctx *ctx, lbm_info *info);
 
@@ -241,13 +247,31 @@ int lbm_profile_enable(lbm_ctx *ctx, int on);
 int lbm_profile_read(lbm_ctx *ctx, lbm_profile *out);
 
 /*
- * lbm_autotune - times each candidate sweep tile on the context's own data
- * (sweeps from the current state into the scratch buffer, which leaves the
- * simulation state unchanged) and keeps the fastest.  cache_path (may be
+ * lbm_autotune - times each candidate sweep configuration (row tiles, runs
+ * of consecutive cells, persistent grids, register budgets, the TMA sweep
+ * where it applies) on the context's own data (sweeps from the current state
+ * into the scratch buffer, which leaves the simulation state unchanged) and
+ * keeps the fastest.  cache_path (may be
  * NULL) names a JSON-lines file: a matching entry is reused instead of
  * timing, a new result is appended.  best (may be NULL) receives the tile.
  */
 int lbm_autotune(lbm_ctx *ctx, const char *cache_path, int best[3]);
+
+/*
+ * lbm_get_sweep_config / lbm_set_sweep_config - the sweep configuration that
+ * lbm_autotune chooses, as 8 ints {kind, tx, ty, tz, grid, minb, zchunk,
+ * mask}: kind 0 = register sweep over row tiles of tx x ty cells and tz z
+ * slices (tx a multiple of 32, tx*ty <= 256); 1 = TMA-staged sweep (only where
+ * it applies) with zchunk z slices per work item; 2 = register sweep over
+ * runs of tx consecutive cells (32..256, a multiple of 32); grid = CTAs of a
+ * persistent launch (0 = one per work item); minb = 3 or 4 resident CTAs per
+ * SM the register budget allows (FP64 storage always uses 2); mask = 1 treats
+ * near-wall cells through precomputed link masks under a warp vote.  Every
+ * configuration gives bitwise identical results.  LBM_EINVAL for an invalid
+ * or inapplicable configuration (the context is then unchanged).
+ */
+int lbm_get_sweep_config(lbm_ctx *ctx, int cfg[8]);
+int lbm_set_sweep_config(lbm_ctx *ctx, const int cfg[8]);
 
 /* Device memory hooks: alloc(bytes, stream, user) returns a device pointer or
  * NULL; release(ptr, bytes, stream, user) frees it.  Passing NULL restores

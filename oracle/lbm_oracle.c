@@ -22,9 +22,12 @@
  *   - Guo forcing (not in the paper): S_i split into a symmetric part
  *     relaxed with omega+ and an antisymmetric part relaxed with omega-.
  *
- * Readings where the paper is silent, garbled or inconsistent are listed in
- * DESIGN.md ("Readings of the paper").  No blocking, fusion or reordering is
- * applied; every cell is updated by the same straight loop.
+ * Where the paper is silent, garbled or inconsistent, the reading taken is
+ * stated beside the code that takes it.  No blocking, fusion or reordering is
+ * applied; every cell is updated by the same straight loop.  orc_step may
+ * spread its z planes over OpenMP threads (orc_set_threads): each cell is
+ * still computed by the same code from the same inputs, so the result does
+ * not depend on the thread count.
  *
  * Grid convention: interior cells only, index c = (z*ny + y)*nx + x, PDF
  * arrays q-major: f[q*N + c].  Anything outside the interior is either a
@@ -186,10 +189,16 @@ static int classify(const orc_problem *p, const uint8_t *flags, int x, int y, in
  * step n-1, dst receives post-collision f~ of step n.  Solid cells are
  * not updated and hold 0.  If u_used is given it receives, per cell, the
  * velocity the collision used (3 x N, component-major). */
+static int orc_threads = 1;
+
+/* Threads used by orc_step (1 = serial; ignored without OpenMP). */
+void orc_set_threads(int n) { orc_threads = n > 0 ? n : 1; }
+
 void orc_step(const orc_problem *p, const uint8_t *flags, const double *src, double *dst,
               double *u_used)
 {
     long N = (long)p->n[0] * p->n[1] * p->n[2];
+#pragma omp parallel for schedule(static) num_threads(orc_threads) if (orc_threads > 1)
     for (int z = 0; z < p->n[2]; ++z)
         for (int y = 0; y < p->n[1]; ++y)
             for (int x = 0; x < p->n[0]; ++x) {
@@ -229,10 +238,14 @@ int orc_run(const orc_problem *p, const uint8_t *flags, double *f, int nsteps)
     long N = (long)p->n[0] * p->n[1] * p->n[2];
     double *tmp = (double *)malloc(sizeof(double) * ORC_Q * N);
     if (!tmp) return -1;
+    double *a = f, *b = tmp;
     for (int s = 0; s < nsteps; ++s) {
-        orc_step(p, flags, f, tmp, NULL);
-        memcpy(f, tmp, sizeof(double) * ORC_Q * N);
+        orc_step(p, flags, a, b, NULL);
+        double *t = a;
+        a = b;
+        b = t;
     }
+    if (a != f) memcpy(f, a, sizeof(double) * ORC_Q * N);
     free(tmp);
     return 0;
 }

@@ -64,8 +64,13 @@ struct lbm_ctx {
     std::vector<XSlab> xslabs;
     std::vector<long long> inst_out_base;
     long long cells = 0, fluid = 0, stored = 0, exchange_pdfs = 0;
-    int tile[3] = {64, 4, 4};
-    int grid = 0;  // 0 = one CTA per tile
+    int tile[3] = {64, 4, 4};     // tiles of the field and reduction kernels (fixed at create)
+    // the sweep's own work list (lbm_autotune changes only this)
+    int sw_tile[3] = {64, 4, 4};  // row tile, or {flat, 1, 1}
+    int flat = 0;                 // > 0: runs of this many consecutive cells per CTA
+    int grid = 0;                 // 0 = one CTA per tile, else a persistent grid
+    int mask = 0;                 // near-wall cells via link masks under a warp vote
+    std::vector<Tile> stiles;
     int minb = 4;  // register budget of the sweep (resident CTAs per SM)
     std::vector<char> h_consts;  // host copy of the per-instance CollideConsts
     // kernel choice and the TMA sweep's launch state
@@ -79,8 +84,10 @@ struct lbm_ctx {
     std::vector<DevMem> owned;
     void *buf[2] = {nullptr, nullptr};
     uint8_t *d_flags = nullptr;
+    uint32_t *d_links = nullptr;
     BlockGeom *d_blocks = nullptr;
     Tile *d_tiles = nullptr;
+    Tile *d_stiles = nullptr;
     XSlab *d_xslabs = nullptr;
     void *d_consts = nullptr;
     long long *d_inst_begin = nullptr;
@@ -342,7 +349,8 @@ void invalidate_graphs(lbm_ctx *c)
         }
 }
 
-int set_tiles(lbm_ctx *c, const int t[3], int grid)
+// Tiles of the field and reduction kernels.
+int set_tiles(lbm_ctx *c, const int t[3])
 {
     std::vector<Tile> tiles;
     std::vector<long long> begin;
@@ -371,7 +379,40 @@ int set_tiles(lbm_ctx *c, const int t[3], int grid)
     c->d_tiles = dt;
     c->d_inst_begin = db;
     for (int a = 0; a < 3; ++a) c->tile[a] = t[a];
+    return LBM_OK;
+}
+
+// The sweep's work list: row tiles of t[0] x t[1] cells over t[2] z slices,
+// or (flat > 0) runs of `flat` consecutive cells of each Block; grid > 0
+// launches that many CTAs, which loop over the list.
+int set_sweep(lbm_ctx *c, const int t[3], int flat, int grid)
+{
+    std::vector<Tile> st;
+    std::vector<long long> unused;
+    if (flat > 0) {
+        for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+            const BlockGeom &b = c->blocks[bi];
+            const long long n = (long long)b.nx * b.ny * b.nz;
+            for (long long i = 0; i < n; i += flat) st.push_back({int(bi), int(i), 0, 0});
+        }
+    } else {
+        build_tiles(c, t, st, unused);
+    }
+    Tile *dt = nullptr;
+    int rc = upload(c, &dt, st);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream), "set_sweep");
+    disown(c, c->d_stiles);
+    c->d_stiles = dt;
+    c->stiles.swap(st);
+    c->flat = flat;
     c->grid = grid;
+    if (flat > 0) {
+        c->sw_tile[0] = flat;
+        c->sw_tile[1] = c->sw_tile[2] = 1;
+    } else {
+        for (int a = 0; a < 3; ++a) c->sw_tile[a] = t[a];
+    }
     invalidate_graphs(c);
     return LBM_OK;
 }
@@ -478,6 +519,8 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
 
     // ---- blocks and flags
     std::vector<uint8_t> hflags;
+    std::vector<uint32_t> hlinks;
+    long long near_cells = 0;
     long long pdf_base = 0, cell_base = 0, out_base = 0;
     for (int k = 0; k < c->ninst; ++k) {
         const InstSpec &s = inst[k];
@@ -530,19 +573,28 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                 f[cidx] = v;
                             }
                     const long long pxy = (long long)b.pxf * b.py;
+                    std::vector<uint32_t> lk(size_t(b.Gf), 0u);
                     for (int z = 0; z < b.nz; ++z)
                         for (int y = 0; y < b.ny; ++y)
                             for (int x = 0; x < b.nx; ++x) {
                                 const long long cidx = (z + 1) * pxy + (long long)(y + 1) * b.pxf + (x + OXF);
                                 if (f[cidx] != F_FLUID) continue;
                                 ++c->fluid;
-                                for (int q = 1; q < Q; ++q)
-                                    if (f[cidx - (ex(q) + ey(q) * (long long)b.pxf + ez(q) * pxy)] & F_KIND) {
-                                        f[cidx] |= F_NEAR;
-                                        break;
-                                    }
+                                uint32_t m = 0;
+                                for (int q = 1; q < Q; ++q) {
+                                    const uint8_t nk =
+                                        f[cidx - (ex(q) + ey(q) * (long long)b.pxf + ez(q) * pxy)] & F_KIND;
+                                    if (nk) m |= 1u << q;
+                                    if (nk == F_MOVING) m |= L_MOVING;
+                                }
+                                if (m) {
+                                    f[cidx] |= F_NEAR;
+                                    lk[cidx] = m;
+                                    ++near_cells;
+                                }
                             }
                     hflags.insert(hflags.end(), f.begin(), f.end());
+                    hlinks.insert(hlinks.end(), lk.begin(), lk.end());
                     c->blocks.push_back(b);
                 }
         // ---- direct reads across x faces
@@ -641,6 +693,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     CK(cudaMemsetAsync(c->buf[0], 0, buf_bytes, c->stream), "memset");
     CK(cudaMemsetAsync(c->buf[1], 0, buf_bytes, c->stream), "memset");
     if ((rc = upload(c, &c->d_flags, hflags))) return rc;
+    if ((rc = upload(c, &c->d_links, hlinks))) return rc;
     if ((rc = upload(c, &c->d_blocks, c->blocks))) return rc;
     if ((rc = upload(c, &c->d_xslabs, c->xslabs))) return rc;
     std::vector<char> consts =
@@ -651,19 +704,30 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     if ((rc = own(c, &c->d_err, sizeof(int)))) return rc;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "memset");
 
+    // default tile: a warp multiple along x covering the block width, 256 threads
+    int maxnx = 0;
+    for (const BlockGeom &b : c->blocks) maxnx = std::max(maxnx, b.nx);
+    int td[3];
+    td[0] = std::min(128, round_up(std::max(maxnx, 1), 32));
+    td[1] = std::max(1, 256 / td[0]);
+    td[2] = 4;
+    if ((rc = set_tiles(c, td))) return rc;
     int t[3] = {p.tile[0], p.tile[1], p.tile[2]};
+    int flat = 0;
     if (t[0] <= 0 || t[1] <= 0 || t[2] <= 0) {
-        // default: a warp-multiple along x covering the block width, 256 threads
-        int maxnx = 0;
-        for (const BlockGeom &b : c->blocks) maxnx = std::max(maxnx, b.nx);
-        t[0] = std::min(128, round_up(std::max(maxnx, 1), 32));
-        t[1] = std::max(1, 256 / t[0]);
-        t[2] = 4;
+        for (int a = 0; a < 3; ++a) t[a] = td[a];
+        // Blocks whose width is not a warp multiple would leave lanes of
+        // every row tile idle: sweep them in runs of 256 consecutive cells
+        bool ragged = false;
+        for (const BlockGeom &b : c->blocks) ragged |= (b.nx % 32) != 0;
+        if (ragged) flat = 256;
     }
     if (t[0] * t[1] > 256 || t[0] % 32 != 0)
         return fail(c, LBM_EINVAL, "tile %dx%d: threads along x must be a multiple of 32 and "
                     "tile[0]*tile[1] <= 256", t[0], t[1]);
-    if ((rc = set_tiles(c, t, 0))) return rc;
+    if ((rc = set_sweep(c, t, flat, 0))) return rc;
+    // link masks pay where near-wall and interior cells share warps
+    c->mask = near_cells * 10 > c->fluid ? 1 : 0;
     // the TMA sweep is set up wherever it applies (lbm_autotune may pick it);
     // it runs by default only when requested: the register sweep is faster
     // on GB300 for every workload measured so far
@@ -694,16 +758,19 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
 SweepArgs sweep_args(const lbm_ctx *c, int from)
 {
     SweepArgs a{};
-    a.tiles = c->d_tiles;
-    a.ntiles = (long long)c->tiles.size();
+    a.tiles = c->d_stiles;
+    a.ntiles = (long long)c->stiles.size();
     a.blocks = c->d_blocks;
     a.consts = c->d_consts;
     a.flags = c->d_flags;
+    a.links = c->d_links;
     a.src = c->buf[from];
     a.dst = c->buf[from ^ 1];
-    a.tx = c->tile[0];
-    a.ty = c->tile[1];
-    a.tz = c->tile[2];
+    a.tx = c->sw_tile[0];
+    a.ty = c->sw_tile[1];
+    a.tz = c->sw_tile[2];
+    a.flat = c->flat > 0 ? 1 : 0;
+    a.mask = c->mask;
     a.collision = c->p.collision;
     a.forced = c->forced ? 1 : 0;
     a.storage = c->storage;
@@ -1197,13 +1264,15 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info)
     info->bytes_per_pdf = c->elem;
     info->exchange_pdfs = c->exchange_pdfs;
     info->device_bytes = c->device_bytes;
-    for (int a = 0; a < 3; ++a) info->tile[a] = c->tile[a];
-    info->tiles = (long long)c->tiles.size();
+    for (int a = 0; a < 3; ++a) info->tile[a] = c->sw_tile[a];
+    info->tiles = (long long)c->stiles.size();
     info->kernel = c->kernel;
     info->stages = c->kernel == LBM_KERNEL_TMA ? tma_stages(c->storage) : 0;
+    info->flat = c->kernel != LBM_KERNEL_TMA ? c->flat : 0;
+    info->mask = c->kernel != LBM_KERNEL_TMA ? c->mask : 0;
     info->sweep_ctas = c->kernel == LBM_KERNEL_TMA ? c->tma_grid
                        : c->grid > 0                ? c->grid
-                                                    : int(c->tiles.size());
+                                                    : int(c->stiles.size());
     if (c->kernel == LBM_KERNEL_TMA) {
         info->tile[0] = c->blocks[0].nx;
         info->tile[1] = 256 / c->blocks[0].nx;
@@ -1245,15 +1314,84 @@ int lbm_profile_read(lbm_ctx *c, lbm_profile *out)
     return LBM_OK;
 }
 
+namespace {
+
+// Sweep configuration {kind, tx, ty, tz, grid, minb, zchunk, mask}: kind 0 =
+// register sweep over row tiles, 1 = TMA sweep, 2 = register sweep over runs
+// of tx consecutive cells.
+int check_cfg(lbm_ctx *c, const int *cd)
+{
+    const bool tma_ok = c->kernel == LBM_KERNEL_TMA || (c->tma_grid > 0);
+    if (cd[0] < 0 || cd[0] > 2) return fail(c, LBM_EINVAL, "sweep config: kind %d", cd[0]);
+    if (cd[0] == 1 && !tma_ok)
+        return fail(c, LBM_EINVAL, "sweep config: the TMA sweep does not apply to this context");
+    if (cd[0] == 2 && (cd[1] < 32 || cd[1] > 256 || cd[1] % 32 != 0))
+        return fail(c, LBM_EINVAL, "sweep config: runs of %d cells (32..256, multiple of 32)", cd[1]);
+    if (cd[0] == 0 && (cd[1] <= 0 || cd[2] <= 0 || cd[3] <= 0 || cd[1] % 32 != 0 || cd[1] * cd[2] > 256))
+        return fail(c, LBM_EINVAL, "sweep config: tile %dx%dx%d", cd[1], cd[2], cd[3]);
+    if (cd[0] == 1 && (cd[6] <= 0 || cd[6] > 1024)) return fail(c, LBM_EINVAL, "sweep config: zchunk %d", cd[6]);
+    if (cd[4] < 0) return fail(c, LBM_EINVAL, "sweep config: grid %d", cd[4]);
+    if (cd[5] != 3 && cd[5] != 4) return fail(c, LBM_EINVAL, "sweep config: minb %d (3 or 4)", cd[5]);
+    if (cd[7] != 0 && cd[7] != 1) return fail(c, LBM_EINVAL, "sweep config: mask %d", cd[7]);
+    return LBM_OK;
+}
+
+int apply_cfg(lbm_ctx *c, const int *cd)
+{
+    int rc = check_cfg(c, cd);
+    if (rc) return rc;
+    // the TMA sweep keeps the current register work list (used if switched back)
+    const int t[3] = {cd[0] == 1 ? c->sw_tile[0] : cd[1], cd[0] == 1 ? c->sw_tile[1] : cd[2],
+                      cd[0] == 1 ? c->sw_tile[2] : cd[3]};
+    const int flat = cd[0] == 2 ? cd[1] : (cd[0] == 1 ? c->flat : 0);
+    if ((rc = set_sweep(c, t, flat, cd[0] == 1 ? c->grid : cd[4]))) return rc;
+    c->minb = cd[5];
+    if (cd[0] == 1) c->tma_zchunk = cd[6];
+    c->mask = cd[7];
+    c->kernel = cd[0] == 1 ? LBM_KERNEL_TMA : LBM_KERNEL_REGISTER;
+    invalidate_graphs(c);
+    return LBM_OK;
+}
+
+void get_cfg(const lbm_ctx *c, int *cd)
+{
+    cd[0] = c->kernel == LBM_KERNEL_TMA ? 1 : (c->flat > 0 ? 2 : 0);
+    cd[1] = c->sw_tile[0];
+    cd[2] = c->sw_tile[1];
+    cd[3] = c->sw_tile[2];
+    cd[4] = c->grid;
+    cd[5] = c->minb;
+    cd[6] = c->tma_zchunk;
+    cd[7] = c->mask;
+}
+
+}  // namespace
+
+int lbm_get_sweep_config(lbm_ctx *c, int cfg[8])
+{
+    if (!c || !cfg) return fail(c, LBM_EINVAL, "lbm_get_sweep_config: NULL argument");
+    get_cfg(c, cfg);
+    return LBM_OK;
+}
+
+int lbm_set_sweep_config(lbm_ctx *c, const int cfg[8])
+{
+    if (!c || !cfg) return fail(c, LBM_EINVAL, "lbm_set_sweep_config: NULL argument");
+    return apply_cfg(c, cfg);
+}
+
 int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
 {
     if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
     const bool tma_ok = c->kernel == LBM_KERNEL_TMA || (c->tma_grid > 0);
     const std::string key = tune_key(c) + (tma_ok ? "|tma" : "");
-    // configuration: kind (0 register sweep, 1 TMA sweep), tx, ty, tz, grid, minb, zchunk
-    using Cfg = std::array<int, 7>;
-    Cfg best = {c->kernel == LBM_KERNEL_TMA ? 1 : 0, c->tile[0], c->tile[1], c->tile[2],
-                c->grid, c->minb, c->tma_zchunk};
+    // configuration: kind (0 register sweep over row tiles, 1 TMA sweep, 2
+    // register sweep over runs of tx consecutive cells), tx, ty, tz, grid,
+    // minb, zchunk, mask
+    using Cfg = std::array<int, 8>;
+    Cfg best;
+    get_cfg(c, best.data());
+    const int kind0 = best[0];
     bool cached = false;
     if (cache_path) {
         std::ifstream in(cache_path);
@@ -1264,22 +1402,14 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
             size_t t = line.find("\"cfg\": [");
             Cfg v;
             if (t != std::string::npos &&
-                std::sscanf(line.c_str() + t, "\"cfg\": [%d, %d, %d, %d, %d, %d, %d]", &v[0], &v[1],
-                            &v[2], &v[3], &v[4], &v[5], &v[6]) == 7) {
+                std::sscanf(line.c_str() + t, "\"cfg\": [%d, %d, %d, %d, %d, %d, %d, %d]", &v[0], &v[1],
+                            &v[2], &v[3], &v[4], &v[5], &v[6], &v[7]) == 8) {
                 best = v;
                 cached = true;
             }
         }
     }
-    auto apply = [&](const Cfg &cd) -> int {
-        int t[3] = {cd[1], cd[2], cd[3]};
-        int rc = set_tiles(c, t, cd[4]);
-        if (rc) return rc;
-        c->minb = cd[5];
-        c->tma_zchunk = cd[6];
-        c->kernel = cd[0] ? LBM_KERNEL_TMA : LBM_KERNEL_REGISTER;
-        return LBM_OK;
-    };
+    auto apply = [&](const Cfg &cd) -> int { return apply_cfg(c, cd.data()); };
     if (!cached) {
         const char *ev = std::getenv("LBM_AUTOTUNE_VERBOSE");
         const bool verbose = ev && ev[0] == '1';
@@ -1288,26 +1418,27 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         int dev = 0, sms = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int zc0 = c->tma_zchunk, m0 = c->mask;
+        const int *st = c->sw_tile;
         std::vector<Cfg> cand;
-        const int zc0 = c->tma_zchunk;
         if (tma_ok)
-            for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, c->tile[0], c->tile[1], c->tile[2], c->grid, c->minb, zc});
-        for (int mb : {3, 4})
+            for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, st[0], st[1], st[2], 0, c->minb, zc, m0});
+        for (int mb : {3, 4}) {
             for (int tx : {32, 64, 128, 256}) {
                 if (tx > std::max(32, round_up(maxnx, 32))) continue;
                 for (int th : {128, 256}) {
                     if (th < tx) continue;
-                    for (int tz : {1, 2, 4, 8, 16}) cand.push_back({0, tx, th / tx, tz, 0, mb, zc0});
+                    for (int tz : {1, 2, 4, 8}) cand.push_back({0, tx, th / tx, tz, 0, mb, zc0, m0});
                 }
             }
-        // persistent variants of the default tile
-        for (int m : {4, 8, 16}) cand.push_back({0, c->tile[0], c->tile[1], c->tile[2], m * sms, c->minb, zc0});
+            for (int th : {128, 256}) cand.push_back({2, th, 1, 1, 0, mb, zc0, m0});
+        }
+        // persistent grids over the default work list
+        for (int m : {4, 8, 16}) cand.push_back({kind0 == 2 ? 2 : 0, st[0], st[1], st[2], m * sms, c->minb, zc0, m0});
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");
-        float best_ms = 1e30f;
-        const int reps = 5;
-        for (const Cfg &cd : cand) {
+        auto time_cfg = [&](const Cfg &cd, int reps, float *ms_out) -> int {
             int rc = apply(cd);
             if (rc) return rc;
             CK(enqueue_sweep(c, c->cur), "tune");
@@ -1317,10 +1448,40 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
             CK(cudaEventSynchronize(e1), "tune sync");
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            *ms_out = ms / reps;
             if (verbose)
                 std::fprintf(stderr,
-                             "lbm_autotune: %s tile %d %d %d grid %d minb %d zchunk %d: %.4f ms/sweep\n",
-                             cd[0] ? "tma" : "reg", cd[1], cd[2], cd[3], cd[4], cd[5], cd[6], ms / reps);
+                             "lbm_autotune: %s tile %d %d %d grid %d minb %d zchunk %d mask %d: %.4f ms/sweep"
+                             " (%d reps)\n",
+                             cd[0] == 1 ? "tma" : (cd[0] == 2 ? "flat" : "rows"), cd[1], cd[2], cd[3], cd[4],
+                             cd[5], cd[6], cd[7], *ms_out, reps);
+            return LBM_OK;
+        };
+        // pass 1: every candidate, briefly
+        std::vector<std::pair<float, Cfg>> timed;
+        for (const Cfg &cd : cand) {
+            float ms = 0;
+            int rc = time_cfg(cd, 5, &ms);
+            if (rc) return rc;
+            timed.push_back({ms, cd});
+        }
+        std::sort(timed.begin(), timed.end(),
+                  [](const std::pair<float, Cfg> &x, const std::pair<float, Cfg> &y) { return x.first < y.first; });
+        // pass 2: the four fastest with both near-wall strategies, longer
+        std::vector<Cfg> fin;
+        for (size_t k = 0; k < timed.size() && k < 4; ++k) {
+            Cfg cd = timed[k].second;
+            fin.push_back(cd);
+            if (cd[0] != 1) {
+                cd[7] ^= 1;
+                fin.push_back(cd);
+            }
+        }
+        float best_ms = 1e30f;
+        for (const Cfg &cd : fin) {
+            float ms = 0;
+            int rc = time_cfg(cd, 20, &ms);
+            if (rc) return rc;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = cd;
@@ -1333,8 +1494,8 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         if (cache_path) {
             std::ofstream o(cache_path, std::ios::app);
             o << "{\"key\": \"" << key << "\", \"cfg\": [" << best[0];
-            for (int k = 1; k < 7; ++k) o << ", " << best[k];
-            o << "], \"ms_per_sweep\": " << best_ms / reps << "}\n";
+            for (int k = 1; k < 8; ++k) o << ", " << best[k];
+            o << "], \"ms_per_sweep\": " << best_ms << "}\n";
         }
     }
     int rc = apply(best);

@@ -30,6 +30,12 @@ enum : uint8_t {
     F_NEAR = 4,   // fluid cell with at least one wall / solid neighbour
 };
 
+// Link mask of a fluid cell with F_NEAR set (one uint32 per flag cell, same
+// indexing as the flags): bit q (1..18) is set when the pull source x - e_q is
+// a wall or solid cell, so that g_q comes from half-way bounce-back; bit
+// L_MOVING when at least one of those sources is a moving wall.
+constexpr uint32_t L_MOVING = 1u << 31;
+
 // Layout of a Block.  PDF planes store (ny+2)(nz+2) rows of px cells: the
 // interior x range [0, nx) padded only up to a 32-byte multiple, plus one ghost
 // row on each y and z side.  There are no x ghost columns: across x faces the
@@ -91,7 +97,8 @@ struct CollideConsts {
 };
 
 // Sweep work item: one CTA updates tx*ty*tz cells starting at (x0,y0,z0)
-// of block `block` (interior coordinates).
+// of block `block` (interior coordinates).  In the flat sweep a tile is the
+// run of tx cells of the Block starting at linear index x0 = (z ny + y) nx + x.
 struct Tile {
     int block, x0, y0, z0;
 };
@@ -119,9 +126,13 @@ struct SweepArgs {
     const BlockGeom *blocks;
     const void *consts;       // CollideConsts<T>[instances], T = double for F64 else float
     const uint8_t *flags;
+    const uint32_t *links;    // link masks of near-wall cells (flag indexing)
     const void *src;
     void *dst;
     int tx, ty, tz;
+    int flat;                 // 1: a tile is a run of tx consecutive cells of a Block in
+                              // (z, y, x) order starting at linear cell index x0
+    int mask;                 // 1: near-wall cells via link masks under a warp vote
     int collision;            // 0 BGK, 1 TRT
     int forced;               // any instance has a nonzero force
     int storage;              // LBM_F32 .. LBM_F64

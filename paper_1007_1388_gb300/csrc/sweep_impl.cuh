@@ -28,6 +28,8 @@ namespace lbm {
 // keep 38 strength-reduced 64-bit load and store addresses live, which
 // spilled at these register budgets.)
 // UNIF: a single instance whose collision constants are kernel parameters.
+// MASK: near-wall cells read precomputed link masks under a warp vote (porous
+// media, where near-wall and interior cells share warps).
 template <typename T>
 __device__ __forceinline__ const CollideConsts<T> &param_consts(const SweepArgs &a);
 template <>
@@ -41,7 +43,7 @@ __device__ __forceinline__ const CollideConsts<double> &param_consts<double>(con
     return a.kd;
 }
 
-template <int ST, int COLL, bool FORCE, int MINB, bool UNIF>
+template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     using Tr = Traits<ST>;
@@ -52,12 +54,22 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
     for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const Tile tile = a.tiles[t];
         const BlockGeom &b = a.blocks[tile.block];
-        const int x = tile.x0 + int(threadIdx.x);
-        const int y = tile.y0 + int(threadIdx.y);
         const int nx = b.nx, ny = b.ny;
-        if (x >= nx || y >= ny) continue;
-        const int z = tile.z0 + int(blockIdx.y);
-        if (z >= b.nz) continue;
+        int x, y, z;
+        if (a.flat) {
+            // a run of consecutive cells of the Block, (z, y, x) order
+            const int i = tile.x0 + int(threadIdx.x);
+            const int yz = i / nx;
+            x = i - yz * nx;
+            z = yz / ny;
+            y = yz - z * ny;
+        } else {
+            x = tile.x0 + int(threadIdx.x);
+            y = tile.y0 + int(threadIdx.y);
+            z = tile.z0 + int(blockIdx.y);
+        }
+        // no lane leaves before the warp vote below
+        const bool inside = x < nx && y < ny && z < b.nz;
         const int px = b.px;
         const int pxy = px * b.py;
         const int G = int(b.G);
@@ -75,56 +87,88 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         const int pxf = b.pxf, pxyf = b.pxf * b.py;
         const int c = (z + 1) * pxy + (y + 1) * px + x;
         const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
-        {
-            const uint8_t flag = fl[cf];
-            if (flag & F_KIND) continue;  // solid cells are not updated
-            T f[Q];
-            if (!(flag & F_NEAR)) {
+        const uint8_t flag = inside ? fl[cf] : uint8_t(F_NOSLIP);
+        const bool near = !(flag & F_KIND) && (flag & F_NEAR);
+        // MASK: warps without a near-wall lane take the plain pull; the others
+        // take one branch-free path in which each direction loads either the
+        // pulled PDF or the bounced one, as the cell's link mask says.
+        // Otherwise each lane branches on its own near-wall bit (no cost where
+        // near-wall cells fill whole warps, as along plane walls).
+        const bool take_mask = MASK ? __any_sync(0xffffffffu, near) : near;
+        if (flag & F_KIND) continue;  // solid cells (and lanes outside the Block) are not updated
+        T f[Q];
+        if (!take_mask) {
 #pragma unroll
-                for (int q = 0; q < Q; ++q) {
+            for (int q = 0; q < Q; ++q) {
+                const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+                f[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
+            }
+        } else if (!MASK) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int n = c - (ex(q) + ey(q) * px + ez(q) * pxy);
+                const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+                if (nf & F_KIND) {
+                    T v = Tr::ld(src + (opp(q) * G + c));
+                    if ((nf & F_KIND) == F_MOVING)
+                        v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
+                    f[q] = v;
+                } else {
                     const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
-                    f[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const int n = c - (ex(q) + ey(q) * px + ez(q) * pxy);
-                    const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                    if (nf & F_KIND) {
-                        T v = Tr::ld(src + (opp(q) * G + c));
-                        if ((nf & F_KIND) == F_MOVING)
-                            v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
-                        f[q] = v;
-                    } else {
-                        const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
-                        f[q] = Tr::ld(s + (q * G + n));
-                    }
+                    f[q] = Tr::ld(s + (q * G + n));
                 }
             }
-            if (UNIF)
-                collide_v<COLL, FORCE>(f, KR);
-            else
-                collide_v<COLL, FORCE>(f, KP);
+        } else {
+            const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
+            const bool mv = (lm & L_MOVING) != 0;
+            f[0] = Tr::ld(src + c);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
+            for (int q = 1; q < Q; ++q) {
+                const bool bq = (lm >> q) & 1u;
+                const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+                const S *pa = bq ? src + (opp(q) * G + c)
+                                 : s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy));
+                T v = Tr::ld(pa);
+                if (mv && bq) {
+                    const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+                    if ((nf & F_KIND) == F_MOVING)
+                        v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
+                }
+                f[q] = v;
+            }
         }
+        if (UNIF)
+            collide_v<COLL, FORCE>(f, KR);
+        else
+            collide_v<COLL, FORCE>(f, KP);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
+    }
+}
+
+template <int ST, int MINB, bool UNIF, bool MASK>
+void launch_sweep_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (a.collision == 0) {
+        if (a.forced)
+            sweep_kernel<ST, 0, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+        else
+            sweep_kernel<ST, 0, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.forced)
+            sweep_kernel<ST, 1, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+        else
+            sweep_kernel<ST, 1, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
     }
 }
 
 template <int ST, int MINB, bool UNIF>
 void launch_sweep_unif(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
-    if (a.collision == 0) {
-        if (a.forced)
-            sweep_kernel<ST, 0, true, MINB, UNIF><<<grid, block, 0, s>>>(a);
-        else
-            sweep_kernel<ST, 0, false, MINB, UNIF><<<grid, block, 0, s>>>(a);
-    } else {
-        if (a.forced)
-            sweep_kernel<ST, 1, true, MINB, UNIF><<<grid, block, 0, s>>>(a);
-        else
-            sweep_kernel<ST, 1, false, MINB, UNIF><<<grid, block, 0, s>>>(a);
-    }
+    if (a.mask)
+        launch_sweep_mask<ST, MINB, UNIF, true>(a, grid, block, s);
+    else
+        launch_sweep_mask<ST, MINB, UNIF, false>(a, grid, block, s);
 }
 
 template <int ST, int MINB>
@@ -139,6 +183,9 @@ void launch_sweep_minb(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s
 template <int ST>
 cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
 {
+    // every warp must be full: the sweep votes across its 32 lanes
+    if ((a.tx * a.ty) % 32 != 0 || a.tx * a.ty > 256 || (a.flat && (a.ty != 1 || a.tz != 1)))
+        return cudaErrorInvalidConfiguration;
     dim3 block(a.tx, a.ty, 1);
     const unsigned gx = unsigned(a.grid > 0 ? a.grid : a.ntiles);
     if (gx == 0) return cudaSuccess;

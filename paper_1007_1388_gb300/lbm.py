@@ -65,6 +65,8 @@ class lbm_info(ctypes.Structure):
         ("kernel", ctypes.c_int),
         ("sweep_ctas", ctypes.c_int),
         ("stages", ctypes.c_int),
+        ("flat", ctypes.c_int),
+        ("mask", ctypes.c_int),
     ]
 
 
@@ -103,6 +105,8 @@ SIGNATURES = {
     "lbm_profile_enable": ([_vp, _i], _i),
     "lbm_profile_read": ([_vp, _P(lbm_profile)], _i),
     "lbm_autotune": ([_vp, ctypes.c_char_p, _P(ctypes.c_int)], _i),
+    "lbm_get_sweep_config": ([_vp, _P(ctypes.c_int)], _i),
+    "lbm_set_sweep_config": ([_vp, _P(ctypes.c_int)], _i),
     "lbm_set_allocator": ([ALLOC_FN, FREE_FN, _vp], _i),
     "lbm_directions": ([_P(ctypes.c_int), _P(_d), _P(ctypes.c_int)], _i),
     "lbm_invariants_noalloc": ([_vp, _vp, _ll, _d, _P(_d), _vp, _vp], _i),
@@ -376,6 +380,21 @@ def lbm_autotune(ctx: Ctx, cache_path: str | None = None):
     best = (ctypes.c_int * 3)()
     _check(lib().lbm_autotune(ctx.ptr, cache_path.encode() if cache_path else None, best), ctx)
     return tuple(best)
+
+
+SWEEP_ROWS, SWEEP_TMA, SWEEP_RUNS = 0, 1, 2
+
+
+def lbm_get_sweep_config(ctx: Ctx):
+    """{kind, tx, ty, tz, grid, minb, zchunk, mask} of the sweep in use."""
+    cfg = (ctypes.c_int * 8)()
+    _check(lib().lbm_get_sweep_config(ctx.ptr, cfg), ctx)
+    return tuple(cfg)
+
+
+def lbm_set_sweep_config(ctx: Ctx, cfg):
+    c = (ctypes.c_int * 8)(*[int(v) for v in cfg])
+    _check(lib().lbm_set_sweep_config(ctx.ptr, c), ctx)
 
 
 def lbm_directions():

@@ -51,38 +51,45 @@ def sphere_packing(rng: np.random.Generator, dims, porosity, rmin=2, rmax=6, max
     Integer radii uniform in [rmin, rmax]; centres uniform; a sphere is
     rejected when it overlaps another (periodic distance along x and z).
     Spheres are added until the solid fraction reaches 1 - porosity or
-    max_failures consecutive draws were rejected.
+    max_failures consecutive draws were rejected.  A cell is solid when its
+    centre lies inside a sphere (distance <= r, periodic along x and z).
     """
     nx, ny, nz = dims
     flags = np.zeros((nz, ny, nx), np.uint8)
-    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     target = (1.0 - porosity) * nx * ny * nz
-    spheres = []
+    cen = np.zeros((0, 3))
+    rad = np.zeros(0)
     fails = 0
     solid = 0
     while solid < target and fails < max_failures:
         r = int(rng.integers(rmin, rmax + 1))
         c = rng.uniform([0, 0, 0], [nx, ny, nz])
-        ok = True
-        for (c2, r2) in spheres:
-            d = np.abs(c - c2)
-            d[0] = min(d[0], nx - d[0])
-            d[2] = min(d[2], nz - d[2])
-            if np.sqrt((d * d).sum()) < r + r2:
-                ok = False
-                break
-        if not ok:
-            fails += 1
-            continue
+        if len(rad):
+            d = np.abs(cen - c)
+            d[:, 0] = np.minimum(d[:, 0], nx - d[:, 0])
+            d[:, 2] = np.minimum(d[:, 2], nz - d[:, 2])
+            if np.any(np.sqrt((d * d).sum(axis=1)) < r + rad):
+                fails += 1
+                continue
         fails = 0
-        spheres.append((c, r))
-        dx = np.abs(x + 0.5 - c[0])
+        cen = np.vstack([cen, c])
+        rad = np.append(rad, r)
+        # stamp the sphere over its bounding box only (wrapped along x and z)
+        xs = np.arange(int(np.floor(c[0] - r - 1)), int(np.ceil(c[0] + r + 1)) + 1)
+        ys = np.arange(max(0, int(np.floor(c[1] - r - 1))), min(ny, int(np.ceil(c[1] + r + 1)) + 1))
+        zs = np.arange(int(np.floor(c[2] - r - 1)), int(np.ceil(c[2] + r + 1)) + 1)
+        xs = np.unique(xs % nx)
+        zs = np.unique(zs % nz)
+        dx = np.abs(xs + 0.5 - c[0])
         dx = np.minimum(dx, nx - dx)
-        dz = np.abs(z + 0.5 - c[2])
+        dz = np.abs(zs + 0.5 - c[2])
         dz = np.minimum(dz, nz - dz)
-        dy = y + 0.5 - c[1]
-        flags[dx * dx + dy * dy + dz * dz <= r * r] = NOSLIP
-        solid = int((flags != FLUID).sum())
+        dy = ys + 0.5 - c[1]
+        inside = (dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2) <= r * r
+        sub = flags[np.ix_(zs, ys, xs)]
+        solid += int(np.count_nonzero(inside & (sub == FLUID)))
+        sub[inside] = NOSLIP
+        flags[np.ix_(zs, ys, xs)] = sub
     return flags
 
 

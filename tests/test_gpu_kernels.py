@@ -4,7 +4,11 @@
   widths 32, 64 and 128; FP32, F16S and BF16S storage; BGK and TRT; forced;
   obstacles and moving walls);
 - a TMA sweep whose staged data never arrives reports LBM_ETIMEOUT through
-  its bounded waits instead of hanging, and the library stays usable.
+  its bounded waits instead of hanging, and the library stays usable;
+- the register sweep's variants (row tiles, runs of consecutive cells,
+  persistent grids, register budgets, near-wall cells by per-lane branch or by
+  link masks under a warp vote) are bitwise equal on ragged, walled, porous
+  and batched geometries.
 """
 import numpy as np
 import pytest
@@ -85,3 +89,77 @@ def test_tma_sweep_bounded_wait_reports_timeout(L):
     # the device and the library remain usable
     f, info = _run(L, dims, dims, 0.8, None, 5, periodic=(1, 1, 1), kernel=L.LBM_KERNEL_TMA)
     assert info.kernel == L.LBM_KERNEL_TMA and np.all(f == 0.0)
+
+
+# -------------------------------------------------- register sweep variants
+def _configs(L, bx):
+    """Row tiles, runs of consecutive cells, persistent grids, both register
+    budgets and both near-wall strategies."""
+    R, U = L.SWEEP_ROWS, L.SWEEP_RUNS
+    out = [(R, 32, 4, 1, 0, 4, 8, 0), (R, 32, 8, 2, 0, 3, 8, 1), (U, 256, 1, 1, 0, 4, 8, 0),
+           (U, 128, 1, 1, 0, 3, 8, 1), (U, 256, 1, 1, 304, 4, 8, 1), (R, 32, 4, 2, 152, 3, 8, 0)]
+    if bx >= 64:
+        out.append((R, 64, 4, 4, 0, 4, 8, 1))
+    return out
+
+
+def _run_cfg(L, ctx, f0, steps, cfg):
+    if cfg is not None:
+        L.lbm_set_sweep_config(ctx, cfg)
+        assert tuple(L.lbm_get_sweep_config(ctx)) == tuple(cfg)
+    L.lbm_set_pdfs(ctx, f0)
+    L.lbm_step(ctx, steps)
+    return L.lbm_get_pdfs(ctx)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_sweep_variants_bitwise_single_patch(L, storage):
+    """A ragged Patch (Block width 40) with obstacles, moving walls and force."""
+    rng = np.random.default_rng(71 + storage)
+    dims, bd = (80, 24, 20), (40, 12, 10)
+    flags = W.random_flags(rng, dims, 0.15)
+    f0 = W.random_pdfs(rng, dims, 1e-2, flags)
+    for coll in (0, 1):
+        p = L.make_params(collision=coll, force=(2e-5, 0, 1e-5), wall_u=(0.04, 0, 0.01),
+                          periodic=(1, 0, 0), face_bc=(1, 1, 1, 2, 1, 1), storage=storage,
+                          storage_scale=(256.0 if storage == 1 else 1.0))
+        ctx = L.lbm_create(dims, bd, 0.62, flags, p)
+        info = L.lbm_get_info(ctx)
+        assert info.flat == 256  # the default for Blocks that are not a warp multiple wide
+        ref = _run_cfg(L, ctx, f0, 17, None)
+        for cfg in _configs(L, bd[0]):
+            got = _run_cfg(L, ctx, f0, 17, cfg)
+            assert np.array_equal(ref, got), (coll, cfg, np.abs(ref - got).max())
+        ctx.destroy()
+
+
+def test_sweep_variants_bitwise_batch(L):
+    """Uneven sphere-packed channels in one batch."""
+    rng = np.random.default_rng(5)
+    inst = []
+    for _ in range(4):
+        dims = tuple(int(v) for v in rng.integers(10, 45, 3))
+        inst.append((dims, float(rng.uniform(0.55, 1.2)), W.sphere_packing(rng, dims, 0.75, 2, 4)))
+    p = L.make_params(force=(1e-4, 0, 0), **W.channel_bc())
+    ctx = L.lbm_batch_create([d for d, _, _ in inst], [t for _, t, _ in inst],
+                             [f for _, _, f in inst], p)
+    assert L.lbm_get_info(ctx).mask == 1  # sphere packings: many near-wall cells
+    f0 = np.concatenate([W.random_pdfs(rng, d, 1e-2, f).reshape(-1) for d, _, f in inst])
+    ref = _run_cfg(L, ctx, f0, 13, None)
+    for cfg in _configs(L, 32):
+        got = _run_cfg(L, ctx, f0, 13, cfg)
+        assert np.array_equal(ref, got), (cfg, np.abs(ref - got).max())
+    ctx.destroy()
+
+
+def test_sweep_config_validation(L):
+    # 40 cells wide: the TMA sweep does not apply, so kind 1 is invalid too
+    ctx = L.lbm_create((40, 16, 8), (40, 16, 8), 0.7, None, L.make_params())
+    before = L.lbm_get_sweep_config(ctx)
+    for bad in [(3, 32, 4, 1, 0, 4, 8, 0), (0, 48, 4, 1, 0, 4, 8, 0), (0, 32, 16, 1, 0, 4, 8, 0),
+                (2, 100, 1, 1, 0, 4, 8, 0), (0, 32, 4, 1, -1, 4, 8, 0), (0, 32, 4, 1, 0, 5, 8, 0),
+                (0, 32, 4, 1, 0, 4, 8, 2), (1, 32, 4, 1, 0, 4, 8, 0)]:
+        with pytest.raises(L.LBMError):
+            L.lbm_set_sweep_config(ctx, bad)
+        assert L.lbm_get_sweep_config(ctx) == before
+    ctx.destroy()

@@ -304,3 +304,22 @@ def test_residual_definition(orc):
     assert abs(orc.residual(p, np.zeros_like(a), a) - 1.0) < 1e-15
     # u_prev = u_cur / 2 -> 1/2
     assert abs(orc.residual(p, a / 2, a) - 0.5) < 1e-15
+
+
+def test_threaded_step_is_identical(orc):
+    """The OpenMP split over z planes changes no result bit."""
+    from paper_1007_1388_gb300 import workloads as W
+
+    rng = np.random.default_rng(44)
+    dims = (9, 7, 11)
+    flags = W.random_flags(rng, dims, 0.2)
+    p = orc.Problem(dims=dims, tau=0.7, flags=flags, collision=orc.TRT,
+                    wall_u=(0.05, 0, 0.01), force=(1e-4, -2e-5, 0))
+    f = W.random_pdfs(rng, dims, 1e-2, flags)
+    a = orc.run(p, f, 5)
+    orc.set_threads(4)
+    try:
+        b = orc.run(p, f, 5)
+    finally:
+        orc.set_threads(1)
+    assert np.array_equal(a, b)
