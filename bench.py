@@ -191,6 +191,11 @@ def run_gpu(args):
             torch.cuda.synchronize()
 
     n, b = args.size, args.block
+    if args.batch_only:
+        out = _batch_variants(args, L, W, barrier, torch)
+        if rank == 0:
+            print(json.dumps({"report": "batch", "batch": out}))
+        return 0
 
     def make(storage=L.LBM_F32, coll=L.LBM_BGK, **extra):
         p = L.make_params(collision=coll, force=(args.force, 0, 0), storage=storage,
@@ -359,7 +364,8 @@ def _batch_variants(args, L, W, barrier, torch):
     for name, kw in [("f32", {}), ("f16s", dict(storage=L.LBM_F16S, storage_scale=256.0))]:
         p = L.make_params(collision=L.LBM_BGK, force=(BATCH_FORCE, 0, 0), **W.channel_bc(), **kw)
         ctx = L.lbm_batch_create(dims, taus, flags, p)
-        L.lbm_autotune(ctx, None)
+        if not args.no_autotune:
+            L.lbm_autotune(ctx, None)
         info = L.lbm_get_info(ctx)
         L.lbm_step(ctx, 10)
         barrier()
@@ -385,6 +391,9 @@ def _batch_variants(args, L, W, barrier, torch):
         res["sweep_gbs"] = BYTES_PER_LUP[st] * info.cells / (sw * 1e-3) / 1e9
         res["launches_per_step"] = (pr.sweep_launches + pr.exchange_launches) / 20
         ctx.destroy()
+        out[name] = res
+        if args.batch_no_separate:
+            continue
         # the same instances, one context (and stream) each
         ctxs = [L.lbm_create(d, d, t, f, p) for d, t, f in inst]
         for c in ctxs:
@@ -399,7 +408,6 @@ def _batch_variants(args, L, W, barrier, torch):
         res["batched_over_separate"] = res["mlups"] / res["separate_mlups"]
         for c in ctxs:
             c.destroy()
-        out[name] = res
     return out
 
 
@@ -492,6 +500,9 @@ def main():
     ap.add_argument("--report-block", type=int, default=128)
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--batch-only", action="store_true", help="only the batched workload (one JSON line)")
+    ap.add_argument("--batch-no-separate", action="store_true",
+                    help="skip the one-context-per-instance comparison")
     ap.add_argument("--size", type=int, default=N, help="cells per axis (profiling runs use less)")
     ap.add_argument("--block", type=int, default=B, help="cells per Block along each axis")
     ap.add_argument("--storage", default="", help="f32 | f16s | bf16s | f64 (default f32)")

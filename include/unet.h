@@ -1,0 +1,114 @@
+/*
+ * unet.h - C ABI of the learned warm start (liblbm.so).
+ *
+ * Not in the paper.  A 3-D U-Net predicts, from a channel's solid-flag field
+ * and its driving force, the steady (delta rho, u) that the lattice
+ * Boltzmann sweep of Sec. 2.1 converges to; the solver is then initialised
+ * at that equilibrium (lbm_init_equilibrium) instead of at rest.  The
+ * network's convolutions run on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation in TMEM); everything else in the forward and backward
+ * passes, the loss and the Adam update run in the library's own CUDA
+ * kernels.  Master parameters, gradients and optimiser state are FP32.
+ *
+ * Network (channels-last activations, n^3 voxels per sample, n a power of
+ * two from 16 to 128; x fastest, then y, then z, then the sample):
+ *   e1 = relu(conv(relu(conv(x, W1a)), W1b))              2 -> 16 -> 16   n^3
+ *   e2 = relu(conv(relu(conv(pool(e1), W2a)), W2b))      16 -> 32 -> 32   (n/2)^3
+ *   e3 = relu(conv(relu(conv(pool(e2), W3a)), W3b))      32 -> 64 -> 64   (n/4)^3
+ *   d2 = relu(conv(relu(conv([up(e3), e2], W4a)), W4b))  96 -> 32 -> 32   (n/2)^3
+ *   d1 = relu(conv(relu(conv([up(d2), e1], W5a)), W5b))  48 -> 16 -> 16   n^3
+ *   y  = d1 Wh^T + bh                                     16 -> 4
+ * conv: 3x3x3 with bias, periodic along x and z, zero padding along y (the
+ * channel's walls); pool: 2x2x2 average; up: nearest 2x; [a, b]: channel
+ * concatenation.  Input channels: solid flag (1 solid, 0 fluid) and the
+ * sample's normalised force; output channels: the four normalised fields.
+ * Loss: mean over voxels and channels of (y - target)^2.
+ *
+ * Parameters in canonical order (unet_param_count floats): for each
+ * convolution W1a, W1b, W2a, W2b, W3a, W3b, W4a, W4b, W5a, W5b its weight
+ * [cout][27][cin] (tap t = 9(dz+1) + 3(dy+1) + (dx+1)) then its bias [cout];
+ * then Wh [4][16] and bh [4].
+ *
+ * Status codes are those of lbm.h.  Every call is asynchronous on the
+ * context's stream unless stated; host outputs synchronise.  One context is
+ * used by one thread at a time.
+ */
+#ifndef UNET_H
+#define UNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct unet_ctx unet_ctx;
+
+/* Number of FP32 parameters in canonical order. */
+long long unet_param_count(void);
+
+/*
+ * unet_create - a network for batches of nb samples of n^3 voxels.  Weights:
+ * He-normal from `seed` (counter-based, reproducible), biases 0; Adam state 0.
+ * stream: a cudaStream_t to run on, or NULL for a library-owned stream.
+ * Device memory comes from the lbm_set_allocator hooks.  LBM_EINVAL for n not
+ * a power of two in [16, 128] or nb < 1.
+ */
+int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx **out);
+void unet_destroy(unet_ctx *ctx);
+
+/* Parameters / Adam step counter: host FP32 arrays of unet_param_count(). */
+int unet_get_params(unet_ctx *ctx, float *host);
+int unet_set_params(unet_ctx *ctx, const float *host);
+
+/*
+ * unet_predict - forward pass.  solid: device uint8 [nb][n^3] (nonzero =
+ * solid); force: host float [nb] (normalised force of each sample); out:
+ * device float [nb][n^3][4].
+ */
+int unet_predict(unet_ctx *ctx, const uint8_t *solid, const float *force, float *out);
+
+/*
+ * unet_loss_grad - forward and backward pass for the device target
+ * [nb][n^3][4]: *loss (host) receives the loss; the gradients stay on the
+ * device for unet_adam_step, and grad_host (may be NULL) receives a copy in
+ * canonical order.  Synchronises.
+ */
+int unet_loss_grad(unet_ctx *ctx, const uint8_t *solid, const float *force, const float *target, double *loss,
+                   float *grad_host);
+
+/* One Adam update with the last gradients (bias-corrected, FP32). */
+int unet_adam_step(unet_ctx *ctx, float lr, float beta1, float beta2, float eps);
+
+/* Message of the last failed call on ctx (or of unet_create when ctx is NULL). */
+const char *unet_last_error(const unet_ctx *ctx);
+
+/*
+ * Layer-level entry points on caller-owned device buffers (bf16 =
+ * __nv_bfloat16 bits), for tests and for users composing their own networks.
+ * Grid: nb grids of 2^lz x 2^ly x 2^lx voxels.
+ *
+ * unet_conv3 - out[m][co] = act(bias[co] + sum_t sum_ci in[m + off_t][ci] w[co][t][ci])
+ * with in = [src0, src1] (channels c0 + c1, multiples of 16; c1 may be 0 and
+ * src1 NULL); up0 = 1: src0 is stored at half resolution and read through
+ * nearest-neighbour upsampling.  w bf16 [cout][27][c0 + c1]; bias fp32 or
+ * NULL; out bf16 (out_f32 = 0) or fp32 [M][cout]; relu 0/1; cout a multiple of
+ * 16 up to 128.  Periodic along x and z, zero padding along y.
+ */
+int unet_conv3(const void *src0, int c0, int up0, const void *src1, int c1, const void *w, const float *bias,
+               void *out, int out_f32, int relu, int cout, int nb, int lz, int ly, int lx, void *stream);
+
+/*
+ * unet_conv3_wgrad - dw[co][t][ci] = sum_m dy[m][co] in[m + off_t][ci] for the
+ * same convolution (dy bf16 [M][cout]; dw fp32 [cout][27][c0 + c1]).  Uses a
+ * temporary workspace from the allocator hooks; synchronises the stream.
+ */
+int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1, const void *dy, int cout,
+                     float *dw, int nb, int lz, int ly, int lx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UNET_H */

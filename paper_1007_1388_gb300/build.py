@@ -33,7 +33,7 @@ def _sources():
 
 def _headers():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + \
-        [os.path.join(ROOT, "include", "lbm.h")]
+        [os.path.join(ROOT, "include", h) for h in ("lbm.h", "unet.h")]
 
 
 def _stale(target: str, deps) -> bool:

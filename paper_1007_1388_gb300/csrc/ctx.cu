@@ -18,6 +18,7 @@
 #include <cstring>
 #include <fstream>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <sstream>
 #include <string>
@@ -40,6 +41,7 @@ struct Allocator {
 };
 Allocator g_alloc;
 thread_local std::string g_create_error;
+std::mutex g_alloc_mu;
 
 struct DevMem {
     void *ptr = nullptr;
@@ -47,6 +49,16 @@ struct DevMem {
 };
 
 }  // namespace
+
+namespace lbm {
+void current_allocator(lbm_alloc_fn *alloc, lbm_free_fn *release, void **user)
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    *alloc = g_alloc.alloc;
+    *release = g_alloc.release;
+    *user = g_alloc.user;
+}
+}  // namespace lbm
 
 struct lbm_ctx {
     // configuration
@@ -1006,7 +1018,10 @@ static int create_common(const std::vector<InstSpec> &inst, const lbm_params *pi
     lbm_ctx *c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(nullptr, LBM_ENOMEM, "out of host memory");
     c->p = p;
-    c->alloc = g_alloc;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        c->alloc = g_alloc;
+    }
     int rc;
     try {
         rc = build_context(c, inst);
@@ -1511,6 +1526,7 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn release, void *user)
 {
     if ((alloc == nullptr) != (release == nullptr))
         return fail(nullptr, LBM_EINVAL, "alloc and release must both be given or both be NULL");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
     g_alloc.alloc = alloc;
     g_alloc.release = release;
     g_alloc.user = user;

@@ -116,6 +116,10 @@ struct XSlab {
 // Sets the calling thread's message for lbm_last_error(NULL).
 void set_global_error(const char *msg);
 
+// The device allocator hooks in effect (lbm_set_allocator; NULL = cudaMalloc).
+void current_allocator(void *(**alloc)(size_t, void *, void *), void (**release)(void *, size_t, void *, void *),
+                       void **user);
+
 // Reduction outputs per tile / instance.
 enum { R_DRHO = 0, R_JX, R_JY, R_JZ, R_NFLUID, R_NONFINITE, R_DU2, R_U2, R_K };
 

@@ -1,0 +1,819 @@
+// The learned warm start's U-Net: element-wise kernels, the forward /
+// backward orchestration and the C ABI of include/unet.h.  The 3x3x3
+// convolutions (the contractions) run on the tensor cores (unet_conv.cu);
+// pooling, upsampling adjoints, ReLU masks, bias sums, the 1x1x1 head, the
+// loss and Adam are the element-wise kernels below.  Activations are bf16
+// channels-last; gradients of activations FP32 until they feed a
+// convolution, where they are rounded to bf16.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "unet.h"
+#include "unet_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int EW = 256;
+
+__host__ __device__ inline int ilog2(long long v)
+{
+    int l = 0;
+    while ((1ll << l) < v) ++l;
+    return l;
+}
+
+// x[m] = {solid, force of the sample, 0, ..., 0} (16 channels)
+__global__ void make_input_kernel(const uint8_t *__restrict__ solid, const float *__restrict__ force,
+                                  bf16 *__restrict__ x, long long V, int lvox)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V) return;
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+    v[0] = __float2bfloat16(solid[i] ? 1.f : 0.f);
+    v[1] = __float2bfloat16(force[i >> lvox]);
+    uint4 *o = reinterpret_cast<uint4 *>(x + i * 16);
+    o[0] = reinterpret_cast<const uint4 *>(v)[0];
+    o[1] = reinterpret_cast<const uint4 *>(v)[1];
+}
+
+// Coordinates of voxel m in grid g, and the index of voxel (b, z, y, x).
+__device__ __forceinline__ void coords(long long m, const VGrid &g, int &b, int &z, int &y, int &x)
+{
+    x = int(m & ((1ll << g.lx) - 1));
+    y = int((m >> g.lx) & ((1ll << g.ly) - 1));
+    z = int((m >> (g.lx + g.ly)) & ((1ll << g.lz) - 1));
+    b = int(m >> (g.lx + g.ly + g.lz));
+}
+__device__ __forceinline__ long long vidx(const VGrid &g, int b, int z, int y, int x)
+{
+    return ((((long long)b << g.lz) + z) << (g.ly + g.lx)) + ((long long)y << g.lx) + x;
+}
+
+// 2x2x2 average: out (grid gh) from in (grid 2 gh), C channels
+__global__ void pool_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ out, VGrid gh, int C)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= gh.voxels() * C) return;
+    const long long p = i / C;
+    const int c = int(i - p * C);
+    int b, z, y, x;
+    coords(p, gh, b, z, y, x);
+    const VGrid gf{gh.nb, gh.lz + 1, gh.ly + 1, gh.lx + 1};
+    float s = 0.f;
+    for (int d = 0; d < 8; ++d)
+        s += __bfloat162float(in[vidx(gf, b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1)) * C + c]);
+    out[i] = __float2bfloat16(0.125f * s);
+}
+
+// dy = bf16(g * (y > 0)); per-block channel sums of g * (y > 0) (bias gradient).
+// blockDim = EW (a multiple of C), grid-stride with a stride that is a
+// multiple of C, so each thread keeps one channel.
+__global__ void relu_bwd_kernel(const float *__restrict__ g, const bf16 *__restrict__ y, bf16 *__restrict__ dy,
+                                float *__restrict__ part, long long n, int C)
+{
+    __shared__ float sh[EW];
+    float acc = 0.f;
+    for (long long i = (long long)blockIdx.x * EW + threadIdx.x; i < n; i += (long long)gridDim.x * EW) {
+        const float v = __bfloat162float(y[i]) > 0.f ? g[i] : 0.f;
+        dy[i] = __float2bfloat16(v);
+        acc += v;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float s = 0.f;
+        for (int k = threadIdx.x; k < EW; k += C) s += sh[k];
+        part[(long long)blockIdx.x * C + threadIdx.x] = s;
+    }
+}
+
+// out[c] (+)= sum over rows (in order) of part[row][c]
+__global__ void reduce_cols_kernel(const float *__restrict__ part, int rows, int C, float *__restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += part[(long long)r * C + c];
+    out[c] = s;
+}
+
+// adjoint of nearest upsampling of the first c0 channels of a concatenation:
+// gu[p][c] = sum over the 8 children v of p of gcat[v][c]  (gu on grid gh)
+__global__ void up_bwd_kernel(const float *__restrict__ gcat, int ctot, int c0, float *__restrict__ gu, VGrid gh)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= gh.voxels() * c0) return;
+    const long long p = i / c0;
+    const int c = int(i - p * c0);
+    int b, z, y, x;
+    coords(p, gh, b, z, y, x);
+    const VGrid gf{gh.nb, gh.lz + 1, gh.ly + 1, gh.lx + 1};
+    float s = 0.f;
+    for (int d = 0; d < 8; ++d)
+        s += gcat[vidx(gf, b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1)) * ctot + c];
+    gu[i] = s;
+}
+
+// ge[v][c] = gcat[v][c0 + c] + gp[parent(v)][c] / 8: the skip connection's
+// share of a concatenation gradient plus the adjoint of the 2x2x2 average
+__global__ void skip_pool_kernel(const float *__restrict__ gcat, int ctot, int c0, const float *__restrict__ gp,
+                                 float *__restrict__ ge, VGrid gf, int C)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= gf.voxels() * C) return;
+    const long long v = i / C;
+    const int c = int(i - v * C);
+    int b, z, y, x;
+    coords(v, gf, b, z, y, x);
+    const VGrid gh{gf.nb, gf.lz - 1, gf.ly - 1, gf.lx - 1};
+    ge[i] = gcat[v * ctot + c0 + c] + 0.125f * gp[vidx(gh, b, z >> 1, y >> 1, x >> 1) * C + c];
+}
+
+// 1x1x1 head y = d1 Wh^T + bh; with a target: loss partials, the gradient
+// g_d1 = gy Wh (gy = 2 (y - target) / (V 4)), and partials of dWh (4 x 16),
+// dbh (4) and the loss: part[block][72] = {dWh[64], dbh[4], sum of squared
+// differences, 3 unused}.
+constexpr int HEAD_PART = 72;
+__global__ void head_kernel(const bf16 *__restrict__ d1, const float *__restrict__ Wh, const float *__restrict__ bh,
+                            const float *__restrict__ target, float *__restrict__ out, float *__restrict__ gd1,
+                            float *__restrict__ part, long long V)
+{
+    __shared__ float sw[64], sb[4];
+    __shared__ float red[EW / 32][HEAD_PART];
+    if (threadIdx.x < 64) sw[threadIdx.x] = Wh[threadIdx.x];
+    if (threadIdx.x < 4) sb[threadIdx.x] = bh[threadIdx.x];
+    __syncthreads();
+    float acc[HEAD_PART];
+#pragma unroll
+    for (int k = 0; k < HEAD_PART; ++k) acc[k] = 0.f;
+    const float gscale = 2.f / float(V * 4);
+    for (long long m = (long long)blockIdx.x * EW + threadIdx.x; m < V; m += (long long)gridDim.x * EW) {
+        __align__(16) bf16 h[16];
+        reinterpret_cast<uint4 *>(h)[0] = reinterpret_cast<const uint4 *>(d1 + m * 16)[0];
+        reinterpret_cast<uint4 *>(h)[1] = reinterpret_cast<const uint4 *>(d1 + m * 16)[1];
+        float a[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = __bfloat162float(h[k]);
+        float y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float s = sb[j];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) s = fmaf(sw[j * 16 + k], a[k], s);
+            y[j] = s;
+        }
+        if (out)
+            reinterpret_cast<float4 *>(out)[m] = make_float4(y[0], y[1], y[2], y[3]);
+        if (target) {
+            const float4 t4 = reinterpret_cast<const float4 *>(target)[m];
+            const float t[4] = {t4.x, t4.y, t4.z, t4.w};
+            float gy[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float d = y[j] - t[j];
+                acc[68] = fmaf(d, d, acc[68]);
+                gy[j] = gscale * d;
+                acc[64 + j] += gy[j];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) acc[j * 16 + k] = fmaf(gy[j], a[k], acc[j * 16 + k]);
+            }
+            float g[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) s = fmaf(gy[j], sw[j * 16 + k], s);
+                g[k] = s;
+            }
+            float4 *o = reinterpret_cast<float4 *>(gd1 + m * 16);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = make_float4(g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
+        }
+    }
+    if (!target || !part) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < HEAD_PART; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < HEAD_PART) {
+        float s = 0.f;
+        for (int w = 0; w < EW / 32; ++w) s += red[w][threadIdx.x];
+        part[(long long)blockIdx.x * HEAD_PART + threadIdx.x] = s;
+    }
+}
+
+// bf16 copies of one convolution's FP32 weight [cout][27][cin]:
+// wf [cout][27][cinp] (zero channels beyond cin) and, when wb is given, the
+// tap-flipped transpose wb [cin][27][cout], wb[ci][t][co] = W[co][26 - t][ci]
+// (the backward-data convolution).
+__global__ void prep_weights_kernel(const float *__restrict__ W, int cout, int cin, int cinp, bf16 *__restrict__ wf,
+                                    bf16 *__restrict__ wb)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)cout * 27 * cinp) return;
+    const int ci = int(i % cinp);
+    const long long r = i / cinp;
+    const int t = int(r % 27), co = int(r / 27);
+    const float w = ci < cin ? W[((long long)co * 27 + t) * cin + ci] : 0.f;
+    wf[i] = __float2bfloat16(w);
+    if (wb && ci < cin) wb[((long long)ci * 27 + (26 - t)) * cout + co] = __float2bfloat16(w);
+}
+
+// dw [cout][27][cin] from the padded weight gradient [cout][27][cinp]
+__global__ void unpad_grad_kernel(const float *__restrict__ src, int cout, int cin, int cinp, float *__restrict__ dst)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)cout * 27 * cin) return;
+    const int ci = int(i % cin);
+    const long long r = i / cin;
+    dst[i] = src[r * cinp + ci];
+}
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// The ten 3x3x3 convolutions in forward order (name, cin, cout).
+struct ConvSpec {
+    int cin, cout;
+};
+constexpr int NCONV = 10;
+constexpr ConvSpec kConv[NCONV] = {{2, 16},  {16, 16}, {16, 32}, {32, 32}, {32, 64},
+                                   {64, 64}, {96, 32}, {32, 32}, {48, 16}, {16, 16}};
+enum { W1A, W1B, W2A, W2B, W3A, W3B, W4A, W4B, W5A, W5B };
+
+struct Layout {
+    long long w[NCONV], b[NCONV], wh, bh, total;
+    Layout()
+    {
+        long long o = 0;
+        for (int k = 0; k < NCONV; ++k) {
+            w[k] = o;
+            o += 27ll * kConv[k].cin * kConv[k].cout;
+            b[k] = o;
+            o += kConv[k].cout;
+        }
+        wh = o;
+        o += 64;
+        bh = o;
+        o += 4;
+        total = o;
+    }
+};
+const Layout kLayout;
+
+int cin_padded(int k) { return kConv[k].cin < 16 ? 16 : kConv[k].cin; }
+
+// counter-based normal numbers: SplitMix64 of (seed, index), Box-Muller
+uint64_t splitmix(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double normal(uint64_t seed, uint64_t i)
+{
+    const uint64_t a = splitmix(seed * 0x100000001B3ull + 2 * i), b = splitmix(seed * 0x100000001B3ull + 2 * i + 1);
+    const double u1 = (double(a >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = double(b >> 11) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct unet_ctx {
+    int n = 0, nb = 0;
+    VGrid g1{}, g2{}, g3{};
+    long long V1 = 0, V2 = 0, V3 = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *(*alloc)(size_t, void *, void *) = nullptr;
+    void (*release)(void *, size_t, void *, void *) = nullptr;
+    void *user = nullptr;
+    std::vector<std::pair<void *, size_t>> owned;
+    float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
+    long long step = 0;
+    bf16 *wf[NCONV] = {}, *wb[NCONV] = {};
+    bool weights_current = false;
+    bf16 *x = nullptr, *e1h = nullptr, *e1 = nullptr, *p1 = nullptr, *e2h = nullptr, *e2 = nullptr, *p2 = nullptr,
+         *e3h = nullptr, *e3 = nullptr, *d2h = nullptr, *d2 = nullptr, *d1h = nullptr, *d1 = nullptr, *dy = nullptr;
+    float *gd1 = nullptr, *gcat1 = nullptr, *gd2 = nullptr, *gcat2 = nullptr, *ge3 = nullptr, *gp2 = nullptr,
+          *ge2 = nullptr, *gp1 = nullptr, *ge1 = nullptr, *gh = nullptr;
+    float *wpart = nullptr, *wtmp = nullptr, *bpart = nullptr, *hpart = nullptr, *dforce = nullptr;
+    size_t wpart_bytes = 0;
+    int relu_blocks = 0, head_blocks = 0;
+    int *derr = nullptr;
+    std::string err;
+};
+
+namespace {
+thread_local std::string g_unet_create_error;
+
+int ufail(unet_ctx *c, int code, const char *fmt, ...)
+{
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = msg;
+    else
+        g_unet_create_error = msg;
+    return code;
+}
+
+#define UCK(call, what)                                                                       \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return ufail(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+void *ualloc(unet_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->alloc) {
+        p = c->alloc(bytes, (void *)c->stream, c->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->owned.push_back({p, bytes});
+    return p;
+}
+
+template <typename P>
+int uown(unet_ctx *c, P **out, size_t count)
+{
+    void *p = ualloc(c, count * sizeof(P));
+    if (!p) return ufail(c, LBM_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(P));
+    *out = static_cast<P *>(p);
+    return LBM_OK;
+}
+
+void ufree_all(unet_ctx *c)
+{
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &o : c->owned) {
+        if (c->release)
+            c->release(o.first, o.second, (void *)c->stream, c->user);
+        else if (!c->alloc)
+            cudaFree(o.first);
+    }
+    c->owned.clear();
+}
+
+unsigned blocks_for(long long n) { return unsigned((n + EW - 1) / EW); }
+
+// launch one 3x3x3 convolution on the context stream
+int conv(unet_ctx *c, const bf16 *s0, int c0, int up0, const bf16 *s1, int c1, const bf16 *w, const float *bias,
+         void *out, int out_f32, int relu, int cout, VGrid g)
+{
+    ConvArgs a{};
+    a.src0 = s0;
+    a.src1 = s1;
+    a.w = w;
+    a.bias = bias;
+    a.out = out;
+    a.c0 = c0;
+    a.c1 = c1;
+    a.up0 = up0;
+    a.cout = cout;
+    a.out_f32 = out_f32;
+    a.relu = relu;
+    a.g = g;
+    a.err = c->derr;
+    UCK(launch_conv3(a, c->stream), "conv3");
+    return LBM_OK;
+}
+
+// voxels per split of a weight gradient: about four waves of CTAs on 152 SMs
+int wgrad_vps(long long V, int tiles)
+{
+    long long nsplit = (608 + tiles - 1) / tiles;
+    if (nsplit < 1) nsplit = 1;
+    long long vps = (V + nsplit - 1) / nsplit;
+    vps = (vps + 63) / 64 * 64;
+    return int(vps < 64 ? 64 : vps);
+}
+
+size_t wgrad_ws_bytes(long long V, int cin, int cout)
+{
+    const int rows_pad = (27 * cin + 127) / 128 * 128;
+    const int vps = wgrad_vps(V, rows_pad / 128);
+    const long long nsplit = (V + vps - 1) / vps;
+    return size_t(nsplit) * rows_pad * cout * sizeof(float);
+}
+
+int wgrad(unet_ctx *c, const bf16 *s0, int c0, int up0, const bf16 *s1, int c1, const bf16 *dy, int cout,
+          float *dw, VGrid g)
+{
+    WgradArgs a{};
+    a.src0 = s0;
+    a.src1 = s1;
+    a.dy = dy;
+    a.c0 = c0;
+    a.c1 = c1;
+    a.up0 = up0;
+    a.cout = cout;
+    a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
+    a.vps = wgrad_vps(g.voxels(), a.rows_pad / 128);
+    a.g = g;
+    a.err = c->derr;
+    a.partial = c->wpart;
+    const int nsplit = wgrad_splits(g, a.vps);
+    if (size_t(nsplit) * a.rows_pad * cout * sizeof(float) > c->wpart_bytes)
+        return ufail(c, LBM_EINVAL, "weight-gradient workspace too small");
+    UCK(launch_wgrad(a, nsplit, dw, c->stream), "wgrad");
+    return LBM_OK;
+}
+
+// ReLU backward into c->dy and the bias gradient of layer k
+int relu_bwd(unet_ctx *c, const float *g, const bf16 *y, long long V, int C, int k)
+{
+    const long long n = V * C;
+    int nblk = int(std::min<long long>(c->relu_blocks, (n + EW - 1) / EW));
+    if (nblk < 1) nblk = 1;
+    relu_bwd_kernel<<<nblk, EW, 0, c->stream>>>(g, y, c->dy, c->bpart, n, C);
+    reduce_cols_kernel<<<1, 128, 0, c->stream>>>(c->bpart, nblk, C, c->grads + kLayout.b[k]);
+    UCK(cudaGetLastError(), "relu backward");
+    return LBM_OK;
+}
+
+int prep_weights(unet_ctx *c)
+{
+    if (c->weights_current) return LBM_OK;
+    for (int k = 0; k < NCONV; ++k) {
+        const int cp = cin_padded(k);
+        const long long n = 27ll * kConv[k].cout * cp;
+        prep_weights_kernel<<<blocks_for(n), EW, 0, c->stream>>>(c->params + kLayout.w[k], kConv[k].cout,
+                                                                 kConv[k].cin, cp, c->wf[k], c->wb[k]);
+    }
+    UCK(cudaGetLastError(), "weights");
+    c->weights_current = true;
+    return LBM_OK;
+}
+
+int forward(unet_ctx *c, const uint8_t *solid, const float *force)
+{
+    int rc;
+    UCK(cudaMemcpyAsync(c->dforce, force, sizeof(float) * c->nb, cudaMemcpyHostToDevice, c->stream), "force");
+    if ((rc = prep_weights(c))) return rc;
+    make_input_kernel<<<blocks_for(c->V1), EW, 0, c->stream>>>(solid, c->dforce, c->x, c->V1,
+                                                               c->g1.lz + c->g1.ly + c->g1.lx);
+    UCK(cudaGetLastError(), "input");
+    const float *P = c->params;
+    const Layout &L = kLayout;
+    if ((rc = conv(c, c->x, 16, 0, nullptr, 0, c->wf[W1A], P + L.b[W1A], c->e1h, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, c->e1h, 16, 0, nullptr, 0, c->wf[W1B], P + L.b[W1B], c->e1, 0, 1, 16, c->g1))) return rc;
+    pool_kernel<<<blocks_for(c->V2 * 16), EW, 0, c->stream>>>(c->e1, c->p1, c->g2, 16);
+    if ((rc = conv(c, c->p1, 16, 0, nullptr, 0, c->wf[W2A], P + L.b[W2A], c->e2h, 0, 1, 32, c->g2))) return rc;
+    if ((rc = conv(c, c->e2h, 32, 0, nullptr, 0, c->wf[W2B], P + L.b[W2B], c->e2, 0, 1, 32, c->g2))) return rc;
+    pool_kernel<<<blocks_for(c->V3 * 32), EW, 0, c->stream>>>(c->e2, c->p2, c->g3, 32);
+    if ((rc = conv(c, c->p2, 32, 0, nullptr, 0, c->wf[W3A], P + L.b[W3A], c->e3h, 0, 1, 64, c->g3))) return rc;
+    if ((rc = conv(c, c->e3h, 64, 0, nullptr, 0, c->wf[W3B], P + L.b[W3B], c->e3, 0, 1, 64, c->g3))) return rc;
+    if ((rc = conv(c, c->e3, 64, 1, c->e2, 32, c->wf[W4A], P + L.b[W4A], c->d2h, 0, 1, 32, c->g2))) return rc;
+    if ((rc = conv(c, c->d2h, 32, 0, nullptr, 0, c->wf[W4B], P + L.b[W4B], c->d2, 0, 1, 32, c->g2))) return rc;
+    if ((rc = conv(c, c->d2, 32, 1, c->e1, 16, c->wf[W5A], P + L.b[W5A], c->d1h, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, c->d1h, 16, 0, nullptr, 0, c->wf[W5B], P + L.b[W5B], c->d1, 0, 1, 16, c->g1))) return rc;
+    UCK(cudaGetLastError(), "forward");
+    return LBM_OK;
+}
+
+int check_err(unet_ctx *c)
+{
+    int h = 0;
+    UCK(cudaStreamSynchronize(c->stream), "sync");
+    UCK(cudaMemcpy(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    if (h) {
+        cudaMemset(c->derr, 0, sizeof(int));
+        return ufail(c, LBM_ETIMEOUT, "a tensor-core wait timed out (bounded mbarrier wait)");
+    }
+    return LBM_OK;
+}
+
+int backward(unet_ctx *c, const float *target, double *loss)
+{
+    int rc;
+    const Layout &L = kLayout;
+    float *G = c->grads;
+    head_kernel<<<c->head_blocks, EW, 0, c->stream>>>(c->d1, c->params + L.wh, c->params + L.bh, target, nullptr,
+                                                      c->gd1, c->hpart, c->V1);
+    reduce_cols_kernel<<<1, 128, 0, c->stream>>>(c->hpart, c->head_blocks, 72, c->wtmp);
+    UCK(cudaGetLastError(), "head");
+    UCK(cudaMemcpyAsync(G + L.wh, c->wtmp, sizeof(float) * 68, cudaMemcpyDeviceToDevice, c->stream), "head grad");
+    float hl = 0.f;
+    UCK(cudaMemcpyAsync(&hl, c->wtmp + 68, sizeof(float), cudaMemcpyDeviceToHost, c->stream), "loss");
+    // level 1 decoder
+    if ((rc = relu_bwd(c, c->gd1, c->d1, c->V1, 16, W5B))) return rc;
+    if ((rc = wgrad(c, c->d1h, 16, 0, nullptr, 0, c->dy, 16, G + L.w[W5B], c->g1))) return rc;
+    if ((rc = conv(c, c->dy, 16, 0, nullptr, 0, c->wb[W5B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->d1h, c->V1, 16, W5A))) return rc;
+    if ((rc = wgrad(c, c->d2, 32, 1, c->e1, 16, c->dy, 16, G + L.w[W5A], c->g1))) return rc;
+    if ((rc = conv(c, c->dy, 16, 0, nullptr, 0, c->wb[W5A], nullptr, c->gcat1, 1, 0, 48, c->g1))) return rc;
+    up_bwd_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gd2, c->g2);
+    // level 2 decoder
+    if ((rc = relu_bwd(c, c->gd2, c->d2, c->V2, 32, W4B))) return rc;
+    if ((rc = wgrad(c, c->d2h, 32, 0, nullptr, 0, c->dy, 32, G + L.w[W4B], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W4B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->d2h, c->V2, 32, W4A))) return rc;
+    if ((rc = wgrad(c, c->e3, 64, 1, c->e2, 32, c->dy, 32, G + L.w[W4A], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W4A], nullptr, c->gcat2, 1, 0, 96, c->g2))) return rc;
+    up_bwd_kernel<<<blocks_for(c->V3 * 64), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->ge3, c->g3);
+    // bottleneck
+    if ((rc = relu_bwd(c, c->ge3, c->e3, c->V3, 64, W3B))) return rc;
+    if ((rc = wgrad(c, c->e3h, 64, 0, nullptr, 0, c->dy, 64, G + L.w[W3B], c->g3))) return rc;
+    if ((rc = conv(c, c->dy, 64, 0, nullptr, 0, c->wb[W3B], nullptr, c->gh, 1, 0, 64, c->g3))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->e3h, c->V3, 64, W3A))) return rc;
+    if ((rc = wgrad(c, c->p2, 32, 0, nullptr, 0, c->dy, 64, G + L.w[W3A], c->g3))) return rc;
+    if ((rc = conv(c, c->dy, 64, 0, nullptr, 0, c->wb[W3A], nullptr, c->gp2, 1, 0, 32, c->g3))) return rc;
+    skip_pool_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->gp2, c->ge2, c->g2, 32);
+    // level 2 encoder
+    if ((rc = relu_bwd(c, c->ge2, c->e2, c->V2, 32, W2B))) return rc;
+    if ((rc = wgrad(c, c->e2h, 32, 0, nullptr, 0, c->dy, 32, G + L.w[W2B], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W2B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->e2h, c->V2, 32, W2A))) return rc;
+    if ((rc = wgrad(c, c->p1, 16, 0, nullptr, 0, c->dy, 32, G + L.w[W2A], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W2A], nullptr, c->gp1, 1, 0, 16, c->g2))) return rc;
+    skip_pool_kernel<<<blocks_for(c->V1 * 16), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gp1, c->ge1, c->g1, 16);
+    // level 1 encoder
+    if ((rc = relu_bwd(c, c->ge1, c->e1, c->V1, 16, W1B))) return rc;
+    if ((rc = wgrad(c, c->e1h, 16, 0, nullptr, 0, c->dy, 16, G + L.w[W1B], c->g1))) return rc;
+    if ((rc = conv(c, c->dy, 16, 0, nullptr, 0, c->wb[W1B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->e1h, c->V1, 16, W1A))) return rc;
+    if ((rc = wgrad(c, c->x, 16, 0, nullptr, 0, c->dy, 16, c->wtmp, c->g1))) return rc;
+    unpad_grad_kernel<<<blocks_for(16 * 27 * 2), EW, 0, c->stream>>>(c->wtmp, 16, 2, 16, G + L.w[W1A]);
+    UCK(cudaGetLastError(), "backward");
+    if ((rc = check_err(c))) return rc;
+    if (loss) *loss = double(hl) / double(c->V1 * 4);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long unet_param_count(void) { return kLayout.total; }
+
+const char *unet_last_error(const unet_ctx *c) { return c ? c->err.c_str() : g_unet_create_error.c_str(); }
+
+void unet_destroy(unet_ctx *c)
+{
+    if (!c) return;
+    ufree_all(c);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx **out)
+{
+    if (!out) return ufail(nullptr, LBM_EINVAL, "unet_create: out is NULL");
+    *out = nullptr;
+    if (n < 16 || n > 128 || (n & (n - 1)) || nb < 1 || nb > 4096)
+        return ufail(nullptr, LBM_EINVAL, "unet_create: n must be a power of two in [16, 128] and nb >= 1");
+    unet_ctx *c = new (std::nothrow) unet_ctx();
+    if (!c) return ufail(nullptr, LBM_ENOMEM, "out of host memory");
+    c->n = n;
+    c->nb = nb;
+    const int l = ilog2(n);
+    c->g1 = VGrid{nb, l, l, l};
+    c->g2 = VGrid{nb, l - 1, l - 1, l - 1};
+    c->g3 = VGrid{nb, l - 2, l - 2, l - 2};
+    c->V1 = c->g1.voxels();
+    c->V2 = c->g2.voxels();
+    c->V3 = c->g3.voxels();
+    current_allocator(&c->alloc, &c->release, &c->user);
+    auto bail = [&](int rc) {
+        g_unet_create_error = c->err;
+        unet_destroy(c);
+        return rc;
+    };
+    if (stream) {
+        c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(ufail(c, LBM_ECUDA, "cudaStreamCreate failed"));
+        c->own_stream = true;
+    }
+    const long long np = kLayout.total;
+    int rc = 0;
+    const long long V1 = c->V1, V2 = c->V2, V3 = c->V3;
+    if ((rc = uown(c, &c->params, np)) || (rc = uown(c, &c->grads, np)) || (rc = uown(c, &c->am, np)) ||
+        (rc = uown(c, &c->av, np)))
+        return bail(rc);
+    for (int k = 0; k < NCONV; ++k) {
+        if ((rc = uown(c, &c->wf[k], size_t(27) * kConv[k].cout * cin_padded(k)))) return bail(rc);
+        if (k != W1A && (rc = uown(c, &c->wb[k], size_t(27) * kConv[k].cout * kConv[k].cin))) return bail(rc);
+    }
+    if ((rc = uown(c, &c->x, V1 * 16)) || (rc = uown(c, &c->e1h, V1 * 16)) || (rc = uown(c, &c->e1, V1 * 16)) ||
+        (rc = uown(c, &c->p1, V2 * 16)) || (rc = uown(c, &c->e2h, V2 * 32)) || (rc = uown(c, &c->e2, V2 * 32)) ||
+        (rc = uown(c, &c->p2, V3 * 32)) || (rc = uown(c, &c->e3h, V3 * 64)) || (rc = uown(c, &c->e3, V3 * 64)) ||
+        (rc = uown(c, &c->d2h, V2 * 32)) || (rc = uown(c, &c->d2, V2 * 32)) || (rc = uown(c, &c->d1h, V1 * 16)) ||
+        (rc = uown(c, &c->d1, V1 * 16)) || (rc = uown(c, &c->dy, V1 * 16)))
+        return bail(rc);
+    if ((rc = uown(c, &c->gd1, V1 * 16)) || (rc = uown(c, &c->gcat1, V1 * 48)) || (rc = uown(c, &c->gd2, V2 * 32)) ||
+        (rc = uown(c, &c->gcat2, V2 * 96)) || (rc = uown(c, &c->ge3, V3 * 64)) || (rc = uown(c, &c->gp2, V3 * 32)) ||
+        (rc = uown(c, &c->ge2, V2 * 32)) || (rc = uown(c, &c->gp1, V2 * 16)) || (rc = uown(c, &c->ge1, V1 * 16)) ||
+        (rc = uown(c, &c->gh, V1 * 16)))
+        return bail(rc);
+    // weight-gradient workspace: the largest of the ten layers
+    const long long Vl[NCONV] = {V1, V1, V2, V2, V3, V3, V2, V2, V1, V1};
+    size_t ws = 0;
+    for (int k = 0; k < NCONV; ++k) ws = std::max(ws, wgrad_ws_bytes(Vl[k], cin_padded(k), kConv[k].cout));
+    c->wpart_bytes = ws;
+    c->relu_blocks = 1024;
+    c->head_blocks = int(std::min<long long>(1024, (V1 + EW - 1) / EW));
+    if ((rc = uown(c, &c->wpart, ws / sizeof(float))) || (rc = uown(c, &c->wtmp, 16 * 27 * 16)) ||
+        (rc = uown(c, &c->bpart, size_t(c->relu_blocks) * 64)) ||
+        (rc = uown(c, &c->hpart, size_t(c->head_blocks) * HEAD_PART)) || (rc = uown(c, &c->dforce, size_t(nb))) ||
+        (rc = uown(c, &c->derr, 1)))
+        return bail(rc);
+    // He-normal weights (std sqrt(2 / (27 cin))), head std sqrt(1/16), zero biases
+    std::vector<float> h(size_t(np), 0.f);
+    for (int k = 0; k < NCONV; ++k) {
+        const double sd = std::sqrt(2.0 / (27.0 * kConv[k].cin));
+        for (long long i = 0; i < 27ll * kConv[k].cin * kConv[k].cout; ++i)
+            h[size_t(kLayout.w[k] + i)] = float(sd * normal(seed, uint64_t(kLayout.w[k] + i)));
+    }
+    for (int i = 0; i < 64; ++i) h[size_t(kLayout.wh + i)] = float(0.25 * normal(seed, uint64_t(kLayout.wh + i)));
+    if (cudaMemcpyAsync(c->params, h.data(), sizeof(float) * np, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->grads, 0, sizeof(float) * np, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->am, 0, sizeof(float) * np, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->av, 0, sizeof(float) * np, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(ufail(c, LBM_ECUDA, "unet_create: initialisation failed"));
+    *out = c;
+    return LBM_OK;
+}
+
+int unet_get_params(unet_ctx *c, float *host)
+{
+    if (!c || !host) return ufail(c, LBM_EINVAL, "unet_get_params: NULL argument");
+    UCK(cudaMemcpyAsync(host, c->params, sizeof(float) * kLayout.total, cudaMemcpyDeviceToHost, c->stream), "params");
+    UCK(cudaStreamSynchronize(c->stream), "sync");
+    return LBM_OK;
+}
+
+int unet_set_params(unet_ctx *c, const float *host)
+{
+    if (!c || !host) return ufail(c, LBM_EINVAL, "unet_set_params: NULL argument");
+    UCK(cudaMemcpyAsync(c->params, host, sizeof(float) * kLayout.total, cudaMemcpyHostToDevice, c->stream), "params");
+    UCK(cudaStreamSynchronize(c->stream), "sync");
+    c->weights_current = false;
+    return LBM_OK;
+}
+
+int unet_predict(unet_ctx *c, const uint8_t *solid, const float *force, float *out)
+{
+    if (!c || !solid || !force || !out) return ufail(c, LBM_EINVAL, "unet_predict: NULL argument");
+    int rc = forward(c, solid, force);
+    if (rc) return rc;
+    head_kernel<<<c->head_blocks, EW, 0, c->stream>>>(c->d1, c->params + kLayout.wh, c->params + kLayout.bh,
+                                                      nullptr, out, nullptr, nullptr, c->V1);
+    UCK(cudaGetLastError(), "head");
+    return check_err(c);
+}
+
+int unet_loss_grad(unet_ctx *c, const uint8_t *solid, const float *force, const float *target, double *loss,
+                   float *grad_host)
+{
+    if (!c || !solid || !force || !target) return ufail(c, LBM_EINVAL, "unet_loss_grad: NULL argument");
+    int rc = forward(c, solid, force);
+    if (rc) return rc;
+    if ((rc = backward(c, target, loss))) return rc;
+    if (grad_host) {
+        UCK(cudaMemcpy(grad_host, c->grads, sizeof(float) * kLayout.total, cudaMemcpyDeviceToHost), "grads");
+    }
+    return LBM_OK;
+}
+
+int unet_adam_step(unet_ctx *c, float lr, float b1, float b2, float eps)
+{
+    if (!c || !(lr >= 0.f) || !(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps > 0.f))
+        return ufail(c, LBM_EINVAL, "unet_adam_step: bad arguments");
+    c->step += 1;
+    const float c1 = float(1.0 - std::pow(double(b1), double(c->step)));
+    const float c2 = float(1.0 - std::pow(double(b2), double(c->step)));
+    adam_kernel<<<blocks_for(kLayout.total), EW, 0, c->stream>>>(c->params, c->grads, c->am, c->av, kLayout.total,
+                                                                 lr, b1, b2, eps, c1, c2);
+    UCK(cudaGetLastError(), "adam");
+    c->weights_current = false;
+    return LBM_OK;
+}
+
+int unet_conv3(const void *src0, int c0, int up0, const void *src1, int c1, const void *w, const float *bias,
+               void *out, int out_f32, int relu, int cout, int nb, int lz, int ly, int lx, void *stream)
+{
+    if (nb < 1 || lz < 0 || ly < 0 || lx < 0 || lz + ly + lx > 30)
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3: bad grid");
+    ConvArgs a{};
+    a.src0 = static_cast<const bf16 *>(src0);
+    a.src1 = static_cast<const bf16 *>(src1);
+    a.w = static_cast<const bf16 *>(w);
+    a.bias = bias;
+    a.out = out;
+    a.c0 = c0;
+    a.c1 = c1;
+    a.up0 = up0 ? 1 : 0;
+    a.cout = cout;
+    a.out_f32 = out_f32 ? 1 : 0;
+    a.relu = relu ? 1 : 0;
+    a.g = VGrid{nb, lz, ly, lx};
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return ufail(nullptr, LBM_ENOMEM, "unet_conv3: error word");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    a.err = err;
+    cudaError_t e = launch_conv3(a, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3: invalid channels or pointers");
+    if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3: %s", cudaGetErrorString(e));
+    if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3: a bounded wait timed out");
+    return LBM_OK;
+}
+
+int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1, const void *dy, int cout, float *dw,
+                     int nb, int lz, int ly, int lx, void *stream)
+{
+    if (nb < 1 || lz < 0 || ly < 0 || lx < 0 || lz + ly + lx > 30 || c0 <= 0 || c1 < 0 || cout <= 0)
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3_wgrad: bad arguments");
+    const VGrid g{nb, lz, ly, lx};
+    WgradArgs a{};
+    a.src0 = static_cast<const bf16 *>(src0);
+    a.src1 = static_cast<const bf16 *>(src1);
+    a.dy = static_cast<const bf16 *>(dy);
+    a.c0 = c0;
+    a.c1 = c1;
+    a.up0 = up0 ? 1 : 0;
+    a.cout = cout;
+    a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
+    a.vps = wgrad_vps(g.voxels(), a.rows_pad / 128);
+    a.g = g;
+    const int nsplit = wgrad_splits(g, a.vps);
+    void *(*al)(size_t, void *, void *) = nullptr;
+    void (*rl)(void *, size_t, void *, void *) = nullptr;
+    void *user = nullptr;
+    current_allocator(&al, &rl, &user);
+    const size_t bytes = size_t(nsplit) * a.rows_pad * cout * sizeof(float) + 256;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    if (al) {
+        ws = al(bytes, stream, user);
+    } else if (cudaMalloc(&ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ws = nullptr;
+    }
+    if (!ws) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_wgrad: workspace of %zu bytes", bytes);
+    a.partial = static_cast<float *>(ws);
+    a.err = reinterpret_cast<int *>(static_cast<char *>(ws) + bytes - 256);
+    cudaMemsetAsync(a.err, 0, sizeof(int), s);
+    cudaError_t e = launch_wgrad(a, nsplit, dw, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (rl)
+        rl(ws, bytes, stream, user);
+    else if (!al)
+        cudaFree(ws);
+    if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_wgrad: invalid channels");
+    if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_wgrad: %s", cudaGetErrorString(e));
+    if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_wgrad: a bounded wait timed out");
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -112,6 +112,18 @@ SIGNATURES = {
     "lbm_invariants_noalloc": ([_vp, _vp, _ll, _d, _P(_d), _vp, _vp], _i),
     "lbm_last_error": ([_vp], ctypes.c_char_p),
     "lbm_version": ([], ctypes.c_char_p),
+    # include/unet.h (the learned warm start; wrapped in unet.py)
+    "unet_param_count": ([], _ll),
+    "unet_create": ([_i, _i, ctypes.c_ulonglong, _vp, _P(_vp)], _i),
+    "unet_destroy": ([_vp], None),
+    "unet_get_params": ([_vp, _vp], _i),
+    "unet_set_params": ([_vp, _vp], _i),
+    "unet_predict": ([_vp, _vp, _vp, _vp], _i),
+    "unet_loss_grad": ([_vp, _vp, _vp, _vp, _P(_d), _vp], _i),
+    "unet_adam_step": ([_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], _i),
+    "unet_last_error": ([_vp], ctypes.c_char_p),
+    "unet_conv3": ([_vp, _i, _i, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp], _i),
+    "unet_conv3_wgrad": ([_vp, _i, _i, _vp, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp], _i),
 }
 
 _lib = None
