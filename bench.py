@@ -466,6 +466,94 @@ def run_precision_report(args):
     return 0
 
 
+WARMSTART_WORKLOAD = ("learned warm start: 64^3 channels (periodic x/z, walls -y/+y), sphere packings "
+                      "(radius 2-6, porosity U[0.7, 0.9]), force U[5e-7, 5e-6] along x, BGK tau=0.8; "
+                      "training seeds 0..N-1, held-out seeds 10000..; residual 1e-6 (change per step over "
+                      "50-step intervals)")
+
+
+def run_warmstart_report(args):
+    """The learned warm start end to end: solve the training channels, train
+    the U-Net, then solve the held-out channels from rest, from the predicted
+    equilibrium and from a consistent start at the predicted velocity.
+    Prints one JSON line (steps, wall times, errors)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1007_1388_gb300 import build
+
+    build.build()
+    import paper_1007_1388_gb300 as L
+    from paper_1007_1388_gb300 import unet, warmstart as WS, workloads as W
+
+    L.use_torch_allocator()
+    n, tol, nb = args.ws_size, 1e-6, 4
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    t0 = time.perf_counter()
+    seeds = list(range(args.ws_train)) + list(range(10000, 10000 + args.ws_eval))
+    samples = W.channel_samples(seeds, n)
+    t_gen = time.perf_counter() - t0
+    log(f"geometries: {len(samples)} in {t_gen:.1f} s")
+    train = WS.make_dataset(None, n, chunk=args.ws_chunk, tol=tol, samples=samples[:args.ws_train])
+    log(f"training set solved: {train.solve_seconds:.1f} s, steps mean {train.steps.mean():.0f}, "
+        f"unconverged {int((train.steps < 0).sum())}")
+    net = unet.UNet(n, nb, seed=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = WS.train(net, train, epochs=args.ws_epochs, lr=2e-3, lr_final=2e-5, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    ev = samples[args.ws_train:]
+    flags = [f for f, _ in ev]
+    forces = [F for _, F in ev]
+    K, V = len(ev), n ** 3
+    out = {"report": "warmstart", "workload": WARMSTART_WORKLOAD, "n": n, "train": args.ws_train,
+           "eval": K, "epochs": args.ws_epochs, "batch": nb, "train_seconds": t_train,
+           "train_steps": len(losses), "ms_per_train_step": 1e3 * t_train / max(1, len(losses)),
+           "loss_first": losses[0], "loss_last": float(np.mean(losses[-50:])), "s_u": train.s_u,
+           "training_set": {"solve_seconds": train.solve_seconds, "steps_mean": float(train.steps.mean())}}
+    ctx_r, steps_r, _, sec_r = WS.solve(flags, forces, n, tol)
+    rho_r, u_r = WS.fields(ctx_r, K, n)
+    ctx_r.destroy()
+
+    def errs(u):
+        e = [float((u[3 * V * k:3 * V * (k + 1)] - u_r[3 * V * k:3 * V * (k + 1)]).norm()
+                   / u_r[3 * V * k:3 * V * (k + 1)].norm()) for k in range(K)]
+        return float(np.mean(e)), float(np.median(e)), float(np.max(e))
+
+    def stats(steps, sec):
+        ok = steps[steps >= 0]
+        return {"steps_mean": float(ok.mean()) if ok.size else None,
+                "steps_median": float(np.median(ok)) if ok.size else None,
+                "unconverged": int((steps < 0).sum()), "wall_seconds": sec}
+
+    out["from_rest"] = stats(steps_r, sec_r)
+    solid = torch.from_numpy(np.concatenate([f.reshape(-1) for f in flags])).cuda()
+    for smooth in (0, 1):
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        init = WS.predict(net, solid, forces, n, train.s_rho, train.s_u, smooth=smooth)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t2
+        pe = errs(init[1])
+        for name, m in (("equilibrium", 0), ("consistent", 10)):
+            ctx, st, _, sec = WS.solve(flags, forces, n, tol, init=init, consistent=m)
+            _, u_w = WS.fields(ctx, K, n)
+            ctx.destroy()
+            row = stats(st, sec + t_inf)
+            row.update(inference_seconds=t_inf, prediction_error_mean=pe[0], prediction_error_median=pe[1],
+                       prediction_error_max=pe[2], final_error_max=errs(u_w)[2])
+            row["speedup_steps"] = (out["from_rest"]["steps_mean"] / row["steps_mean"]
+                                    if row["steps_mean"] else None)
+            row["speedup_wall"] = sec_r / (sec + t_inf)
+            out[f"warm_{name}_smooth{smooth}"] = row
+            log(f"{name} smooth {smooth}: {row}")
+    net.destroy()
+    print(json.dumps(out))
+    return 0
+
+
 def _ncu_traffic(name):
     """DRAM bytes per launch from the committed ncu summary, if it is current."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -493,8 +581,14 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
-    ap.add_argument("--report", default="", choices=["", "precision"],
-                    help="precision: storage-precision report on the 384^3 cavity (one JSON line)")
+    ap.add_argument("--report", default="", choices=["", "precision", "warmstart"],
+                    help="precision: storage-precision report on the 384^3 cavity; warmstart: the learned "
+                         "warm start end to end (one JSON line each)")
+    ap.add_argument("--ws-size", type=int, default=64)
+    ap.add_argument("--ws-train", type=int, default=2000)
+    ap.add_argument("--ws-eval", type=int, default=200)
+    ap.add_argument("--ws-epochs", type=int, default=40)
+    ap.add_argument("--ws-chunk", type=int, default=250)
     ap.add_argument("--report-size", type=int, default=384)
     ap.add_argument("--report-steps", type=int, default=5000)
     ap.add_argument("--report-block", type=int, default=128)
@@ -517,6 +611,8 @@ def main():
         return run_reference(args)
     if args.report == "precision":
         return run_precision_report(args)
+    if args.report == "warmstart":
+        return run_warmstart_report(args)
     return run_gpu(args)
 
 

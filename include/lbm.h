@@ -207,6 +207,58 @@ int lbm_residual(lbm_ctx *ctx, double *r, double *per_instance);
 int lbm_run_to_residual(lbm_ctx *ctx, double tol, int check_every, long long max_steps,
                         long long *steps, double *r);
 
+/*
+ * lbm_set_forces - per-instance body force: force[3*k + a] is component a of
+ * the force density of instance k (replaces lbm_params.force for every
+ * instance; the Guo source and the moment shift use it).  Synchronises.
+ * LBM_EINVAL for a non-finite value.
+ */
+int lbm_set_forces(lbm_ctx *ctx, const double *force);
+
+/*
+ * lbm_impose_velocity_device - in every fluid cell adds
+ * f~eq(drho, u_target) - f~eq(drho, u_now) (Eq. (2)), so that the velocity of
+ * the moments becomes u_target (device float[3*N], macroscopic layout) while
+ * the density and the non-equilibrium part are kept.  Asynchronous.
+ *
+ * lbm_init_consistent_device - lbm_init_equilibrium_device(rho, u), then
+ * `iterations` rounds of one time step followed by
+ * lbm_impose_velocity_device(u): the density and the non-equilibrium part
+ * relax to values consistent with the prescribed velocity (Mei et al.'s
+ * consistent initial conditions), so a warm start from a known velocity
+ * field does not begin with the transient of a bare equilibrium.
+ */
+int lbm_impose_velocity_device(lbm_ctx *ctx, const float *u);
+int lbm_init_consistent_device(lbm_ctx *ctx, const float *rho, const float *u, int iterations);
+
+/*
+ * lbm_snapshot_velocity - stores the current velocity field (library-owned
+ * device copy, float32).  lbm_residual_vs_snapshot - the change per step
+ * since then, r = ||u - u_snap||_2 / (steps_since ||u||_2) over fluid cells
+ * (FP64 sums; per_instance may be NULL; NaN for an instance holding a
+ * non-finite value).  Over an even number of steps this residual is blind to
+ * period-2 oscillations, which the one-step residual is not: bounce-back on
+ * obstacles in a periodic channel excites an undamped staggered (period-2)
+ * mode of the D3Q19 scheme, on which the one-step residual stalls while the
+ * flow itself is steady.  LBM_EINVAL before the first snapshot.
+ */
+int lbm_snapshot_velocity(lbm_ctx *ctx);
+int lbm_residual_vs_snapshot(lbm_ctx *ctx, int steps_since, double *r, double *per_instance);
+
+/*
+ * lbm_run_to_residual_each - steps a batch in chunks of check_every until
+ * every instance's own residual falls below tol or max_steps is reached: the
+ * one-step residual of lbm_residual (interval = 0) or the change per step
+ * over the chunk (interval = 1, check_every even; lbm_residual_vs_snapshot).  An instance that has converged is frozen: its
+ * state is kept (in both buffers) and the sweep skips it, so the remaining
+ * work shrinks as instances converge.  steps[k] receives the steps after
+ * which instance k first met tol (a multiple of check_every), or -1; res[k]
+ * (res may be NULL) its residual then, or its last residual.  Afterwards the
+ * context sweeps every instance again.  LBM_ENUMERIC if a residual is NaN.
+ */
+int lbm_run_to_residual_each(lbm_ctx *ctx, double tol, int check_every, int interval, long long max_steps,
+                             long long *steps, double *res);
+
 /* Sizes of a context. */
 typedef struct {
     long long cells;          /* interior cells over all Blocks / instances */

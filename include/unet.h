@@ -107,6 +107,37 @@ int unet_conv3(const void *src0, int c0, int up0, const void *src1, int c1, cons
 int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1, const void *dy, int cout,
                      float *dw, int nb, int lz, int ly, int lx, void *stream);
 
+/*
+ * unet_targets_from_fields - normalised training targets from the fields of
+ * nb instances of V cells (device; the batch layout of
+ * lbm_macroscopic_device: rho [nb][V], u [nb][3][V]):
+ *   target[k][c] = {(rho - rho0) / (F_k s_rho), u_x / (F_k s_u),
+ *                   u_y / (F_k s_u), u_z / (F_k s_u)},  0 in solid cells,
+ * target device float [nb][V][4]; solid device uint8 [nb][V]; force device
+ * float [nb] (each instance's force magnitude F_k, nonzero).  Asynchronous.
+ * In Stokes flow the steady fields are proportional to the force, so the
+ * targets depend on the geometry only.
+ *
+ * unet_fields_from_prediction - the inverse map, for
+ * lbm_init_equilibrium_device: rho = rho0 + F_k s_rho y_0 and
+ * u_a = F_k s_u y_{1+a} in fluid cells, rho0 and 0 in solid cells.
+ */
+int unet_targets_from_fields(const float *rho, const float *u, const uint8_t *solid, const float *force, int nb,
+                             long long V, float rho0, float s_rho, float s_u, float *target, void *stream);
+int unet_fields_from_prediction(const float *pred, const uint8_t *solid, const float *force, int nb, long long V,
+                                float rho0, float s_rho, float s_u, float *rho, float *u, void *stream);
+
+/*
+ * unet_smooth_fields - `passes` rounds of a separable [1 2 1]/4 filter along
+ * x, y and z over K fields of `comps` components on n^3 grids (device float
+ * [K][comps][n^3], x fastest; n a power of two): periodic along x and z, the
+ * edge value repeated beyond the y walls, solid cells (device uint8 [K][n^3])
+ * set to 0.  Removes the short-wavelength part of a predicted field, which
+ * otherwise slows the solver's start.  scratch: device float of the same size.
+ */
+int unet_smooth_fields(float *f, float *scratch, const uint8_t *solid, int K, int comps, int n, int passes,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ struct lbm_ctx {
     int ninst = 0;
     std::vector<int> idims;        // 3 per instance
     std::vector<double> itau;
+    std::vector<double> iforce;    // 3 per instance (lbm_params.force, or lbm_set_forces)
     int storage = LBM_F32;
     int elem = 4;
     bool forced = false;
@@ -83,6 +84,7 @@ struct lbm_ctx {
     int grid = 0;                 // 0 = one CTA per tile, else a persistent grid
     int mask = 0;                 // near-wall cells via link masks under a warp vote
     std::vector<Tile> stiles;
+    std::vector<char> active;     // per instance: swept (1) or frozen (0)
     int minb = 4;  // register budget of the sweep (resident CTAs per SM)
     std::vector<char> h_consts;  // host copy of the per-instance CollideConsts
     // kernel choice and the TMA sweep's launch state
@@ -104,6 +106,7 @@ struct lbm_ctx {
     void *d_consts = nullptr;
     long long *d_inst_begin = nullptr;
     double *d_partial = nullptr;
+    float *d_snap = nullptr;       // velocity snapshot: rho [cells] then u [3 cells]
     double *d_red = nullptr;
     size_t partial_cap = 0;
     long long device_bytes = 0;
@@ -308,9 +311,10 @@ std::vector<char> make_consts(const lbm_ctx *c)
         const double wm = p.collision == LBM_TRT ? 1.0 / (0.5 + p.magic / (tau - 0.5)) : wp;
         cc.rho0s = T(s * p.rho0);
         cc.ufac = T(1.0 / (s * p.rho0));
+        const double *F = &c->iforce[size_t(3 * k)];
         for (int a = 0; a < 3; ++a) {
-            cc.uoff[a] = T(p.force[a] / (2.0 * p.rho0));
-            cc.Fs[a] = T(s * p.force[a]);
+            cc.uoff[a] = T(F[a] / (2.0 * p.rho0));
+            cc.Fs[a] = T(s * F[a]);
         }
         cc.omega_p = T(wp);
         cc.omega_m = T(wm);
@@ -331,7 +335,7 @@ std::vector<char> make_consts(const lbm_ctx *c)
         cc.hwp = T(0.5 * wp);
         cc.hwm = T(0.5 * wm);
         for (int a = 0; a < 3; ++a) {
-            const double Fs = s * p.force[a];
+            const double Fs = s * F[a];
             cc.Fs[a] = T(Fs);
             cc.k9F[a] = T(9.0 * ap * Fs);
             cc.nk3F[a] = T(-3.0 * ap * Fs);
@@ -342,7 +346,7 @@ std::vector<char> make_consts(const lbm_ctx *c)
             cc.nwpw[c2] = T(-wp * wc[c2]);
             cc.nwmc3[c2] = T(-wm * 3.0 * rho0s * wc[c2]);
             for (int a = 0; a < 3; ++a) {
-                const double Fs = s * p.force[a];
+                const double Fs = s * F[a];
                 cc.okF[c2][a] = T(wp * 3.0 * am * wc[c2] * Fs);
                 cc.nwmkF[c2][a] = T(-wm * 3.0 * am * wc[c2] * Fs);
             }
@@ -409,6 +413,14 @@ int set_sweep(lbm_ctx *c, const int t[3], int flat, int grid)
         }
     } else {
         build_tiles(c, t, st, unused);
+    }
+    // frozen instances (lbm_run_to_residual_each) are left out
+    if (!c->active.empty()) {
+        std::vector<Tile> kept;
+        kept.reserve(st.size());
+        for (const Tile &tl : st)
+            if (c->active[size_t(c->blocks[size_t(tl.block)].inst)]) kept.push_back(tl);
+        st.swap(kept);
     }
     Tile *dt = nullptr;
     int rc = upload(c, &dt, st);
@@ -521,6 +533,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     c->storage = p.storage;
     c->elem = p.storage == LBM_F32 ? 4 : (p.storage == LBM_F64 ? 8 : 2);
     c->forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
+    for (int k = 0; k < c->ninst; ++k) c->iforce.insert(c->iforce.end(), p.force, p.force + 3);
 
     if (p.stream) {
         c->stream = static_cast<cudaStream_t>(p.stream);
@@ -1199,9 +1212,9 @@ int lbm_invariants(lbm_ctx *c, double *mass, double mom[3], double *nonfinite, d
     for (int k = 0; k < c->ninst; ++k) {
         const double *v = &r[size_t(R_K) * k];
         const double m = v[R_NFLUID] * p.rho0 + v[R_DRHO];
-        const double j[3] = {v[R_JX] - v[R_NFLUID] * 0.5 * p.force[0],
-                             v[R_JY] - v[R_NFLUID] * 0.5 * p.force[1],
-                             v[R_JZ] - v[R_NFLUID] * 0.5 * p.force[2]};
+        const double *F = &c->iforce[size_t(3 * k)];
+        const double j[3] = {v[R_JX] - v[R_NFLUID] * 0.5 * F[0], v[R_JY] - v[R_NFLUID] * 0.5 * F[1],
+                             v[R_JZ] - v[R_NFLUID] * 0.5 * F[2]};
         M += m;
         for (int a = 0; a < 3; ++a) J[a] += j[a];
         bad += v[R_NONFINITE];
@@ -1265,6 +1278,141 @@ int lbm_run_to_residual(lbm_ctx *c, double tol, int check_every, long long max_s
     if (steps) *steps = done;
     if (res) *res = r;
     return LBM_OK;
+}
+
+int lbm_impose_velocity_device(lbm_ctx *c, const float *u)
+{
+    if (!c || !u) return fail(c, LBM_EINVAL, "lbm_impose_velocity_device: NULL argument");
+    CK(launch_impose_velocity(field_args(c), c->buf[c->cur], u, c->stream), "impose velocity");
+    c->have_prev = false;
+    return LBM_OK;
+}
+
+int lbm_init_consistent_device(lbm_ctx *c, const float *rho, const float *u, int iterations)
+{
+    if (!c || !rho || !u || iterations < 0) return fail(c, LBM_EINVAL, "lbm_init_consistent_device: bad arguments");
+    int rc = lbm_init_equilibrium_device(c, rho, u);
+    for (int k = 0; k < iterations && rc == LBM_OK; ++k) {
+        if ((rc = lbm_step(c, 1))) break;
+        rc = lbm_impose_velocity_device(c, u);
+    }
+    return rc;
+}
+
+int lbm_snapshot_velocity(lbm_ctx *c)
+{
+    if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
+    if (!c->d_snap) {
+        int rc = own(c, &c->d_snap, sizeof(float) * 4 * size_t(c->cells));
+        if (rc) return rc;
+    }
+    CK(launch_macroscopic(field_args(c), c->buf[c->cur], c->d_snap, c->d_snap + c->cells, c->stream), "snapshot");
+    return LBM_OK;
+}
+
+int lbm_residual_vs_snapshot(lbm_ctx *c, int steps_since, double *res, double *per_instance)
+{
+    if (!c || !res || steps_since <= 0) return fail(c, LBM_EINVAL, "lbm_residual_vs_snapshot: bad arguments");
+    if (!c->d_snap) return fail(c, LBM_EINVAL, "lbm_residual_vs_snapshot: no snapshot taken");
+    int rc = check_device_error(c);
+    if (rc) return rc;
+    std::vector<double> r(size_t(R_K) * c->ninst, 0.0);
+    CK(launch_reduce_snap(field_args(c), c->buf[c->cur], c->d_snap + c->cells, c->d_partial, c->d_inst_begin,
+                          c->ninst, c->d_red, c->stream),
+       "snapshot residual");
+    CK(cudaMemcpyAsync(r.data(), c->d_red, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    auto ratio = [&](double a, double b) {
+        if (b == 0.0) return a == 0.0 ? 0.0 : INFINITY;
+        return std::sqrt(a) / (std::sqrt(b) * double(steps_since));
+    };
+    double num = 0, den = 0;
+    for (int k = 0; k < c->ninst; ++k) {
+        const double *v = &r[size_t(R_K) * k];
+        num += v[R_DU2];
+        den += v[R_U2];
+        if (per_instance) per_instance[k] = v[R_NONFINITE] > 0 ? NAN : ratio(v[R_DU2], v[R_U2]);
+    }
+    *res = ratio(num, den);
+    return LBM_OK;
+}
+
+int lbm_set_forces(lbm_ctx *c, const double *force)
+{
+    if (!c || !force) return fail(c, LBM_EINVAL, "lbm_set_forces: NULL argument");
+    for (int i = 0; i < 3 * c->ninst; ++i)
+        if (!std::isfinite(force[i])) return fail(c, LBM_EINVAL, "lbm_set_forces: non-finite force");
+    c->iforce.assign(force, force + 3 * c->ninst);
+    bool forced = false;
+    for (double f : c->iforce) forced |= f != 0.0;
+    std::vector<char> consts = c->storage == LBM_F64 ? make_consts<double>(c) : make_consts<float>(c);
+    if (consts.size() != c->h_consts.size()) return fail(c, LBM_EINVAL, "lbm_set_forces: constants size");
+    CK(cudaStreamSynchronize(c->stream), "lbm_set_forces");
+    CK(cudaMemcpy(c->d_consts, consts.data(), consts.size(), cudaMemcpyHostToDevice), "lbm_set_forces upload");
+    c->h_consts.swap(consts);
+    c->forced = forced;
+    invalidate_graphs(c);
+    return LBM_OK;
+}
+
+int lbm_run_to_residual_each(lbm_ctx *c, double tol, int check_every, int interval, long long max_steps,
+                             long long *steps, double *res)
+{
+    if (!c || check_every <= 0 || max_steps < 0 || !steps || (interval && (check_every & 1)))
+        return fail(c, LBM_EINVAL, "lbm_run_to_residual_each: bad arguments (interval residuals need an "
+                    "even check_every)");
+    const int K = c->ninst;
+    std::vector<double> r(size_t(K), INFINITY);
+    // PDF range of each instance (its Blocks are contiguous)
+    std::vector<long long> lo(size_t(K), -1), hi(size_t(K), 0);
+    for (const BlockGeom &b : c->blocks) {
+        if (lo[size_t(b.inst)] < 0) lo[size_t(b.inst)] = b.pdf_base;
+        hi[size_t(b.inst)] = b.pdf_base + (long long)Q * b.G;
+    }
+    for (int k = 0; k < K; ++k) steps[k] = -1;
+    c->active.assign(size_t(K), 1);
+    int remaining = K, rc = LBM_OK;
+    long long done = 0;
+    if (interval && (rc = lbm_snapshot_velocity(c))) {
+        c->active.clear();
+        return rc;
+    }
+    while (remaining > 0 && done < max_steps) {
+        const int n = int(std::min<long long>(check_every, max_steps - done));
+        if ((rc = lbm_step(c, n))) break;
+        done += n;
+        double tot = 0;
+        if (interval) {
+            if ((rc = lbm_residual_vs_snapshot(c, n, &tot, r.data()))) break;
+            if ((rc = lbm_snapshot_velocity(c))) break;
+        } else if ((rc = lbm_residual(c, &tot, r.data()))) {
+            break;
+        }
+        bool changed = false;
+        for (int k = 0; k < K && rc == LBM_OK; ++k) {
+            if (steps[k] >= 0) continue;
+            if (std::isnan(r[size_t(k)])) {
+                rc = fail(c, LBM_ENUMERIC, "instance %d: residual is NaN after %lld steps", k, done);
+            } else if (r[size_t(k)] < tol) {
+                // converged: keep its state in both buffers and stop sweeping it
+                steps[k] = done;
+                if (res) res[k] = r[size_t(k)];
+                char *b0 = static_cast<char *>(c->buf[c->cur]), *b1 = static_cast<char *>(c->buf[c->cur ^ 1]);
+                const size_t off = size_t(lo[size_t(k)]) * c->elem, len = size_t(hi[size_t(k)] - lo[size_t(k)]) * c->elem;
+                CK(cudaMemcpyAsync(b1 + off, b0 + off, len, cudaMemcpyDeviceToDevice, c->stream), "freeze copy");
+                c->active[size_t(k)] = 0;
+                --remaining;
+                changed = true;
+            }
+        }
+        if (rc) break;
+        if (changed && remaining > 0 && (rc = set_sweep(c, c->sw_tile, c->flat, c->grid))) break;
+    }
+    for (int k = 0; k < K; ++k)
+        if (steps[k] < 0 && res) res[k] = r[size_t(k)];
+    c->active.clear();
+    const int rc2 = set_sweep(c, c->sw_tile, c->flat, c->grid);
+    return rc ? rc : rc2;
 }
 
 int lbm_get_info(lbm_ctx *c, lbm_info *info)

@@ -154,6 +154,49 @@ __global__ void __launch_bounds__(256) init_eq_kernel(const __grid_constant__ Fi
     });
 }
 
+// f~ += f~eq(drho, u_target) - f~eq(drho, u_now) in every fluid cell: the
+// velocity becomes u_target (the moments' definition of u), the density and
+// the non-equilibrium part stay.  Alternated with time steps this relaxes
+// the stress and density to a prescribed velocity field (consistent
+// initialisation in the sense of Mei et al.).
+template <int ST>
+__global__ void __launch_bounds__(256) impose_u_kernel(const __grid_constant__ FieldArgs a, void *buf,
+                                                       const float *u)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    for_each_cell(a, [&](const CellPos &p) {
+        const BlockGeom &b = *p.b;
+        if (a.flags[b.cell_base + p.cf] & F_KIND) return;
+        const CollideConsts<T> &P = cs[b.inst];
+        const long long N = inst_cells(b);
+        S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
+        T f[Q];
+        T jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            f[q] = Tr::to_t(g[(long long)q * b.G]);
+            jx += T(ex(q)) * f[q];
+            jy += T(ey(q)) * f[q];
+            jz += T(ez(q)) * f[q];
+        }
+        const T n0 = jx * P.ufac - P.uoff[0], n1 = jy * P.ufac - P.uoff[1], n2 = jz * P.ufac - P.uoff[2];
+        const float *v = u + 3 * b.out_base;
+        const T t0 = v[p.o], t1 = v[N + p.o], t2 = v[2 * N + p.o];
+        const T nsq = n0 * n0 + n1 * n1 + n2 * n2, tsq = t0 * t0 + t1 * t1 + t2 * t2;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const T en = T(ex(q)) * n0 + T(ey(q)) * n1 + T(ez(q)) * n2;
+            const T et = T(ex(q)) * t0 + T(ey(q)) * t1 + T(ez(q)) * t2;
+            const T d = T(wq(q)) * P.rho0s *
+                        (T(3) * (et - en) + T(4.5) * (et * et - en * en) - T(1.5) * (tsq - nsq));
+            g[(long long)q * b.G] = Tr::from_t(f[q] + d);
+        }
+    });
+}
+
 // ------------------------------------------------------------ PDF in/out
 template <int ST>
 __global__ void __launch_bounds__(256) get_pdfs_kernel(const __grid_constant__ FieldArgs a,
@@ -337,6 +380,67 @@ __global__ void __launch_bounds__(256) residual_tiles_kernel(const __grid_consta
     block_partials(acc, partial + t * R_K);
 }
 
+// Velocity change against a stored velocity field (the macroscopic output
+// layout): per tile sum |u - u_snap|^2 and |u|^2 over fluid cells; the
+// per-cell velocity is formed in the storage's arithmetic type, the sums in
+// FP64.
+template <int ST>
+__global__ void __launch_bounds__(256) residual_snap_kernel(const __grid_constant__ FieldArgs a,
+                                                            const void *cur, const float *usnap,
+                                                            double *partial)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> *cs = static_cast<const CollideConsts<T> *>(a.consts);
+    double acc[R_K];
+#pragma unroll
+    for (int k = 0; k < R_K; ++k) acc[k] = 0.0;
+    const long long t = blockIdx.x;
+    const Tile tile = a.tiles[t];
+    const BlockGeom &b = a.blocks[tile.block];
+    const int x = tile.x0 + int(threadIdx.x);
+    const int y = tile.y0 + int(threadIdx.y);
+    if (x < b.nx && y < b.ny) {
+        const CollideConsts<T> &P = cs[b.inst];
+        const T ufac = P.ufac, uo[3] = {P.uoff[0], P.uoff[1], P.uoff[2]};
+        const int zend = min(tile.z0 + a.tz, b.nz);
+        const int pxy = b.px * b.py, pxyf = b.pxf * b.py;
+        const long long N = inst_cells(b);
+        const float *us = usnap + 3 * b.out_base;
+        T du2 = T(0), u2 = T(0), nf = T(0), bad = T(0);
+        for (int z = tile.z0; z < zend; ++z) {
+            const int c = (z + 1) * pxy + (y + 1) * b.px + x;
+            const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
+            if (a.flags[b.cell_base + cf] & F_KIND) continue;
+            const long long o = ((long long)(b.gz + z) * b.NY + (b.gy + y)) * b.NX + (b.gx + x);
+            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
+            T j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const T v = Tr::to_t(g[(long long)q * b.G]);
+                if (ex(q)) j[0] += ex(q) > 0 ? v : -v;
+                if (ey(q)) j[1] += ey(q) > 0 ? v : -v;
+                if (ez(q)) j[2] += ez(q) > 0 ? v : -v;
+            }
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const T u = j[m] * ufac - uo[m];
+                const T du = u - T(us[m * N + o]);
+                u2 += u * u;
+                du2 += du * du;
+            }
+            nf += T(1);
+            if (!isfinite(j[0] + j[1] + j[2])) bad += T(1);
+        }
+        acc[R_DU2] = double(du2);
+        acc[R_U2] = double(u2);
+        acc[R_NFLUID] = double(nf);
+        acc[R_NONFINITE] = double(bad);
+    }
+    block_partials(acc, partial + t * R_K);
+}
+
 __global__ void __launch_bounds__(256) reduce_instances_kernel(const double *partial,
                                                                const long long *begin, double *out)
 {
@@ -433,6 +537,30 @@ cudaError_t launch_reduce(const FieldArgs &a, const void *cur, const void *prev,
             LBM_DISPATCH_ST(a.storage, CALL)
 #undef CALL
         }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    reduce_instances_kernel<<<ninst, 256, 0, s>>>(partial, inst_tile_begin, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_impose_velocity(const FieldArgs &a, void *buf, const float *u, cudaStream_t s)
+{
+    if (a.ntiles == 0) return cudaSuccess;
+#define CALL(ST) impose_u_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, buf, u)
+    LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_snap(const FieldArgs &a, const void *cur, const float *usnap, double *partial,
+                               const long long *inst_tile_begin, int ninst, double *out, cudaStream_t s)
+{
+    if (a.tx * a.ty > 256) return cudaErrorInvalidValue;
+    if (a.ntiles > 0) {
+#define CALL(ST) residual_snap_kernel<ST><<<field_grid(a), field_block(a), 0, s>>>(a, cur, usnap, partial)
+        LBM_DISPATCH_ST(a.storage, CALL)
+#undef CALL
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

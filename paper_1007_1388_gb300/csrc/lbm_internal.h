@@ -202,6 +202,12 @@ cudaError_t launch_init_equilibrium(const FieldArgs &a, void *buf, const float *
 cudaError_t launch_get_pdfs(const FieldArgs &a, const void *buf, double *f, cudaStream_t s);
 cudaError_t launch_set_pdfs(const FieldArgs &a, void *buf, const double *f, cudaStream_t s);
 cudaError_t launch_zero(void *buf, size_t bytes, cudaStream_t s);
+// Sets the velocity of every fluid cell to u (macroscopic layout), keeping
+// density and the non-equilibrium part
+cudaError_t launch_impose_velocity(const FieldArgs &a, void *buf, const float *u, cudaStream_t s);
+// Velocity change against a stored velocity field (macroscopic layout)
+cudaError_t launch_reduce_snap(const FieldArgs &a, const void *cur, const float *usnap, double *partial,
+                               const long long *inst_tile_begin, int ninst, double *out, cudaStream_t s);
 // FP64 reductions: per-tile partials then per-instance totals
 cudaError_t launch_reduce(const FieldArgs &a, const void *cur, const void *prev, double *partial,
                           const long long *inst_tile_begin, int ninst, double *out,

@@ -245,6 +245,83 @@ __global__ void unpad_grad_kernel(const float *__restrict__ src, int cout, int c
     dst[i] = src[r * cinp + ci];
 }
 
+// target[k][c][0..3] = {(rho - rho0) / (F_k s_rho), u_a / (F_k s_u)} (0 in solid cells)
+// from the batch layout rho [nb][V], u [nb][3][V]
+__global__ void targets_kernel(const float *__restrict__ rho, const float *__restrict__ u,
+                               const uint8_t *__restrict__ solid, const float *__restrict__ force, long long V,
+                               long long n, float rho0, float s_rho, float s_u, float *__restrict__ target)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long k = i / V, c = i - k * V;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!solid[i]) {
+        const float f = force[k];
+        const float *uk = u + 3 * k * V;
+        t = make_float4((rho[i] - rho0) / (f * s_rho), uk[c] / (f * s_u), uk[V + c] / (f * s_u),
+                        uk[2 * V + c] / (f * s_u));
+    }
+    reinterpret_cast<float4 *>(target)[i] = t;
+}
+
+// the inverse map: rho = rho0 + F_k s_rho y0, u_a = F_k s_u y_{1+a}; solid cells rho0, 0
+__global__ void fields_kernel(const float *__restrict__ pred, const uint8_t *__restrict__ solid,
+                              const float *__restrict__ force, long long V, long long n, float rho0, float s_rho,
+                              float s_u, float *__restrict__ rho, float *__restrict__ u)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long k = i / V, c = i - k * V;
+    const float4 y = reinterpret_cast<const float4 *>(pred)[i];
+    const bool fl = !solid[i];
+    const float f = force[k];
+    rho[i] = fl ? rho0 + f * s_rho * y.x : rho0;
+    float *uk = u + 3 * k * V;
+    uk[c] = fl ? f * s_u * y.y : 0.f;
+    uk[V + c] = fl ? f * s_u * y.z : 0.f;
+    uk[2 * V + c] = fl ? f * s_u * y.w : 0.f;
+}
+
+// One [1 2 1]/4 pass along axis `ax` (0 = x, 1 = y, 2 = z) of K fields of
+// `comps` components on n^3 grids ([K][comps][V], x fastest): periodic along
+// x and z, the edge value repeated beyond the y walls; solid cells hold 0 and
+// contribute 0.
+__global__ void smooth_kernel(const float *__restrict__ in, float *__restrict__ out, const uint8_t *__restrict__ solid,
+                              long long n_total, int comps, int ln, int ax)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_total) return;
+    const int n = 1 << ln;
+    const long long V = 1ll << (3 * ln);
+    const long long kc = i >> (3 * ln);        // field index k * comps + component
+    const long long c = i & (V - 1);
+    const long long k = kc / comps;
+    if (solid[k * V + c]) {
+        out[i] = 0.f;
+        return;
+    }
+    const int x = int(c & (n - 1)), y = int((c >> ln) & (n - 1)), z = int(c >> (2 * ln));
+    int m[2];
+    if (ax == 0) {
+        m[0] = (x - 1) & (n - 1);
+        m[1] = (x + 1) & (n - 1);
+    } else if (ax == 1) {
+        m[0] = y > 0 ? y - 1 : y;
+        m[1] = y < n - 1 ? y + 1 : y;
+    } else {
+        m[0] = (z - 1) & (n - 1);
+        m[1] = (z + 1) & (n - 1);
+    }
+    const long long base = kc * V;
+    auto at = [&](int j) {
+        const long long cc = ax == 0 ? ((long long)z << (2 * ln)) + ((long long)y << ln) + j
+                           : ax == 1 ? ((long long)z << (2 * ln)) + ((long long)j << ln) + x
+                                     : ((long long)j << (2 * ln)) + ((long long)y << ln) + x;
+        return in[base + cc];
+    };
+    out[i] = 0.25f * at(m[0]) + 0.5f * in[i] + 0.25f * at(m[1]);
+}
+
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
                             float c2)
@@ -814,6 +891,48 @@ int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_wgrad: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_wgrad: a bounded wait timed out");
     return LBM_OK;
+}
+
+int unet_targets_from_fields(const float *rho, const float *u, const uint8_t *solid, const float *force, int nb,
+                             long long V, float rho0, float s_rho, float s_u, float *target, void *stream)
+{
+    if (!rho || !u || !solid || !force || !target || nb < 1 || V < 1 || !(s_rho != 0.f) || !(s_u != 0.f))
+        return ufail(nullptr, LBM_EINVAL, "unet_targets_from_fields: bad arguments");
+    const long long n = (long long)nb * V;
+    targets_kernel<<<blocks_for(n), EW, 0, static_cast<cudaStream_t>(stream)>>>(rho, u, solid, force, V, n, rho0,
+                                                                                s_rho, s_u, target);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : ufail(nullptr, LBM_ECUDA, "targets: %s", cudaGetErrorString(e));
+}
+
+int unet_fields_from_prediction(const float *pred, const uint8_t *solid, const float *force, int nb, long long V,
+                                float rho0, float s_rho, float s_u, float *rho, float *u, void *stream)
+{
+    if (!pred || !solid || !force || !rho || !u || nb < 1 || V < 1)
+        return ufail(nullptr, LBM_EINVAL, "unet_fields_from_prediction: bad arguments");
+    const long long n = (long long)nb * V;
+    fields_kernel<<<blocks_for(n), EW, 0, static_cast<cudaStream_t>(stream)>>>(pred, solid, force, V, n, rho0, s_rho,
+                                                                               s_u, rho, u);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : ufail(nullptr, LBM_ECUDA, "fields: %s", cudaGetErrorString(e));
+}
+
+int unet_smooth_fields(float *f, float *scratch, const uint8_t *solid, int K, int comps, int n, int passes,
+                       void *stream)
+{
+    if (!f || !scratch || !solid || K < 1 || comps < 1 || n < 2 || (n & (n - 1)) || passes < 0)
+        return ufail(nullptr, LBM_EINVAL, "unet_smooth_fields: bad arguments");
+    const int ln = ilog2(n);
+    const long long tot = (long long)K * comps << (3 * ln);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int p = 0; p < passes; ++p)
+        for (int ax = 0; ax < 3; ++ax) {
+            smooth_kernel<<<blocks_for(tot), EW, 0, s>>>(f, scratch, solid, tot, comps, ln, ax);
+            const cudaError_t e = cudaMemcpyAsync(f, scratch, sizeof(float) * tot, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "smooth: %s", cudaGetErrorString(e));
+        }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LBM_OK : ufail(nullptr, LBM_ECUDA, "smooth: %s", cudaGetErrorString(e));
 }
 
 }  // extern "C"

@@ -101,6 +101,12 @@ SIGNATURES = {
     "lbm_invariants": ([_vp, _P(_d), _P(_d), _P(_d), _vp], _i),
     "lbm_residual": ([_vp, _P(_d), _vp], _i),
     "lbm_run_to_residual": ([_vp, _d, _i, _ll, _P(_ll), _P(_d)], _i),
+    "lbm_run_to_residual_each": ([_vp, _d, _i, _i, _ll, _vp, _vp], _i),
+    "lbm_snapshot_velocity": ([_vp], _i),
+    "lbm_impose_velocity_device": ([_vp, _vp], _i),
+    "lbm_init_consistent_device": ([_vp, _vp, _vp, _i], _i),
+    "lbm_residual_vs_snapshot": ([_vp, _i, _P(_d), _vp], _i),
+    "lbm_set_forces": ([_vp, _vp], _i),
     "lbm_get_info": ([_vp, _P(lbm_info)], _i),
     "lbm_profile_enable": ([_vp, _i], _i),
     "lbm_profile_read": ([_vp, _P(lbm_profile)], _i),
@@ -124,6 +130,11 @@ SIGNATURES = {
     "unet_last_error": ([_vp], ctypes.c_char_p),
     "unet_conv3": ([_vp, _i, _i, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp], _i),
     "unet_conv3_wgrad": ([_vp, _i, _i, _vp, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp], _i),
+    "unet_targets_from_fields": ([_vp, _vp, _vp, _vp, _i, _ll, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  _vp, _vp], _i),
+    "unet_fields_from_prediction": ([_vp, _vp, _vp, _i, _ll, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     _vp, _vp, _vp], _i),
+    "unet_smooth_fields": ([_vp, _vp, _vp, _i, _i, _i, _i, _vp], _i),
 }
 
 _lib = None
@@ -370,6 +381,46 @@ def lbm_run_to_residual(ctx: Ctx, tol: float, check_every: int = 10, max_steps: 
     _check(lib().lbm_run_to_residual(ctx.ptr, float(tol), int(check_every), int(max_steps),
                                      ctypes.byref(steps), ctypes.byref(r)), ctx)
     return steps.value, r.value
+
+
+def lbm_set_forces(ctx: Ctx, force):
+    """force: (instances, 3) array of per-instance body forces."""
+    f = np.ascontiguousarray(np.asarray(force, np.float64).reshape(-1))
+    if f.size != 3 * lbm_get_info(ctx).instances:
+        raise ValueError("need 3 force components per instance")
+    _check(lib().lbm_set_forces(ctx.ptr, f.ctypes.data_as(ctypes.c_void_p)), ctx)
+
+
+def lbm_run_to_residual_each(ctx: Ctx, tol: float, check_every: int = 50, max_steps: int = 10**6,
+                             interval: bool = False):
+    """Per-instance steps to residual tol (-1 where not reached) and residuals;
+    interval: the change per step over each chunk instead of the one-step residual."""
+    k = lbm_get_info(ctx).instances
+    steps = np.empty(k, np.int64)
+    res = np.empty(k, np.float64)
+    _check(lib().lbm_run_to_residual_each(ctx.ptr, float(tol), int(check_every), int(bool(interval)),
+                                          int(max_steps), steps.ctypes.data_as(ctypes.c_void_p),
+                                          res.ctypes.data_as(ctypes.c_void_p)), ctx)
+    return steps, res
+
+
+def lbm_impose_velocity_device(ctx: Ctx, u):
+    _check(lib().lbm_impose_velocity_device(ctx.ptr, _ptr(u)), ctx)
+
+
+def lbm_init_consistent_device(ctx: Ctx, rho, u, iterations: int):
+    _check(lib().lbm_init_consistent_device(ctx.ptr, _ptr(rho), _ptr(u), int(iterations)), ctx)
+
+
+def lbm_snapshot_velocity(ctx: Ctx):
+    _check(lib().lbm_snapshot_velocity(ctx.ptr), ctx)
+
+
+def lbm_residual_vs_snapshot(ctx: Ctx, steps_since: int, per_instance: bool = False):
+    r = ctypes.c_double()
+    per = np.zeros(ctx.ninst) if per_instance else None
+    _check(lib().lbm_residual_vs_snapshot(ctx.ptr, int(steps_since), ctypes.byref(r), _ptr(per)), ctx)
+    return (r.value, per) if per_instance else r.value
 
 
 def lbm_get_info(ctx: Ctx) -> lbm_info:

@@ -129,3 +129,32 @@ def conv3_wgrad(src0, c0, dy, cout, dw, grid, *, up0=False, src1=None, c1=0, str
         ctypes.c_void_p(dy.data_ptr()), cout, ctypes.c_void_p(dw.data_ptr()), nb, lz, ly, lx,
         ctypes.c_void_p(s.cuda_stream)))
     return dw
+
+
+def targets_from_fields(rho, u, solid, force, nb, V, rho0, s_rho, s_u, target, stream):
+    """Normalised targets [nb][V][4] from batch fields (all CUDA tensors)."""
+    _check(lib().unet_targets_from_fields(
+        ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(solid.data_ptr()),
+        ctypes.c_void_p(force.data_ptr()), nb, V, rho0, s_rho, s_u, ctypes.c_void_p(target.data_ptr()),
+        ctypes.c_void_p(stream.cuda_stream)))
+    return target
+
+
+def fields_from_prediction(pred, solid, force, nb, V, rho0, s_rho, s_u, rho, u, stream):
+    """Batch fields rho [nb][V], u [nb][3][V] from a prediction (all CUDA tensors)."""
+    _check(lib().unet_fields_from_prediction(
+        ctypes.c_void_p(pred.data_ptr()), ctypes.c_void_p(solid.data_ptr()), ctypes.c_void_p(force.data_ptr()),
+        nb, V, rho0, s_rho, s_u, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+        ctypes.c_void_p(stream.cuda_stream)))
+    return rho, u
+
+
+def smooth_fields(f, solid, K, comps, n, passes, stream):
+    """In-place binomial smoothing of device fields [K][comps][n^3] (float32)."""
+    import torch
+
+    scratch = torch.empty_like(f)
+    _check(lib().unet_smooth_fields(ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(scratch.data_ptr()),
+                                    ctypes.c_void_p(solid.data_ptr()), K, comps, n, passes,
+                                    ctypes.c_void_p(stream.cuda_stream)))
+    return f

@@ -10,8 +10,12 @@ channel / porous-media cases of the benchmark configurations):
   channel(dims)        periodic x and z, resting walls at -y/+y (Poiseuille)
   sphere_packing(...)  random non-overlapping spheres in a channel
   batch_instances(...) many uneven channels with sphere packings and tau
+  channel_samples(...) the learned warm start's samples: n^3 sphere-packed
+                       channels with porosity and driving force per seed
 """
 from __future__ import annotations
+
+import os
 
 import numpy as np
 
@@ -105,3 +109,28 @@ def batch_instances(seed=1234, n=256, lo=16, hi=96, tau_lo=0.55, tau_hi=1.2,
         por = float(rng.uniform(por_lo, por_hi))
         out.append((dims, tau, sphere_packing(rng, dims, por)))
     return out
+
+
+def channel_sample(seed: int, n: int = 64, f_lo: float = 5e-7, f_hi: float = 5e-6, por_lo: float = 0.7,
+                   por_hi: float = 0.9):
+    """One warm-start sample from default_rng(seed): porosity U[por_lo, por_hi],
+    force U[f_lo, f_hi] along x, then the sphere packing of an n^3 channel."""
+    rng = np.random.default_rng(seed)
+    porosity = float(rng.uniform(por_lo, por_hi))
+    force = float(rng.uniform(f_lo, f_hi))
+    return sphere_packing(rng, (n, n, n), porosity), force
+
+
+def channel_samples(seeds, n: int = 64, processes: int | None = None):
+    """channel_sample for every seed, in order; a pool of spawned processes
+    (no CUDA state is inherited) when there are many."""
+    seeds = [int(s) for s in seeds]
+    if processes == 1 or len(seeds) < 16:
+        return [channel_sample(s, n) for s in seeds]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    procs = processes or min(len(seeds), os.cpu_count() or 1)
+    # a worker that cannot start raises BrokenProcessPool here instead of hanging
+    with ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(channel_sample, seeds, [n] * len(seeds), chunksize=max(1, len(seeds) // (4 * procs))))

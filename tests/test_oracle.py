@@ -323,3 +323,29 @@ def test_threaded_step_is_identical(orc):
     finally:
         orc.set_threads(1)
     assert np.array_equal(a, b)
+
+
+def test_staggered_mode_stalls_the_one_step_residual(orc):
+    """Bounce-back on spheres in a periodic channel excites a period-2
+    (staggered) mode that neither BGK nor TRT damps: the one-step velocity
+    residual stalls near 1e-4 while the change over two steps is at
+    roundoff, i.e. the flow itself is steady.  This fixes the reading of the
+    convergence criterion for sphere packings (change per step over an even
+    interval)."""
+    from paper_1007_1388_gb300 import workloads as W
+
+    n = 16
+    fl, F = W.channel_sample(6, n)
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        for coll in (orc.BGK, orc.TRT):
+            p = orc.Problem(dims=(n, n, n), tau=0.8, flags=fl, periodic=(1, 0, 1), force=(F, 0, 0),
+                            collision=coll)
+            f = orc.run(p, orc.zeros(p), 6000)
+            g = orc.step(p, f)
+            h = orc.step(p, g)
+            one = orc.residual(p, f, g)
+            two = orc.residual(p, f, h)
+            assert one > 1e-5 and two < 1e-12, (coll, one, two)
+    finally:
+        orc.set_threads(1)
