@@ -554,6 +554,115 @@ def run_warmstart_report(args):
     return 0
 
 
+def _peak_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+def run_unet_report(args):
+    """Tensor-core U-Net at 64^3 x 4 samples: training-step time, and each
+    convolution shape's forward and weight-gradient launch with CUDA events,
+    as TFLOP/s against the measured bf16 peak.  One JSON line."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1007_1388_gb300 import build
+
+    build.build()
+    import paper_1007_1388_gb300 as L
+    from paper_1007_1388_gb300 import unet, workloads as W
+
+    L.use_torch_allocator()
+    n, nb = args.ws_size, 4
+    V = nb * n ** 3
+    rng = np.random.default_rng(0)
+    solid = torch.from_numpy(np.concatenate([W.channel_sample(s, n)[0].reshape(-1) for s in range(nb)])).cuda()
+    target = torch.randn(V * 4, device="cuda") * 0.5
+    net = unet.UNet(n, nb, seed=3)
+    force = [0.5] * nb
+    for _ in range(3):
+        net.train_step(solid, force, target, 1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = args.unet_steps
+    e0.record(net.stream)
+    for _ in range(steps):
+        net.train_step(solid, force, target, 1e-4)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / steps
+    out = torch.empty(V * 4, device="cuda")
+    e0.record(net.stream)
+    for _ in range(steps):
+        net.predict(solid, force, out)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    ms_pred = e0.elapsed_time(e1) / steps
+    # forward FLOPs (2 per multiply-add) of the ten convolutions and the head
+    l = int(round(np.log2(n)))
+    convs = [("W1a", 16, 0, 0, 16, 0), ("W1b", 16, 0, 0, 16, 0), ("W2a", 16, 0, 0, 32, 1), ("W2b", 32, 0, 0, 32, 1),
+             ("W3a", 32, 0, 0, 64, 2), ("W3b", 64, 0, 0, 64, 2), ("W4a", 64, 1, 32, 32, 1),
+             ("W4b", 32, 0, 0, 32, 1), ("W5a", 32, 1, 16, 16, 0), ("W5b", 16, 0, 0, 16, 0)]
+    true_cin = {"W1a": 2}
+    fwd_flops = 0.0
+    layers = {}
+    peak, peak_sus, kind = _peak_bf16()
+    s = torch.cuda.current_stream()
+    for name, c0, up0, c1, cout, lev in convs:
+        g = (nb, l - lev, l - lev, l - lev)
+        Vl = nb << (3 * (l - lev))
+        cin = c0 + c1
+        useful = 2.0 * 27 * true_cin.get(name, cin) * cout * Vl
+        fwd_flops += useful
+        s0 = torch.randn((Vl >> 3 if up0 else Vl) * c0, device="cuda").to(torch.bfloat16)
+        s1 = torch.randn(Vl * c1, device="cuda").to(torch.bfloat16) if c1 else None
+        w = (torch.randn(cout * 27 * cin, device="cuda") * 0.05).to(torch.bfloat16)
+        o = torch.empty(Vl * cout, device="cuda", dtype=torch.bfloat16)
+        dy = torch.randn(Vl * cout, device="cuda").to(torch.bfloat16)
+        dw = torch.empty(cout * 27 * cin, device="cuda")
+        for _ in range(3):
+            unet.conv3(s0, c0, w, o, cout, g, up0=bool(up0), src1=s1, c1=c1, relu=True, stream=s)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(20):
+            unet.conv3(s0, c0, w, o, cout, g, up0=bool(up0), src1=s1, c1=c1, relu=True, stream=s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_f = e0.elapsed_time(e1) / 20
+        unet.conv3_wgrad(s0, c0, dy, cout, dw, g, up0=bool(up0), src1=s1, c1=c1, stream=s)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(5):
+            unet.conv3_wgrad(s0, c0, dy, cout, dw, g, up0=bool(up0), src1=s1, c1=c1, stream=s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t_w = e0.elapsed_time(e1) / 5
+        mma = 2.0 * 27 * cin * cout * Vl  # what the tensor cores execute (padded channels included)
+        # algorithmic bytes of a forward launch: read the input once, write the output once (bf16)
+        bytes_f = 2.0 * ((Vl >> 3 if up0 else Vl) * c0 + Vl * c1 + Vl * cout)
+        layers[name] = {"voxels": Vl, "cin": cin, "cout": cout, "fwd_ms": t_f, "fwd_tflops": mma / t_f / 1e9,
+                        "fwd_gbs": bytes_f / t_f / 1e6, "wgrad_ms": t_w, "wgrad_tflops": mma / t_w / 1e9}
+    fwd_flops += 2.0 * 16 * 4 * V
+    train_flops = 3.0 * fwd_flops
+    top = max(layers, key=lambda k: layers[k]["fwd_ms"])
+    res = {"report": "unet", "workload": f"U-Net training step, {nb} samples of {n}^3 (bf16 operands, FP32 "
+                                         "accumulation, tcgen05)",
+           "ms_per_train_step": ms_step, "ms_per_prediction": ms_pred,
+           "train_tflops_effective": train_flops / ms_step / 1e9, "forward_gflop": fwd_flops / 1e9,
+           "layers": layers, "peak_bf16_tflops": peak, "peak_kind": kind,
+           "roofline": {"kernel": "lbm::conv3_kernel", "layer": top, "bound": "tensor",
+                        "achieved": layers[top]["fwd_tflops"], "peak": peak, "unit": "TFLOP/s",
+                        "frac": layers[top]["fwd_tflops"] / peak}}
+    net.destroy()
+    print(json.dumps(res))
+    return 0
+
+
 def _ncu_traffic(name):
     """DRAM bytes per launch from the committed ncu summary, if it is current."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -581,7 +690,7 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
-    ap.add_argument("--report", default="", choices=["", "precision", "warmstart"],
+    ap.add_argument("--report", default="", choices=["", "precision", "warmstart", "unet"],
                     help="precision: storage-precision report on the 384^3 cavity; warmstart: the learned "
                          "warm start end to end (one JSON line each)")
     ap.add_argument("--ws-size", type=int, default=64)
@@ -589,6 +698,7 @@ def main():
     ap.add_argument("--ws-eval", type=int, default=200)
     ap.add_argument("--ws-epochs", type=int, default=40)
     ap.add_argument("--ws-chunk", type=int, default=250)
+    ap.add_argument("--unet-steps", type=int, default=20)
     ap.add_argument("--report-size", type=int, default=384)
     ap.add_argument("--report-steps", type=int, default=5000)
     ap.add_argument("--report-block", type=int, default=128)
@@ -613,6 +723,8 @@ def main():
         return run_precision_report(args)
     if args.report == "warmstart":
         return run_warmstart_report(args)
+    if args.report == "unet":
+        return run_unet_report(args)
     return run_gpu(args)
 
 
