@@ -98,14 +98,21 @@ __global__ void relu_bwd_kernel(const float *__restrict__ g, const bf16 *__restr
     }
 }
 
-// out[c] (+)= sum over rows (in order) of part[row][c]
+// out[c] = sum over rows of part[row][c]: one block per column, a fixed
+// tree order (deterministic)
 __global__ void reduce_cols_kernel(const float *__restrict__ part, int rows, int C, float *__restrict__ out)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+    __shared__ float sh[EW];
+    const int c = blockIdx.x;
     float s = 0.f;
-    for (int r = 0; r < rows; ++r) s += part[(long long)r * C + c];
-    out[c] = s;
+    for (int r = threadIdx.x; r < rows; r += EW) s += part[(long long)r * C + c];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = EW / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sh[0];
 }
 
 // adjoint of nearest upsampling of the first c0 channels of a concatenation:
@@ -543,7 +550,7 @@ int relu_bwd(unet_ctx *c, const float *g, const bf16 *y, long long V, int C, int
     int nblk = int(std::min<long long>(c->relu_blocks, (n + EW - 1) / EW));
     if (nblk < 1) nblk = 1;
     relu_bwd_kernel<<<nblk, EW, 0, c->stream>>>(g, y, c->dy, c->bpart, n, C);
-    reduce_cols_kernel<<<1, 128, 0, c->stream>>>(c->bpart, nblk, C, c->grads + kLayout.b[k]);
+    reduce_cols_kernel<<<C, EW, 0, c->stream>>>(c->bpart, nblk, C, c->grads + kLayout.b[k]);
     UCK(cudaGetLastError(), "relu backward");
     return LBM_OK;
 }
@@ -607,7 +614,7 @@ int backward(unet_ctx *c, const float *target, double *loss)
     float *G = c->grads;
     head_kernel<<<c->head_blocks, EW, 0, c->stream>>>(c->d1, c->params + L.wh, c->params + L.bh, target, nullptr,
                                                       c->gd1, c->hpart, c->V1);
-    reduce_cols_kernel<<<1, 128, 0, c->stream>>>(c->hpart, c->head_blocks, 72, c->wtmp);
+    reduce_cols_kernel<<<72, EW, 0, c->stream>>>(c->hpart, c->head_blocks, 72, c->wtmp);
     UCK(cudaGetLastError(), "head");
     UCK(cudaMemcpyAsync(G + L.wh, c->wtmp, sizeof(float) * 68, cudaMemcpyDeviceToDevice, c->stream), "head grad");
     float hl = 0.f;
