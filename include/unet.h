@@ -6,7 +6,7 @@
  * Boltzmann sweep of Sec. 2.1 converges to; the solver is then initialised
  * at that equilibrium (lbm_init_equilibrium) instead of at rest.  The
  * network's convolutions run on the tensor cores (tcgen05, BF16 operands,
- * FP32 accumulation in TMEM); everything else in the forward and backward
+ * FP32 accumulation in TMEM, operand tiles staged by TMA); everything else in the forward and backward
  * passes, the loss and the Adam update run in the library's own CUDA
  * kernels.  Master parameters, gradients and optimiser state are FP32.
  *
@@ -106,6 +106,28 @@ int unet_conv3(const void *src0, int c0, int up0, const void *src1, int c1, cons
  */
 int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1, const void *dy, int cout,
                      float *dw, int nb, int lz, int ly, int lx, void *stream);
+
+/*
+ * Halo layout (the network's own activations): a bf16 tensor of nb grids of
+ * 2^lz x 2^ly x 2^lx voxels with C channels stored as
+ * [nb][nz + 2][ny][nx + 2][C]; padded x column 0 repeats x = nx - 1, column
+ * nx + 1 repeats x = 0, padded z plane 0 repeats z = nz - 1 and plane nz + 1
+ * repeats z = 0; voxel (b, z, y, x) is at (b, z + 1, y, x + 1).
+ *
+ * unet_conv3_halo - the convolution of unet_conv3 (no upsampled source) on
+ * halo-layout bf16 tensors with TMA-fed tensor-core tiles; a bf16 out is
+ * written in the halo layout (periodic copies included), an fp32 out as
+ * [M][cout].  Same result as unet_conv3 on the same data.  Synchronises.
+ * nb * nz * ny * nx must be a multiple of 128; pointers 16-byte aligned.
+ *
+ * unet_conv3_halo_wgrad - the weight gradient on halo-layout src0 / src1 / dy
+ * (dw fp32 [cout][27][c0 + c1]).  Workspace from the allocator hooks;
+ * synchronises.
+ */
+int unet_conv3_halo(const void *src0, int c0, const void *src1, int c1, const void *w, const float *bias, void *out,
+                    int out_f32, int relu, int cout, int nb, int lz, int ly, int lx, void *stream);
+int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, const void *dy, int cout, float *dw,
+                          int nb, int lz, int ly, int lx, void *stream);
 
 /*
  * unet_targets_from_fields - normalised training targets from the fields of

@@ -28,7 +28,7 @@
 
 #include <cuda_runtime.h>
 
-#include "lbm_internal.h"
+#include "sweep_types.h"
 
 namespace lbm {
 

@@ -51,6 +51,24 @@ struct DevMem {
 }  // namespace
 
 namespace lbm {
+void *tma_encode_fn()
+{
+    static void *fn = nullptr;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
 void current_allocator(lbm_alloc_fn *alloc, lbm_free_fn *release, void **user)
 {
     std::lock_guard<std::mutex> lk(g_alloc_mu);

@@ -6,7 +6,7 @@
 #include <cuda_fp16.h>
 
 #include "collide.cuh"
-#include "lbm_internal.h"
+#include "sweep_types.h"
 
 namespace lbm {
 

@@ -4,6 +4,7 @@
 #include <cstdio>
 
 #include "device_common.cuh"
+#include "lbm_internal.h"
 
 namespace lbm {
 

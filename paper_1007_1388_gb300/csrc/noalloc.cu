@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "device_common.cuh"
+#include "lbm_internal.h"
 #include "lbm.h"
 
 namespace lbm {

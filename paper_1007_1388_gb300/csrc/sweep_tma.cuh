@@ -18,6 +18,7 @@
 #pragma once
 
 #include "device_common.cuh"
+#include "lbm_internal.h"
 
 namespace lbm {
 

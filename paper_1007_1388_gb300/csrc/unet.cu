@@ -31,20 +31,43 @@ __host__ __device__ inline int ilog2(long long v)
     return l;
 }
 
-// x[m] = {solid, force of the sample, 0, ..., 0} (16 channels)
+// Padded element offsets (in voxels) of the periodic copies of voxel m:
+// along x (dx) and along z (dz); 0 where there is none.
+__device__ __forceinline__ void halo_copies(const VGrid &g, long long m, long long &dx, long long &dz)
+{
+    const long long nx = 1ll << g.lx, ny = 1ll << g.ly, nz = 1ll << g.lz;
+    const long long x = m & (nx - 1), z = (m >> (g.lx + g.ly)) & (nz - 1);
+    const long long plane = ny * (nx + 2);
+    dx = x == 0 ? nx : (x == nx - 1 ? -nx : 0);
+    dz = z == 0 ? nz * plane : (z == nz - 1 ? -nz * plane : 0);
+}
+
+// Stores 8 channels (from channel c0) of voxel m of a halo-layout tensor with
+// C channels, and its periodic copies.
+__device__ __forceinline__ void halo_store(bf16 *t, const VGrid &g, long long m, int C, int c0, const uint4 &v)
+{
+    long long dx, dz;
+    halo_copies(g, m, dx, dz);
+    const long long hi = halo_index(g, m);
+    *reinterpret_cast<uint4 *>(t + hi * C + c0) = v;
+    if (dx) *reinterpret_cast<uint4 *>(t + (hi + dx) * C + c0) = v;
+    if (dz) *reinterpret_cast<uint4 *>(t + (hi + dz) * C + c0) = v;
+    if (dx && dz) *reinterpret_cast<uint4 *>(t + (hi + dx + dz) * C + c0) = v;
+}
+
+// x[m] = {solid, force of the sample, 0, ..., 0} (16 channels, halo layout)
 __global__ void make_input_kernel(const uint8_t *__restrict__ solid, const float *__restrict__ force,
-                                  bf16 *__restrict__ x, long long V, int lvox)
+                                  bf16 *__restrict__ x, VGrid g)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= V) return;
+    if (i >= g.voxels()) return;
     __align__(16) bf16 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
     v[0] = __float2bfloat16(solid[i] ? 1.f : 0.f);
-    v[1] = __float2bfloat16(force[i >> lvox]);
-    uint4 *o = reinterpret_cast<uint4 *>(x + i * 16);
-    o[0] = reinterpret_cast<const uint4 *>(v)[0];
-    o[1] = reinterpret_cast<const uint4 *>(v)[1];
+    v[1] = __float2bfloat16(force[i >> (g.lx + g.ly + g.lz)]);
+    halo_store(x, g, i, 16, 0, reinterpret_cast<const uint4 *>(v)[0]);
+    halo_store(x, g, i, 16, 8, reinterpret_cast<const uint4 *>(v)[1]);
 }
 
 // Coordinates of voxel m in grid g, and the index of voxel (b, z, y, x).
@@ -60,41 +83,85 @@ __device__ __forceinline__ long long vidx(const VGrid &g, int b, int z, int y, i
     return ((((long long)b << g.lz) + z) << (g.ly + g.lx)) + ((long long)y << g.lx) + x;
 }
 
-// 2x2x2 average: out (grid gh) from in (grid 2 gh), C channels
+// 2x2x2 average: out (grid gh) from in (grid 2 gh), C channels, halo layout;
+// one thread per 8 channels of an output voxel
 __global__ void pool_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ out, VGrid gh, int C)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= gh.voxels() * C) return;
-    const long long p = i / C;
-    const int c = int(i - p * C);
+    const int C8 = C >> 3;
+    if (i >= gh.voxels() * C8) return;
+    const long long p = i / C8;
+    const int c = int(i - p * C8) * 8;
     int b, z, y, x;
     coords(p, gh, b, z, y, x);
     const VGrid gf{gh.nb, gh.lz + 1, gh.ly + 1, gh.lx + 1};
-    float s = 0.f;
-    for (int d = 0; d < 8; ++d)
-        s += __bfloat162float(in[vidx(gf, b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1)) * C + c]);
-    out[i] = __float2bfloat16(0.125f * s);
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int d = 0; d < 8; ++d) {
+        const long long m = vidx(gf, b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1));
+        __align__(16) bf16 h[8];
+        *reinterpret_cast<uint4 *>(h) = *reinterpret_cast<const uint4 *>(in + halo_index(gf, m) * C + c);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(h[k]);
+    }
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16(0.125f * s[k]);
+    halo_store(out, gh, p, C, c, *reinterpret_cast<const uint4 *>(o));
 }
 
-// dy = bf16(g * (y > 0)); per-block channel sums of g * (y > 0) (bias gradient).
-// blockDim = EW (a multiple of C), grid-stride with a stride that is a
-// multiple of C, so each thread keeps one channel.
-__global__ void relu_bwd_kernel(const float *__restrict__ g, const bf16 *__restrict__ y, bf16 *__restrict__ dy,
-                                float *__restrict__ part, long long n, int C)
+// nearest 2x upsampling: out (grid gf, halo layout) from in (grid gf / 2,
+// halo layout), C channels; one thread per 8 channels of an output voxel
+__global__ void upsample_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ out, VGrid gf, int C)
 {
-    __shared__ float sh[EW];
-    float acc = 0.f;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int C8 = C >> 3;
+    if (i >= gf.voxels() * C8) return;
+    const long long m = i / C8;
+    const int c = int(i - m * C8) * 8;
+    int b, z, y, x;
+    coords(m, gf, b, z, y, x);
+    const VGrid gh{gf.nb, gf.lz - 1, gf.ly - 1, gf.lx - 1};
+    const uint4 v = *reinterpret_cast<const uint4 *>(in + halo_index(gh, vidx(gh, b, z >> 1, y >> 1, x >> 1)) * C + c);
+    halo_store(out, gf, m, C, c, v);
+}
+
+// dy = bf16(g * (y > 0)) (y, dy: halo layout with periodic copies; g:
+// [V][C] fp32); per-block channel sums of g * (y > 0) (bias gradient).  A
+// thread handles 8 channels of a voxel; blockDim = EW and the grid stride are
+// multiples of C / 8, so each thread keeps one channel group.
+__global__ void relu_bwd_kernel(const float *__restrict__ g, const bf16 *__restrict__ y, bf16 *__restrict__ dy,
+                                float *__restrict__ part, VGrid grid, int C)
+{
+    __shared__ float sh[EW][9];
+    const int C8 = C >> 3;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const long long n = grid.voxels() * C8;
     for (long long i = (long long)blockIdx.x * EW + threadIdx.x; i < n; i += (long long)gridDim.x * EW) {
-        const float v = __bfloat162float(y[i]) > 0.f ? g[i] : 0.f;
-        dy[i] = __float2bfloat16(v);
-        acc += v;
+        const long long m = i / C8;
+        const int c = int(i - m * C8) * 8;
+        const long long hi = halo_index(grid, m);
+        __align__(16) bf16 yv[8];
+        *reinterpret_cast<uint4 *>(yv) = *reinterpret_cast<const uint4 *>(y + hi * C + c);
+        const float4 g0 = *reinterpret_cast<const float4 *>(g + m * C + c);
+        const float4 g1 = *reinterpret_cast<const float4 *>(g + m * C + c + 4);
+        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        __align__(16) bf16 o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float v = __bfloat162float(yv[k]) > 0.f ? gv[k] : 0.f;
+            o[k] = __float2bfloat16(v);
+            acc[k] += v;
+        }
+        halo_store(dy, grid, m, C, c, *reinterpret_cast<const uint4 *>(o));
     }
-    sh[threadIdx.x] = acc;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];
     __syncthreads();
     if (threadIdx.x < C) {
-        float s = 0.f;
-        for (int k = threadIdx.x; k < EW; k += C) s += sh[k];
-        part[(long long)blockIdx.x * C + threadIdx.x] = s;
+        const int grp = threadIdx.x >> 3, k = threadIdx.x & 7;
+        float t = 0.f;
+        for (int r = grp; r < EW; r += C8) t += sh[r][k];
+        part[(long long)blockIdx.x * C + threadIdx.x] = t;
     }
 }
 
@@ -147,15 +214,16 @@ __global__ void skip_pool_kernel(const float *__restrict__ gcat, int ctot, int c
     ge[i] = gcat[v * ctot + c0 + c] + 0.125f * gp[vidx(gh, b, z >> 1, y >> 1, x >> 1) * C + c];
 }
 
-// 1x1x1 head y = d1 Wh^T + bh; with a target: loss partials, the gradient
+// 1x1x1 head y = d1 Wh^T + bh (d1 in the halo layout); with a target: loss partials, the gradient
 // g_d1 = gy Wh (gy = 2 (y - target) / (V 4)), and partials of dWh (4 x 16),
 // dbh (4) and the loss: part[block][72] = {dWh[64], dbh[4], sum of squared
 // differences, 3 unused}.
 constexpr int HEAD_PART = 72;
 __global__ void head_kernel(const bf16 *__restrict__ d1, const float *__restrict__ Wh, const float *__restrict__ bh,
                             const float *__restrict__ target, float *__restrict__ out, float *__restrict__ gd1,
-                            float *__restrict__ part, long long V)
+                            float *__restrict__ part, VGrid g)
 {
+    const long long V = g.voxels();
     __shared__ float sw[64], sb[4];
     __shared__ float red[EW / 32][HEAD_PART];
     if (threadIdx.x < 64) sw[threadIdx.x] = Wh[threadIdx.x];
@@ -167,8 +235,9 @@ __global__ void head_kernel(const bf16 *__restrict__ d1, const float *__restrict
     const float gscale = 2.f / float(V * 4);
     for (long long m = (long long)blockIdx.x * EW + threadIdx.x; m < V; m += (long long)gridDim.x * EW) {
         __align__(16) bf16 h[16];
-        reinterpret_cast<uint4 *>(h)[0] = reinterpret_cast<const uint4 *>(d1 + m * 16)[0];
-        reinterpret_cast<uint4 *>(h)[1] = reinterpret_cast<const uint4 *>(d1 + m * 16)[1];
+        const bf16 *row = d1 + halo_index(g, m) * 16;
+        reinterpret_cast<uint4 *>(h)[0] = reinterpret_cast<const uint4 *>(row)[0];
+        reinterpret_cast<uint4 *>(h)[1] = reinterpret_cast<const uint4 *>(row)[1];
         float a[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) a[k] = __bfloat162float(h[k]);
@@ -410,7 +479,8 @@ struct unet_ctx {
     bf16 *wf[NCONV] = {}, *wb[NCONV] = {};
     bool weights_current = false;
     bf16 *x = nullptr, *e1h = nullptr, *e1 = nullptr, *p1 = nullptr, *e2h = nullptr, *e2 = nullptr, *p2 = nullptr,
-         *e3h = nullptr, *e3 = nullptr, *d2h = nullptr, *d2 = nullptr, *d1h = nullptr, *d1 = nullptr, *dy = nullptr;
+         *e3h = nullptr, *e3 = nullptr, *d2h = nullptr, *d2 = nullptr, *d1h = nullptr, *d1 = nullptr, *dy = nullptr,
+         *up3 = nullptr, *up2 = nullptr;  // bf16 activations: halo layout (unet_internal.h)
     float *gd1 = nullptr, *gcat1 = nullptr, *gd2 = nullptr, *gcat2 = nullptr, *ge3 = nullptr, *gp2 = nullptr,
           *ge2 = nullptr, *gp1 = nullptr, *ge1 = nullptr, *gh = nullptr;
     float *wpart = nullptr, *wtmp = nullptr, *bpart = nullptr, *hpart = nullptr, *dforce = nullptr;
@@ -481,24 +551,26 @@ void ufree_all(unet_ctx *c)
 unsigned blocks_for(long long n) { return unsigned((n + EW - 1) / EW); }
 
 // launch one 3x3x3 convolution on the context stream
-int conv(unet_ctx *c, const bf16 *s0, int c0, int up0, const bf16 *s1, int c1, const bf16 *w, const float *bias,
-         void *out, int out_f32, int relu, int cout, VGrid g)
+// one TMA-fed 3x3x3 convolution on the context stream (halo-layout sources)
+int conv(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf16 *w, const float *bias, void *out,
+         int out_f32, int relu, int cout, VGrid g)
 {
-    ConvArgs a{};
-    a.src0 = s0;
-    a.src1 = s1;
-    a.w = w;
+    ConvTmaArgs a{};
+    const VBox box = vbox(g, 128);
+    if (!make_halo_map(&a.a0, s0, c0, g, box) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box)) ||
+        !make_weight_map(&a.w, w, c0 + c1, cout))
+        return ufail(c, LBM_ECUDA, "conv3: tensor map encoding failed");
+    if (!c1) a.a1 = a.a0;
     a.bias = bias;
     a.out = out;
     a.c0 = c0;
     a.c1 = c1;
-    a.up0 = up0;
     a.cout = cout;
     a.out_f32 = out_f32;
     a.relu = relu;
     a.g = g;
     a.err = c->derr;
-    UCK(launch_conv3(a, c->stream), "conv3");
+    UCK(launch_conv3_tma(a, c->stream), "conv3");
     return LBM_OK;
 }
 
@@ -520,16 +592,17 @@ size_t wgrad_ws_bytes(long long V, int cin, int cout)
     return size_t(nsplit) * rows_pad * cout * sizeof(float);
 }
 
-int wgrad(unet_ctx *c, const bf16 *s0, int c0, int up0, const bf16 *s1, int c1, const bf16 *dy, int cout,
-          float *dw, VGrid g)
+int wgrad(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf16 *dy, int cout, float *dw,
+          VGrid g)
 {
-    WgradArgs a{};
-    a.src0 = s0;
-    a.src1 = s1;
-    a.dy = dy;
+    WgradTmaArgs a{};
+    const VBox box = vbox(g, 64);
+    if (!make_halo_map(&a.a0, s0, c0, g, box) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box)) ||
+        !make_halo_map(&a.dy, dy, cout, g, box))
+        return ufail(c, LBM_ECUDA, "wgrad: tensor map encoding failed");
+    if (!c1) a.a1 = a.a0;
     a.c0 = c0;
     a.c1 = c1;
-    a.up0 = up0;
     a.cout = cout;
     a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
     a.vps = wgrad_vps(g.voxels(), a.rows_pad / 128);
@@ -539,17 +612,17 @@ int wgrad(unet_ctx *c, const bf16 *s0, int c0, int up0, const bf16 *s1, int c1, 
     const int nsplit = wgrad_splits(g, a.vps);
     if (size_t(nsplit) * a.rows_pad * cout * sizeof(float) > c->wpart_bytes)
         return ufail(c, LBM_EINVAL, "weight-gradient workspace too small");
-    UCK(launch_wgrad(a, nsplit, dw, c->stream), "wgrad");
+    UCK(launch_wgrad_tma(a, nsplit, dw, c->stream), "wgrad");
     return LBM_OK;
 }
 
 // ReLU backward into c->dy and the bias gradient of layer k
-int relu_bwd(unet_ctx *c, const float *g, const bf16 *y, long long V, int C, int k)
+int relu_bwd(unet_ctx *c, const float *g, const bf16 *y, VGrid grid, int C, int k)
 {
-    const long long n = V * C;
+    const long long n = grid.voxels() * (C / 8);
     int nblk = int(std::min<long long>(c->relu_blocks, (n + EW - 1) / EW));
     if (nblk < 1) nblk = 1;
-    relu_bwd_kernel<<<nblk, EW, 0, c->stream>>>(g, y, c->dy, c->bpart, n, C);
+    relu_bwd_kernel<<<nblk, EW, 0, c->stream>>>(g, y, c->dy, c->bpart, grid, C);
     reduce_cols_kernel<<<C, EW, 0, c->stream>>>(c->bpart, nblk, C, c->grads + kLayout.b[k]);
     UCK(cudaGetLastError(), "relu backward");
     return LBM_OK;
@@ -574,23 +647,24 @@ int forward(unet_ctx *c, const uint8_t *solid, const float *force)
     int rc;
     UCK(cudaMemcpyAsync(c->dforce, force, sizeof(float) * c->nb, cudaMemcpyHostToDevice, c->stream), "force");
     if ((rc = prep_weights(c))) return rc;
-    make_input_kernel<<<blocks_for(c->V1), EW, 0, c->stream>>>(solid, c->dforce, c->x, c->V1,
-                                                               c->g1.lz + c->g1.ly + c->g1.lx);
+    make_input_kernel<<<blocks_for(c->V1), EW, 0, c->stream>>>(solid, c->dforce, c->x, c->g1);
     UCK(cudaGetLastError(), "input");
     const float *P = c->params;
     const Layout &L = kLayout;
-    if ((rc = conv(c, c->x, 16, 0, nullptr, 0, c->wf[W1A], P + L.b[W1A], c->e1h, 0, 1, 16, c->g1))) return rc;
-    if ((rc = conv(c, c->e1h, 16, 0, nullptr, 0, c->wf[W1B], P + L.b[W1B], c->e1, 0, 1, 16, c->g1))) return rc;
-    pool_kernel<<<blocks_for(c->V2 * 16), EW, 0, c->stream>>>(c->e1, c->p1, c->g2, 16);
-    if ((rc = conv(c, c->p1, 16, 0, nullptr, 0, c->wf[W2A], P + L.b[W2A], c->e2h, 0, 1, 32, c->g2))) return rc;
-    if ((rc = conv(c, c->e2h, 32, 0, nullptr, 0, c->wf[W2B], P + L.b[W2B], c->e2, 0, 1, 32, c->g2))) return rc;
-    pool_kernel<<<blocks_for(c->V3 * 32), EW, 0, c->stream>>>(c->e2, c->p2, c->g3, 32);
-    if ((rc = conv(c, c->p2, 32, 0, nullptr, 0, c->wf[W3A], P + L.b[W3A], c->e3h, 0, 1, 64, c->g3))) return rc;
-    if ((rc = conv(c, c->e3h, 64, 0, nullptr, 0, c->wf[W3B], P + L.b[W3B], c->e3, 0, 1, 64, c->g3))) return rc;
-    if ((rc = conv(c, c->e3, 64, 1, c->e2, 32, c->wf[W4A], P + L.b[W4A], c->d2h, 0, 1, 32, c->g2))) return rc;
-    if ((rc = conv(c, c->d2h, 32, 0, nullptr, 0, c->wf[W4B], P + L.b[W4B], c->d2, 0, 1, 32, c->g2))) return rc;
-    if ((rc = conv(c, c->d2, 32, 1, c->e1, 16, c->wf[W5A], P + L.b[W5A], c->d1h, 0, 1, 16, c->g1))) return rc;
-    if ((rc = conv(c, c->d1h, 16, 0, nullptr, 0, c->wf[W5B], P + L.b[W5B], c->d1, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, c->x, 16, nullptr, 0, c->wf[W1A], P + L.b[W1A], c->e1h, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, c->e1h, 16, nullptr, 0, c->wf[W1B], P + L.b[W1B], c->e1, 0, 1, 16, c->g1))) return rc;
+    pool_kernel<<<blocks_for(c->V2 * 2), EW, 0, c->stream>>>(c->e1, c->p1, c->g2, 16);
+    if ((rc = conv(c, c->p1, 16, nullptr, 0, c->wf[W2A], P + L.b[W2A], c->e2h, 0, 1, 32, c->g2))) return rc;
+    if ((rc = conv(c, c->e2h, 32, nullptr, 0, c->wf[W2B], P + L.b[W2B], c->e2, 0, 1, 32, c->g2))) return rc;
+    pool_kernel<<<blocks_for(c->V3 * 4), EW, 0, c->stream>>>(c->e2, c->p2, c->g3, 32);
+    if ((rc = conv(c, c->p2, 32, nullptr, 0, c->wf[W3A], P + L.b[W3A], c->e3h, 0, 1, 64, c->g3))) return rc;
+    if ((rc = conv(c, c->e3h, 64, nullptr, 0, c->wf[W3B], P + L.b[W3B], c->e3, 0, 1, 64, c->g3))) return rc;
+    upsample_kernel<<<blocks_for(c->V2 * 8), EW, 0, c->stream>>>(c->e3, c->up3, c->g2, 64);
+    if ((rc = conv(c, c->up3, 64, c->e2, 32, c->wf[W4A], P + L.b[W4A], c->d2h, 0, 1, 32, c->g2))) return rc;
+    if ((rc = conv(c, c->d2h, 32, nullptr, 0, c->wf[W4B], P + L.b[W4B], c->d2, 0, 1, 32, c->g2))) return rc;
+    upsample_kernel<<<blocks_for(c->V1 * 4), EW, 0, c->stream>>>(c->d2, c->up2, c->g1, 32);
+    if ((rc = conv(c, c->up2, 32, c->e1, 16, c->wf[W5A], P + L.b[W5A], c->d1h, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, c->d1h, 16, nullptr, 0, c->wf[W5B], P + L.b[W5B], c->d1, 0, 1, 16, c->g1))) return rc;
     UCK(cudaGetLastError(), "forward");
     return LBM_OK;
 }
@@ -613,50 +687,50 @@ int backward(unet_ctx *c, const float *target, double *loss)
     const Layout &L = kLayout;
     float *G = c->grads;
     head_kernel<<<c->head_blocks, EW, 0, c->stream>>>(c->d1, c->params + L.wh, c->params + L.bh, target, nullptr,
-                                                      c->gd1, c->hpart, c->V1);
+                                                      c->gd1, c->hpart, c->g1);
     reduce_cols_kernel<<<72, EW, 0, c->stream>>>(c->hpart, c->head_blocks, 72, c->wtmp);
     UCK(cudaGetLastError(), "head");
     UCK(cudaMemcpyAsync(G + L.wh, c->wtmp, sizeof(float) * 68, cudaMemcpyDeviceToDevice, c->stream), "head grad");
     float hl = 0.f;
     UCK(cudaMemcpyAsync(&hl, c->wtmp + 68, sizeof(float), cudaMemcpyDeviceToHost, c->stream), "loss");
     // level 1 decoder
-    if ((rc = relu_bwd(c, c->gd1, c->d1, c->V1, 16, W5B))) return rc;
-    if ((rc = wgrad(c, c->d1h, 16, 0, nullptr, 0, c->dy, 16, G + L.w[W5B], c->g1))) return rc;
-    if ((rc = conv(c, c->dy, 16, 0, nullptr, 0, c->wb[W5B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->d1h, c->V1, 16, W5A))) return rc;
-    if ((rc = wgrad(c, c->d2, 32, 1, c->e1, 16, c->dy, 16, G + L.w[W5A], c->g1))) return rc;
-    if ((rc = conv(c, c->dy, 16, 0, nullptr, 0, c->wb[W5A], nullptr, c->gcat1, 1, 0, 48, c->g1))) return rc;
+    if ((rc = relu_bwd(c, c->gd1, c->d1, c->g1, 16, W5B))) return rc;
+    if ((rc = wgrad(c, c->d1h, 16, nullptr, 0, c->dy, 16, G + L.w[W5B], c->g1))) return rc;
+    if ((rc = conv(c, c->dy, 16, nullptr, 0, c->wb[W5B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->d1h, c->g1, 16, W5A))) return rc;
+    if ((rc = wgrad(c, c->up2, 32, c->e1, 16, c->dy, 16, G + L.w[W5A], c->g1))) return rc;
+    if ((rc = conv(c, c->dy, 16, nullptr, 0, c->wb[W5A], nullptr, c->gcat1, 1, 0, 48, c->g1))) return rc;
     up_bwd_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gd2, c->g2);
     // level 2 decoder
-    if ((rc = relu_bwd(c, c->gd2, c->d2, c->V2, 32, W4B))) return rc;
-    if ((rc = wgrad(c, c->d2h, 32, 0, nullptr, 0, c->dy, 32, G + L.w[W4B], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W4B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->d2h, c->V2, 32, W4A))) return rc;
-    if ((rc = wgrad(c, c->e3, 64, 1, c->e2, 32, c->dy, 32, G + L.w[W4A], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W4A], nullptr, c->gcat2, 1, 0, 96, c->g2))) return rc;
+    if ((rc = relu_bwd(c, c->gd2, c->d2, c->g2, 32, W4B))) return rc;
+    if ((rc = wgrad(c, c->d2h, 32, nullptr, 0, c->dy, 32, G + L.w[W4B], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W4B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->d2h, c->g2, 32, W4A))) return rc;
+    if ((rc = wgrad(c, c->up3, 64, c->e2, 32, c->dy, 32, G + L.w[W4A], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W4A], nullptr, c->gcat2, 1, 0, 96, c->g2))) return rc;
     up_bwd_kernel<<<blocks_for(c->V3 * 64), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->ge3, c->g3);
     // bottleneck
-    if ((rc = relu_bwd(c, c->ge3, c->e3, c->V3, 64, W3B))) return rc;
-    if ((rc = wgrad(c, c->e3h, 64, 0, nullptr, 0, c->dy, 64, G + L.w[W3B], c->g3))) return rc;
-    if ((rc = conv(c, c->dy, 64, 0, nullptr, 0, c->wb[W3B], nullptr, c->gh, 1, 0, 64, c->g3))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->e3h, c->V3, 64, W3A))) return rc;
-    if ((rc = wgrad(c, c->p2, 32, 0, nullptr, 0, c->dy, 64, G + L.w[W3A], c->g3))) return rc;
-    if ((rc = conv(c, c->dy, 64, 0, nullptr, 0, c->wb[W3A], nullptr, c->gp2, 1, 0, 32, c->g3))) return rc;
+    if ((rc = relu_bwd(c, c->ge3, c->e3, c->g3, 64, W3B))) return rc;
+    if ((rc = wgrad(c, c->e3h, 64, nullptr, 0, c->dy, 64, G + L.w[W3B], c->g3))) return rc;
+    if ((rc = conv(c, c->dy, 64, nullptr, 0, c->wb[W3B], nullptr, c->gh, 1, 0, 64, c->g3))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->e3h, c->g3, 64, W3A))) return rc;
+    if ((rc = wgrad(c, c->p2, 32, nullptr, 0, c->dy, 64, G + L.w[W3A], c->g3))) return rc;
+    if ((rc = conv(c, c->dy, 64, nullptr, 0, c->wb[W3A], nullptr, c->gp2, 1, 0, 32, c->g3))) return rc;
     skip_pool_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->gp2, c->ge2, c->g2, 32);
     // level 2 encoder
-    if ((rc = relu_bwd(c, c->ge2, c->e2, c->V2, 32, W2B))) return rc;
-    if ((rc = wgrad(c, c->e2h, 32, 0, nullptr, 0, c->dy, 32, G + L.w[W2B], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W2B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->e2h, c->V2, 32, W2A))) return rc;
-    if ((rc = wgrad(c, c->p1, 16, 0, nullptr, 0, c->dy, 32, G + L.w[W2A], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, 0, nullptr, 0, c->wb[W2A], nullptr, c->gp1, 1, 0, 16, c->g2))) return rc;
+    if ((rc = relu_bwd(c, c->ge2, c->e2, c->g2, 32, W2B))) return rc;
+    if ((rc = wgrad(c, c->e2h, 32, nullptr, 0, c->dy, 32, G + L.w[W2B], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W2B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->e2h, c->g2, 32, W2A))) return rc;
+    if ((rc = wgrad(c, c->p1, 16, nullptr, 0, c->dy, 32, G + L.w[W2A], c->g2))) return rc;
+    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W2A], nullptr, c->gp1, 1, 0, 16, c->g2))) return rc;
     skip_pool_kernel<<<blocks_for(c->V1 * 16), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gp1, c->ge1, c->g1, 16);
     // level 1 encoder
-    if ((rc = relu_bwd(c, c->ge1, c->e1, c->V1, 16, W1B))) return rc;
-    if ((rc = wgrad(c, c->e1h, 16, 0, nullptr, 0, c->dy, 16, G + L.w[W1B], c->g1))) return rc;
-    if ((rc = conv(c, c->dy, 16, 0, nullptr, 0, c->wb[W1B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->e1h, c->V1, 16, W1A))) return rc;
-    if ((rc = wgrad(c, c->x, 16, 0, nullptr, 0, c->dy, 16, c->wtmp, c->g1))) return rc;
+    if ((rc = relu_bwd(c, c->ge1, c->e1, c->g1, 16, W1B))) return rc;
+    if ((rc = wgrad(c, c->e1h, 16, nullptr, 0, c->dy, 16, G + L.w[W1B], c->g1))) return rc;
+    if ((rc = conv(c, c->dy, 16, nullptr, 0, c->wb[W1B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd(c, c->gh, c->e1h, c->g1, 16, W1A))) return rc;
+    if ((rc = wgrad(c, c->x, 16, nullptr, 0, c->dy, 16, c->wtmp, c->g1))) return rc;
     unpad_grad_kernel<<<blocks_for(16 * 27 * 2), EW, 0, c->stream>>>(c->wtmp, 16, 2, 16, G + L.w[W1A]);
     UCK(cudaGetLastError(), "backward");
     if ((rc = check_err(c))) return rc;
@@ -684,8 +758,9 @@ int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx *
 {
     if (!out) return ufail(nullptr, LBM_EINVAL, "unet_create: out is NULL");
     *out = nullptr;
-    if (n < 16 || n > 128 || (n & (n - 1)) || nb < 1 || nb > 4096)
-        return ufail(nullptr, LBM_EINVAL, "unet_create: n must be a power of two in [16, 128] and nb >= 1");
+    if (n < 16 || n > 128 || (n & (n - 1)) || nb < 1 || nb > 4096 || ((long long)nb * (n / 4) * (n / 4) * (n / 4)) % 128)
+        return ufail(nullptr, LBM_EINVAL, "unet_create: n must be a power of two in [16, 128], nb >= 1, and "
+                     "nb (n/4)^3 a multiple of 128 (the tensor-core tile)");
     unet_ctx *c = new (std::nothrow) unet_ctx();
     if (!c) return ufail(nullptr, LBM_ENOMEM, "out of host memory");
     c->n = n;
@@ -720,11 +795,16 @@ int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx *
         if ((rc = uown(c, &c->wf[k], size_t(27) * kConv[k].cout * cin_padded(k)))) return bail(rc);
         if (k != W1A && (rc = uown(c, &c->wb[k], size_t(27) * kConv[k].cout * kConv[k].cin))) return bail(rc);
     }
-    if ((rc = uown(c, &c->x, V1 * 16)) || (rc = uown(c, &c->e1h, V1 * 16)) || (rc = uown(c, &c->e1, V1 * 16)) ||
-        (rc = uown(c, &c->p1, V2 * 16)) || (rc = uown(c, &c->e2h, V2 * 32)) || (rc = uown(c, &c->e2, V2 * 32)) ||
-        (rc = uown(c, &c->p2, V3 * 32)) || (rc = uown(c, &c->e3h, V3 * 64)) || (rc = uown(c, &c->e3, V3 * 64)) ||
-        (rc = uown(c, &c->d2h, V2 * 32)) || (rc = uown(c, &c->d2, V2 * 32)) || (rc = uown(c, &c->d1h, V1 * 16)) ||
-        (rc = uown(c, &c->d1, V1 * 16)) || (rc = uown(c, &c->dy, V1 * 16)))
+    const VGrid g1 = c->g1, g2 = c->g2, g3 = c->g3;
+    if ((rc = uown(c, &c->x, halo_elems(g1, 16))) || (rc = uown(c, &c->e1h, halo_elems(g1, 16))) ||
+        (rc = uown(c, &c->e1, halo_elems(g1, 16))) || (rc = uown(c, &c->p1, halo_elems(g2, 16))) ||
+        (rc = uown(c, &c->e2h, halo_elems(g2, 32))) || (rc = uown(c, &c->e2, halo_elems(g2, 32))) ||
+        (rc = uown(c, &c->p2, halo_elems(g3, 32))) || (rc = uown(c, &c->e3h, halo_elems(g3, 64))) ||
+        (rc = uown(c, &c->e3, halo_elems(g3, 64))) || (rc = uown(c, &c->up3, halo_elems(g2, 64))) ||
+        (rc = uown(c, &c->d2h, halo_elems(g2, 32))) || (rc = uown(c, &c->d2, halo_elems(g2, 32))) ||
+        (rc = uown(c, &c->up2, halo_elems(g1, 32))) || (rc = uown(c, &c->d1h, halo_elems(g1, 16))) ||
+        (rc = uown(c, &c->d1, halo_elems(g1, 16))) ||
+        (rc = uown(c, &c->dy, std::max(halo_elems(g1, 16), std::max(halo_elems(g2, 32), halo_elems(g3, 64))))))
         return bail(rc);
     if ((rc = uown(c, &c->gd1, V1 * 16)) || (rc = uown(c, &c->gcat1, V1 * 48)) || (rc = uown(c, &c->gd2, V2 * 32)) ||
         (rc = uown(c, &c->gcat2, V2 * 96)) || (rc = uown(c, &c->ge3, V3 * 64)) || (rc = uown(c, &c->gp2, V3 * 32)) ||
@@ -785,7 +865,7 @@ int unet_predict(unet_ctx *c, const uint8_t *solid, const float *force, float *o
     int rc = forward(c, solid, force);
     if (rc) return rc;
     head_kernel<<<c->head_blocks, EW, 0, c->stream>>>(c->d1, c->params + kLayout.wh, c->params + kLayout.bh,
-                                                      nullptr, out, nullptr, nullptr, c->V1);
+                                                      nullptr, out, nullptr, nullptr, c->g1);
     UCK(cudaGetLastError(), "head");
     return check_err(c);
 }
@@ -897,6 +977,93 @@ int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_wgrad: invalid channels");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_wgrad: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_wgrad: a bounded wait timed out");
+    return LBM_OK;
+}
+
+int unet_conv3_halo(const void *src0, int c0, const void *src1, int c1, const void *w, const float *bias, void *out,
+                    int out_f32, int relu, int cout, int nb, int lz, int ly, int lx, void *stream)
+{
+    if (nb < 1 || lz < 0 || ly < 0 || lx < 0 || lz + ly + lx > 30 || c0 <= 0 || c1 < 0 || (c1 && !src1))
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo: bad arguments");
+    const VGrid g{nb, lz, ly, lx};
+    ConvTmaArgs a{};
+    const VBox box = vbox(g, 128);
+    if (g.voxels() % 128 || !make_halo_map(&a.a0, src0, c0, g, box) ||
+        (c1 && !make_halo_map(&a.a1, src1, c1, g, box)) || !make_weight_map(&a.w, w, c0 + c1, cout))
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo: tensor maps (alignment, channels or grid)");
+    if (!c1) a.a1 = a.a0;
+    a.bias = bias;
+    a.out = out;
+    a.c0 = c0;
+    a.c1 = c1;
+    a.cout = cout;
+    a.out_f32 = out_f32 ? 1 : 0;
+    a.relu = relu ? 1 : 0;
+    a.g = g;
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_halo: error word");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    a.err = err;
+    cudaError_t e = launch_conv3_tma(a, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo: invalid channels or grid");
+    if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_halo: %s", cudaGetErrorString(e));
+    if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_halo: a bounded wait timed out");
+    return LBM_OK;
+}
+
+int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, const void *dy, int cout, float *dw,
+                          int nb, int lz, int ly, int lx, void *stream)
+{
+    if (nb < 1 || lz < 0 || ly < 0 || lx < 0 || lz + ly + lx > 30 || c0 <= 0 || c1 < 0 || cout <= 0 ||
+        (c1 && !src1))
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo_wgrad: bad arguments");
+    const VGrid g{nb, lz, ly, lx};
+    WgradTmaArgs a{};
+    const VBox box = vbox(g, 64);
+    if (g.voxels() % 64 || !make_halo_map(&a.a0, src0, c0, g, box) ||
+        (c1 && !make_halo_map(&a.a1, src1, c1, g, box)) || !make_halo_map(&a.dy, dy, cout, g, box))
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo_wgrad: tensor maps (alignment, channels or grid)");
+    if (!c1) a.a1 = a.a0;
+    a.c0 = c0;
+    a.c1 = c1;
+    a.cout = cout;
+    a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
+    a.vps = wgrad_vps(g.voxels(), a.rows_pad / 128);
+    a.g = g;
+    const int nsplit = wgrad_splits(g, a.vps);
+    void *(*al)(size_t, void *, void *) = nullptr;
+    void (*rl)(void *, size_t, void *, void *) = nullptr;
+    void *user = nullptr;
+    current_allocator(&al, &rl, &user);
+    const size_t bytes = size_t(nsplit) * a.rows_pad * cout * sizeof(float) + 256;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    if (al) {
+        ws = al(bytes, stream, user);
+    } else if (cudaMalloc(&ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ws = nullptr;
+    }
+    if (!ws) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_halo_wgrad: workspace of %zu bytes", bytes);
+    a.partial = static_cast<float *>(ws);
+    a.err = reinterpret_cast<int *>(static_cast<char *>(ws) + bytes - 256);
+    cudaMemsetAsync(a.err, 0, sizeof(int), s);
+    cudaError_t e = launch_wgrad_tma(a, nsplit, dw, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (rl)
+        rl(ws, bytes, stream, user);
+    else if (!al)
+        cudaFree(ws);
+    if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo_wgrad: invalid channels");
+    if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_halo_wgrad: %s", cudaGetErrorString(e));
+    if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_halo_wgrad: a bounded wait timed out");
     return LBM_OK;
 }
 

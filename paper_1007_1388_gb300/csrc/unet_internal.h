@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -51,7 +52,85 @@ struct WgradArgs {
     int *err;
 };
 
+// Halo layout of the TMA-fed kernels: a bf16 tensor of nb grids with C
+// channels stored as [nb][nz + 2][ny][nx + 2][C]; padded column 0 repeats
+// x = nx - 1, column nx + 1 repeats x = 0, padded plane 0 repeats z = nz - 1
+// and plane nz + 1 repeats z = 0 (the periodic neighbours), so that every
+// tap's operand tile is one tensor-map box (rows beyond the y walls come back
+// zero-filled).  Voxel (b, z, y, x) lives at padded (b, z + 1, y, x + 1).
+__host__ __device__ inline long long halo_index(const VGrid &g, long long m)
+{
+    const long long nx = 1ll << g.lx, ny = 1ll << g.ly, nz = 1ll << g.lz;
+    const long long x = m & (nx - 1), y = (m >> g.lx) & (ny - 1), z = (m >> (g.lx + g.ly)) & (nz - 1);
+    const long long b = m >> (g.lx + g.ly + g.lz);
+    return ((b * (nz + 2) + z + 1) * ny + y) * (nx + 2) + x + 1;
+}
+__host__ __device__ inline long long halo_elems(const VGrid &g, int C)
+{
+    return (long long)g.nb * ((1ll << g.lz) + 2) * (1ll << g.ly) * ((1ll << g.lx) + 2) * C;
+}
+
+// A box of `count` consecutive voxels (a power of two dividing the grid's
+// total) in whole rows, planes and grids: extents {bx, by, bz, bb}.
+struct VBox {
+    int bx, by, bz, bb;
+};
+__host__ __device__ inline VBox vbox(const VGrid &g, int count)
+{
+    VBox v{1, 1, 1, 1};
+    const int nx = 1 << g.lx, ny = 1 << g.ly, nz = 1 << g.lz;
+    if (count <= nx) {
+        v.bx = count;
+    } else if (count <= nx * ny) {
+        v.bx = nx;
+        v.by = count / nx;
+    } else if (count <= nx * ny * nz) {
+        v.bx = nx;
+        v.by = ny;
+        v.bz = count / (nx * ny);
+    } else {
+        v.bx = nx;
+        v.by = ny;
+        v.bz = nz;
+        v.bb = count / (nx * ny * nz);
+    }
+    return v;
+}
+
+// TMA-fed convolution over halo-layout tensors (same result as conv3, bitwise:
+// the same shared-memory tiles and MMA sequence).  Maps: a0 / a1 over the
+// sources with the box vbox(g, 128); w over the weights [cout][27][cin] with
+// box {8, 1, cout}.  out: bf16 in the halo layout (periodic copies written
+// too), or fp32 [M][cout] without halo.  No upsampled source.
+struct ConvTmaArgs {
+    CUtensorMap a0, a1, w;
+    const float *bias;
+    void *out;
+    int c0, c1, cout;
+    int out_f32, relu;
+    VGrid g;
+    int *err;
+};
+
+// TMA-fed weight gradient over halo-layout tensors (same result as the
+// cp.async version).  Maps a0 / a1 / dy with the box vbox(g, 64): 64 voxels
+// per stage.
+struct WgradTmaArgs {
+    CUtensorMap a0, a1, dy;
+    float *partial;
+    int c0, c1, cout;
+    int rows_pad, vps;
+    VGrid g;
+    int *err;
+};
+
+// Tensor maps (false when the driver's encoder is unavailable or rejects the map)
+bool make_halo_map(CUtensorMap *m, const void *base, int C, const VGrid &g, const VBox &box);
+bool make_weight_map(CUtensorMap *m, const void *w, int cin, int cout);
+
 cudaError_t launch_conv3(const ConvArgs &a, cudaStream_t s);
+cudaError_t launch_conv3_tma(const ConvTmaArgs &a, cudaStream_t s);
+cudaError_t launch_wgrad_tma(const WgradTmaArgs &a, int nsplit, float *dw, cudaStream_t s);
 cudaError_t launch_wgrad(const WgradArgs &a, int nsplit, float *dw, cudaStream_t s);
 int wgrad_splits(const VGrid &g, int vps);
 size_t conv3_smem(int cin, int cout);

@@ -135,6 +135,8 @@ SIGNATURES = {
     "unet_fields_from_prediction": ([_vp, _vp, _vp, _i, _ll, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                      _vp, _vp, _vp], _i),
     "unet_smooth_fields": ([_vp, _vp, _vp, _i, _i, _i, _i, _vp], _i),
+    "unet_conv3_halo": ([_vp, _i, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp], _i),
+    "unet_conv3_halo_wgrad": ([_vp, _i, _vp, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp], _i),
 }
 
 _lib = None

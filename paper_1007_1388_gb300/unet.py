@@ -158,3 +158,30 @@ def smooth_fields(f, solid, K, comps, n, passes, stream):
                                     ctypes.c_void_p(solid.data_ptr()), K, comps, n, passes,
                                     ctypes.c_void_p(stream.cuda_stream)))
     return f
+
+
+def conv3_halo(src0, c0, w, out, cout, grid, *, src1=None, c1=0, bias=None, relu=False, stream=None):
+    """conv3 on halo-layout tensors (TMA-fed tiles)."""
+    import torch
+
+    nb, lz, ly, lx = grid
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().unet_conv3_halo(
+        ctypes.c_void_p(src0.data_ptr()), c0, ctypes.c_void_p(src1.data_ptr()) if src1 is not None else None, c1,
+        ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(bias.data_ptr()) if bias is not None else None,
+        ctypes.c_void_p(out.data_ptr()), int(out.dtype == torch.float32), int(relu), cout, nb, lz, ly, lx,
+        ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def conv3_halo_wgrad(src0, c0, dy, cout, dw, grid, *, src1=None, c1=0, stream=None):
+    """Weight gradient on halo-layout tensors (TMA-fed tiles)."""
+    import torch
+
+    nb, lz, ly, lx = grid
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().unet_conv3_halo_wgrad(
+        ctypes.c_void_p(src0.data_ptr()), c0, ctypes.c_void_p(src1.data_ptr()) if src1 is not None else None, c1,
+        ctypes.c_void_p(dy.data_ptr()), cout, ctypes.c_void_p(dw.data_ptr()), nb, lz, ly, lx,
+        ctypes.c_void_p(s.cuda_stream)))
+    return dw

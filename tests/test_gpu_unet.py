@@ -9,7 +9,10 @@
   activations and bf16 gradient operands put about twenty roundings of up to
   2^-9 on the path from the loss to the deepest layers (measured: 0.1% at
   the head, up to 2.4% at the bottleneck);
-- a few Adam steps lower the loss.
+- a few Adam steps lower the loss;
+- the TMA-fed kernels on halo-layout tensors (the network's own path) equal
+  the cp.async kernels: forward bitwise (periodic copies included), weight
+  gradient to FP32 accumulation order.
 """
 import numpy as np
 import pytest
@@ -243,3 +246,65 @@ def test_prediction_matches_oracle_and_training_lowers_loss(env):
         l1 = net.train_step(sd, force, tg, 1e-3)
     assert l1 < 0.9 * l0, (l0, l1)
     net.destroy()
+
+
+# ------------------------------------------------------------- TMA-fed (halo layout)
+def _to_halo(torch, t, nb, lz, ly, lx, c):
+    """(nb*nz*ny*nx*c) -> halo layout [nb][nz+2][ny][nx+2][c] with periodic x/z copies."""
+    a = t.view(nb, 1 << lz, 1 << ly, 1 << lx, c)
+    a = torch.cat([a[:, :, :, -1:], a, a[:, :, :, :1]], dim=3)
+    a = torch.cat([a[:, -1:], a, a[:, :1]], dim=1)
+    return a.contiguous().view(-1)
+
+
+def _from_halo(torch, t, nb, lz, ly, lx, c):
+    a = t.view(nb, (1 << lz) + 2, 1 << ly, (1 << lx) + 2, c)
+    return a[:, 1:-1, :, 1:-1].contiguous().view(-1)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if not c[1]])
+def test_tma_conv3_equals_cpasync_conv3(env, case):
+    torch, unet = env
+    c0, _, c1, cout, grid, relu, bias, out_f32 = case
+    nb, lz, ly, lx = grid
+    rng = np.random.default_rng(17 + hash(case) % 2**31)
+    V = nb << (lz + ly + lx)
+    s0, _ = _bf16(torch, rng.normal(size=V * c0))
+    s1, _ = (_bf16(torch, rng.normal(size=V * c1)) if c1 else (None, None))
+    w, _ = _bf16(torch, rng.normal(0, 0.1, size=cout * 27 * (c0 + c1)))
+    b = torch.from_numpy(rng.normal(size=cout).astype(np.float32)).cuda() if bias else None
+    dt = torch.float32 if out_f32 else torch.bfloat16
+    ref = torch.empty(V * cout, dtype=dt, device="cuda")
+    unet.conv3(s0, c0, w, ref, cout, grid, src1=s1, c1=c1, bias=b, relu=relu)
+    h0 = _to_halo(torch, s0, nb, lz, ly, lx, c0)
+    h1 = _to_halo(torch, s1, nb, lz, ly, lx, c1) if c1 else None
+    if out_f32:
+        got = torch.empty(V * cout, dtype=dt, device="cuda")
+        unet.conv3_halo(h0, c0, w, got, cout, grid, src1=h1, c1=c1, bias=b, relu=relu)
+        assert torch.equal(got, ref)
+    else:
+        n_h = nb * ((1 << lz) + 2) * (1 << ly) * ((1 << lx) + 2) * cout
+        got = torch.full((n_h,), float("nan"), dtype=dt, device="cuda")
+        unet.conv3_halo(h0, c0, w, got, cout, grid, src1=h1, c1=c1, bias=b, relu=relu)
+        torch.cuda.synchronize()
+        assert torch.equal(got, _to_halo(torch, ref, nb, lz, ly, lx, cout))  # interior and periodic copies
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if not c[1] and c[3] <= 64])
+def test_tma_wgrad_equals_cpasync_wgrad(env, case):
+    torch, unet = env
+    c0, _, c1, cout, grid, _, _, _ = case
+    nb, lz, ly, lx = grid
+    rng = np.random.default_rng(23 + hash(case) % 2**31)
+    V = nb << (lz + ly + lx)
+    s0, _ = _bf16(torch, rng.normal(size=V * c0))
+    s1, _ = (_bf16(torch, rng.normal(size=V * c1)) if c1 else (None, None))
+    dy, _ = _bf16(torch, rng.normal(size=V * cout))
+    ref = torch.empty(cout * 27 * (c0 + c1), dtype=torch.float32, device="cuda")
+    unet.conv3_wgrad(s0, c0, dy, cout, ref, grid, src1=s1, c1=c1)
+    got = torch.empty_like(ref)
+    unet.conv3_halo_wgrad(_to_halo(torch, s0, nb, lz, ly, lx, c0), c0, _to_halo(torch, dy, nb, lz, ly, lx, cout),
+                          cout, got, grid, src1=_to_halo(torch, s1, nb, lz, ly, lx, c1) if c1 else None, c1=c1)
+    # same products, the splits may differ: FP32 accumulation order only
+    mag = float(ref.abs().max())
+    assert float((got - ref).abs().max()) <= 1e-5 * mag + 1e-6
