@@ -260,7 +260,8 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind,
-                "kernel": "lbm::sweep_tma_kernel" if info.kernel == L.LBM_KERNEL_TMA else "lbm::sweep_kernel",
+                "kernel": ("lbm::sweep_tma_kernel" if info.kernel == L.LBM_KERNEL_TMA
+                           else "lbm::sweep2_kernel" if info.pair else "lbm::sweep_kernel"),
                 "bytes_per_lup": BYTES_PER_LUP[st_main], "sweep_ms": sweep_ms,
                 "exchange_ms": xch_ms, "exchange_pdfs": info.exchange_pdfs}
 

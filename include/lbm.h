@@ -87,9 +87,12 @@ typedef struct {
     double storage_scale; /* power of two multiplying f~ in F16S/BF16S storage; default 1 */
     void *stream;         /* cudaStream_t to enqueue on; NULL = the library creates one */
     int tile[3];          /* sweep tile: threads along x (a multiple of 32), rows along
-                             y, z slices; {0,0,0} = the library's default: row tiles, or
-                             runs of 256 consecutive cells per CTA where a Block's width
-                             is not a multiple of 32 (lbm_autotune may change either) */
+                             y, z slices, one cell per thread; {0,0,0} = the library's
+                             default: two cells per thread where every Block width is even
+                             (FP32 / 16-bit storage; row tiles of 64 x 4 x 2 cells where the
+                             widths are multiples of 64, else runs of 256 cells), otherwise
+                             row tiles, or runs of 256 cells where a width is not a multiple
+                             of 32 (lbm_autotune may change any of these) */
     int graph_steps;      /* steps per captured CUDA graph; 0 = automatic, -1 = no graphs */
     int kernel;           /* LBM_KERNEL_AUTO (default): the register sweep, with the
                              TMA-staged sweep prepared where the Patch allows it so
@@ -279,6 +282,8 @@ typedef struct {
                                  consecutive cells per CTA (tile[] is then {flat, 1, 1}) */
     int mask;                 /* 1: the register sweep treats near-wall cells through
                                  precomputed link masks under a warp vote */
+    int pair;                 /* 1: the register sweep updates two neighbouring cells per
+                                 thread (tile[0] then counts threads, each covering 2 cells) */
 } lbm_info;
 int lbm_get_info(lbm_ctx *ctx, lbm_info *info);
 
@@ -315,7 +320,9 @@ int lbm_autotune(lbm_ctx *ctx, const char *cache_path, int best[3]);
  * mask}: kind 0 = register sweep over row tiles of tx x ty cells and tz z
  * slices (tx a multiple of 32, tx*ty <= 256); 1 = TMA-staged sweep (only where
  * it applies) with zchunk z slices per work item; 2 = register sweep over
- * runs of tx consecutive cells (32..256, a multiple of 32); grid = CTAs of a
+ * runs of tx consecutive cells (32..256, a multiple of 32); 3 and 4 = kinds 0
+ * and 2 with two neighbouring cells per thread (tx threads cover 2 tx cells;
+ * even Block widths, FP32 / F16S / BF16S storage); grid = CTAs of a
  * persistent launch (0 = one per work item); minb = 3 or 4 resident CTAs per
  * SM the register budget allows (FP64 storage always uses 2); mask = 1 treats
  * near-wall cells through precomputed link masks under a warp vote.  Every

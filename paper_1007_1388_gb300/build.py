@@ -43,7 +43,8 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-SWEEP_SOURCES = ("sweep_impl.cuh", "collide.cuh", "device_common.cuh", "sweep_types.h", "sweep_f32.cu",
+SWEEP_SOURCES = ("sweep_impl.cuh", "sweep2_impl.cuh", "collide.cuh", "device_common.cuh", "sweep_types.h",
+                 "sweep_f32.cu", "sweep2_f32.cu",
                  "sweep_f16s.cu", "sweep_bf16s.cu", "sweep_f64.cu")
 
 

@@ -101,6 +101,7 @@ struct lbm_ctx {
     int flat = 0;                 // > 0: runs of this many consecutive cells per CTA
     int grid = 0;                 // 0 = one CTA per tile, else a persistent grid
     int mask = 0;                 // near-wall cells via link masks under a warp vote
+    int pair = 0;                 // two neighbouring cells per thread (FP32 / 16-bit storage)
     std::vector<Tile> stiles;
     std::vector<char> active;     // per instance: swept (1) or frozen (0)
     int minb = 4;  // register budget of the sweep (resident CTAs per SM)
@@ -419,18 +420,20 @@ int set_tiles(lbm_ctx *c, const int t[3])
 // The sweep's work list: row tiles of t[0] x t[1] cells over t[2] z slices,
 // or (flat > 0) runs of `flat` consecutive cells of each Block; grid > 0
 // launches that many CTAs, which loop over the list.
-int set_sweep(lbm_ctx *c, const int t[3], int flat, int grid)
+int set_sweep(lbm_ctx *c, const int t[3], int flat, int grid, int pair = 0)
 {
     std::vector<Tile> st;
     std::vector<long long> unused;
+    const int cpt = pair ? 2 : 1;  // cells per thread along x
     if (flat > 0) {
         for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
             const BlockGeom &b = c->blocks[bi];
             const long long n = (long long)b.nx * b.ny * b.nz;
-            for (long long i = 0; i < n; i += flat) st.push_back({int(bi), int(i), 0, 0});
+            for (long long i = 0; i < n; i += (long long)cpt * flat) st.push_back({int(bi), int(i), 0, 0});
         }
     } else {
-        build_tiles(c, t, st, unused);
+        const int tc[3] = {cpt * t[0], t[1], t[2]};
+        build_tiles(c, tc, st, unused);
     }
     // frozen instances (lbm_run_to_residual_each) are left out
     if (!c->active.empty()) {
@@ -449,6 +452,7 @@ int set_sweep(lbm_ctx *c, const int t[3], int flat, int grid)
     c->stiles.swap(st);
     c->flat = flat;
     c->grid = grid;
+    c->pair = pair;
     if (flat > 0) {
         c->sw_tile[0] = flat;
         c->sw_tile[1] = c->sw_tile[2] = 1;
@@ -756,19 +760,35 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     td[2] = 4;
     if ((rc = set_tiles(c, td))) return rc;
     int t[3] = {p.tile[0], p.tile[1], p.tile[2]};
-    int flat = 0;
+    int flat = 0, pair = 0;
     if (t[0] <= 0 || t[1] <= 0 || t[2] <= 0) {
         for (int a = 0; a < 3; ++a) t[a] = td[a];
-        // Blocks whose width is not a warp multiple would leave lanes of
-        // every row tile idle: sweep them in runs of 256 consecutive cells
-        bool ragged = false;
-        for (const BlockGeom &b : c->blocks) ragged |= (b.nx % 32) != 0;
-        if (ragged) flat = 256;
+        // Two cells per thread wherever the Block widths are even (FP32 and
+        // 16-bit storage): twice the bytes in flight per thread.  Blocks whose
+        // width is not a multiple of the tile's cells would leave lanes of
+        // every row tile idle: sweep them in runs of consecutive cells.
+        bool even = c->storage != LBM_F64, w64 = true, w32 = true;
+        for (const BlockGeom &b : c->blocks) {
+            even = even && (b.nx % 2 == 0);
+            w64 = w64 && (b.nx % 64 == 0);
+            w32 = w32 && (b.nx % 32 == 0);
+        }
+        if (even && w64) {
+            pair = 1;
+            t[0] = 32;
+            t[1] = 4;
+            t[2] = 2;
+        } else if (even) {
+            pair = 1;
+            flat = 128;
+        } else if (!w32) {
+            flat = 256;
+        }
     }
     if (t[0] * t[1] > 256 || t[0] % 32 != 0)
         return fail(c, LBM_EINVAL, "tile %dx%d: threads along x must be a multiple of 32 and "
                     "tile[0]*tile[1] <= 256", t[0], t[1]);
-    if ((rc = set_sweep(c, t, flat, 0))) return rc;
+    if ((rc = set_sweep(c, t, flat, 0, pair))) return rc;
     // link masks pay where near-wall and interior cells share warps
     c->mask = near_cells * 10 > c->fluid ? 1 : 0;
     // the TMA sweep is set up wherever it applies (lbm_autotune may pick it);
@@ -814,6 +834,7 @@ SweepArgs sweep_args(const lbm_ctx *c, int from)
     a.tz = c->sw_tile[2];
     a.flat = c->flat > 0 ? 1 : 0;
     a.mask = c->mask;
+    a.pair = c->pair;
     a.collision = c->p.collision;
     a.forced = c->forced ? 1 : 0;
     a.storage = c->storage;
@@ -1450,6 +1471,7 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info)
     info->kernel = c->kernel;
     info->stages = c->kernel == LBM_KERNEL_TMA ? tma_stages(c->storage) : 0;
     info->flat = c->kernel != LBM_KERNEL_TMA ? c->flat : 0;
+    info->pair = c->kernel != LBM_KERNEL_TMA ? c->pair : 0;
     info->mask = c->kernel != LBM_KERNEL_TMA ? c->mask : 0;
     info->sweep_ctas = c->kernel == LBM_KERNEL_TMA ? c->tma_grid
                        : c->grid > 0                ? c->grid
@@ -1503,12 +1525,20 @@ namespace {
 int check_cfg(lbm_ctx *c, const int *cd)
 {
     const bool tma_ok = c->kernel == LBM_KERNEL_TMA || (c->tma_grid > 0);
-    if (cd[0] < 0 || cd[0] > 2) return fail(c, LBM_EINVAL, "sweep config: kind %d", cd[0]);
+    if (cd[0] < 0 || cd[0] > 4) return fail(c, LBM_EINVAL, "sweep config: kind %d", cd[0]);
     if (cd[0] == 1 && !tma_ok)
         return fail(c, LBM_EINVAL, "sweep config: the TMA sweep does not apply to this context");
-    if (cd[0] == 2 && (cd[1] < 32 || cd[1] > 256 || cd[1] % 32 != 0))
-        return fail(c, LBM_EINVAL, "sweep config: runs of %d cells (32..256, multiple of 32)", cd[1]);
-    if (cd[0] == 0 && (cd[1] <= 0 || cd[2] <= 0 || cd[3] <= 0 || cd[1] % 32 != 0 || cd[1] * cd[2] > 256))
+    if (cd[0] >= 3) {
+        bool even = c->storage != LBM_F64;
+        for (const BlockGeom &b : c->blocks) even = even && (b.nx % 2 == 0);
+        if (!even)
+            return fail(c, LBM_EINVAL, "sweep config: two cells per thread need even Block widths and "
+                        "FP32 / F16S / BF16S storage");
+    }
+    if ((cd[0] == 2 || cd[0] == 4) && (cd[1] < 32 || cd[1] > 256 || cd[1] % 32 != 0))
+        return fail(c, LBM_EINVAL, "sweep config: runs of %d threads (32..256, multiple of 32)", cd[1]);
+    if ((cd[0] == 0 || cd[0] == 3) &&
+        (cd[1] <= 0 || cd[2] <= 0 || cd[3] <= 0 || cd[1] % 32 != 0 || cd[1] * cd[2] > 256))
         return fail(c, LBM_EINVAL, "sweep config: tile %dx%dx%d", cd[1], cd[2], cd[3]);
     if (cd[0] == 1 && (cd[6] <= 0 || cd[6] > 1024)) return fail(c, LBM_EINVAL, "sweep config: zchunk %d", cd[6]);
     if (cd[4] < 0) return fail(c, LBM_EINVAL, "sweep config: grid %d", cd[4]);
@@ -1524,8 +1554,9 @@ int apply_cfg(lbm_ctx *c, const int *cd)
     // the TMA sweep keeps the current register work list (used if switched back)
     const int t[3] = {cd[0] == 1 ? c->sw_tile[0] : cd[1], cd[0] == 1 ? c->sw_tile[1] : cd[2],
                       cd[0] == 1 ? c->sw_tile[2] : cd[3]};
-    const int flat = cd[0] == 2 ? cd[1] : (cd[0] == 1 ? c->flat : 0);
-    if ((rc = set_sweep(c, t, flat, cd[0] == 1 ? c->grid : cd[4]))) return rc;
+    const int flat = (cd[0] == 2 || cd[0] == 4) ? cd[1] : (cd[0] == 1 ? c->flat : 0);
+    const int pair = cd[0] >= 3 ? 1 : (cd[0] == 1 ? c->pair : 0);
+    if ((rc = set_sweep(c, t, flat, cd[0] == 1 ? c->grid : cd[4], pair))) return rc;
     c->minb = cd[5];
     if (cd[0] == 1) c->tma_zchunk = cd[6];
     c->mask = cd[7];
@@ -1536,7 +1567,7 @@ int apply_cfg(lbm_ctx *c, const int *cd)
 
 void get_cfg(const lbm_ctx *c, int *cd)
 {
-    cd[0] = c->kernel == LBM_KERNEL_TMA ? 1 : (c->flat > 0 ? 2 : 0);
+    cd[0] = c->kernel == LBM_KERNEL_TMA ? 1 : (c->flat > 0 ? (c->pair ? 4 : 2) : (c->pair ? 3 : 0));
     cd[1] = c->sw_tile[0];
     cd[2] = c->sw_tile[1];
     cd[3] = c->sw_tile[2];
@@ -1600,6 +1631,8 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int zc0 = c->tma_zchunk, m0 = c->mask;
+        bool pair_ok = c->storage != LBM_F64;
+        for (const BlockGeom &b : c->blocks) pair_ok = pair_ok && (b.nx % 2 == 0);
         const int *st = c->sw_tile;
         std::vector<Cfg> cand;
         if (tma_ok)
@@ -1613,9 +1646,21 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
                 }
             }
             for (int th : {128, 256}) cand.push_back({2, th, 1, 1, 0, mb, zc0, m0});
+            if (pair_ok) {
+                // two cells per thread: row tiles of 2 tx cells, runs of 2 th cells
+                for (int tx : {32, 64}) {
+                    if (tx > std::max(32, round_up((maxnx + 1) / 2, 32))) continue;
+                    for (int th : {128, 256}) {
+                        if (th < tx) continue;
+                        for (int tz : {1, 2, 4}) cand.push_back({3, tx, th / tx, tz, 0, mb, zc0, m0});
+                    }
+                }
+                for (int th : {128, 256}) cand.push_back({4, th, 1, 1, 0, mb, zc0, m0});
+            }
         }
         // persistent grids over the default work list
-        for (int m : {4, 8, 16}) cand.push_back({kind0 == 2 ? 2 : 0, st[0], st[1], st[2], m * sms, c->minb, zc0, m0});
+        for (int m : {4, 8, 16})
+            cand.push_back({kind0 == 1 ? 0 : kind0, st[0], st[1], st[2], m * sms, c->minb, zc0, m0});
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");

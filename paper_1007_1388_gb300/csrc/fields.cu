@@ -603,9 +603,18 @@ int tma_stages(int storage) { return storage == 0 ? 4 : 5; }
 
 // Sweep dispatch over the storage formats (kernels live in sweep_*.cu).
 template <int ST> cudaError_t launch_sweep_st(const SweepArgs &, cudaStream_t);
+template <int ST> cudaError_t launch_sweep2_st(const SweepArgs &, cudaStream_t);
 
 cudaError_t launch_sweep(const SweepArgs &a, cudaStream_t s)
 {
+    if (a.pair) {
+        switch (a.storage) {
+        case 0: return launch_sweep2_st<0>(a, s);
+        case 1: return launch_sweep2_st<1>(a, s);
+        case 2: return launch_sweep2_st<2>(a, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.storage) {
     case 0: return launch_sweep_st<0>(a, s);
     case 1: return launch_sweep_st<1>(a, s);

@@ -1,0 +1,256 @@
+// The fused sweep with two neighbouring cells (x, x + 1; x even) per thread,
+// for FP32 and the 16-bit storage formats.  Same physics, pulls and rounding
+// as the one-cell sweep (sweep_impl.cuh): the collision runs on the packed
+// FP32x2 lane type of collide.cuh, whose rounding sequence per cell is that
+// of the scalar one, so both sweeps give bitwise equal results.
+//
+// Why: the sweep is bound by the bytes each SM keeps in flight, and with one
+// cell per thread a 16-bit PDF puts half as many bytes in flight per register
+// as an FP32 one.  With two cells per thread the 9 directions with e_x = 0
+// load both cells' values with one aligned vector load, the others with two
+// scalar loads of adjacent elements, and the stores are vector stores.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace lbm {
+
+template <int ST> struct Pair;
+template <> struct Pair<0> {
+    static __device__ __forceinline__ F2 ld2(const float *p)
+    {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        return f2_pack(v.x, v.y);
+    }
+    static __device__ __forceinline__ void st2(float *p, F2 v)
+    {
+        float lo, hi;
+        f2_unpack(v, lo, hi);
+        *reinterpret_cast<float2 *>(p) = make_float2(lo, hi);
+    }
+};
+template <> struct Pair<1> {
+    static __device__ __forceinline__ F2 ld2(const __half *p)
+    {
+        const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+        return f2_pack(v.x, v.y);
+    }
+    static __device__ __forceinline__ void st2(__half *p, F2 v)
+    {
+        float lo, hi;
+        f2_unpack(v, lo, hi);
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(lo, hi);
+    }
+};
+template <> struct Pair<2> {
+    static __device__ __forceinline__ F2 ld2(const __nv_bfloat16 *p)
+    {
+        const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+        return f2_pack(v.x, v.y);
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16 *p, F2 v)
+    {
+        float lo, hi;
+        f2_unpack(v, lo, hi);
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(lo, hi);
+    }
+};
+
+// The 19 pulled values of one cell next to a wall (half-way bounce-back),
+// from its link mask (MASK) or its neighbours' flags.
+template <int ST, bool MASK, bool UNIF>
+__device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, const BlockGeom &b,
+                                          const CollideConsts<float> *cc, const typename Traits<ST>::S *src,
+                                          const typename Traits<ST>::S *srcm, const typename Traits<ST>::S *srcp,
+                                          const uint8_t *fl, int c, int cf, int px, int pxy, int pxf, int pxyf, int G)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    if (MASK) {
+        const uint32_t lm = __ldg(a.links + b.cell_base + cf);
+        const bool mv = (lm & L_MOVING) != 0;
+        v[0] = Tr::ld(src + c);
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            const bool bq = (lm >> q) & 1u;
+            const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+            const S *pa = bq ? src + (opp(q) * G + c) : s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy));
+            float w = Tr::ld(pa);
+            if (mv && bq) {
+                const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+                if ((nf & F_KIND) == F_MOVING) w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
+            }
+            v[q] = w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+            if (nf & F_KIND) {
+                float w = Tr::ld(src + (opp(q) * G + c));
+                if ((nf & F_KIND) == F_MOVING) w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
+                v[q] = w;
+            } else {
+                const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+                v[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
+            }
+        }
+    }
+}
+
+// the plain pull of one cell (no wall among its sources)
+template <int ST>
+__device__ __forceinline__ void pull_plain(float (&v)[Q], const typename Traits<ST>::S *src,
+                                           const typename Traits<ST>::S *srcm, const typename Traits<ST>::S *srcp,
+                                           int c, int px, int pxy, int G)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+        v[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
+    }
+}
+
+template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK>
+__global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant__ SweepArgs a)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    const CollideConsts<float> *__restrict__ consts = static_cast<const CollideConsts<float> *>(a.consts);
+
+    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const Tile tile = a.tiles[t];
+        const BlockGeom &b = a.blocks[tile.block];
+        const int nx = b.nx, ny = b.ny;
+        int x, y, z;  // x: the first (even) cell of the pair
+        if (a.flat) {
+            const int i = tile.x0 + 2 * int(threadIdx.x);
+            const int yz = i / nx;
+            x = i - yz * nx;
+            z = yz / ny;
+            y = yz - z * ny;
+        } else {
+            x = tile.x0 + 2 * int(threadIdx.x);
+            y = tile.y0 + int(threadIdx.y);
+            z = tile.z0 + int(blockIdx.y);
+        }
+        // no lane leaves before the warp vote below (nx is even: x + 1 < nx too)
+        const bool inside = x < nx && y < ny && z < b.nz;
+        const int px = b.px;
+        const int pxy = px * b.py;
+        const int G = int(b.G);
+        const CollideConsts<float> *cc = consts + b.inst;
+        const CollKPtr<float> KP{cc};
+        const CollKRef<float> KR{a.kf};
+        const S *__restrict__ src = static_cast<const S *>(a.src) + b.pdf_base;
+        // cell x pulls across the -x face when x = 0; cell x + 1 across the +x face when x + 1 = nx - 1
+        const S *__restrict__ srcm0 = src + (x == 0 ? b.xm_off : 0ll);
+        const S *__restrict__ srcp1 = src + (x + 2 == nx ? b.xp_off : 0ll);
+        S *__restrict__ dst = static_cast<S *>(a.dst) + b.pdf_base;
+        const uint8_t *__restrict__ fl = a.flags + b.cell_base;
+
+        const int pxf = b.pxf, pxyf = b.pxf * b.py;
+        const int c = (z + 1) * pxy + (y + 1) * px + x;
+        const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
+        const uint8_t fl0 = inside ? fl[cf] : uint8_t(F_NOSLIP), fl1 = inside ? fl[cf + 1] : uint8_t(F_NOSLIP);
+        const bool solid0 = fl0 & F_KIND, solid1 = fl1 & F_KIND;
+        const bool near0 = !solid0 && (fl0 & F_NEAR), near1 = !solid1 && (fl1 & F_NEAR);
+        const bool take_near = MASK ? __any_sync(0xffffffffu, near0 || near1) : (near0 || near1);
+        if (solid0 && solid1) continue;  // solid cells (and lanes outside the Block) are not updated
+        F2 f[Q];
+        if (!take_near) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int a0 = q * G + c - (ey(q) * px + ez(q) * pxy);
+                if (ex(q) == 0)
+                    f[q] = Pair<ST>::ld2(src + a0);
+                else if (ex(q) > 0)
+                    f[q] = f2_pack(Tr::ld(srcm0 + (a0 - 1)), Tr::ld(src + a0));
+                else
+                    f[q] = f2_pack(Tr::ld(src + (a0 + 1)), Tr::ld(srcp1 + (a0 + 2)));
+            }
+        } else {
+            float v0[Q], v1[Q];
+            const S *srcp0 = src, *srcm1 = src;  // the inner faces of the pair stay in the Block
+            if (near0)
+                pull_near<ST, MASK, UNIF>(v0, a, b, cc, src, srcm0, srcp0, fl, c, cf, px, pxy, pxf, pxyf, G);
+            else
+                pull_plain<ST>(v0, src, srcm0, srcp0, c, px, pxy, G);
+            if (near1)
+                pull_near<ST, MASK, UNIF>(v1, a, b, cc, src, srcm1, srcp1, fl, c + 1, cf + 1, px, pxy, pxf, pxyf, G);
+            else
+                pull_plain<ST>(v1, src, srcm1, srcp1, c + 1, px, pxy, G);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = f2_pack(v0[q], v1[q]);
+        }
+        if (UNIF)
+            collide_v<COLL, FORCE>(f, KR);
+        else
+            collide_v<COLL, FORCE>(f, KP);
+        if (!solid0 && !solid1) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) Pair<ST>::st2(dst + (q * G + c), f[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                float lo, hi;
+                f2_unpack(f[q], lo, hi);
+                if (!solid0) Tr::st(dst + (q * G + c), lo);
+                if (!solid1) Tr::st(dst + (q * G + c + 1), hi);
+            }
+        }
+    }
+}
+
+template <int ST, int MINB, bool UNIF, bool MASK>
+void launch_sweep2_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (a.collision == 0) {
+        if (a.forced)
+            sweep2_kernel<ST, 0, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+        else
+            sweep2_kernel<ST, 0, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.forced)
+            sweep2_kernel<ST, 1, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+        else
+            sweep2_kernel<ST, 1, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+    }
+}
+
+template <int ST, int MINB>
+void launch_sweep2_minb(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (a.unif) {
+        if (a.mask)
+            launch_sweep2_mask<ST, MINB, true, true>(a, grid, block, s);
+        else
+            launch_sweep2_mask<ST, MINB, true, false>(a, grid, block, s);
+    } else {
+        if (a.mask)
+            launch_sweep2_mask<ST, MINB, false, true>(a, grid, block, s);
+        else
+            launch_sweep2_mask<ST, MINB, false, false>(a, grid, block, s);
+    }
+}
+
+// Two cells per thread: block (tx, ty) threads cover 2 tx x ty cells.
+template <int ST>
+cudaError_t launch_sweep2_st(const SweepArgs &a, cudaStream_t s)
+{
+    if ((a.tx * a.ty) % 32 != 0 || a.tx * a.ty > 256 || (a.flat && (a.ty != 1 || a.tz != 1)))
+        return cudaErrorInvalidConfiguration;
+    dim3 block(a.tx, a.ty, 1);
+    const unsigned gx = unsigned(a.grid > 0 ? a.grid : a.ntiles);
+    if (gx == 0) return cudaSuccess;
+    const dim3 grid(gx, unsigned(a.tz), 1);
+    if (a.minb == 4)
+        launch_sweep2_minb<ST, 4>(a, grid, block, s);
+    else
+        launch_sweep2_minb<ST, 3>(a, grid, block, s);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

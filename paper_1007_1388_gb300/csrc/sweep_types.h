@@ -116,6 +116,8 @@ struct SweepArgs {
     int flat;                 // 1: a tile is a run of tx consecutive cells of a Block in
                               // (z, y, x) order starting at linear cell index x0
     int mask;                 // 1: near-wall cells via link masks under a warp vote
+    int pair;                 // 1: two neighbouring cells (x even, x + 1) per thread; tx threads
+                              // cover 2 tx cells (a flat tile: 2 tx consecutive cells)
     int collision;            // 0 BGK, 1 TRT
     int forced;               // any instance has a nonzero force
     int storage;              // LBM_F32 .. LBM_F64

@@ -67,6 +67,7 @@ class lbm_info(ctypes.Structure):
         ("stages", ctypes.c_int),
         ("flat", ctypes.c_int),
         ("mask", ctypes.c_int),
+        ("pair", ctypes.c_int),
     ]
 
 
@@ -447,7 +448,7 @@ def lbm_autotune(ctx: Ctx, cache_path: str | None = None):
     return tuple(best)
 
 
-SWEEP_ROWS, SWEEP_TMA, SWEEP_RUNS = 0, 1, 2
+SWEEP_ROWS, SWEEP_TMA, SWEEP_RUNS, SWEEP_ROWS2, SWEEP_RUNS2 = 0, 1, 2, 3, 4
 
 
 def lbm_get_sweep_config(ctx: Ctx):

@@ -5,10 +5,10 @@
   obstacles and moving walls);
 - a TMA sweep whose staged data never arrives reports LBM_ETIMEOUT through
   its bounded waits instead of hanging, and the library stays usable;
-- the register sweep's variants (row tiles, runs of consecutive cells,
-  persistent grids, register budgets, near-wall cells by per-lane branch or by
-  link masks under a warp vote) are bitwise equal on ragged, walled, porous
-  and batched geometries.
+- the register sweep's variants (row tiles, runs of consecutive cells, one or
+  two cells per thread, persistent grids, register budgets, near-wall cells by
+  per-lane branch or by link masks under a warp vote) are bitwise equal on
+  ragged, walled, porous and batched geometries.
 """
 import numpy as np
 import pytest
@@ -95,9 +95,11 @@ def test_tma_sweep_bounded_wait_reports_timeout(L):
 def _configs(L, bx):
     """Row tiles, runs of consecutive cells, persistent grids, both register
     budgets and both near-wall strategies."""
-    R, U = L.SWEEP_ROWS, L.SWEEP_RUNS
+    R, U, R2, U2 = L.SWEEP_ROWS, L.SWEEP_RUNS, L.SWEEP_ROWS2, L.SWEEP_RUNS2
     out = [(R, 32, 4, 1, 0, 4, 8, 0), (R, 32, 8, 2, 0, 3, 8, 1), (U, 256, 1, 1, 0, 4, 8, 0),
-           (U, 128, 1, 1, 0, 3, 8, 1), (U, 256, 1, 1, 304, 4, 8, 1), (R, 32, 4, 2, 152, 3, 8, 0)]
+           (U, 128, 1, 1, 0, 3, 8, 1), (U, 256, 1, 1, 304, 4, 8, 1), (R, 32, 4, 2, 152, 3, 8, 0),
+           (R2, 32, 4, 1, 0, 3, 8, 0), (R2, 32, 8, 2, 0, 4, 8, 1), (U2, 128, 1, 1, 0, 3, 8, 1),
+           (U2, 256, 1, 1, 304, 4, 8, 0)]
     if bx >= 64:
         out.append((R, 64, 4, 4, 0, 4, 8, 1))
     return out
@@ -125,7 +127,8 @@ def test_sweep_variants_bitwise_single_patch(L, storage):
                           storage_scale=(256.0 if storage == 1 else 1.0))
         ctx = L.lbm_create(dims, bd, 0.62, flags, p)
         info = L.lbm_get_info(ctx)
-        assert info.flat == 256  # the default for Blocks that are not a warp multiple wide
+        # the default for even Blocks that are not a multiple of 64 wide: runs, two cells per thread
+        assert info.flat == 128 and info.pair == 1
         ref = _run_cfg(L, ctx, f0, 17, None)
         for cfg in _configs(L, bd[0]):
             got = _run_cfg(L, ctx, f0, 17, cfg)
@@ -146,7 +149,12 @@ def test_sweep_variants_bitwise_batch(L):
     assert L.lbm_get_info(ctx).mask == 1  # sphere packings: many near-wall cells
     f0 = np.concatenate([W.random_pdfs(rng, d, 1e-2, f).reshape(-1) for d, _, f in inst])
     ref = _run_cfg(L, ctx, f0, 13, None)
+    even = all(d[0] % 2 == 0 for d, _, _ in inst)
     for cfg in _configs(L, 32):
+        if cfg[0] >= L.SWEEP_ROWS2 and not even:
+            with pytest.raises(L.LBMError):
+                L.lbm_set_sweep_config(ctx, cfg)
+            continue
         got = _run_cfg(L, ctx, f0, 13, cfg)
         assert np.array_equal(ref, got), (cfg, np.abs(ref - got).max())
     ctx.destroy()
@@ -156,7 +164,7 @@ def test_sweep_config_validation(L):
     # 40 cells wide: the TMA sweep does not apply, so kind 1 is invalid too
     ctx = L.lbm_create((40, 16, 8), (40, 16, 8), 0.7, None, L.make_params())
     before = L.lbm_get_sweep_config(ctx)
-    for bad in [(3, 32, 4, 1, 0, 4, 8, 0), (0, 48, 4, 1, 0, 4, 8, 0), (0, 32, 16, 1, 0, 4, 8, 0),
+    for bad in [(5, 32, 4, 1, 0, 4, 8, 0), (0, 48, 4, 1, 0, 4, 8, 0), (0, 32, 16, 1, 0, 4, 8, 0),
                 (2, 100, 1, 1, 0, 4, 8, 0), (0, 32, 4, 1, -1, 4, 8, 0), (0, 32, 4, 1, 0, 5, 8, 0),
                 (0, 32, 4, 1, 0, 4, 8, 2), (1, 32, 4, 1, 0, 4, 8, 0)]:
         with pytest.raises(L.LBMError):
