@@ -31,6 +31,24 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same for the 32-byte swizzled K-major layout that TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_32B: rows of 32 bytes (16 bf16), 8-row atoms of 256
+// bytes (the two 16-byte halves of rows 4..7 of an atom swapped), SBO = 256.
+__device__ __forceinline__ uint64_t sdesc_sw32(uint32_t addr)
+{
+    return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t(1) << 16) | (uint64_t(256 >> 4) << 32) | (1ull << 46) |
+           (6ull << 61);
+}
+
+// 32-byte swizzled MN-major layout (TMA box of 16 MN elements x K rows with
+// CU_TENSOR_MAP_SWIZZLE_32B): 8-row K groups of 256 bytes (SBO), blocks of 16
+// MN elements `lbo` bytes apart (LBO).
+__device__ __forceinline__ uint64_t sdesc_sw32_mn(uint32_t addr, uint32_t lbo)
+{
+    return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) | (uint64_t(256 >> 4) << 32) |
+           (1ull << 46) | (6ull << 61);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // M = 128, N = n; a_mn / b_mn select MN-major operands.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n, bool a_mn, bool b_mn)

@@ -557,7 +557,7 @@ int conv(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf16
 {
     ConvTmaArgs a{};
     const VBox box = vbox(g, 128);
-    if (!make_halo_map(&a.a0, s0, c0, g, box) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box)) ||
+    if (!make_halo_map(&a.a0, s0, c0, g, box, 16) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box, 16)) ||
         !make_weight_map(&a.w, w, c0 + c1, cout))
         return ufail(c, LBM_ECUDA, "conv3: tensor map encoding failed");
     if (!c1) a.a1 = a.a0;
@@ -597,8 +597,8 @@ int wgrad(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf1
 {
     WgradTmaArgs a{};
     const VBox box = vbox(g, 64);
-    if (!make_halo_map(&a.a0, s0, c0, g, box) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box)) ||
-        !make_halo_map(&a.dy, dy, cout, g, box))
+    if (!make_halo_map(&a.a0, s0, c0, g, box, 16) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box, 16)) ||
+        !make_halo_map(&a.dy, dy, cout, g, box, 16))
         return ufail(c, LBM_ECUDA, "wgrad: tensor map encoding failed");
     if (!c1) a.a1 = a.a0;
     a.c0 = c0;
@@ -988,8 +988,8 @@ int unet_conv3_halo(const void *src0, int c0, const void *src1, int c1, const vo
     const VGrid g{nb, lz, ly, lx};
     ConvTmaArgs a{};
     const VBox box = vbox(g, 128);
-    if (g.voxels() % 128 || !make_halo_map(&a.a0, src0, c0, g, box) ||
-        (c1 && !make_halo_map(&a.a1, src1, c1, g, box)) || !make_weight_map(&a.w, w, c0 + c1, cout))
+    if (g.voxels() % 128 || !make_halo_map(&a.a0, src0, c0, g, box, 16) ||
+        (c1 && !make_halo_map(&a.a1, src1, c1, g, box, 16)) || !make_weight_map(&a.w, w, c0 + c1, cout))
         return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo: tensor maps (alignment, channels or grid)");
     if (!c1) a.a1 = a.a0;
     a.bias = bias;
@@ -1025,8 +1025,8 @@ int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, co
     const VGrid g{nb, lz, ly, lx};
     WgradTmaArgs a{};
     const VBox box = vbox(g, 64);
-    if (g.voxels() % 64 || !make_halo_map(&a.a0, src0, c0, g, box) ||
-        (c1 && !make_halo_map(&a.a1, src1, c1, g, box)) || !make_halo_map(&a.dy, dy, cout, g, box))
+    if (g.voxels() % 64 || !make_halo_map(&a.a0, src0, c0, g, box, 16) ||
+        (c1 && !make_halo_map(&a.a1, src1, c1, g, box, 16)) || !make_halo_map(&a.dy, dy, cout, g, box, 16))
         return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo_wgrad: tensor maps (alignment, channels or grid)");
     if (!c1) a.a1 = a.a0;
     a.c0 = c0;

@@ -73,13 +73,14 @@ __global__ void __launch_bounds__(THREADS) conv3_tma_kernel(const __grid_constan
             unsigned char *sb = sa + abytes;
             umma::mbar_arrive_expect_tx(&full[s], bytes);
             const int xs = 1 + tap_dx(t), ys = y0 + tap_dy(t), zs = 1 + z + tap_dz(t);
-            for (int k = 0; k < kc; ++k) {
-                if (k < kc0)
-                    umma::tma_load_5d(sa + k * 2048, &a.a0, 8 * k, xs, ys, zs, b, &full[s]);
+            // 16-channel chunks: 128 rows x 32 bytes (A), cout rows x 32 bytes (B), 32B swizzle
+            for (int k = 0; k < (cin >> 4); ++k) {
+                if (k < (kc0 >> 1))
+                    umma::tma_load_5d(sa + k * 4096, &a.a0, 16 * k, xs, ys, zs, b, &full[s]);
                 else
-                    umma::tma_load_5d(sa + k * 2048, &a.a1, 8 * (k - kc0), xs, ys, zs, b, &full[s]);
+                    umma::tma_load_5d(sa + k * 4096, &a.a1, 16 * k - a.c0, xs, ys, zs, b, &full[s]);
             }
-            for (int k = 0; k < kc; ++k) umma::tma_load_3d(sb + k * cout * 16, &a.w, 8 * k, t, 0, &full[s]);
+            for (int k = 0; k < (cin >> 4); ++k) umma::tma_load_3d(sb + k * cout * 32, &a.w, 16 * k, t, 0, &full[s]);
         }
     } else if (tid == 32) {
         // MMA issuer
@@ -95,8 +96,8 @@ __global__ void __launch_bounds__(THREADS) conv3_tma_kernel(const __grid_constan
             umma::fence_after();
             const uint32_t sa = umma::smem_addr(smem + s * sbytes), sb = sa + abytes;
             for (int j = 0; j < (cin >> 4); ++j)
-                umma::mma_bf16(tmem, umma::sdesc(sa + j * 4096, 2048, 128),
-                               umma::sdesc(sb + j * cout * 32, cout * 16, 128), idesc, (t > 0 || j > 0) ? 1u : 0u);
+                umma::mma_bf16(tmem, umma::sdesc_sw32(sa + j * 4096), umma::sdesc_sw32(sb + j * cout * 32), idesc,
+                               (t > 0 || j > 0) ? 1u : 0u);
             umma::mma_commit(&empty[s]);
         }
         if (ok) umma::mma_commit(&done);
@@ -149,10 +150,10 @@ __global__ void __launch_bounds__(THREADS) conv3_tma_kernel(const __grid_constan
     if (warp == 0) umma::tmem_dealloc(tmem, tcols);
 }
 
-// Weight gradient: row group g (8 rows = channels ci0 .. ci0+7 of one tap) of
-// the 128-row tile, for the chunk's 64 voxels, is one box of 64 voxels x 16
-// bytes at (g * 8 + kg) * 128: MN-major A with LBO 128 (K) and SBO 1024 (M);
-// the output gradient likewise for B.
+// Weight gradient: block g (16 rows = channels ci0 .. ci0+15 of one tap) of
+// the 128-row tile, for the chunk's 64 voxels, is one box of 64 voxels x 32
+// bytes (32B swizzle) at g * 2048: MN-major A with LBO 2048 (16-row blocks)
+// and SBO 256 (8-voxel groups); the output gradient likewise for B.
 __global__ void __launch_bounds__(THREADS) wgrad_tma_kernel(const __grid_constant__ WgradTmaArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(THREADS) wgrad_tma_kernel(const __grid_constan
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int cin = a.c0 + a.c1, cout = a.cout;
-    const int abytes = 16 * 1024, sbytes = abytes + (cout >> 3) * 1024;
+    const int abytes = 16 * 1024, sbytes = abytes + (cout >> 4) * 2048;
     const uint32_t tcols = cout <= 32 ? 32u : (cout <= 64 ? 64u : 128u);
     const long long M = a.g.voxels();
     const long long vbeg = (long long)blockIdx.y * a.vps;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(THREADS) wgrad_tma_kernel(const __grid_constan
     const uint32_t tmem = tslot;
 
     if (tid == 0) {
-        const uint32_t bytes = uint32_t(abytes + (cout >> 3) * 1024);
+        const uint32_t bytes = uint32_t(abytes + (cout >> 4) * 2048);
         for (int c = 0; c < nchunks; ++c) {
             const int s = c % STAGES;
             if (c >= STAGES && !umma::mbar_wait(&empty[s], ((c / STAGES) - 1) & 1, kWait)) {
@@ -198,22 +199,22 @@ __global__ void __launch_bounds__(THREADS) wgrad_tma_kernel(const __grid_constan
             const int y = int((m >> a.g.lx) & (ny - 1));
             const int zz = int((m >> (a.g.lx + a.g.ly)) & (nz - 1));
             const int bb = int(m >> (a.g.lx + a.g.ly + a.g.lz));
-            for (int g = 0; g < 16; ++g) {
-                const int row = blockIdx.x * 128 + g * 8;
+            for (int g = 0; g < 8; ++g) {
+                const int row = blockIdx.x * 128 + g * 16;
                 if (row < 27 * cin) {
                     const int t = row / cin, ci = row - t * cin;
                     const int xs = 1 + x0 + tap_dx(t), ys = y + tap_dy(t), zs = 1 + zz + tap_dz(t);
                     if (ci < a.c0)
-                        umma::tma_load_5d(sa + g * 1024, &a.a0, ci, xs, ys, zs, bb, &full[s]);
+                        umma::tma_load_5d(sa + g * 2048, &a.a0, ci, xs, ys, zs, bb, &full[s]);
                     else
-                        umma::tma_load_5d(sa + g * 1024, &a.a1, ci - a.c0, xs, ys, zs, bb, &full[s]);
+                        umma::tma_load_5d(sa + g * 2048, &a.a1, ci - a.c0, xs, ys, zs, bb, &full[s]);
                 } else {
                     // rows past the last tap: a box wholly beyond the walls (zeros)
-                    umma::tma_load_5d(sa + g * 1024, &a.a0, 0, 1, -64, 0, 0, &full[s]);
+                    umma::tma_load_5d(sa + g * 2048, &a.a0, 0, 1, -64, 0, 0, &full[s]);
                 }
             }
-            for (int g = 0; g < (cout >> 3); ++g)
-                umma::tma_load_5d(sb + g * 1024, &a.dy, 8 * g, 1 + x0, y, 1 + zz, bb, &full[s]);
+            for (int g = 0; g < (cout >> 4); ++g)
+                umma::tma_load_5d(sb + g * 2048, &a.dy, 16 * g, 1 + x0, y, 1 + zz, bb, &full[s]);
         }
     } else if (tid == 32) {
         const uint32_t idesc = umma::idesc_bf16(cout, true, true);
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(THREADS) wgrad_tma_kernel(const __grid_constan
             umma::fence_after();
             const uint32_t sa = umma::smem_addr(smem + s * sbytes), sb = sa + abytes;
             for (int j = 0; j < 4; ++j)
-                umma::mma_bf16(tmem, umma::sdesc(sa + j * 256, 128, 1024), umma::sdesc(sb + j * 256, 128, 1024),
+                umma::mma_bf16(tmem, umma::sdesc_sw32_mn(sa + j * 512, 2048), umma::sdesc_sw32_mn(sb + j * 512, 2048),
                                idesc, (c > 0 || j > 0) ? 1u : 0u);
             umma::mma_commit(&empty[s]);
         }
@@ -278,35 +279,37 @@ size_t conv3_tma_smem(int cin, int cout)
     return ring > share ? ring : share;
 }
 
-size_t wgrad_tma_smem(int cout) { return size_t(STAGES) * (16 * 1024 + (cout >> 3) * 1024); }
+// the ring, plus 8 KB so that every descriptor's reach stays inside the allocation
+size_t wgrad_tma_smem(int cout) { return size_t(STAGES) * (16 * 1024 + (cout >> 4) * 2048) + 8192; }
 
 }  // namespace
 
-bool make_halo_map(CUtensorMap *m, const void *base, int C, const VGrid &g, const VBox &bx)
+bool make_halo_map(CUtensorMap *m, const void *base, int C, const VGrid &g, const VBox &bx, int chans)
 {
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tma_encode_fn());
-    if (!enc || !base || C % 8 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    if (!enc || !base || C % chans || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
     const cuuint64_t nx = 1ull << g.lx, ny = 1ull << g.ly, nz = 1ull << g.lz;
     cuuint64_t dims[5] = {cuuint64_t(C), nx + 2, ny, nz + 2, cuuint64_t(g.nb)};
     cuuint64_t strides[4] = {cuuint64_t(C) * 2, (nx + 2) * C * 2, ny * (nx + 2) * C * 2,
                              (nz + 2) * ny * (nx + 2) * C * 2};
-    cuuint32_t box[5] = {8, cuuint32_t(bx.bx), cuuint32_t(bx.by), cuuint32_t(bx.bz), cuuint32_t(bx.bb)};
+    cuuint32_t box[5] = {cuuint32_t(chans), cuuint32_t(bx.bx), cuuint32_t(bx.by), cuuint32_t(bx.bz),
+                         cuuint32_t(bx.bb)};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, chans == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool make_weight_map(CUtensorMap *m, const void *w, int cin, int cout)
 {
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tma_encode_fn());
-    if (!enc || !w || cin % 8 || cout > 256 || (reinterpret_cast<uintptr_t>(w) & 15)) return false;
+    if (!enc || !w || cin % 16 || cout > 256 || (reinterpret_cast<uintptr_t>(w) & 15)) return false;
     cuuint64_t dims[3] = {cuuint64_t(cin), 27, cuuint64_t(cout)};
     cuuint64_t strides[2] = {cuuint64_t(cin) * 2, 27ull * cin * 2};
-    cuuint32_t box[3] = {8, 1, cuuint32_t(cout)};
+    cuuint32_t box[3] = {16, 1, cuuint32_t(cout)};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(w), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

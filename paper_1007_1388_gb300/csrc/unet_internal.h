@@ -98,9 +98,9 @@ __host__ __device__ inline VBox vbox(const VGrid &g, int count)
 }
 
 // TMA-fed convolution over halo-layout tensors (same result as conv3, bitwise:
-// the same shared-memory tiles and MMA sequence).  Maps: a0 / a1 over the
-// sources with the box vbox(g, 128); w over the weights [cout][27][cin] with
-// box {8, 1, cout}.  out: bf16 in the halo layout (periodic copies written
+// the same operands and MMA sequence).  Maps: a0 / a1 over the sources with the
+// box {16 channels} x vbox(g, 128); w over the weights [cout][27][cin] with box
+// {16, 1, cout}; both with 32-byte swizzle (32-byte rows, whole L2 sectors).  out: bf16 in the halo layout (periodic copies written
 // too), or fp32 [M][cout] without halo.  No upsampled source.
 struct ConvTmaArgs {
     CUtensorMap a0, a1, w;
@@ -113,8 +113,8 @@ struct ConvTmaArgs {
 };
 
 // TMA-fed weight gradient over halo-layout tensors (same result as the
-// cp.async version).  Maps a0 / a1 / dy with the box vbox(g, 64): 64 voxels
-// per stage.
+// cp.async version).  Maps a0 / a1 / dy with the box {16 channels} x
+// vbox(g, 64), 32-byte swizzle: 64 voxels per stage.
 struct WgradTmaArgs {
     CUtensorMap a0, a1, dy;
     float *partial;
@@ -125,7 +125,9 @@ struct WgradTmaArgs {
 };
 
 // Tensor maps (false when the driver's encoder is unavailable or rejects the map)
-bool make_halo_map(CUtensorMap *m, const void *base, int C, const VGrid &g, const VBox &box);
+// chans = channels per box row: 16 (32-byte rows, 32B swizzle; the TMA
+// kernels' operand tiles) or 8 (16-byte rows, no swizzle)
+bool make_halo_map(CUtensorMap *m, const void *base, int C, const VGrid &g, const VBox &box, int chans);
 bool make_weight_map(CUtensorMap *m, const void *w, int cin, int cout);
 
 cudaError_t launch_conv3(const ConvArgs &a, cudaStream_t s);
