@@ -98,12 +98,15 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _oracle_sample(seconds, warm_steps=0):
+def _oracle_sample(seconds, warm_steps=0, threads=1):
     """The FP64 oracle on a bounded sample of the workload (a 64^3 channel with
-    the same boundaries and physics), stepped until `seconds` have passed."""
+    the same boundaries and physics), stepped until `seconds` have passed, on
+    `threads` host threads (OpenMP over z planes when the oracle was built with
+    it; the result does not depend on the thread count)."""
     import oracle
 
     oracle.build()
+    oracle.set_threads(threads)
     n = 64
     p = oracle.Problem(dims=(n, n, n), tau=TAU, periodic=(1, 0, 1), force=(FORCE, 0, 0))
     f = oracle.zeros(p)
@@ -126,6 +129,8 @@ def run_reference(args):
     import oracle
 
     oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     n = 64
     p = oracle.Problem(dims=(n, n, n), tau=TAU, periodic=(1, 0, 1), force=(FORCE, 0, 0))
     # each step: one oracle time step of a 64^3 block of the channel; the run
@@ -149,12 +154,12 @@ def run_reference(args):
         f = oracle.step(p, f)
     el = time.perf_counter() - t0
     v = cells * args.steps / el / 1e6
-    sample = f"64x64x{cells // 4096} channel block per step, FP64 C oracle, single thread"
+    sample = f"64x64x{cells // 4096} channel block per step, FP64 C oracle, OpenMP on {cores} threads"
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-           "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -320,10 +325,14 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
-        v, steps, el = _oracle_sample(args.cpu_seconds)
-        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        cores = os.cpu_count() or 1
+        v, steps, el = _oracle_sample(args.cpu_seconds, threads=cores)
+        v1, steps1, el1 = _oracle_sample(args.cpu_seconds / 2, threads=1)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": f"64^3 block of the same channel, {steps} FP64 steps in {el:.1f} s, "
-                         "single-threaded C"}
+                         f"C with OpenMP over z planes on {cores} threads",
+               "single_thread": {"value": v1, "cores": 1,
+                                 "sample": f"{steps1} steps in {el1:.1f} s on one thread"}}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
@@ -464,6 +473,66 @@ def run_precision_report(args):
         print(name, row, file=sys.stderr, flush=True)
         del rho, u
     print(json.dumps(out))
+    return 0
+
+
+SIZES_WORKLOAD = ("D3Q19 channel (periodic x/z, no-slip walls -y/+y), BGK tau=0.8, force 1e-6 along x, FP32; "
+                  "cubes 64^3 .. 512^3 split into 1, 8 and 64 Blocks")
+
+
+def run_sizes_report(args):
+    """Domain size and Block count (Sec. 4.1's single-GPU measurements): the
+    autotuned step of a channel cube of each size, as one Block and split into
+    2^3 and 4^3 Blocks, with MLUPS, the sweep's fraction of the measured HBM
+    bandwidth and the exchange's share.  Prints one JSON line."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1007_1388_gb300 import build
+
+    build.build()
+    import paper_1007_1388_gb300 as L
+    from paper_1007_1388_gb300 import workloads as W
+
+    L.use_torch_allocator()
+    peak = _peaks()[0]
+    rows = []
+    for n in args.sizes:
+        for per_axis in (1, 2, 4):
+            b = n // per_axis
+            p = L.make_params(force=(FORCE, 0, 0), **W.channel_bc())
+            try:
+                ctx = L.lbm_create((n,) * 3, (b,) * 3, TAU, None, p)
+            except L.LBMError as e:  # e.g. a Block beyond 32-bit plane offsets
+                rows.append({"n": n, "blocks": per_axis**3, "block": b, "refused": str(e)})
+                continue
+            L.lbm_autotune(ctx, None)
+            steps = int(min(2000, max(50, 3e10 // n**3)))
+            L.lbm_step(ctx, 10)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            L.lbm_step(ctx, steps)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            L.lbm_profile_enable(ctx, True)
+            L.lbm_profile_read(ctx)
+            L.lbm_step(ctx, 20)
+            pr = L.lbm_profile_read(ctx)
+            L.lbm_profile_enable(ctx, False)
+            sw = pr.sweep_ms / max(1, pr.sweep_launches)
+            ex = pr.exchange_ms / 20
+            m, _, nonfinite = L.lbm_invariants(ctx)
+            row = {"n": n, "blocks": per_axis**3, "block": b, "steps": steps,
+                   "mlups": n**3 * steps / (ms * 1e-3) / 1e6,
+                   "sweep_hbm_frac": BYTES_PER_LUP[0] * n**3 / (sw * 1e-3) / 1e9 / peak,
+                   "exchange_share": ex / (ex + sw), "sweep_config": list(L.lbm_get_sweep_config(ctx)),
+                   "nonfinite": nonfinite}
+            ctx.destroy()
+            rows.append(row)
+            print(row, file=sys.stderr, flush=True)
+    print(json.dumps({"report": "sizes", "workload": SIZES_WORKLOAD, "peak_hbm_gbs": peak, "rows": rows}))
     return 0
 
 
@@ -654,7 +723,7 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
-    ap.add_argument("--report", default="", choices=["", "precision", "warmstart", "unet"],
+    ap.add_argument("--report", default="", choices=["", "precision", "warmstart", "unet", "sizes"],
                     help="precision: storage-precision report on the 384^3 cavity; warmstart: the learned "
                          "warm start end to end (one JSON line each)")
     ap.add_argument("--ws-size", type=int, default=64)
@@ -664,6 +733,8 @@ def main():
     ap.add_argument("--ws-chunk", type=int, default=250)
     ap.add_argument("--unet-steps", type=int, default=20)
     ap.add_argument("--report-size", type=int, default=384)
+    ap.add_argument("--sizes", type=int, nargs="+", default=[64, 128, 256, 384, 512],
+                    help="cube sizes of --report sizes (each divisible by 4)")
     ap.add_argument("--report-steps", type=int, default=5000)
     ap.add_argument("--report-block", type=int, default=128)
     ap.add_argument("--batch-instances", type=int, default=256)
@@ -689,6 +760,8 @@ def main():
         return run_warmstart_report(args)
     if args.report == "unet":
         return run_unet_report(args)
+    if args.report == "sizes":
+        return run_sizes_report(args)
     return run_gpu(args)
 
 

@@ -48,14 +48,24 @@ typedef struct unet_ctx unet_ctx;
 /* Number of FP32 parameters in canonical order. */
 long long unet_param_count(void);
 
+/* Arithmetic of a network's convolutions and activations. */
+enum {
+    UNET_BF16 = 0, /* bf16 activations and weight copies, tensor cores, FP32 accumulation */
+    UNET_F32 = 1   /* debug mode: FP32 activations and weights, CUDA cores; for gradient checks only */
+};
+
 /*
- * unet_create - a network for batches of nb samples of n^3 voxels.  Weights:
- * He-normal from `seed` (counter-based, reproducible), biases 0; Adam state 0.
- * stream: a cudaStream_t to run on, or NULL for a library-owned stream.
- * Device memory comes from the lbm_set_allocator hooks.  LBM_EINVAL for n not
- * a power of two in [16, 128] or nb < 1.
+ * unet_create - a network for batches of nb samples of n^3 voxels, UNET_BF16.
+ * Weights: He-normal from `seed` (counter-based, reproducible), biases 0;
+ * Adam state 0.  stream: a cudaStream_t to run on, or NULL for a
+ * library-owned stream.  Device memory comes from the lbm_set_allocator
+ * hooks.  LBM_EINVAL for n not a power of two in [16, 128], nb < 1, or
+ * nb (n/4)^3 not a multiple of 128 (the tensor-core tile).
+ * unet_create_ex - the same with the precision UNET_BF16 or UNET_F32 (same
+ * size rules, same parameters for the same seed; LBM_EINVAL otherwise).
  */
 int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx **out);
+int unet_create_ex(int n, int nb, unsigned long long seed, int precision, void *stream, unet_ctx **out);
 void unet_destroy(unet_ctx *ctx);
 
 /* Parameters / Adam step counter: host FP32 arrays of unet_param_count(). */

@@ -4,7 +4,9 @@
 // pooling, upsampling adjoints, ReLU masks, bias sums, the 1x1x1 head, the
 // loss and Adam are the element-wise kernels below.  Activations are bf16
 // channels-last; gradients of activations FP32 until they feed a
-// convolution, where they are rounded to bf16.
+// convolution, where they are rounded to bf16.  In the FP32 debug mode
+// (UNET_F32) activations and weight copies are FP32 and the convolutions run
+// on the CUDA cores (unet_conv_f32.cu); everything else is the same code.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -42,32 +44,78 @@ __device__ __forceinline__ void halo_copies(const VGrid &g, long long m, long lo
     dz = z == 0 ? nz * plane : (z == nz - 1 ? -nz * plane : 0);
 }
 
+// Eight channels of an activation: bf16 (the tensor-core path; one 16-byte
+// word) or float (the FP32 debug mode; two).  Values pass through float, so
+// the bf16 results are those of plain bf16 rounding.
+template <typename A> struct Act8;
+template <> struct Act8<bf16> {
+    uint4 r;
+    __device__ __forceinline__ void load(const bf16 *p) { r = *reinterpret_cast<const uint4 *>(p); }
+    __device__ __forceinline__ void store(bf16 *p) const { *reinterpret_cast<uint4 *>(p) = r; }
+    __device__ __forceinline__ void get(float *v) const
+    {
+        const bf16 *h = reinterpret_cast<const bf16 *>(&r);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __bfloat162float(h[k]);
+    }
+    __device__ __forceinline__ void set(const float *v)
+    {
+        bf16 *h = reinterpret_cast<bf16 *>(&r);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = __float2bfloat16(v[k]);
+    }
+};
+template <> struct Act8<float> {
+    float4 a, b;
+    __device__ __forceinline__ void load(const float *p)
+    {
+        a = reinterpret_cast<const float4 *>(p)[0];
+        b = reinterpret_cast<const float4 *>(p)[1];
+    }
+    __device__ __forceinline__ void store(float *p) const
+    {
+        reinterpret_cast<float4 *>(p)[0] = a;
+        reinterpret_cast<float4 *>(p)[1] = b;
+    }
+    __device__ __forceinline__ void get(float *v) const
+    {
+        v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    }
+    __device__ __forceinline__ void set(const float *v)
+    {
+        a = make_float4(v[0], v[1], v[2], v[3]);
+        b = make_float4(v[4], v[5], v[6], v[7]);
+    }
+};
+
 // Stores 8 channels (from channel c0) of voxel m of a halo-layout tensor with
 // C channels, and its periodic copies.
-__device__ __forceinline__ void halo_store(bf16 *t, const VGrid &g, long long m, int C, int c0, const uint4 &v)
+template <typename A>
+__device__ __forceinline__ void halo_store(A *t, const VGrid &g, long long m, int C, int c0, const Act8<A> &v)
 {
     long long dx, dz;
     halo_copies(g, m, dx, dz);
     const long long hi = halo_index(g, m);
-    *reinterpret_cast<uint4 *>(t + hi * C + c0) = v;
-    if (dx) *reinterpret_cast<uint4 *>(t + (hi + dx) * C + c0) = v;
-    if (dz) *reinterpret_cast<uint4 *>(t + (hi + dz) * C + c0) = v;
-    if (dx && dz) *reinterpret_cast<uint4 *>(t + (hi + dx + dz) * C + c0) = v;
+    v.store(t + hi * C + c0);
+    if (dx) v.store(t + (hi + dx) * C + c0);
+    if (dz) v.store(t + (hi + dz) * C + c0);
+    if (dx && dz) v.store(t + (hi + dx + dz) * C + c0);
 }
 
 // x[m] = {solid, force of the sample, 0, ..., 0} (16 channels, halo layout)
+template <typename A>
 __global__ void make_input_kernel(const uint8_t *__restrict__ solid, const float *__restrict__ force,
-                                  bf16 *__restrict__ x, VGrid g)
+                                  A *__restrict__ x, VGrid g)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.voxels()) return;
-    __align__(16) bf16 v[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
-    v[0] = __float2bfloat16(solid[i] ? 1.f : 0.f);
-    v[1] = __float2bfloat16(force[i >> (g.lx + g.ly + g.lz)]);
-    halo_store(x, g, i, 16, 0, reinterpret_cast<const uint4 *>(v)[0]);
-    halo_store(x, g, i, 16, 8, reinterpret_cast<const uint4 *>(v)[1]);
+    float v[8] = {solid[i] ? 1.f : 0.f, force[i >> (g.lx + g.ly + g.lz)], 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    Act8<A> a;
+    a.set(v);
+    halo_store(x, g, i, 16, 0, a);
+    v[0] = v[1] = 0.f;
+    a.set(v);
+    halo_store(x, g, i, 16, 8, a);
 }
 
 // Coordinates of voxel m in grid g, and the index of voxel (b, z, y, x).
@@ -85,7 +133,8 @@ __device__ __forceinline__ long long vidx(const VGrid &g, int b, int z, int y, i
 
 // 2x2x2 average: out (grid gh) from in (grid 2 gh), C channels, halo layout;
 // one thread per 8 channels of an output voxel
-__global__ void pool_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ out, VGrid gh, int C)
+template <typename A>
+__global__ void pool_kernel(const A *__restrict__ in, A *__restrict__ out, VGrid gh, int C)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int C8 = C >> 3;
@@ -98,20 +147,24 @@ __global__ void pool_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ out,
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int d = 0; d < 8; ++d) {
         const long long m = vidx(gf, b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1));
-        __align__(16) bf16 h[8];
-        *reinterpret_cast<uint4 *>(h) = *reinterpret_cast<const uint4 *>(in + halo_index(gf, m) * C + c);
+        Act8<A> a;
+        a.load(in + halo_index(gf, m) * C + c);
+        float h[8];
+        a.get(h);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(h[k]);
+        for (int k = 0; k < 8; ++k) s[k] += h[k];
     }
-    __align__(16) bf16 o[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16(0.125f * s[k]);
-    halo_store(out, gh, p, C, c, *reinterpret_cast<const uint4 *>(o));
+    for (int k = 0; k < 8; ++k) s[k] *= 0.125f;
+    Act8<A> o;
+    o.set(s);
+    halo_store(out, gh, p, C, c, o);
 }
 
 // nearest 2x upsampling: out (grid gf, halo layout) from in (grid gf / 2,
 // halo layout), C channels; one thread per 8 channels of an output voxel
-__global__ void upsample_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ out, VGrid gf, int C)
+template <typename A>
+__global__ void upsample_kernel(const A *__restrict__ in, A *__restrict__ out, VGrid gf, int C)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int C8 = C >> 3;
@@ -121,15 +174,17 @@ __global__ void upsample_kernel(const bf16 *__restrict__ in, bf16 *__restrict__ 
     int b, z, y, x;
     coords(m, gf, b, z, y, x);
     const VGrid gh{gf.nb, gf.lz - 1, gf.ly - 1, gf.lx - 1};
-    const uint4 v = *reinterpret_cast<const uint4 *>(in + halo_index(gh, vidx(gh, b, z >> 1, y >> 1, x >> 1)) * C + c);
+    Act8<A> v;
+    v.load(in + halo_index(gh, vidx(gh, b, z >> 1, y >> 1, x >> 1)) * C + c);
     halo_store(out, gf, m, C, c, v);
 }
 
-// dy = bf16(g * (y > 0)) (y, dy: halo layout with periodic copies; g:
-// [V][C] fp32); per-block channel sums of g * (y > 0) (bias gradient).  A
-// thread handles 8 channels of a voxel; blockDim = EW and the grid stride are
-// multiples of C / 8, so each thread keeps one channel group.
-__global__ void relu_bwd_kernel(const float *__restrict__ g, const bf16 *__restrict__ y, bf16 *__restrict__ dy,
+// dy = g * (y > 0) in the activation type (y, dy: halo layout with periodic
+// copies; g: [V][C] fp32); per-block channel sums of g * (y > 0) (bias
+// gradient).  A thread handles 8 channels of a voxel; blockDim = EW and the
+// grid stride are multiples of C / 8, so each thread keeps one channel group.
+template <typename A>
+__global__ void relu_bwd_kernel(const float *__restrict__ g, const A *__restrict__ y, A *__restrict__ dy,
                                 float *__restrict__ part, VGrid grid, int C)
 {
     __shared__ float sh[EW][9];
@@ -140,19 +195,22 @@ __global__ void relu_bwd_kernel(const float *__restrict__ g, const bf16 *__restr
         const long long m = i / C8;
         const int c = int(i - m * C8) * 8;
         const long long hi = halo_index(grid, m);
-        __align__(16) bf16 yv[8];
-        *reinterpret_cast<uint4 *>(yv) = *reinterpret_cast<const uint4 *>(y + hi * C + c);
+        Act8<A> ya;
+        ya.load(y + hi * C + c);
+        float yv[8];
+        ya.get(yv);
         const float4 g0 = *reinterpret_cast<const float4 *>(g + m * C + c);
         const float4 g1 = *reinterpret_cast<const float4 *>(g + m * C + c + 4);
         const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-        __align__(16) bf16 o[8];
+        float o[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const float v = __bfloat162float(yv[k]) > 0.f ? gv[k] : 0.f;
-            o[k] = __float2bfloat16(v);
-            acc[k] += v;
+            o[k] = yv[k] > 0.f ? gv[k] : 0.f;
+            acc[k] += o[k];
         }
-        halo_store(dy, grid, m, C, c, *reinterpret_cast<const uint4 *>(o));
+        Act8<A> oa;
+        oa.set(o);
+        halo_store(dy, grid, m, C, c, oa);
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];
@@ -219,7 +277,8 @@ __global__ void skip_pool_kernel(const float *__restrict__ gcat, int ctot, int c
 // dbh (4) and the loss: part[block][72] = {dWh[64], dbh[4], sum of squared
 // differences, 3 unused}.
 constexpr int HEAD_PART = 72;
-__global__ void head_kernel(const bf16 *__restrict__ d1, const float *__restrict__ Wh, const float *__restrict__ bh,
+template <typename A>
+__global__ void head_kernel(const A *__restrict__ d1, const float *__restrict__ Wh, const float *__restrict__ bh,
                             const float *__restrict__ target, float *__restrict__ out, float *__restrict__ gd1,
                             float *__restrict__ part, VGrid g)
 {
@@ -234,13 +293,13 @@ __global__ void head_kernel(const bf16 *__restrict__ d1, const float *__restrict
     for (int k = 0; k < HEAD_PART; ++k) acc[k] = 0.f;
     const float gscale = 2.f / float(V * 4);
     for (long long m = (long long)blockIdx.x * EW + threadIdx.x; m < V; m += (long long)gridDim.x * EW) {
-        __align__(16) bf16 h[16];
-        const bf16 *row = d1 + halo_index(g, m) * 16;
-        reinterpret_cast<uint4 *>(h)[0] = reinterpret_cast<const uint4 *>(row)[0];
-        reinterpret_cast<uint4 *>(h)[1] = reinterpret_cast<const uint4 *>(row)[1];
+        const A *row = d1 + halo_index(g, m) * 16;
+        Act8<A> h0, h1;
+        h0.load(row);
+        h1.load(row + 8);
         float a[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) a[k] = __bfloat162float(h[k]);
+        h0.get(a);
+        h1.get(a + 8);
         float y[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -294,12 +353,14 @@ __global__ void head_kernel(const bf16 *__restrict__ d1, const float *__restrict
     }
 }
 
-// bf16 copies of one convolution's FP32 weight [cout][27][cin]:
+// bf16 (or, in the FP32 debug mode, FP32) copies of one convolution's FP32
+// weight [cout][27][cin]:
 // wf [cout][27][cinp] (zero channels beyond cin) and, when wb is given, the
 // tap-flipped transpose wb [cin][27][cout], wb[ci][t][co] = W[co][26 - t][ci]
 // (the backward-data convolution).
-__global__ void prep_weights_kernel(const float *__restrict__ W, int cout, int cin, int cinp, bf16 *__restrict__ wf,
-                                    bf16 *__restrict__ wb)
+template <typename A>
+__global__ void prep_weights_kernel(const float *__restrict__ W, int cout, int cin, int cinp, A *__restrict__ wf,
+                                    A *__restrict__ wb)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)cout * 27 * cinp) return;
@@ -307,8 +368,8 @@ __global__ void prep_weights_kernel(const float *__restrict__ W, int cout, int c
     const long long r = i / cinp;
     const int t = int(r % 27), co = int(r / 27);
     const float w = ci < cin ? W[((long long)co * 27 + t) * cin + ci] : 0.f;
-    wf[i] = __float2bfloat16(w);
-    if (wb && ci < cin) wb[((long long)ci * 27 + (26 - t)) * cout + co] = __float2bfloat16(w);
+    wf[i] = A(w);
+    if (wb && ci < cin) wb[((long long)ci * 27 + (26 - t)) * cout + co] = A(w);
 }
 
 // dw [cout][27][cin] from the padded weight gradient [cout][27][cinp]
@@ -476,11 +537,12 @@ struct unet_ctx {
     std::vector<std::pair<void *, size_t>> owned;
     float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
     long long step = 0;
-    bf16 *wf[NCONV] = {}, *wb[NCONV] = {};
+    int precision = UNET_BF16;  // element type of weights copies and activations: bf16 or float
+    void *wf[NCONV] = {}, *wb[NCONV] = {};
     bool weights_current = false;
-    bf16 *x = nullptr, *e1h = nullptr, *e1 = nullptr, *p1 = nullptr, *e2h = nullptr, *e2 = nullptr, *p2 = nullptr,
+    void *x = nullptr, *e1h = nullptr, *e1 = nullptr, *p1 = nullptr, *e2h = nullptr, *e2 = nullptr, *p2 = nullptr,
          *e3h = nullptr, *e3 = nullptr, *d2h = nullptr, *d2 = nullptr, *d1h = nullptr, *d1 = nullptr, *dy = nullptr,
-         *up3 = nullptr, *up2 = nullptr;  // bf16 activations: halo layout (unet_internal.h)
+         *up3 = nullptr, *up2 = nullptr;  // activations: halo layout (unet_internal.h)
     float *gd1 = nullptr, *gcat1 = nullptr, *gd2 = nullptr, *gcat2 = nullptr, *ge3 = nullptr, *gp2 = nullptr,
           *ge2 = nullptr, *gp1 = nullptr, *ge1 = nullptr, *gh = nullptr;
     float *wpart = nullptr, *wtmp = nullptr, *bpart = nullptr, *hpart = nullptr, *dforce = nullptr;
@@ -550,9 +612,9 @@ void ufree_all(unet_ctx *c)
 
 unsigned blocks_for(long long n) { return unsigned((n + EW - 1) / EW); }
 
-// launch one 3x3x3 convolution on the context stream
-// one TMA-fed 3x3x3 convolution on the context stream (halo-layout sources)
-int conv(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf16 *w, const float *bias, void *out,
+// one 3x3x3 convolution on the context stream (halo-layout sources): TMA-fed
+// tensor cores for bf16, the CUDA-core kernel in the FP32 debug mode
+int conv(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const void *w, const float *bias, void *out,
          int out_f32, int relu, int cout, VGrid g)
 {
     ConvTmaArgs a{};
@@ -571,6 +633,24 @@ int conv(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf16
     a.g = g;
     a.err = c->derr;
     UCK(launch_conv3_tma(a, c->stream), "conv3");
+    return LBM_OK;
+}
+int conv(unet_ctx *c, const float *s0, int c0, const float *s1, int c1, const void *w, const float *bias, void *out,
+         int out_f32, int relu, int cout, VGrid g)
+{
+    ConvF32Args a{};
+    a.src0 = s0;
+    a.src1 = s1;
+    a.w = static_cast<const float *>(w);
+    a.bias = bias;
+    a.out = static_cast<float *>(out);
+    a.c0 = c0;
+    a.c1 = c1;
+    a.cout = cout;
+    a.out_halo = !out_f32;  // activations are halo-layout, gradients [M][cout]
+    a.relu = relu;
+    a.g = g;
+    UCK(launch_conv3_f32(a, c->stream), "conv3 (fp32)");
     return LBM_OK;
 }
 
@@ -615,56 +695,77 @@ int wgrad(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf1
     UCK(launch_wgrad_tma(a, nsplit, dw, c->stream), "wgrad");
     return LBM_OK;
 }
+int wgrad(unet_ctx *c, const float *s0, int c0, const float *s1, int c1, const float *dy, int cout, float *dw,
+          VGrid g)
+{
+    WgradF32Args a{};
+    a.src0 = s0;
+    a.src1 = s1;
+    a.dy = dy;
+    a.dw = dw;
+    a.c0 = c0;
+    a.c1 = c1;
+    a.cout = cout;
+    a.g = g;
+    UCK(launch_wgrad_f32(a, c->stream), "wgrad (fp32)");
+    return LBM_OK;
+}
 
 // ReLU backward into c->dy and the bias gradient of layer k
-int relu_bwd(unet_ctx *c, const float *g, const bf16 *y, VGrid grid, int C, int k)
+template <typename A>
+int relu_bwd(unet_ctx *c, const float *g, const void *y, VGrid grid, int C, int k)
 {
     const long long n = grid.voxels() * (C / 8);
     int nblk = int(std::min<long long>(c->relu_blocks, (n + EW - 1) / EW));
     if (nblk < 1) nblk = 1;
-    relu_bwd_kernel<<<nblk, EW, 0, c->stream>>>(g, y, c->dy, c->bpart, grid, C);
+    relu_bwd_kernel<A><<<nblk, EW, 0, c->stream>>>(g, static_cast<const A *>(y), static_cast<A *>(c->dy), c->bpart,
+                                                   grid, C);
     reduce_cols_kernel<<<C, EW, 0, c->stream>>>(c->bpart, nblk, C, c->grads + kLayout.b[k]);
     UCK(cudaGetLastError(), "relu backward");
     return LBM_OK;
 }
 
+template <typename A>
 int prep_weights(unet_ctx *c)
 {
     if (c->weights_current) return LBM_OK;
     for (int k = 0; k < NCONV; ++k) {
         const int cp = cin_padded(k);
         const long long n = 27ll * kConv[k].cout * cp;
-        prep_weights_kernel<<<blocks_for(n), EW, 0, c->stream>>>(c->params + kLayout.w[k], kConv[k].cout,
-                                                                 kConv[k].cin, cp, c->wf[k], c->wb[k]);
+        prep_weights_kernel<A><<<blocks_for(n), EW, 0, c->stream>>>(c->params + kLayout.w[k], kConv[k].cout,
+                                                                    kConv[k].cin, cp, static_cast<A *>(c->wf[k]),
+                                                                    static_cast<A *>(c->wb[k]));
     }
     UCK(cudaGetLastError(), "weights");
     c->weights_current = true;
     return LBM_OK;
 }
 
+template <typename A>
 int forward(unet_ctx *c, const uint8_t *solid, const float *force)
 {
     int rc;
+    auto T = [](void *p) { return static_cast<A *>(p); };
     UCK(cudaMemcpyAsync(c->dforce, force, sizeof(float) * c->nb, cudaMemcpyHostToDevice, c->stream), "force");
-    if ((rc = prep_weights(c))) return rc;
-    make_input_kernel<<<blocks_for(c->V1), EW, 0, c->stream>>>(solid, c->dforce, c->x, c->g1);
+    if ((rc = prep_weights<A>(c))) return rc;
+    make_input_kernel<A><<<blocks_for(c->V1), EW, 0, c->stream>>>(solid, c->dforce, T(c->x), c->g1);
     UCK(cudaGetLastError(), "input");
     const float *P = c->params;
     const Layout &L = kLayout;
-    if ((rc = conv(c, c->x, 16, nullptr, 0, c->wf[W1A], P + L.b[W1A], c->e1h, 0, 1, 16, c->g1))) return rc;
-    if ((rc = conv(c, c->e1h, 16, nullptr, 0, c->wf[W1B], P + L.b[W1B], c->e1, 0, 1, 16, c->g1))) return rc;
-    pool_kernel<<<blocks_for(c->V2 * 2), EW, 0, c->stream>>>(c->e1, c->p1, c->g2, 16);
-    if ((rc = conv(c, c->p1, 16, nullptr, 0, c->wf[W2A], P + L.b[W2A], c->e2h, 0, 1, 32, c->g2))) return rc;
-    if ((rc = conv(c, c->e2h, 32, nullptr, 0, c->wf[W2B], P + L.b[W2B], c->e2, 0, 1, 32, c->g2))) return rc;
-    pool_kernel<<<blocks_for(c->V3 * 4), EW, 0, c->stream>>>(c->e2, c->p2, c->g3, 32);
-    if ((rc = conv(c, c->p2, 32, nullptr, 0, c->wf[W3A], P + L.b[W3A], c->e3h, 0, 1, 64, c->g3))) return rc;
-    if ((rc = conv(c, c->e3h, 64, nullptr, 0, c->wf[W3B], P + L.b[W3B], c->e3, 0, 1, 64, c->g3))) return rc;
-    upsample_kernel<<<blocks_for(c->V2 * 8), EW, 0, c->stream>>>(c->e3, c->up3, c->g2, 64);
-    if ((rc = conv(c, c->up3, 64, c->e2, 32, c->wf[W4A], P + L.b[W4A], c->d2h, 0, 1, 32, c->g2))) return rc;
-    if ((rc = conv(c, c->d2h, 32, nullptr, 0, c->wf[W4B], P + L.b[W4B], c->d2, 0, 1, 32, c->g2))) return rc;
-    upsample_kernel<<<blocks_for(c->V1 * 4), EW, 0, c->stream>>>(c->d2, c->up2, c->g1, 32);
-    if ((rc = conv(c, c->up2, 32, c->e1, 16, c->wf[W5A], P + L.b[W5A], c->d1h, 0, 1, 16, c->g1))) return rc;
-    if ((rc = conv(c, c->d1h, 16, nullptr, 0, c->wf[W5B], P + L.b[W5B], c->d1, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, T(c->x), 16, (const A *)nullptr, 0, c->wf[W1A], P + L.b[W1A], c->e1h, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, T(c->e1h), 16, (const A *)nullptr, 0, c->wf[W1B], P + L.b[W1B], c->e1, 0, 1, 16, c->g1))) return rc;
+    pool_kernel<A><<<blocks_for(c->V2 * 2), EW, 0, c->stream>>>(T(c->e1), T(c->p1), c->g2, 16);
+    if ((rc = conv(c, T(c->p1), 16, (const A *)nullptr, 0, c->wf[W2A], P + L.b[W2A], c->e2h, 0, 1, 32, c->g2))) return rc;
+    if ((rc = conv(c, T(c->e2h), 32, (const A *)nullptr, 0, c->wf[W2B], P + L.b[W2B], c->e2, 0, 1, 32, c->g2))) return rc;
+    pool_kernel<A><<<blocks_for(c->V3 * 4), EW, 0, c->stream>>>(T(c->e2), T(c->p2), c->g3, 32);
+    if ((rc = conv(c, T(c->p2), 32, (const A *)nullptr, 0, c->wf[W3A], P + L.b[W3A], c->e3h, 0, 1, 64, c->g3))) return rc;
+    if ((rc = conv(c, T(c->e3h), 64, (const A *)nullptr, 0, c->wf[W3B], P + L.b[W3B], c->e3, 0, 1, 64, c->g3))) return rc;
+    upsample_kernel<A><<<blocks_for(c->V2 * 8), EW, 0, c->stream>>>(T(c->e3), T(c->up3), c->g2, 64);
+    if ((rc = conv(c, T(c->up3), 64, T(c->e2), 32, c->wf[W4A], P + L.b[W4A], c->d2h, 0, 1, 32, c->g2))) return rc;
+    if ((rc = conv(c, T(c->d2h), 32, (const A *)nullptr, 0, c->wf[W4B], P + L.b[W4B], c->d2, 0, 1, 32, c->g2))) return rc;
+    upsample_kernel<A><<<blocks_for(c->V1 * 4), EW, 0, c->stream>>>(T(c->d2), T(c->up2), c->g1, 32);
+    if ((rc = conv(c, T(c->up2), 32, T(c->e1), 16, c->wf[W5A], P + L.b[W5A], c->d1h, 0, 1, 16, c->g1))) return rc;
+    if ((rc = conv(c, T(c->d1h), 16, (const A *)nullptr, 0, c->wf[W5B], P + L.b[W5B], c->d1, 0, 1, 16, c->g1))) return rc;
     UCK(cudaGetLastError(), "forward");
     return LBM_OK;
 }
@@ -681,56 +782,58 @@ int check_err(unet_ctx *c)
     return LBM_OK;
 }
 
+template <typename A>
 int backward(unet_ctx *c, const float *target, double *loss)
 {
     int rc;
+    auto T = [](void *p) { return static_cast<A *>(p); };
     const Layout &L = kLayout;
     float *G = c->grads;
-    head_kernel<<<c->head_blocks, EW, 0, c->stream>>>(c->d1, c->params + L.wh, c->params + L.bh, target, nullptr,
-                                                      c->gd1, c->hpart, c->g1);
+    head_kernel<A><<<c->head_blocks, EW, 0, c->stream>>>(T(c->d1), c->params + L.wh, c->params + L.bh, target,
+                                                         nullptr, c->gd1, c->hpart, c->g1);
     reduce_cols_kernel<<<72, EW, 0, c->stream>>>(c->hpart, c->head_blocks, 72, c->wtmp);
     UCK(cudaGetLastError(), "head");
     UCK(cudaMemcpyAsync(G + L.wh, c->wtmp, sizeof(float) * 68, cudaMemcpyDeviceToDevice, c->stream), "head grad");
     float hl = 0.f;
     UCK(cudaMemcpyAsync(&hl, c->wtmp + 68, sizeof(float), cudaMemcpyDeviceToHost, c->stream), "loss");
     // level 1 decoder
-    if ((rc = relu_bwd(c, c->gd1, c->d1, c->g1, 16, W5B))) return rc;
-    if ((rc = wgrad(c, c->d1h, 16, nullptr, 0, c->dy, 16, G + L.w[W5B], c->g1))) return rc;
-    if ((rc = conv(c, c->dy, 16, nullptr, 0, c->wb[W5B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->d1h, c->g1, 16, W5A))) return rc;
-    if ((rc = wgrad(c, c->up2, 32, c->e1, 16, c->dy, 16, G + L.w[W5A], c->g1))) return rc;
-    if ((rc = conv(c, c->dy, 16, nullptr, 0, c->wb[W5A], nullptr, c->gcat1, 1, 0, 48, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gd1, c->d1, c->g1, 16, W5B))) return rc;
+    if ((rc = wgrad(c, T(c->d1h), 16, (const A *)nullptr, 0, T(c->dy), 16, G + L.w[W5B], c->g1))) return rc;
+    if ((rc = conv(c, T(c->dy), 16, (const A *)nullptr, 0, c->wb[W5B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->d1h, c->g1, 16, W5A))) return rc;
+    if ((rc = wgrad(c, T(c->up2), 32, T(c->e1), 16, T(c->dy), 16, G + L.w[W5A], c->g1))) return rc;
+    if ((rc = conv(c, T(c->dy), 16, (const A *)nullptr, 0, c->wb[W5A], nullptr, c->gcat1, 1, 0, 48, c->g1))) return rc;
     up_bwd_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gd2, c->g2);
     // level 2 decoder
-    if ((rc = relu_bwd(c, c->gd2, c->d2, c->g2, 32, W4B))) return rc;
-    if ((rc = wgrad(c, c->d2h, 32, nullptr, 0, c->dy, 32, G + L.w[W4B], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W4B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->d2h, c->g2, 32, W4A))) return rc;
-    if ((rc = wgrad(c, c->up3, 64, c->e2, 32, c->dy, 32, G + L.w[W4A], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W4A], nullptr, c->gcat2, 1, 0, 96, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gd2, c->d2, c->g2, 32, W4B))) return rc;
+    if ((rc = wgrad(c, T(c->d2h), 32, (const A *)nullptr, 0, T(c->dy), 32, G + L.w[W4B], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W4B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->d2h, c->g2, 32, W4A))) return rc;
+    if ((rc = wgrad(c, T(c->up3), 64, T(c->e2), 32, T(c->dy), 32, G + L.w[W4A], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W4A], nullptr, c->gcat2, 1, 0, 96, c->g2))) return rc;
     up_bwd_kernel<<<blocks_for(c->V3 * 64), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->ge3, c->g3);
     // bottleneck
-    if ((rc = relu_bwd(c, c->ge3, c->e3, c->g3, 64, W3B))) return rc;
-    if ((rc = wgrad(c, c->e3h, 64, nullptr, 0, c->dy, 64, G + L.w[W3B], c->g3))) return rc;
-    if ((rc = conv(c, c->dy, 64, nullptr, 0, c->wb[W3B], nullptr, c->gh, 1, 0, 64, c->g3))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->e3h, c->g3, 64, W3A))) return rc;
-    if ((rc = wgrad(c, c->p2, 32, nullptr, 0, c->dy, 64, G + L.w[W3A], c->g3))) return rc;
-    if ((rc = conv(c, c->dy, 64, nullptr, 0, c->wb[W3A], nullptr, c->gp2, 1, 0, 32, c->g3))) return rc;
+    if ((rc = relu_bwd<A>(c, c->ge3, c->e3, c->g3, 64, W3B))) return rc;
+    if ((rc = wgrad(c, T(c->e3h), 64, (const A *)nullptr, 0, T(c->dy), 64, G + L.w[W3B], c->g3))) return rc;
+    if ((rc = conv(c, T(c->dy), 64, (const A *)nullptr, 0, c->wb[W3B], nullptr, c->gh, 1, 0, 64, c->g3))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->e3h, c->g3, 64, W3A))) return rc;
+    if ((rc = wgrad(c, T(c->p2), 32, (const A *)nullptr, 0, T(c->dy), 64, G + L.w[W3A], c->g3))) return rc;
+    if ((rc = conv(c, T(c->dy), 64, (const A *)nullptr, 0, c->wb[W3A], nullptr, c->gp2, 1, 0, 32, c->g3))) return rc;
     skip_pool_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->gp2, c->ge2, c->g2, 32);
     // level 2 encoder
-    if ((rc = relu_bwd(c, c->ge2, c->e2, c->g2, 32, W2B))) return rc;
-    if ((rc = wgrad(c, c->e2h, 32, nullptr, 0, c->dy, 32, G + L.w[W2B], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W2B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->e2h, c->g2, 32, W2A))) return rc;
-    if ((rc = wgrad(c, c->p1, 16, nullptr, 0, c->dy, 32, G + L.w[W2A], c->g2))) return rc;
-    if ((rc = conv(c, c->dy, 32, nullptr, 0, c->wb[W2A], nullptr, c->gp1, 1, 0, 16, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->ge2, c->e2, c->g2, 32, W2B))) return rc;
+    if ((rc = wgrad(c, T(c->e2h), 32, (const A *)nullptr, 0, T(c->dy), 32, G + L.w[W2B], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W2B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->e2h, c->g2, 32, W2A))) return rc;
+    if ((rc = wgrad(c, T(c->p1), 16, (const A *)nullptr, 0, T(c->dy), 32, G + L.w[W2A], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W2A], nullptr, c->gp1, 1, 0, 16, c->g2))) return rc;
     skip_pool_kernel<<<blocks_for(c->V1 * 16), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gp1, c->ge1, c->g1, 16);
     // level 1 encoder
-    if ((rc = relu_bwd(c, c->ge1, c->e1, c->g1, 16, W1B))) return rc;
-    if ((rc = wgrad(c, c->e1h, 16, nullptr, 0, c->dy, 16, G + L.w[W1B], c->g1))) return rc;
-    if ((rc = conv(c, c->dy, 16, nullptr, 0, c->wb[W1B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
-    if ((rc = relu_bwd(c, c->gh, c->e1h, c->g1, 16, W1A))) return rc;
-    if ((rc = wgrad(c, c->x, 16, nullptr, 0, c->dy, 16, c->wtmp, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->ge1, c->e1, c->g1, 16, W1B))) return rc;
+    if ((rc = wgrad(c, T(c->e1h), 16, (const A *)nullptr, 0, T(c->dy), 16, G + L.w[W1B], c->g1))) return rc;
+    if ((rc = conv(c, T(c->dy), 16, (const A *)nullptr, 0, c->wb[W1B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->e1h, c->g1, 16, W1A))) return rc;
+    if ((rc = wgrad(c, T(c->x), 16, (const A *)nullptr, 0, T(c->dy), 16, c->wtmp, c->g1))) return rc;
     unpad_grad_kernel<<<blocks_for(16 * 27 * 2), EW, 0, c->stream>>>(c->wtmp, 16, 2, 16, G + L.w[W1A]);
     UCK(cudaGetLastError(), "backward");
     if ((rc = check_err(c))) return rc;
@@ -756,8 +859,15 @@ void unet_destroy(unet_ctx *c)
 
 int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx **out)
 {
+    return unet_create_ex(n, nb, seed, UNET_BF16, stream, out);
+}
+
+int unet_create_ex(int n, int nb, unsigned long long seed, int precision, void *stream, unet_ctx **out)
+{
     if (!out) return ufail(nullptr, LBM_EINVAL, "unet_create: out is NULL");
     *out = nullptr;
+    if (precision != UNET_BF16 && precision != UNET_F32)
+        return ufail(nullptr, LBM_EINVAL, "unet_create: precision must be UNET_BF16 or UNET_F32");
     if (n < 16 || n > 128 || (n & (n - 1)) || nb < 1 || nb > 4096 || ((long long)nb * (n / 4) * (n / 4) * (n / 4)) % 128)
         return ufail(nullptr, LBM_EINVAL, "unet_create: n must be a power of two in [16, 128], nb >= 1, and "
                      "nb (n/4)^3 a multiple of 128 (the tensor-core tile)");
@@ -765,6 +875,8 @@ int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx *
     if (!c) return ufail(nullptr, LBM_ENOMEM, "out of host memory");
     c->n = n;
     c->nb = nb;
+    c->precision = precision;
+    const size_t es = precision == UNET_F32 ? sizeof(float) : sizeof(bf16);  // activation element
     const int l = ilog2(n);
     c->g1 = VGrid{nb, l, l, l};
     c->g2 = VGrid{nb, l - 1, l - 1, l - 1};
@@ -791,20 +903,25 @@ int unet_create(int n, int nb, unsigned long long seed, void *stream, unet_ctx *
     if ((rc = uown(c, &c->params, np)) || (rc = uown(c, &c->grads, np)) || (rc = uown(c, &c->am, np)) ||
         (rc = uown(c, &c->av, np)))
         return bail(rc);
+    // untyped buffers of `count` activation elements
+    auto act = [&](void **p, long long count) {
+        *p = ualloc(c, size_t(count) * es);
+        return *p ? LBM_OK : ufail(c, LBM_ENOMEM, "device allocation of %zu bytes failed", size_t(count) * es);
+    };
     for (int k = 0; k < NCONV; ++k) {
-        if ((rc = uown(c, &c->wf[k], size_t(27) * kConv[k].cout * cin_padded(k)))) return bail(rc);
-        if (k != W1A && (rc = uown(c, &c->wb[k], size_t(27) * kConv[k].cout * kConv[k].cin))) return bail(rc);
+        if ((rc = act(&c->wf[k], 27ll * kConv[k].cout * cin_padded(k)))) return bail(rc);
+        if (k != W1A && (rc = act(&c->wb[k], 27ll * kConv[k].cout * kConv[k].cin))) return bail(rc);
     }
     const VGrid g1 = c->g1, g2 = c->g2, g3 = c->g3;
-    if ((rc = uown(c, &c->x, halo_elems(g1, 16))) || (rc = uown(c, &c->e1h, halo_elems(g1, 16))) ||
-        (rc = uown(c, &c->e1, halo_elems(g1, 16))) || (rc = uown(c, &c->p1, halo_elems(g2, 16))) ||
-        (rc = uown(c, &c->e2h, halo_elems(g2, 32))) || (rc = uown(c, &c->e2, halo_elems(g2, 32))) ||
-        (rc = uown(c, &c->p2, halo_elems(g3, 32))) || (rc = uown(c, &c->e3h, halo_elems(g3, 64))) ||
-        (rc = uown(c, &c->e3, halo_elems(g3, 64))) || (rc = uown(c, &c->up3, halo_elems(g2, 64))) ||
-        (rc = uown(c, &c->d2h, halo_elems(g2, 32))) || (rc = uown(c, &c->d2, halo_elems(g2, 32))) ||
-        (rc = uown(c, &c->up2, halo_elems(g1, 32))) || (rc = uown(c, &c->d1h, halo_elems(g1, 16))) ||
-        (rc = uown(c, &c->d1, halo_elems(g1, 16))) ||
-        (rc = uown(c, &c->dy, std::max(halo_elems(g1, 16), std::max(halo_elems(g2, 32), halo_elems(g3, 64))))))
+    if ((rc = act(&c->x, halo_elems(g1, 16))) || (rc = act(&c->e1h, halo_elems(g1, 16))) ||
+        (rc = act(&c->e1, halo_elems(g1, 16))) || (rc = act(&c->p1, halo_elems(g2, 16))) ||
+        (rc = act(&c->e2h, halo_elems(g2, 32))) || (rc = act(&c->e2, halo_elems(g2, 32))) ||
+        (rc = act(&c->p2, halo_elems(g3, 32))) || (rc = act(&c->e3h, halo_elems(g3, 64))) ||
+        (rc = act(&c->e3, halo_elems(g3, 64))) || (rc = act(&c->up3, halo_elems(g2, 64))) ||
+        (rc = act(&c->d2h, halo_elems(g2, 32))) || (rc = act(&c->d2, halo_elems(g2, 32))) ||
+        (rc = act(&c->up2, halo_elems(g1, 32))) || (rc = act(&c->d1h, halo_elems(g1, 16))) ||
+        (rc = act(&c->d1, halo_elems(g1, 16))) ||
+        (rc = act(&c->dy, std::max(halo_elems(g1, 16), std::max(halo_elems(g2, 32), halo_elems(g3, 64))))))
         return bail(rc);
     if ((rc = uown(c, &c->gd1, V1 * 16)) || (rc = uown(c, &c->gcat1, V1 * 48)) || (rc = uown(c, &c->gd2, V2 * 32)) ||
         (rc = uown(c, &c->gcat2, V2 * 96)) || (rc = uown(c, &c->ge3, V3 * 64)) || (rc = uown(c, &c->gp2, V3 * 32)) ||
@@ -862,10 +979,17 @@ int unet_set_params(unet_ctx *c, const float *host)
 int unet_predict(unet_ctx *c, const uint8_t *solid, const float *force, float *out)
 {
     if (!c || !solid || !force || !out) return ufail(c, LBM_EINVAL, "unet_predict: NULL argument");
-    int rc = forward(c, solid, force);
+    const bool f32 = c->precision == UNET_F32;
+    int rc = f32 ? forward<float>(c, solid, force) : forward<bf16>(c, solid, force);
     if (rc) return rc;
-    head_kernel<<<c->head_blocks, EW, 0, c->stream>>>(c->d1, c->params + kLayout.wh, c->params + kLayout.bh,
-                                                      nullptr, out, nullptr, nullptr, c->g1);
+    if (f32)
+        head_kernel<float><<<c->head_blocks, EW, 0, c->stream>>>(static_cast<const float *>(c->d1),
+                                                                 c->params + kLayout.wh, c->params + kLayout.bh,
+                                                                 nullptr, out, nullptr, nullptr, c->g1);
+    else
+        head_kernel<bf16><<<c->head_blocks, EW, 0, c->stream>>>(static_cast<const bf16 *>(c->d1),
+                                                                c->params + kLayout.wh, c->params + kLayout.bh,
+                                                                nullptr, out, nullptr, nullptr, c->g1);
     UCK(cudaGetLastError(), "head");
     return check_err(c);
 }
@@ -874,9 +998,10 @@ int unet_loss_grad(unet_ctx *c, const uint8_t *solid, const float *force, const 
                    float *grad_host)
 {
     if (!c || !solid || !force || !target) return ufail(c, LBM_EINVAL, "unet_loss_grad: NULL argument");
-    int rc = forward(c, solid, force);
+    const bool f32 = c->precision == UNET_F32;
+    int rc = f32 ? forward<float>(c, solid, force) : forward<bf16>(c, solid, force);
     if (rc) return rc;
-    if ((rc = backward(c, target, loss))) return rc;
+    if ((rc = f32 ? backward<float>(c, target, loss) : backward<bf16>(c, target, loss))) return rc;
     if (grad_host) {
         UCK(cudaMemcpy(grad_host, c->grads, sizeof(float) * kLayout.total, cudaMemcpyDeviceToHost), "grads");
     }

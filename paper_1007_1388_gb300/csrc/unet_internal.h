@@ -124,6 +124,28 @@ struct WgradTmaArgs {
     int *err;
 };
 
+// FP32 debug mode: the same convolution on FP32 halo-layout sources with FP32
+// weights [cout][27][c0 + c1] on the CUDA cores; out is FP32 in the halo
+// layout (out_halo = 1, periodic copies written too) or [M][cout].
+struct ConvF32Args {
+    const float *src0, *src1, *w, *bias;
+    float *out;
+    int c0, c1, cout, out_halo, relu;
+    VGrid g;
+};
+
+// FP32 weight gradient dw[co][t][ci] (ci over c0 + c1) from FP32 halo-layout
+// sources and dy (halo layout, cout channels), written (not accumulated).
+struct WgradF32Args {
+    const float *src0, *src1, *dy;
+    float *dw;
+    int c0, c1, cout;
+    VGrid g;
+};
+
+cudaError_t launch_conv3_f32(const ConvF32Args &a, cudaStream_t s);
+cudaError_t launch_wgrad_f32(const WgradF32Args &a, cudaStream_t s);
+
 // Tensor maps (false when the driver's encoder is unavailable or rejects the map)
 // chans = channels per box row: 16 (32-byte rows, 32B swizzle; the TMA
 // kernels' operand tiles) or 8 (16-byte rows, no swizzle)

@@ -122,6 +122,7 @@ SIGNATURES = {
     # include/unet.h (the learned warm start; wrapped in unet.py)
     "unet_param_count": ([], _ll),
     "unet_create": ([_i, _i, ctypes.c_ulonglong, _vp, _P(_vp)], _i),
+    "unet_create_ex": ([_i, _i, ctypes.c_ulonglong, _i, _vp, _P(_vp)], _i),
     "unet_destroy": ([_vp], None),
     "unet_get_params": ([_vp, _vp], _i),
     "unet_set_params": ([_vp, _vp], _i),

@@ -35,17 +35,21 @@ def param_count() -> int:
     return int(lib().unet_param_count())
 
 
-class UNet:
-    """A network for batches of nb samples of n^3 voxels (n a power of two)."""
+BF16, F32 = 0, 1  # UNET_BF16 (tensor cores), UNET_F32 (debug mode, CUDA cores)
 
-    def __init__(self, n: int, nb: int, seed: int = 0, stream=None):
+
+class UNet:
+    """A network for batches of nb samples of n^3 voxels (n a power of two).
+    precision: BF16 (the training path) or F32 (debug mode for gradient checks)."""
+
+    def __init__(self, n: int, nb: int, seed: int = 0, stream=None, precision: int = BF16):
         import torch
 
-        self.n, self.nb = n, nb
+        self.n, self.nb, self.precision = n, nb, precision
         self.stream = stream if stream is not None else torch.cuda.Stream()
         p = ctypes.c_void_p()
-        _check(lib().unet_create(n, nb, ctypes.c_ulonglong(seed), ctypes.c_void_p(self.stream.cuda_stream),
-                                 ctypes.byref(p)))
+        _check(lib().unet_create_ex(n, nb, ctypes.c_ulonglong(seed), precision,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(p)))
         self.ptr = p
         self._fin = weakref.finalize(self, lib().unet_destroy, p)
 

@@ -9,6 +9,11 @@
   activations and bf16 gradient operands put about twenty roundings of up to
   2^-9 on the path from the loss to the deepest layers (measured: 0.1% at
   the head, up to 2.4% at the bottleneck);
+- the FP32 debug mode (FP32 activations and weights, CUDA-core
+  convolutions, the same element-wise kernels): loss, prediction and the
+  gradient of every parameter tensor within 1e-5 relative of the FP64
+  oracle, on parameters whose every ReLU decision has a margin of at least
+  0.5 (checked in the oracle), so that FP32 rounding cannot flip a mask;
 - a few Adam steps lower the loss;
 - the TMA-fed kernels on halo-layout tensors (the network's own path) equal
   the cp.async kernels: forward bitwise (periodic copies included), weight
@@ -218,6 +223,65 @@ def test_network_loss_and_gradients_match_oracle(env):
     rels = {k: float(np.linalg.norm(gp[k] - rp[k]) / max(np.linalg.norm(rp[k]), 1e-30)) for k in rp}
     print("gradient relative errors", rels)
     bad = {k: v for k, v in rels.items() if not v <= 3e-2}
+    assert not bad, bad
+    net.destroy()
+
+
+def _margin_params(rng):
+    """Parameters whose ReLU decisions all have a wide margin: every channel's
+    bias is +1 (three of four channels) or -1, the weights are small, so each
+    pre-activation stays near its bias while the convolutions still carry the
+    inputs' spatial structure."""
+    p = {}
+    for name, ci, co in U.CONVS:
+        p[name] = rng.normal(0, 0.12 / np.sqrt(27 * ci), (co, 27, ci))
+        p["b" + name[1:]] = np.where(np.arange(co) % 4 == 3, -1.0, 1.0) + rng.normal(0, 0.05, co)
+    p["Wh"] = rng.normal(0, 0.25, (4, 16))
+    p["bh"] = rng.normal(0, 0.05, 4)
+    return p
+
+
+def _relu_margin(p, a):
+    """Smallest |pre-activation| over every ReLU of the oracle's forward pass."""
+    worst = np.inf
+    for na, nb, key in (("W1a", "W1b", "e1"), ("W2a", "W2b", "e2"), ("W3a", "W3b", "e3"),
+                        ("W4a", "W4b", "d2"), ("W5a", "W5b", "d1")):
+        for name, inp in ((na, a[key + "_in"]), (nb, a[key + "_h"])):
+            worst = min(worst, float(np.min(np.abs(U.conv(inp, p[name], p["b" + name[1:]])))))
+    return worst
+
+
+def test_f32_debug_mode_gradients_match_oracle_to_1e5(env):
+    torch, unet = env
+    n, nb = 16, 2
+    rng = np.random.default_rng(3)
+    flat = _oracle_flat(_margin_params(rng)).astype(np.float32)
+    p = _oracle_params(flat)
+    solid, force, target = _sample_inputs(rng, n, nb)
+    net = unet.UNet(n, nb, seed=1, precision=unet.F32)
+    net.set_params(flat)
+    sd = torch.from_numpy(solid.reshape(-1)).cuda()
+    out = torch.empty(nb * n**3 * 4, dtype=torch.float32, device="cuda")
+    net.predict(sd, force, out)
+    got = out.cpu().numpy().reshape(nb, -1, 4)
+    loss, g = net.loss_grad(sd, force, torch.from_numpy(target.reshape(-1)).cuda(), grads=True)
+    ref_loss, ref_g = 0.0, None
+    for b in range(nb):
+        x = np.zeros((n, n, n, 2))
+        x[..., 0] = solid[b] != 0
+        x[..., 1] = np.float64(force[b])
+        y, a = U.forward(p, x)
+        assert _relu_margin(p, a) > 0.5
+        assert np.linalg.norm(got[b] - y.reshape(-1, 4)) <= 1e-6 * np.linalg.norm(y)
+        ref_loss += U.loss(y, target[b]) / nb
+        gb = _oracle_flat(U.backward(p, a, y, target[b])) / nb
+        ref_g = gb if ref_g is None else ref_g + gb
+    assert abs(loss - ref_loss) <= 1e-6 * ref_loss
+    rp = _oracle_params(ref_g)
+    gp = _oracle_params(g.astype(np.float64))
+    rels = {k: float(np.linalg.norm(gp[k] - rp[k]) / max(np.linalg.norm(rp[k]), 1e-30)) for k in rp}
+    print("FP32 gradient relative errors", rels)
+    bad = {k: v for k, v in rels.items() if not v <= 1e-5}
     assert not bad, bad
     net.destroy()
 
