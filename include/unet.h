@@ -140,6 +140,38 @@ int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, co
                           int nb, int lz, int ly, int lx, void *stream);
 
 /*
+ * Planar layout (the network's own activations): a bf16 tensor of C channels
+ * (C a multiple of 8) over nb grids of nz x ny x nx voxels is stored as
+ * [C / 8][P][8] with P = unet_planar_positions(nb, lz, ly, lx) positions per
+ * 8-channel group.  Padded voxel (b, z', y', x') with z' in [0, nz + 2),
+ * y' in [0, ny + 2), x' in [0, nx + 2) is at position
+ *   G + ((b (nz + 2) + z') (ny + 2) + y') (nx + 2) + x',
+ * G = 1024 + (ny + 2) (nx + 2) + nx + 2,
+ * voxel (b, z, y, x) at padded (b, z + 1, y + 1, x + 1).  Columns x' = 0 /
+ * nx + 1 and planes z' = 0 / nz + 1 must hold the periodic copies (x = nx - 1
+ * / x = 0, z = nz - 1 / z = 0), rows y' = 0 / ny + 1 and all other positions
+ * zeros.  unet_planar_positions returns -1 for a bad grid (each side >= 2).
+ *
+ * unet_conv3_planar - the convolution of unet_conv3 (no upsampled source) on
+ * planar bf16 tensors: every 16 input channels' operands are bulk copies of
+ * contiguous position runs, the taps offsets into them.  wpk: the weights
+ * packed per 16 input channels, bf16 [cin / 16][27][2][cout][8] with element
+ * (k, t, h, co, e) = w[co][t][16 k + 8 h + e].  A bf16 out is written planar
+ * (periodic copies included; other positions untouched), an fp32 out as
+ * [M][cout].  cin, cout multiples of 16.  Synchronises.
+ *
+ * unet_conv3_planar_wgrad - the weight gradient on planar src0 / src1 / dy
+ * (dw fp32 [cout][27][c0 + c1]).  dy holds zeros at every position that is
+ * not an interior voxel (no periodic copies): the reduction runs over all
+ * positions.  Workspace from the allocator hooks; synchronises.
+ */
+long long unet_planar_positions(int nb, int lz, int ly, int lx);
+int unet_conv3_planar(const void *src0, int c0, const void *src1, int c1, const void *wpk, const float *bias,
+                      void *out, int out_f32, int relu, int cout, int nb, int lz, int ly, int lx, void *stream);
+int unet_conv3_planar_wgrad(const void *src0, int c0, const void *src1, int c1, const void *dy, int cout, float *dw,
+                            int nb, int lz, int ly, int lx, void *stream);
+
+/*
  * unet_targets_from_fields - normalised training targets from the fields of
  * nb instances of V cells (device; the batch layout of
  * lbm_macroscopic_device: rho [nb][V], u [nb][3][V]):

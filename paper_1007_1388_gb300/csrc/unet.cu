@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm.h"
@@ -33,15 +34,21 @@ __host__ __device__ inline int ilog2(long long v)
     return l;
 }
 
-// Padded element offsets (in voxels) of the periodic copies of voxel m:
+// Position offsets of the periodic copies of voxel m in the planar layout:
 // along x (dx) and along z (dz); 0 where there is none.
-__device__ __forceinline__ void halo_copies(const VGrid &g, long long m, long long &dx, long long &dz)
+__device__ __forceinline__ void halo_copies(const VGrid &g, const Planar &p, long long m, long long &dx, long long &dz)
 {
-    const long long nx = 1ll << g.lx, ny = 1ll << g.ly, nz = 1ll << g.lz;
+    const long long nx = 1ll << g.lx, nz = 1ll << g.lz;
     const long long x = m & (nx - 1), z = (m >> (g.lx + g.ly)) & (nz - 1);
-    const long long plane = ny * (nx + 2);
     dx = x == 0 ? nx : (x == nx - 1 ? -nx : 0);
-    dz = z == 0 ? nz * plane : (z == nz - 1 ? -nz * plane : 0);
+    dz = z == 0 ? nz * p.sz : (z == nz - 1 ? -nz * p.sz : 0);
+}
+
+// first element of channels c0 .. c0 + 7 at position q of a planar tensor
+template <typename A>
+__device__ __forceinline__ A *planar_at(A *t, const Planar &p, long long q, int c0)
+{
+    return t + ((long long)(c0 >> 3) * p.ptot + q) * 8;
 }
 
 // Eight channels of an activation: bf16 (the tensor-core path; one 16-byte
@@ -88,21 +95,22 @@ template <> struct Act8<float> {
     }
 };
 
-// Stores 8 channels (from channel c0) of voxel m of a halo-layout tensor with
-// C channels, and its periodic copies.
+// Stores channels c0 .. c0 + 7 of voxel m of a planar tensor, and the
+// voxel's periodic copies.
 template <typename A>
-__device__ __forceinline__ void halo_store(A *t, const VGrid &g, long long m, int C, int c0, const Act8<A> &v)
+__device__ __forceinline__ void planar_store(A *t, const VGrid &g, long long m, int c0, const Act8<A> &v)
 {
+    const Planar p = planar_of(g);
     long long dx, dz;
-    halo_copies(g, m, dx, dz);
-    const long long hi = halo_index(g, m);
-    v.store(t + hi * C + c0);
-    if (dx) v.store(t + (hi + dx) * C + c0);
-    if (dz) v.store(t + (hi + dz) * C + c0);
-    if (dx && dz) v.store(t + (hi + dx + dz) * C + c0);
+    halo_copies(g, p, m, dx, dz);
+    A *at = planar_at(t, p, planar_q(g, p, m), c0);
+    v.store(at);
+    if (dx) v.store(at + dx * 8);
+    if (dz) v.store(at + dz * 8);
+    if (dx && dz) v.store(at + (dx + dz) * 8);
 }
 
-// x[m] = {solid, force of the sample, 0, ..., 0} (16 channels, halo layout)
+// x[m] = {solid, force of the sample, 0, ..., 0} (16 channels, planar)
 template <typename A>
 __global__ void make_input_kernel(const uint8_t *__restrict__ solid, const float *__restrict__ force,
                                   A *__restrict__ x, VGrid g)
@@ -112,10 +120,10 @@ __global__ void make_input_kernel(const uint8_t *__restrict__ solid, const float
     float v[8] = {solid[i] ? 1.f : 0.f, force[i >> (g.lx + g.ly + g.lz)], 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     Act8<A> a;
     a.set(v);
-    halo_store(x, g, i, 16, 0, a);
+    planar_store(x, g, i, 0, a);
     v[0] = v[1] = 0.f;
     a.set(v);
-    halo_store(x, g, i, 16, 8, a);
+    planar_store(x, g, i, 8, a);
 }
 
 // Coordinates of voxel m in grid g, and the index of voxel (b, z, y, x).
@@ -131,7 +139,7 @@ __device__ __forceinline__ long long vidx(const VGrid &g, int b, int z, int y, i
     return ((((long long)b << g.lz) + z) << (g.ly + g.lx)) + ((long long)y << g.lx) + x;
 }
 
-// 2x2x2 average: out (grid gh) from in (grid 2 gh), C channels, halo layout;
+// 2x2x2 average: out (grid gh) from in (grid 2 gh), C channels, planar;
 // one thread per 8 channels of an output voxel
 template <typename A>
 __global__ void pool_kernel(const A *__restrict__ in, A *__restrict__ out, VGrid gh, int C)
@@ -144,11 +152,12 @@ __global__ void pool_kernel(const A *__restrict__ in, A *__restrict__ out, VGrid
     int b, z, y, x;
     coords(p, gh, b, z, y, x);
     const VGrid gf{gh.nb, gh.lz + 1, gh.ly + 1, gh.lx + 1};
+    const Planar pf = planar_of(gf);
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int d = 0; d < 8; ++d) {
         const long long m = vidx(gf, b, 2 * z + (d >> 2), 2 * y + ((d >> 1) & 1), 2 * x + (d & 1));
         Act8<A> a;
-        a.load(in + halo_index(gf, m) * C + c);
+        a.load(planar_at(in, pf, planar_q(gf, pf, m), c));
         float h[8];
         a.get(h);
 #pragma unroll
@@ -158,11 +167,11 @@ __global__ void pool_kernel(const A *__restrict__ in, A *__restrict__ out, VGrid
     for (int k = 0; k < 8; ++k) s[k] *= 0.125f;
     Act8<A> o;
     o.set(s);
-    halo_store(out, gh, p, C, c, o);
+    planar_store(out, gh, p, c, o);
 }
 
-// nearest 2x upsampling: out (grid gf, halo layout) from in (grid gf / 2,
-// halo layout), C channels; one thread per 8 channels of an output voxel
+// nearest 2x upsampling: out (grid gf) from in (grid gf / 2), C channels,
+// planar; one thread per 8 channels of an output voxel
 template <typename A>
 __global__ void upsample_kernel(const A *__restrict__ in, A *__restrict__ out, VGrid gf, int C)
 {
@@ -174,29 +183,31 @@ __global__ void upsample_kernel(const A *__restrict__ in, A *__restrict__ out, V
     int b, z, y, x;
     coords(m, gf, b, z, y, x);
     const VGrid gh{gf.nb, gf.lz - 1, gf.ly - 1, gf.lx - 1};
+    const Planar ph = planar_of(gh);
     Act8<A> v;
-    v.load(in + halo_index(gh, vidx(gh, b, z >> 1, y >> 1, x >> 1)) * C + c);
-    halo_store(out, gf, m, C, c, v);
+    v.load(planar_at(in, ph, planar_q(gh, ph, vidx(gh, b, z >> 1, y >> 1, x >> 1)), c));
+    planar_store(out, gf, m, c, v);
 }
 
-// dy = g * (y > 0) in the activation type (y, dy: halo layout with periodic
-// copies; g: [V][C] fp32); per-block channel sums of g * (y > 0) (bias
+// dy = g * (y > 0) in the activation type (y, dy: planar with periodic
+// copies; dyz: the same values without the copies, zeros elsewhere, for the
+// weight gradient; g: [V][C] fp32); per-block channel sums of g * (y > 0) (bias
 // gradient).  A thread handles 8 channels of a voxel; blockDim = EW and the
 // grid stride are multiples of C / 8, so each thread keeps one channel group.
 template <typename A>
 __global__ void relu_bwd_kernel(const float *__restrict__ g, const A *__restrict__ y, A *__restrict__ dy,
-                                float *__restrict__ part, VGrid grid, int C)
+                                A *__restrict__ dyz, float *__restrict__ part, VGrid grid, int C)
 {
     __shared__ float sh[EW][9];
     const int C8 = C >> 3;
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const long long n = grid.voxels() * C8;
+    const Planar pl = planar_of(grid);
     for (long long i = (long long)blockIdx.x * EW + threadIdx.x; i < n; i += (long long)gridDim.x * EW) {
         const long long m = i / C8;
         const int c = int(i - m * C8) * 8;
-        const long long hi = halo_index(grid, m);
         Act8<A> ya;
-        ya.load(y + hi * C + c);
+        ya.load(planar_at(y, pl, planar_q(grid, pl, m), c));
         float yv[8];
         ya.get(yv);
         const float4 g0 = *reinterpret_cast<const float4 *>(g + m * C + c);
@@ -210,7 +221,8 @@ __global__ void relu_bwd_kernel(const float *__restrict__ g, const A *__restrict
         }
         Act8<A> oa;
         oa.set(o);
-        halo_store(dy, grid, m, C, c, oa);
+        planar_store(dy, grid, m, c, oa);
+        oa.store(planar_at(dyz, pl, planar_q(grid, pl, m), c));
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];
@@ -272,7 +284,7 @@ __global__ void skip_pool_kernel(const float *__restrict__ gcat, int ctot, int c
     ge[i] = gcat[v * ctot + c0 + c] + 0.125f * gp[vidx(gh, b, z >> 1, y >> 1, x >> 1) * C + c];
 }
 
-// 1x1x1 head y = d1 Wh^T + bh (d1 in the halo layout); with a target: loss partials, the gradient
+// 1x1x1 head y = d1 Wh^T + bh (d1 planar); with a target: loss partials, the gradient
 // g_d1 = gy Wh (gy = 2 (y - target) / (V 4)), and partials of dWh (4 x 16),
 // dbh (4) and the loss: part[block][72] = {dWh[64], dbh[4], sum of squared
 // differences, 3 unused}.
@@ -292,11 +304,12 @@ __global__ void head_kernel(const A *__restrict__ d1, const float *__restrict__ 
 #pragma unroll
     for (int k = 0; k < HEAD_PART; ++k) acc[k] = 0.f;
     const float gscale = 2.f / float(V * 4);
+    const Planar pl = planar_of(g);
     for (long long m = (long long)blockIdx.x * EW + threadIdx.x; m < V; m += (long long)gridDim.x * EW) {
-        const A *row = d1 + halo_index(g, m) * 16;
+        const long long q = planar_q(g, pl, m);
         Act8<A> h0, h1;
-        h0.load(row);
-        h1.load(row + 8);
+        h0.load(planar_at(d1, pl, q, 0));
+        h1.load(planar_at(d1, pl, q, 8));
         float a[16];
         h0.get(a);
         h1.get(a + 8);
@@ -370,6 +383,42 @@ __global__ void prep_weights_kernel(const float *__restrict__ W, int cout, int c
     const float w = ci < cin ? W[((long long)co * 27 + t) * cin + ci] : 0.f;
     wf[i] = A(w);
     if (wb && ci < cin) wb[((long long)ci * 27 + (26 - t)) * cout + co] = A(w);
+}
+
+// bf16 weights of one convolution packed for the bulk-copy kernels, stage by
+// stage (16 input channels): wf[k][t][h][co][e] = W[co][t][16 k + 8 h + e]
+// (0 beyond cin), and, when wb is given, the backward-data convolution's
+// (input channels = cout, output channels = cin, taps flipped)
+// wb[k][t][h][ci][e] = W[16 k + 8 h + e][26 - t][ci].
+__global__ void pack_weights_kernel(const float *__restrict__ W, int cout, int cin, int cinp, bf16 *__restrict__ wf,
+                                    bf16 *__restrict__ wb)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)cout * 27 * cinp) return;
+    {
+        // forward: i = (((k 27 + t) 2 + h) cout + co) 8 + e
+        const int e = int(i & 7);
+        long long r = i >> 3;
+        const int co = int(r % cout);
+        r /= cout;
+        const int h = int(r & 1);
+        r >>= 1;
+        const int t = int(r % 27), k = int(r / 27);
+        const int ci = 16 * k + 8 * h + e;
+        wf[i] = __float2bfloat16(ci < cin ? W[((long long)co * 27 + t) * cin + ci] : 0.f);
+    }
+    if (wb && i < (long long)cout * 27 * cin) {
+        // backward data: i = (((k 27 + t) 2 + h) cin + ci) 8 + e, output channel ci, input channel 16 k + 8 h + e
+        const int e = int(i & 7);
+        long long r = i >> 3;
+        const int ci = int(r % cin);
+        r /= cin;
+        const int h = int(r & 1);
+        r >>= 1;
+        const int t = int(r % 27), k = int(r / 27);
+        const int co = 16 * k + 8 * h + e;
+        wb[i] = __float2bfloat16(W[((long long)co * 27 + (26 - t)) * cin + ci]);
+    }
 }
 
 // dw [cout][27][cin] from the padded weight gradient [cout][27][cinp]
@@ -541,8 +590,10 @@ struct unet_ctx {
     void *wf[NCONV] = {}, *wb[NCONV] = {};
     bool weights_current = false;
     void *x = nullptr, *e1h = nullptr, *e1 = nullptr, *p1 = nullptr, *e2h = nullptr, *e2 = nullptr, *p2 = nullptr,
-         *e3h = nullptr, *e3 = nullptr, *d2h = nullptr, *d2 = nullptr, *d1h = nullptr, *d1 = nullptr, *dy = nullptr,
-         *up3 = nullptr, *up2 = nullptr;  // activations: halo layout (unet_internal.h)
+         *e3h = nullptr, *e3 = nullptr, *d2h = nullptr, *d2 = nullptr, *d1h = nullptr, *d1 = nullptr,
+         *up3 = nullptr, *up2 = nullptr;  // activations: planar layout (unet_internal.h)
+    void *dy1 = nullptr, *dy2 = nullptr, *dy3 = nullptr;  // masked output gradients of levels 1, 2, 3 (planar)
+    void *dyz1 = nullptr, *dyz2 = nullptr, *dyz3 = nullptr;  // the same without periodic copies
     float *gd1 = nullptr, *gcat1 = nullptr, *gd2 = nullptr, *gcat2 = nullptr, *ge3 = nullptr, *gp2 = nullptr,
           *ge2 = nullptr, *gp1 = nullptr, *ge1 = nullptr, *gh = nullptr;
     float *wpart = nullptr, *wtmp = nullptr, *bpart = nullptr, *hpart = nullptr, *dforce = nullptr;
@@ -612,17 +663,27 @@ void ufree_all(unet_ctx *c)
 
 unsigned blocks_for(long long n) { return unsigned((n + EW - 1) / EW); }
 
-// one 3x3x3 convolution on the context stream (halo-layout sources): TMA-fed
-// tensor cores for bf16, the CUDA-core kernel in the FP32 debug mode
+// 128-position tiles per work item of the bulk convolution: the most whose
+// two accumulator buffers fit TMEM with a ring of at least two stages
+int conv_tiles(const VGrid &g, int cin, int cout)
+{
+    for (int t = 4; t >= 1; t >>= 1)
+        if (2 * t * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 2) return t;
+    for (int t = 4; t >= 1; t >>= 1)
+        if (2 * t * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 1) return t;
+    return 1;
+}
+
+// one 3x3x3 convolution on the context stream (planar sources): bulk-copy
+// tensor cores for bf16 (w packed per stage), the CUDA-core kernel in the
+// FP32 debug mode (w [cout][27][cin])
 int conv(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const void *w, const float *bias, void *out,
          int out_f32, int relu, int cout, VGrid g)
 {
-    ConvTmaArgs a{};
-    const VBox box = vbox(g, 128);
-    if (!make_halo_map(&a.a0, s0, c0, g, box, 16) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box, 16)) ||
-        !make_weight_map(&a.w, w, c0 + c1, cout))
-        return ufail(c, LBM_ECUDA, "conv3: tensor map encoding failed");
-    if (!c1) a.a1 = a.a0;
+    ConvBulkArgs a{};
+    a.src0 = s0;
+    a.src1 = s1;
+    a.w = static_cast<const bf16 *>(w);
     a.bias = bias;
     a.out = out;
     a.c0 = c0;
@@ -630,9 +691,10 @@ int conv(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const void
     a.cout = cout;
     a.out_f32 = out_f32;
     a.relu = relu;
+    a.tiles = conv_tiles(g, c0 + c1, cout);
     a.g = g;
     a.err = c->derr;
-    UCK(launch_conv3_tma(a, c->stream), "conv3");
+    UCK(launch_conv3_bulk(a, c->stream), "conv3");
     return LBM_OK;
 }
 int conv(unet_ctx *c, const float *s0, int c0, const float *s1, int c1, const void *w, const float *bias, void *out,
@@ -664,35 +726,33 @@ int wgrad_vps(long long V, int tiles)
     return int(vps < 64 ? 64 : vps);
 }
 
-size_t wgrad_ws_bytes(long long V, int cin, int cout)
+size_t wgrad_ws_bytes(const VGrid &g, int cin, int cout)
 {
     const int rows_pad = (27 * cin + 127) / 128 * 128;
-    const int vps = wgrad_vps(V, rows_pad / 128);
-    const long long nsplit = (V + vps - 1) / vps;
+    const int nsplit = wgrad_bulk_splits(g, wgrad_bulk_pps(g, rows_pad / 128, wgrad_bulk_run(cout)));
     return size_t(nsplit) * rows_pad * cout * sizeof(float);
 }
 
-int wgrad(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf16 *dy, int cout, float *dw,
+int wgrad(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf16 *dyz, int cout, float *dw,
           VGrid g)
 {
-    WgradTmaArgs a{};
-    const VBox box = vbox(g, 64);
-    if (!make_halo_map(&a.a0, s0, c0, g, box, 16) || (c1 && !make_halo_map(&a.a1, s1, c1, g, box, 16)) ||
-        !make_halo_map(&a.dy, dy, cout, g, box, 16))
-        return ufail(c, LBM_ECUDA, "wgrad: tensor map encoding failed");
-    if (!c1) a.a1 = a.a0;
+    WgradBulkArgs a{};
+    a.src0 = s0;
+    a.src1 = s1;
+    a.dyz = dyz;
     a.c0 = c0;
     a.c1 = c1;
     a.cout = cout;
     a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
-    a.vps = wgrad_vps(g.voxels(), a.rows_pad / 128);
+    a.run = wgrad_bulk_run(cout);
+    a.pps = wgrad_bulk_pps(g, a.rows_pad / 128, a.run);
     a.g = g;
     a.err = c->derr;
     a.partial = c->wpart;
-    const int nsplit = wgrad_splits(g, a.vps);
+    const int nsplit = wgrad_bulk_splits(g, a.pps);
     if (size_t(nsplit) * a.rows_pad * cout * sizeof(float) > c->wpart_bytes)
         return ufail(c, LBM_EINVAL, "weight-gradient workspace too small");
-    UCK(launch_wgrad_tma(a, nsplit, dw, c->stream), "wgrad");
+    UCK(launch_wgrad_bulk(a, nsplit, dw, c->stream), "wgrad");
     return LBM_OK;
 }
 int wgrad(unet_ctx *c, const float *s0, int c0, const float *s1, int c1, const float *dy, int cout, float *dw,
@@ -711,15 +771,15 @@ int wgrad(unet_ctx *c, const float *s0, int c0, const float *s1, int c1, const f
     return LBM_OK;
 }
 
-// ReLU backward into c->dy and the bias gradient of layer k
+// ReLU backward into dy (planar) and the bias gradient of layer k
 template <typename A>
-int relu_bwd(unet_ctx *c, const float *g, const void *y, VGrid grid, int C, int k)
+int relu_bwd(unet_ctx *c, const float *g, const void *y, void *dy, void *dyz, VGrid grid, int C, int k)
 {
     const long long n = grid.voxels() * (C / 8);
     int nblk = int(std::min<long long>(c->relu_blocks, (n + EW - 1) / EW));
     if (nblk < 1) nblk = 1;
-    relu_bwd_kernel<A><<<nblk, EW, 0, c->stream>>>(g, static_cast<const A *>(y), static_cast<A *>(c->dy), c->bpart,
-                                                   grid, C);
+    relu_bwd_kernel<A><<<nblk, EW, 0, c->stream>>>(g, static_cast<const A *>(y), static_cast<A *>(dy),
+                                                   static_cast<A *>(dyz), c->bpart, grid, C);
     reduce_cols_kernel<<<C, EW, 0, c->stream>>>(c->bpart, nblk, C, c->grads + kLayout.b[k]);
     UCK(cudaGetLastError(), "relu backward");
     return LBM_OK;
@@ -732,9 +792,14 @@ int prep_weights(unet_ctx *c)
     for (int k = 0; k < NCONV; ++k) {
         const int cp = cin_padded(k);
         const long long n = 27ll * kConv[k].cout * cp;
-        prep_weights_kernel<A><<<blocks_for(n), EW, 0, c->stream>>>(c->params + kLayout.w[k], kConv[k].cout,
-                                                                    kConv[k].cin, cp, static_cast<A *>(c->wf[k]),
-                                                                    static_cast<A *>(c->wb[k]));
+        if (std::is_same<A, float>::value)
+            prep_weights_kernel<float><<<blocks_for(n), EW, 0, c->stream>>>(
+                c->params + kLayout.w[k], kConv[k].cout, kConv[k].cin, cp, static_cast<float *>(c->wf[k]),
+                static_cast<float *>(c->wb[k]));
+        else
+            pack_weights_kernel<<<blocks_for(n), EW, 0, c->stream>>>(c->params + kLayout.w[k], kConv[k].cout,
+                                                                     kConv[k].cin, cp, static_cast<bf16 *>(c->wf[k]),
+                                                                     static_cast<bf16 *>(c->wb[k]));
     }
     UCK(cudaGetLastError(), "weights");
     c->weights_current = true;
@@ -797,43 +862,43 @@ int backward(unet_ctx *c, const float *target, double *loss)
     float hl = 0.f;
     UCK(cudaMemcpyAsync(&hl, c->wtmp + 68, sizeof(float), cudaMemcpyDeviceToHost, c->stream), "loss");
     // level 1 decoder
-    if ((rc = relu_bwd<A>(c, c->gd1, c->d1, c->g1, 16, W5B))) return rc;
-    if ((rc = wgrad(c, T(c->d1h), 16, (const A *)nullptr, 0, T(c->dy), 16, G + L.w[W5B], c->g1))) return rc;
-    if ((rc = conv(c, T(c->dy), 16, (const A *)nullptr, 0, c->wb[W5B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
-    if ((rc = relu_bwd<A>(c, c->gh, c->d1h, c->g1, 16, W5A))) return rc;
-    if ((rc = wgrad(c, T(c->up2), 32, T(c->e1), 16, T(c->dy), 16, G + L.w[W5A], c->g1))) return rc;
-    if ((rc = conv(c, T(c->dy), 16, (const A *)nullptr, 0, c->wb[W5A], nullptr, c->gcat1, 1, 0, 48, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gd1, c->d1, c->dy1, c->dyz1, c->g1, 16, W5B))) return rc;
+    if ((rc = wgrad(c, T(c->d1h), 16, (const A *)nullptr, 0, T(c->dyz1), 16, G + L.w[W5B], c->g1))) return rc;
+    if ((rc = conv(c, T(c->dy1), 16, (const A *)nullptr, 0, c->wb[W5B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->d1h, c->dy1, c->dyz1, c->g1, 16, W5A))) return rc;
+    if ((rc = wgrad(c, T(c->up2), 32, T(c->e1), 16, T(c->dyz1), 16, G + L.w[W5A], c->g1))) return rc;
+    if ((rc = conv(c, T(c->dy1), 16, (const A *)nullptr, 0, c->wb[W5A], nullptr, c->gcat1, 1, 0, 48, c->g1))) return rc;
     up_bwd_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gd2, c->g2);
     // level 2 decoder
-    if ((rc = relu_bwd<A>(c, c->gd2, c->d2, c->g2, 32, W4B))) return rc;
-    if ((rc = wgrad(c, T(c->d2h), 32, (const A *)nullptr, 0, T(c->dy), 32, G + L.w[W4B], c->g2))) return rc;
-    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W4B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
-    if ((rc = relu_bwd<A>(c, c->gh, c->d2h, c->g2, 32, W4A))) return rc;
-    if ((rc = wgrad(c, T(c->up3), 64, T(c->e2), 32, T(c->dy), 32, G + L.w[W4A], c->g2))) return rc;
-    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W4A], nullptr, c->gcat2, 1, 0, 96, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gd2, c->d2, c->dy2, c->dyz2, c->g2, 32, W4B))) return rc;
+    if ((rc = wgrad(c, T(c->d2h), 32, (const A *)nullptr, 0, T(c->dyz2), 32, G + L.w[W4B], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy2), 32, (const A *)nullptr, 0, c->wb[W4B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->d2h, c->dy2, c->dyz2, c->g2, 32, W4A))) return rc;
+    if ((rc = wgrad(c, T(c->up3), 64, T(c->e2), 32, T(c->dyz2), 32, G + L.w[W4A], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy2), 32, (const A *)nullptr, 0, c->wb[W4A], nullptr, c->gcat2, 1, 0, 96, c->g2))) return rc;
     up_bwd_kernel<<<blocks_for(c->V3 * 64), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->ge3, c->g3);
     // bottleneck
-    if ((rc = relu_bwd<A>(c, c->ge3, c->e3, c->g3, 64, W3B))) return rc;
-    if ((rc = wgrad(c, T(c->e3h), 64, (const A *)nullptr, 0, T(c->dy), 64, G + L.w[W3B], c->g3))) return rc;
-    if ((rc = conv(c, T(c->dy), 64, (const A *)nullptr, 0, c->wb[W3B], nullptr, c->gh, 1, 0, 64, c->g3))) return rc;
-    if ((rc = relu_bwd<A>(c, c->gh, c->e3h, c->g3, 64, W3A))) return rc;
-    if ((rc = wgrad(c, T(c->p2), 32, (const A *)nullptr, 0, T(c->dy), 64, G + L.w[W3A], c->g3))) return rc;
-    if ((rc = conv(c, T(c->dy), 64, (const A *)nullptr, 0, c->wb[W3A], nullptr, c->gp2, 1, 0, 32, c->g3))) return rc;
+    if ((rc = relu_bwd<A>(c, c->ge3, c->e3, c->dy3, c->dyz3, c->g3, 64, W3B))) return rc;
+    if ((rc = wgrad(c, T(c->e3h), 64, (const A *)nullptr, 0, T(c->dyz3), 64, G + L.w[W3B], c->g3))) return rc;
+    if ((rc = conv(c, T(c->dy3), 64, (const A *)nullptr, 0, c->wb[W3B], nullptr, c->gh, 1, 0, 64, c->g3))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->e3h, c->dy3, c->dyz3, c->g3, 64, W3A))) return rc;
+    if ((rc = wgrad(c, T(c->p2), 32, (const A *)nullptr, 0, T(c->dyz3), 64, G + L.w[W3A], c->g3))) return rc;
+    if ((rc = conv(c, T(c->dy3), 64, (const A *)nullptr, 0, c->wb[W3A], nullptr, c->gp2, 1, 0, 32, c->g3))) return rc;
     skip_pool_kernel<<<blocks_for(c->V2 * 32), EW, 0, c->stream>>>(c->gcat2, 96, 64, c->gp2, c->ge2, c->g2, 32);
     // level 2 encoder
-    if ((rc = relu_bwd<A>(c, c->ge2, c->e2, c->g2, 32, W2B))) return rc;
-    if ((rc = wgrad(c, T(c->e2h), 32, (const A *)nullptr, 0, T(c->dy), 32, G + L.w[W2B], c->g2))) return rc;
-    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W2B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
-    if ((rc = relu_bwd<A>(c, c->gh, c->e2h, c->g2, 32, W2A))) return rc;
-    if ((rc = wgrad(c, T(c->p1), 16, (const A *)nullptr, 0, T(c->dy), 32, G + L.w[W2A], c->g2))) return rc;
-    if ((rc = conv(c, T(c->dy), 32, (const A *)nullptr, 0, c->wb[W2A], nullptr, c->gp1, 1, 0, 16, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->ge2, c->e2, c->dy2, c->dyz2, c->g2, 32, W2B))) return rc;
+    if ((rc = wgrad(c, T(c->e2h), 32, (const A *)nullptr, 0, T(c->dyz2), 32, G + L.w[W2B], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy2), 32, (const A *)nullptr, 0, c->wb[W2B], nullptr, c->gh, 1, 0, 32, c->g2))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->e2h, c->dy2, c->dyz2, c->g2, 32, W2A))) return rc;
+    if ((rc = wgrad(c, T(c->p1), 16, (const A *)nullptr, 0, T(c->dyz2), 32, G + L.w[W2A], c->g2))) return rc;
+    if ((rc = conv(c, T(c->dy2), 32, (const A *)nullptr, 0, c->wb[W2A], nullptr, c->gp1, 1, 0, 16, c->g2))) return rc;
     skip_pool_kernel<<<blocks_for(c->V1 * 16), EW, 0, c->stream>>>(c->gcat1, 48, 32, c->gp1, c->ge1, c->g1, 16);
     // level 1 encoder
-    if ((rc = relu_bwd<A>(c, c->ge1, c->e1, c->g1, 16, W1B))) return rc;
-    if ((rc = wgrad(c, T(c->e1h), 16, (const A *)nullptr, 0, T(c->dy), 16, G + L.w[W1B], c->g1))) return rc;
-    if ((rc = conv(c, T(c->dy), 16, (const A *)nullptr, 0, c->wb[W1B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
-    if ((rc = relu_bwd<A>(c, c->gh, c->e1h, c->g1, 16, W1A))) return rc;
-    if ((rc = wgrad(c, T(c->x), 16, (const A *)nullptr, 0, T(c->dy), 16, c->wtmp, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->ge1, c->e1, c->dy1, c->dyz1, c->g1, 16, W1B))) return rc;
+    if ((rc = wgrad(c, T(c->e1h), 16, (const A *)nullptr, 0, T(c->dyz1), 16, G + L.w[W1B], c->g1))) return rc;
+    if ((rc = conv(c, T(c->dy1), 16, (const A *)nullptr, 0, c->wb[W1B], nullptr, c->gh, 1, 0, 16, c->g1))) return rc;
+    if ((rc = relu_bwd<A>(c, c->gh, c->e1h, c->dy1, c->dyz1, c->g1, 16, W1A))) return rc;
+    if ((rc = wgrad(c, T(c->x), 16, (const A *)nullptr, 0, T(c->dyz1), 16, c->wtmp, c->g1))) return rc;
     unpad_grad_kernel<<<blocks_for(16 * 27 * 2), EW, 0, c->stream>>>(c->wtmp, 16, 2, 16, G + L.w[W1A]);
     UCK(cudaGetLastError(), "backward");
     if ((rc = check_err(c))) return rc;
@@ -913,25 +978,30 @@ int unet_create_ex(int n, int nb, unsigned long long seed, int precision, void *
         if (k != W1A && (rc = act(&c->wb[k], 27ll * kConv[k].cout * kConv[k].cin))) return bail(rc);
     }
     const VGrid g1 = c->g1, g2 = c->g2, g3 = c->g3;
-    if ((rc = act(&c->x, halo_elems(g1, 16))) || (rc = act(&c->e1h, halo_elems(g1, 16))) ||
-        (rc = act(&c->e1, halo_elems(g1, 16))) || (rc = act(&c->p1, halo_elems(g2, 16))) ||
-        (rc = act(&c->e2h, halo_elems(g2, 32))) || (rc = act(&c->e2, halo_elems(g2, 32))) ||
-        (rc = act(&c->p2, halo_elems(g3, 32))) || (rc = act(&c->e3h, halo_elems(g3, 64))) ||
-        (rc = act(&c->e3, halo_elems(g3, 64))) || (rc = act(&c->up3, halo_elems(g2, 64))) ||
-        (rc = act(&c->d2h, halo_elems(g2, 32))) || (rc = act(&c->d2, halo_elems(g2, 32))) ||
-        (rc = act(&c->up2, halo_elems(g1, 32))) || (rc = act(&c->d1h, halo_elems(g1, 16))) ||
-        (rc = act(&c->d1, halo_elems(g1, 16))) ||
-        (rc = act(&c->dy, std::max(halo_elems(g1, 16), std::max(halo_elems(g2, 32), halo_elems(g3, 64))))))
-        return bail(rc);
+    // planar activations, zeroed once: the wall rows and guards stay zero
+    struct {
+        void **p;
+        VGrid g;
+        int C;
+    } acts[] = {{&c->x, g1, 16},   {&c->e1h, g1, 16}, {&c->e1, g1, 16},  {&c->p1, g2, 16},  {&c->e2h, g2, 32},
+                {&c->e2, g2, 32},  {&c->p2, g3, 32},  {&c->e3h, g3, 64}, {&c->e3, g3, 64},  {&c->up3, g2, 64},
+                {&c->d2h, g2, 32}, {&c->d2, g2, 32},  {&c->up2, g1, 32}, {&c->d1h, g1, 16}, {&c->d1, g1, 16},
+                {&c->dy1, g1, 16}, {&c->dy2, g2, 32}, {&c->dy3, g3, 64}, {&c->dyz1, g1, 16},
+                {&c->dyz2, g2, 32}, {&c->dyz3, g3, 64}};
+    for (auto &t : acts) {
+        if ((rc = act(t.p, planar_elems(t.g, t.C)))) return bail(rc);
+        if (cudaMemsetAsync(*t.p, 0, size_t(planar_elems(t.g, t.C)) * es, c->stream) != cudaSuccess)
+            return bail(ufail(c, LBM_ECUDA, "unet_create: clearing activations failed"));
+    }
     if ((rc = uown(c, &c->gd1, V1 * 16)) || (rc = uown(c, &c->gcat1, V1 * 48)) || (rc = uown(c, &c->gd2, V2 * 32)) ||
         (rc = uown(c, &c->gcat2, V2 * 96)) || (rc = uown(c, &c->ge3, V3 * 64)) || (rc = uown(c, &c->gp2, V3 * 32)) ||
         (rc = uown(c, &c->ge2, V2 * 32)) || (rc = uown(c, &c->gp1, V2 * 16)) || (rc = uown(c, &c->ge1, V1 * 16)) ||
         (rc = uown(c, &c->gh, V1 * 16)))
         return bail(rc);
     // weight-gradient workspace: the largest of the ten layers
-    const long long Vl[NCONV] = {V1, V1, V2, V2, V3, V3, V2, V2, V1, V1};
+    const VGrid gl[NCONV] = {g1, g1, g2, g2, g3, g3, g2, g2, g1, g1};
     size_t ws = 0;
-    for (int k = 0; k < NCONV; ++k) ws = std::max(ws, wgrad_ws_bytes(Vl[k], cin_padded(k), kConv[k].cout));
+    for (int k = 0; k < NCONV; ++k) ws = std::max(ws, wgrad_ws_bytes(gl[k], cin_padded(k), kConv[k].cout));
     c->wpart_bytes = ws;
     c->relu_blocks = 1024;
     c->head_blocks = int(std::min<long long>(1024, (V1 + EW - 1) / EW));
@@ -1189,6 +1259,101 @@ int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, co
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo_wgrad: invalid channels");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_halo_wgrad: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_halo_wgrad: a bounded wait timed out");
+    return LBM_OK;
+}
+
+long long unet_planar_positions(int nb, int lz, int ly, int lx)
+{
+    if (nb < 1 || lz < 1 || ly < 1 || lx < 1 || lz + ly + lx > 30) return -1;
+    return planar_of(VGrid{nb, lz, ly, lx}).ptot;
+}
+
+int unet_conv3_planar(const void *src0, int c0, const void *src1, int c1, const void *wpk, const float *bias,
+                      void *out, int out_f32, int relu, int cout, int nb, int lz, int ly, int lx, void *stream)
+{
+    if (unet_planar_positions(nb, lz, ly, lx) < 0 || c0 <= 0 || c1 < 0 || (c1 && !src1) || !src0 || !wpk || !out ||
+        ((reinterpret_cast<uintptr_t>(src0) | reinterpret_cast<uintptr_t>(src1) | reinterpret_cast<uintptr_t>(wpk)) &
+         15))
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3_planar: bad arguments");
+    const VGrid g{nb, lz, ly, lx};
+    ConvBulkArgs a{};
+    a.src0 = static_cast<const bf16 *>(src0);
+    a.src1 = static_cast<const bf16 *>(src1);
+    a.w = static_cast<const bf16 *>(wpk);
+    a.bias = bias;
+    a.out = out;
+    a.c0 = c0;
+    a.c1 = c1;
+    a.cout = cout;
+    a.out_f32 = out_f32 ? 1 : 0;
+    a.relu = relu ? 1 : 0;
+    a.tiles = cout > 0 ? conv_tiles(g, c0 + c1, cout) : 1;
+    a.g = g;
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_planar: error word");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    a.err = err;
+    cudaError_t e = launch_conv3_bulk(a, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_planar: invalid channels or grid");
+    if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_planar: %s", cudaGetErrorString(e));
+    if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_planar: a bounded wait timed out");
+    return LBM_OK;
+}
+
+int unet_conv3_planar_wgrad(const void *src0, int c0, const void *src1, int c1, const void *dy, int cout, float *dw,
+                            int nb, int lz, int ly, int lx, void *stream)
+{
+    if (unet_planar_positions(nb, lz, ly, lx) < 0 || c0 <= 0 || c1 < 0 || cout <= 0 || (c1 && !src1) || !src0 ||
+        !dy || !dw ||
+        ((reinterpret_cast<uintptr_t>(src0) | reinterpret_cast<uintptr_t>(src1) | reinterpret_cast<uintptr_t>(dy)) &
+         15))
+        return ufail(nullptr, LBM_EINVAL, "unet_conv3_planar_wgrad: bad arguments");
+    const VGrid g{nb, lz, ly, lx};
+    WgradBulkArgs a{};
+    a.src0 = static_cast<const bf16 *>(src0);
+    a.src1 = static_cast<const bf16 *>(src1);
+    a.dyz = static_cast<const bf16 *>(dy);
+    a.c0 = c0;
+    a.c1 = c1;
+    a.cout = cout;
+    a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
+    a.run = wgrad_bulk_run(cout);
+    a.pps = wgrad_bulk_pps(g, a.rows_pad / 128, a.run);
+    a.g = g;
+    const int nsplit = wgrad_bulk_splits(g, a.pps);
+    void *(*al)(size_t, void *, void *) = nullptr;
+    void (*rl)(void *, size_t, void *, void *) = nullptr;
+    void *user = nullptr;
+    current_allocator(&al, &rl, &user);
+    const size_t bytes = size_t(nsplit) * a.rows_pad * cout * sizeof(float) + 256;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *ws = nullptr;
+    if (al) {
+        ws = al(bytes, stream, user);
+    } else if (cudaMalloc(&ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ws = nullptr;
+    }
+    if (!ws) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_planar_wgrad: workspace of %zu bytes", bytes);
+    a.partial = static_cast<float *>(ws);
+    a.err = reinterpret_cast<int *>(static_cast<char *>(ws) + bytes - 256);
+    cudaMemsetAsync(a.err, 0, sizeof(int), s);
+    cudaError_t e = launch_wgrad_bulk(a, nsplit, dw, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (rl)
+        rl(ws, bytes, stream, user);
+    else if (!al)
+        cudaFree(ws);
+    if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_planar_wgrad: invalid channels");
+    if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_planar_wgrad: %s", cudaGetErrorString(e));
+    if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_planar_wgrad: a bounded wait timed out");
     return LBM_OK;
 }
 

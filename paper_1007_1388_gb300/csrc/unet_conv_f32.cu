@@ -1,5 +1,5 @@
 // FP32 debug mode of the U-Net's 3x3x3 convolutions: plain CUDA-core kernels
-// over FP32 halo-layout activations (the layout of unet_internal.h with float
+// over FP32 planar activations (the layout of unet_internal.h with float
 // elements).  They compute the same contractions as the tensor-core kernels,
 // with FP32 operands and FP32 accumulation instead of bf16 operands, so the
 // whole network's gradients can be checked against an FP64 implementation to
@@ -12,14 +12,16 @@ namespace {
 
 constexpr int CT = 256;
 
-// offset in voxels of tap t (t = 9 (dz+1) + 3 (dy+1) + (dx+1)) in the halo
-// layout, and whether the tap's row lies beyond a y wall
-__device__ __forceinline__ long long tap_offset(const VGrid &g, int t, int y, bool &wall)
+// position offset of tap t (t = 9 (dz+1) + 3 (dy+1) + (dx+1)) in the planar
+// layout (rows beyond the walls hold zeros there)
+__device__ __forceinline__ long long tap_offset(const Planar &p, int t)
 {
-    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-    const long long nx2 = (1ll << g.lx) + 2, ny = 1ll << g.ly;
-    wall = y + dy < 0 || y + dy >= ny;
-    return (dz * ny + dy) * nx2 + dx;
+    return (long long)(t / 9 - 1) * p.sz + ((t / 3) % 3 - 1) * p.sy + (t % 3 - 1);
+}
+
+__device__ __forceinline__ float at(const float *t, const Planar &p, long long q, int c)
+{
+    return t[((long long)(c >> 3) * p.ptot + q) * 8 + (c & 7)];
 }
 
 // one thread per (voxel, output channel)
@@ -30,33 +32,31 @@ __global__ void conv3_f32_kernel(ConvF32Args a)
     if (i >= V * a.cout) return;
     const long long m = i / a.cout;
     const int co = int(i - m * a.cout);
-    const int y = int((m >> a.g.lx) & ((1ll << a.g.ly) - 1));
-    const long long hi = halo_index(a.g, m);
+    const Planar p = planar_of(a.g);
+    const long long q = planar_q(a.g, p, m);
     const int cin = a.c0 + a.c1;
     float s = a.bias ? a.bias[co] : 0.f;
     for (int t = 0; t < 27; ++t) {
-        bool wall;
-        const long long o = hi + tap_offset(a.g, t, y, wall);
-        if (wall) continue;
+        const long long o = q + tap_offset(p, t);
         const float *w = a.w + ((long long)co * 27 + t) * cin;
-        for (int ci = 0; ci < a.c0; ++ci) s = fmaf(a.src0[o * a.c0 + ci], w[ci], s);
-        for (int ci = 0; ci < a.c1; ++ci) s = fmaf(a.src1[o * a.c1 + ci], w[a.c0 + ci], s);
+        for (int ci = 0; ci < a.c0; ++ci) s = fmaf(at(a.src0, p, o, ci), w[ci], s);
+        for (int ci = 0; ci < a.c1; ++ci) s = fmaf(at(a.src1, p, o, ci), w[a.c0 + ci], s);
     }
     if (a.relu) s = fmaxf(s, 0.f);
     if (!a.out_halo) {
         a.out[i] = s;
         return;
     }
-    // halo layout: the voxel and its periodic copies along x and z
+    // planar: the voxel and its periodic copies along x and z
     const long long nx = 1ll << a.g.lx, nz = 1ll << a.g.lz;
     const long long x = m & (nx - 1), z = (m >> (a.g.lx + a.g.ly)) & (nz - 1);
-    const long long plane = (1ll << a.g.ly) * (nx + 2);
     const long long dx = x == 0 ? nx : (x == nx - 1 ? -nx : 0);
-    const long long dz = z == 0 ? nz * plane : (z == nz - 1 ? -nz * plane : 0);
-    a.out[hi * a.cout + co] = s;
-    if (dx) a.out[(hi + dx) * a.cout + co] = s;
-    if (dz) a.out[(hi + dz) * a.cout + co] = s;
-    if (dx && dz) a.out[(hi + dx + dz) * a.cout + co] = s;
+    const long long dz = z == 0 ? nz * p.sz : (z == nz - 1 ? -nz * p.sz : 0);
+    float *o = a.out + ((long long)(co >> 3) * p.ptot + q) * 8 + (co & 7);
+    o[0] = s;
+    if (dx) o[dx * 8] = s;
+    if (dz) o[dz * 8] = s;
+    if (dx && dz) o[(dx + dz) * 8] = s;
 }
 
 // one block per (co, t, group of 8 input channels): every thread sums over a
@@ -69,18 +69,16 @@ __global__ void wgrad_f32_kernel(WgradF32Args a)
     const int gi = blockIdx.x % groups, t = (blockIdx.x / groups) % 27, co = blockIdx.x / (groups * 27);
     const int ci0 = gi * 8;
     const float *src = ci0 < a.c0 ? a.src0 : a.src1;
-    const int C = ci0 < a.c0 ? a.c0 : a.c1, cs = ci0 < a.c0 ? ci0 : ci0 - a.c0;
+    const int cs = ci0 < a.c0 ? ci0 : ci0 - a.c0;
     const long long V = a.g.voxels();
+    const Planar p = planar_of(a.g);
+    const long long off = tap_offset(p, t);
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (long long m = threadIdx.x; m < V; m += CT) {
-        const int y = int((m >> a.g.lx) & ((1ll << a.g.ly) - 1));
-        bool wall;
-        const long long hi = halo_index(a.g, m);
-        const long long o = hi + tap_offset(a.g, t, y, wall);
-        if (wall) continue;
-        const float d = a.dy[hi * a.cout + co];
+        const long long q = planar_q(a.g, p, m);
+        const float d = at(a.dy, p, q, co);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = fmaf(d, src[o * C + cs + k], acc[k]);
+        for (int k = 0; k < 8; ++k) acc[k] = fmaf(d, at(src, p, q + off, cs + k), acc[k]);
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];

@@ -70,6 +70,78 @@ __host__ __device__ inline long long halo_elems(const VGrid &g, int C)
     return (long long)g.nb * ((1ll << g.lz) + 2) * (1ll << g.ly) * ((1ll << g.lx) + 2) * C;
 }
 
+// Planar halo layout (the network's activations): a tensor of C channels (C a
+// multiple of 8) over grid g is stored as [C / 8][ptot][8], eight channels of
+// one padded voxel (16 bytes in bf16) per position.  Padded voxel (b, z', y',
+// x'), with z' in [0, nz + 2), y' in [0, ny + 2), x' in [0, nx + 2), is at
+//   q = guard + ((b (nz + 2) + z') (ny + 2) + y') (nx + 2) + x'
+// and voxel (b, z, y, x) at padded (b, z + 1, y + 1, x + 1).  Columns x' = 0
+// and nx + 1 and planes z' = 0 and nz + 1 hold the periodic copies; rows y' =
+// 0 and ny + 1 (beyond the walls) and the guards hold zeros.  Every run of
+// positions of one 8-channel group is contiguous, so a tap of a convolution is
+// a fixed offset dz sz + dy sy + dx, and operand tiles are single bulk copies.
+struct Planar {
+    long long sy, sz, pg, guard, ptot;  // row, plane and grid strides; guard; positions per group
+};
+__host__ __device__ inline Planar planar_of(const VGrid &g)
+{
+    Planar p;
+    p.sy = (1ll << g.lx) + 2;
+    p.sz = ((1ll << g.ly) + 2) * p.sy;
+    p.pg = ((1ll << g.lz) + 2) * p.sz;
+    p.guard = 1024 + p.sz + p.sy;  // covers a tile's or a run's overhang plus one plane, one row and one voxel
+    p.ptot = 2 * p.guard + g.nb * p.pg;
+    return p;
+}
+__host__ __device__ inline long long planar_q(const VGrid &g, const Planar &p, long long m)
+{
+    const long long nx = 1ll << g.lx, ny = 1ll << g.ly, nz = 1ll << g.lz;
+    const long long x = m & (nx - 1), y = (m >> g.lx) & (ny - 1), z = (m >> (g.lx + g.ly)) & (nz - 1);
+    const long long b = m >> (g.lx + g.ly + g.lz);
+    return p.guard + b * p.pg + (z + 1) * p.sz + (y + 1) * p.sy + x + 1;
+}
+__host__ __device__ inline long long planar_elems(const VGrid &g, int C) { return (long long)C * planar_of(g).ptot; }
+
+// Bulk-copy tensor-core convolution over planar tensors.  A work item is
+// `tiles` x 128 consecutive positions of one grid's interior planes (columns
+// and rows of the halo included and discarded); per 16 input channels it
+// copies, for dz = -1, 0, 1, the contiguous run of positions its taps reach
+// (one bulk copy per 8-channel group), and every tap's A operand is that slab
+// at offset dy sy + dx.  Persistent CTAs, one per SM.  w: packed bf16 weights [cin / 16][27][2][cout][8]
+// (element (k, t, h, co, e) = W[co][t][16 k + 8 h + e]).  out: bf16 planar
+// (periodic copies written too) or fp32 [M][cout].
+struct ConvBulkArgs {
+    const bf16 *src0, *src1, *w;
+    const float *bias;
+    void *out;
+    int c0, c1, cout, out_f32, relu, tiles;
+    VGrid g;
+    int *err;
+};
+
+// Bulk-copy weight gradient over planar tensors: rows (t, ci) x cout per CTA
+// tile of 128 rows; K = every position of the grids (halo and all), in runs
+// of `run` (wgrad_bulk_run), split into `nsplit` ranges of pps positions (a
+// multiple of run)
+// whose partial sums [nsplit][rows_pad][cout] are then added in a fixed
+// order.  dyz: the output gradient with zeros at every position that is not
+// an interior voxel (no periodic copies), so halo positions add nothing.
+struct WgradBulkArgs {
+    const bf16 *src0, *src1, *dyz;
+    float *partial;
+    int c0, c1, cout, rows_pad, pps, run;
+    VGrid g;
+    int *err;
+};
+int wgrad_bulk_splits(const VGrid &g, int pps);
+int wgrad_bulk_run(int cout);
+int wgrad_bulk_pps(const VGrid &g, int row_tiles, int run);
+int conv3_bulk_stages(const VGrid &g, int cin, int cout, int tiles);
+
+cudaError_t launch_conv3_bulk(const ConvBulkArgs &a, cudaStream_t s);
+cudaError_t launch_wgrad_bulk(const WgradBulkArgs &a, int nsplit, float *dw, cudaStream_t s);
+size_t conv3_bulk_smem(const VGrid &g, int cin, int cout, int tiles);
+
 // A box of `count` consecutive voxels (a power of two dividing the grid's
 // total) in whole rows, planes and grids: extents {bx, by, bz, bb}.
 struct VBox {
@@ -124,9 +196,9 @@ struct WgradTmaArgs {
     int *err;
 };
 
-// FP32 debug mode: the same convolution on FP32 halo-layout sources with FP32
-// weights [cout][27][c0 + c1] on the CUDA cores; out is FP32 in the halo
-// layout (out_halo = 1, periodic copies written too) or [M][cout].
+// FP32 debug mode: the same convolution on FP32 planar sources with FP32
+// weights [cout][27][c0 + c1] on the CUDA cores; out is FP32 planar
+// (out_halo = 1, periodic copies written too) or [M][cout].
 struct ConvF32Args {
     const float *src0, *src1, *w, *bias;
     float *out;
@@ -134,8 +206,8 @@ struct ConvF32Args {
     VGrid g;
 };
 
-// FP32 weight gradient dw[co][t][ci] (ci over c0 + c1) from FP32 halo-layout
-// sources and dy (halo layout, cout channels), written (not accumulated).
+// FP32 weight gradient dw[co][t][ci] (ci over c0 + c1) from FP32 planar
+// sources and dy (planar, cout channels), written (not accumulated).
 struct WgradF32Args {
     const float *src0, *src1, *dy;
     float *dw;

@@ -139,6 +139,9 @@ SIGNATURES = {
     "unet_smooth_fields": ([_vp, _vp, _vp, _i, _i, _i, _i, _vp], _i),
     "unet_conv3_halo": ([_vp, _i, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp], _i),
     "unet_conv3_halo_wgrad": ([_vp, _i, _vp, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp], _i),
+    "unet_planar_positions": ([_i, _i, _i, _i], _ll),
+    "unet_conv3_planar": ([_vp, _i, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp], _i),
+    "unet_conv3_planar_wgrad": ([_vp, _i, _vp, _i, _vp, _i, _vp, _i, _i, _i, _i, _vp], _i),
 }
 
 _lib = None

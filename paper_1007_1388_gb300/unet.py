@@ -189,3 +189,40 @@ def conv3_halo_wgrad(src0, c0, dy, cout, dw, grid, *, src1=None, c1=0, stream=No
         ctypes.c_void_p(dy.data_ptr()), cout, ctypes.c_void_p(dw.data_ptr()), nb, lz, ly, lx,
         ctypes.c_void_p(s.cuda_stream)))
     return dw
+
+
+def planar_positions(grid) -> int:
+    """Positions per 8-channel group of a planar tensor over grid (nb, lz, ly, lx)."""
+    nb, lz, ly, lx = grid
+    p = lib().unet_planar_positions(nb, lz, ly, lx)
+    if p < 0:
+        raise ValueError("bad grid")
+    return int(p)
+
+
+def conv3_planar(src0, c0, wpk, out, cout, grid, *, src1=None, c1=0, bias=None, relu=False, stream=None):
+    """conv3 on planar bf16 tensors (bulk-copied operands); wpk: weights packed
+    per 16 input channels, [cin / 16][27][2][cout][8]."""
+    import torch
+
+    nb, lz, ly, lx = grid
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().unet_conv3_planar(
+        ctypes.c_void_p(src0.data_ptr()), c0, ctypes.c_void_p(src1.data_ptr()) if src1 is not None else None, c1,
+        ctypes.c_void_p(wpk.data_ptr()), ctypes.c_void_p(bias.data_ptr()) if bias is not None else None,
+        ctypes.c_void_p(out.data_ptr()), int(out.dtype == torch.float32), int(relu), cout, nb, lz, ly, lx,
+        ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def conv3_planar_wgrad(src0, c0, dy, cout, dw, grid, *, src1=None, c1=0, stream=None):
+    """Weight gradient on planar bf16 tensors (bulk-copied operands)."""
+    import torch
+
+    nb, lz, ly, lx = grid
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().unet_conv3_planar_wgrad(
+        ctypes.c_void_p(src0.data_ptr()), c0, ctypes.c_void_p(src1.data_ptr()) if src1 is not None else None, c1,
+        ctypes.c_void_p(dy.data_ptr()), cout, ctypes.c_void_p(dw.data_ptr()), nb, lz, ly, lx,
+        ctypes.c_void_p(s.cuda_stream)))
+    return dw

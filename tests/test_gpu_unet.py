@@ -15,9 +15,13 @@
   oracle, on parameters whose every ReLU decision has a margin of at least
   0.5 (checked in the oracle), so that FP32 rounding cannot flip a mask;
 - a few Adam steps lower the loss;
-- the TMA-fed kernels on halo-layout tensors (the network's own path) equal
-  the cp.async kernels: forward bitwise (periodic copies included), weight
-  gradient to FP32 accumulation order.
+- the TMA-fed kernels on halo-layout tensors equal the cp.async kernels:
+  forward bitwise (periodic copies included), weight gradient to FP32
+  accumulation order;
+- the bulk-copy kernels on planar tensors (the network's own path) equal the
+  cp.async kernels: bitwise where the MMA order is the same (16 input
+  channels), else to FP32 accumulation order; a bf16 output touches exactly
+  the interior and the periodic copies.
 """
 import numpy as np
 import pytest
@@ -370,5 +374,89 @@ def test_tma_wgrad_equals_cpasync_wgrad(env, case):
     unet.conv3_halo_wgrad(_to_halo(torch, s0, nb, lz, ly, lx, c0), c0, _to_halo(torch, dy, nb, lz, ly, lx, cout),
                           cout, got, grid, src1=_to_halo(torch, s1, nb, lz, ly, lx, c1) if c1 else None, c1=c1)
     # same products, the splits may differ: FP32 accumulation order only
+    mag = float(ref.abs().max())
+    assert float((got - ref).abs().max()) <= 1e-5 * mag + 1e-6
+
+
+# ------------------------------------------------------------- bulk copies (planar layout)
+def _to_planar(torch, unet, t, grid, c, copies=True):
+    """(nb*nz*ny*nx*c) channels-last -> planar [c/8][P][8]: periodic x/z copies
+    (or zeros without `copies`), zero wall rows and guards."""
+    nb, lz, ly, lx = grid
+    a = t.view(nb, 1 << lz, 1 << ly, 1 << lx, c)
+    if copies:
+        a = torch.cat([a[:, :, :, -1:], a, a[:, :, :, :1]], dim=3)
+        a = torch.cat([a[:, -1:], a, a[:, :1]], dim=1)
+    else:
+        zx = torch.zeros_like(a[:, :, :, :1])
+        a = torch.cat([zx, a, zx], dim=3)
+        zz = torch.zeros_like(a[:, :1])
+        a = torch.cat([zz, a, zz], dim=1)
+    z = torch.zeros_like(a[:, :, :1])
+    a = torch.cat([z, a, z], dim=2).reshape(-1, c // 8, 8).permute(1, 0, 2)
+    out = torch.zeros(c // 8, unet.planar_positions(grid), 8, dtype=t.dtype, device=t.device)
+    g0 = 1024 + ((1 << ly) + 2) * ((1 << lx) + 2) + (1 << lx) + 2
+    out[:, g0:g0 + a.shape[1]] = a
+    return out.reshape(-1)
+
+
+def _pack(torch, w, cout, cin):
+    """bf16 [cout][27][cin] -> [cin/16][27][2][cout][8]."""
+    return w.view(cout, 27, cin // 16, 2, 8).permute(2, 1, 3, 0, 4).contiguous().view(-1)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if not c[1]])
+def test_planar_conv3_matches_cpasync_conv3(env, case):
+    torch, unet = env
+    c0, _, c1, cout, grid, relu, bias, out_f32 = case
+    nb, lz, ly, lx = grid
+    rng = np.random.default_rng(29 + hash(case) % 2**31)
+    V = nb << (lz + ly + lx)
+    s0, _ = _bf16(torch, rng.normal(size=V * c0))
+    s1, _ = (_bf16(torch, rng.normal(size=V * c1)) if c1 else (None, None))
+    w, _ = _bf16(torch, rng.normal(0, 0.1, size=cout * 27 * (c0 + c1)))
+    b = torch.from_numpy(rng.normal(size=cout).astype(np.float32)).cuda() if bias else None
+    dt = torch.float32 if out_f32 else torch.bfloat16
+    ref = torch.empty(V * cout, dtype=dt, device="cuda")
+    unet.conv3(s0, c0, w, ref, cout, grid, src1=s1, c1=c1, bias=b, relu=relu)
+    p0 = _to_planar(torch, unet, s0, grid, c0)
+    p1 = _to_planar(torch, unet, s1, grid, c1) if c1 else None
+    wpk = _pack(torch, w, cout, c0 + c1)
+    same_order = c0 + c1 == 16
+    if out_f32:
+        got = torch.empty(V * cout, dtype=dt, device="cuda")
+        unet.conv3_planar(p0, c0, wpk, got, cout, grid, src1=p1, c1=c1, bias=b, relu=relu)
+        want = ref
+    else:
+        got = torch.full((cout * unet.planar_positions(grid),), float("nan"), dtype=dt, device="cuda")
+        unet.conv3_planar(p0, c0, wpk, got, cout, grid, src1=p1, c1=c1, bias=b, relu=relu)
+        torch.cuda.synchronize()
+        # untouched positions (wall rows, guards) stay NaN: count them as zero
+        got = torch.nan_to_num(got, nan=0.0)
+        want = _to_planar(torch, unet, ref, grid, cout)
+    if same_order:
+        assert torch.equal(got, want)
+    else:
+        g, r = got.float(), want.float()
+        tol = (1e-5 if out_f32 else 2.0**-7) * float(r.abs().max())
+        assert float((g - r).abs().max()) <= tol
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if not c[1] and c[3] <= 128])
+def test_planar_wgrad_matches_cpasync_wgrad(env, case):
+    torch, unet = env
+    c0, _, c1, cout, grid, _, _, _ = case
+    nb, lz, ly, lx = grid
+    rng = np.random.default_rng(31 + hash(case) % 2**31)
+    V = nb << (lz + ly + lx)
+    s0, _ = _bf16(torch, rng.normal(size=V * c0))
+    s1, _ = (_bf16(torch, rng.normal(size=V * c1)) if c1 else (None, None))
+    dy, _ = _bf16(torch, rng.normal(size=V * cout))
+    ref = torch.empty(cout * 27 * (c0 + c1), dtype=torch.float32, device="cuda")
+    unet.conv3_wgrad(s0, c0, dy, cout, ref, grid, src1=s1, c1=c1)
+    got = torch.empty_like(ref)
+    dyz = _to_planar(torch, unet, dy, grid, cout, copies=False)
+    unet.conv3_planar_wgrad(_to_planar(torch, unet, s0, grid, c0), c0, dyz, cout, got, grid,
+                            src1=_to_planar(torch, unet, s1, grid, c1) if c1 else None, c1=c1)
     mag = float(ref.abs().max())
     assert float((got - ref).abs().max()) <= 1e-5 * mag + 1e-6
