@@ -155,8 +155,9 @@ int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, co
  * unet_conv3_planar - the convolution of unet_conv3 (no upsampled source) on
  * planar bf16 tensors: every 16 input channels' operands are bulk copies of
  * contiguous position runs, the taps offsets into them.  wpk: the weights
- * packed per 16 input channels, bf16 [cin / 16][27][2][cout][8] with element
- * (k, t, h, co, e) = w[co][t][16 k + 8 h + e].  A bf16 out is written planar
+ * packed per 16 input channels, bf16 [cin / 16][9][2][3][cout][8] with element
+ * (k, p, h, d, co, e) = w[co][3 p + d][16 k + 8 h + e] (the three x taps of
+ * each (dz, dy) pair side by side).  A bf16 out is written planar
  * (periodic copies included; other positions untouched), an fp32 out as
  * [M][cout].  cin, cout multiples of 16.  Synchronises.
  *

@@ -386,38 +386,43 @@ __global__ void prep_weights_kernel(const float *__restrict__ W, int cout, int c
 }
 
 // bf16 weights of one convolution packed for the bulk-copy kernels, stage by
-// stage (16 input channels): wf[k][t][h][co][e] = W[co][t][16 k + 8 h + e]
-// (0 beyond cin), and, when wb is given, the backward-data convolution's
-// (input channels = cout, output channels = cin, taps flipped)
-// wb[k][t][h][ci][e] = W[16 k + 8 h + e][26 - t][ci].
+// stage (16 input channels), the three x taps of each (dz, dy) pair side by
+// side along the output axis: wf[k][p][h][d][co][e] = W[co][3 p + d][16 k +
+// 8 h + e] (0 beyond cin), and, when wb is given, the backward-data
+// convolution's (input channels = cout, output channels = cin, taps flipped)
+// wb[k][p][h][d][ci][e] = W[16 k + 8 h + e][26 - (3 p + d)][ci].
 __global__ void pack_weights_kernel(const float *__restrict__ W, int cout, int cin, int cinp, bf16 *__restrict__ wf,
                                     bf16 *__restrict__ wb)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)cout * 27 * cinp) return;
     {
-        // forward: i = (((k 27 + t) 2 + h) cout + co) 8 + e
+        // forward: i = ((((k 9 + p) 2 + h) 3 + d) cout + co) 8 + e
         const int e = int(i & 7);
         long long r = i >> 3;
         const int co = int(r % cout);
         r /= cout;
+        const int d = int(r % 3);
+        r /= 3;
         const int h = int(r & 1);
         r >>= 1;
-        const int t = int(r % 27), k = int(r / 27);
+        const int p = int(r % 9), k = int(r / 9);
         const int ci = 16 * k + 8 * h + e;
-        wf[i] = __float2bfloat16(ci < cin ? W[((long long)co * 27 + t) * cin + ci] : 0.f);
+        wf[i] = __float2bfloat16(ci < cin ? W[((long long)co * 27 + 3 * p + d) * cin + ci] : 0.f);
     }
     if (wb && i < (long long)cout * 27 * cin) {
-        // backward data: i = (((k 27 + t) 2 + h) cin + ci) 8 + e, output channel ci, input channel 16 k + 8 h + e
+        // backward data: output channel ci, input channel 16 k + 8 h + e
         const int e = int(i & 7);
         long long r = i >> 3;
         const int ci = int(r % cin);
         r /= cin;
+        const int d = int(r % 3);
+        r /= 3;
         const int h = int(r & 1);
         r >>= 1;
-        const int t = int(r % 27), k = int(r / 27);
+        const int p = int(r % 9), k = int(r / 9);
         const int co = 16 * k + 8 * h + e;
-        wb[i] = __float2bfloat16(W[((long long)co * 27 + (26 - t)) * cin + ci]);
+        wb[i] = __float2bfloat16(W[((long long)co * 27 + (26 - (3 * p + d))) * cin + ci]);
     }
 }
 
@@ -663,14 +668,15 @@ void ufree_all(unet_ctx *c)
 
 unsigned blocks_for(long long n) { return unsigned((n + EW - 1) / EW); }
 
-// 128-position tiles per work item of the bulk convolution: the most whose
-// two accumulator buffers fit TMEM with a ring of at least two stages
+// 128-row tiles per work item of the bulk convolution: the most whose two
+// accumulator buffers (3 cout columns a tile) fit TMEM with a ring of at
+// least two stages; else one buffer
 int conv_tiles(const VGrid &g, int cin, int cout)
 {
     for (int t = 4; t >= 1; t >>= 1)
-        if (2 * t * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 2) return t;
+        if (2 * t * 3 * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 2) return t;
     for (int t = 4; t >= 1; t >>= 1)
-        if (2 * t * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 1) return t;
+        if (t * 3 * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 1) return t;
     return 1;
 }
 
@@ -729,7 +735,9 @@ int wgrad_vps(long long V, int tiles)
 size_t wgrad_ws_bytes(const VGrid &g, int cin, int cout)
 {
     const int rows_pad = (27 * cin + 127) / 128 * 128;
-    const int nsplit = wgrad_bulk_splits(g, wgrad_bulk_pps(g, rows_pad / 128, wgrad_bulk_run(cout)));
+    int run, stages;
+    wgrad_bulk_config(cout, &run, &stages);
+    const int nsplit = wgrad_bulk_splits(g, wgrad_bulk_pps(g, rows_pad / 128, run));
     return size_t(nsplit) * rows_pad * cout * sizeof(float);
 }
 
@@ -744,7 +752,7 @@ int wgrad(unet_ctx *c, const bf16 *s0, int c0, const bf16 *s1, int c1, const bf1
     a.c1 = c1;
     a.cout = cout;
     a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
-    a.run = wgrad_bulk_run(cout);
+    wgrad_bulk_config(cout, &a.run, &a.stages);
     a.pps = wgrad_bulk_pps(g, a.rows_pad / 128, a.run);
     a.g = g;
     a.err = c->derr;
@@ -1322,7 +1330,7 @@ int unet_conv3_planar_wgrad(const void *src0, int c0, const void *src1, int c1, 
     a.c1 = c1;
     a.cout = cout;
     a.rows_pad = (27 * (c0 + c1) + 127) / 128 * 128;
-    a.run = wgrad_bulk_run(cout);
+    wgrad_bulk_config(cout, &a.run, &a.stages);
     a.pps = wgrad_bulk_pps(g, a.rows_pad / 128, a.run);
     a.g = g;
     const int nsplit = wgrad_bulk_splits(g, a.pps);

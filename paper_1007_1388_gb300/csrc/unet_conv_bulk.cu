@@ -21,7 +21,7 @@
 //
 // Weight gradient: each 16-row unit (tap, 16 input channels) of the 128-row
 // tile and each 8-channel group of dy is a run of `run` positions (256, or
-// 128 where three such stages do not fit), copied by the lanes of the
+// 128 where two such stages do not fit), copied by the lanes of the
 // producer warp; the MN-major operands have LBO 128 (8 positions) and SBO
 // run x 16 bytes (8 channels).  K runs over every position of
 // the grids, so dy comes with zeros at all non-interior positions.
@@ -36,10 +36,10 @@
 namespace lbm {
 namespace {
 
-constexpr int CTHREADS = 192;  // warp 0: copies, warp 1: MMAs, warps 2-5: epilogue
+constexpr int CTHREADS = 320;  // warp 0: copies, warp 1: MMAs, warps 2-5 and 6-9: two epilogue groups
 constexpr int CSTAGES = 3;
 constexpr int WTHREADS = 128;
-constexpr int WSTAGES = 3;
+constexpr int WSTAGES = 4;  // weight-gradient ring depth, at most
 constexpr int WRUN = 256;  // positions per weight-gradient stage, at most
 constexpr long long kWait = 2000000000ll;
 constexpr int kSmemBudget = 220 * 1024;
@@ -52,8 +52,11 @@ struct ConvPlan {
     int wres;      // bytes of the resident weights (0 if not)
     int stage;     // bytes of one ring stage
     int nstages;   // ring depth
-    int bufcols;   // TMEM columns of one accumulator buffer (tiles x cout)
-    int tcols;     // TMEM columns allocated (a power of two >= 2 bufcols)
+    int ncols;     // accumulator columns of one tile: 3 cout (the three x taps side by side)
+    int nsplit;    // MMAs per (tap pair, tile): 1, or 3 where 3 cout > 256
+    int bufcols;   // TMEM columns of one accumulator buffer (tiles x ncols)
+    int nbuf;      // accumulator buffers: 2, or 1 where two do not fit TMEM
+    int tcols;     // TMEM columns allocated (a power of two)
     int smem;      // dynamic shared memory
 };
 
@@ -61,7 +64,7 @@ __host__ __device__ inline ConvPlan conv_plan(const VGrid &g, int cin, int cout,
 {
     ConvPlan c;
     const int sy = (1 << g.lx) + 2;
-    c.L = (128 * tiles + 2 * sy + 2 + 7) / 8 * 8;
+    c.L = (126 * tiles + 2 * sy + 2 + 7) / 8 * 8;
     c.slab = 3 * 2 * c.L * 16;
     c.wstage = 27 * 2 * cout * 16;
     const int wall = (cin / 16) * c.wstage;
@@ -70,9 +73,12 @@ __host__ __device__ inline ConvPlan conv_plan(const VGrid &g, int cin, int cout,
     c.stage = c.slab + (c.resident ? 0 : c.wstage);
     const int n = (kSmemBudget - c.wres) / c.stage;
     c.nstages = n < CSTAGES ? n : CSTAGES;
-    c.bufcols = tiles * cout;
+    c.ncols = 3 * cout;
+    c.nsplit = c.ncols > 256 ? 3 : 1;
+    c.bufcols = tiles * c.ncols;
+    c.nbuf = 2 * c.bufcols <= 512 ? 2 : 1;
     c.tcols = 32;
-    while (c.tcols < 2 * c.bufcols) c.tcols <<= 1;
+    while (c.tcols < c.nbuf * c.bufcols) c.tcols <<= 1;
     c.smem = c.wres + c.nstages * c.stage;
     return c;
 }
@@ -87,12 +93,15 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[CSTAGES], empty[CSTAGES], tfull[2], tempty[2], wbar;
     __shared__ uint32_t tslot;
+    __shared__ int s_ok[2];
+    __shared__ float xch[2][4][2][16];  // per epilogue group, rows at the lane-quarter seams: x tap -1 of
+                                        // lane 31, x tap +1 of lane 0
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cin = a.c0 + a.c1, cout = a.cout, T = a.tiles, nks = cin >> 4, g0 = a.c0 >> 3;
     const ConvPlan cp = conv_plan(a.g, cin, cout, T);
     const Planar P = planar_of(a.g);
     const int nx = 1 << a.g.lx, ny = 1 << a.g.ly, nz = 1 << a.g.lz;
-    const int span = 128 * T;
+    const int span = 126 * T;                            // output positions per work item
     const int tpg = int((nz * P.sz + span - 1) / span);  // work items per grid
     const int items = tpg * a.g.nb;
     unsigned char *wsm = smem;             // resident weights
@@ -152,14 +161,19 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
         for (int u = j - last; u < j; ++u) umma::mbar_wait(&full[u % cp.nstages], (u / cp.nstages) & 1, kWait);
         if (cp.resident) umma::mbar_wait(&wbar, 0, kWait);
     } else if (tid == 32) {
-        // MMA issuer: 27 taps x T tiles per stage into accumulator buffer it % 2
-        const uint32_t idesc = umma::idesc_bf16(cout, false, false);
+        // MMA issuer: per stage, 9 (dz, dy) pairs x T tiles, N = the three x
+        // taps' output channels.  Row r of tile i is position q0 + 126 i - 1 + r,
+        // at slab offset 126 i + r + (dy + 1) sy.  Descriptors are built once per
+        // stage; a pair or tile moves only the start address field (16-byte
+        // units, no carry out of its 14 bits: shared memory stays below 256 KB).
+        const int nn = cp.ncols / cp.nsplit;
+        const uint32_t idesc = umma::idesc_bf16(nn, false, false);
         bool ok = !cp.resident || umma::mbar_wait(&wbar, 0, kWait);
         if (!ok) atomicExch(a.err, 1);
         int j = 0, it = 0;
         for (int item = blockIdx.x; ok && item < items; item += gridDim.x, ++it) {
-            const int buf = it & 1;
-            if (it >= 2 && !umma::mbar_wait(&tempty[buf], ((it >> 1) - 1) & 1, kWait)) {
+            const int buf = cp.nbuf == 2 ? (it & 1) : 0, use = cp.nbuf == 2 ? (it >> 1) : it;
+            if (use >= 1 && !umma::mbar_wait(&tempty[buf], (use - 1) & 1, kWait)) {
                 atomicExch(a.err, 1);
                 ok = false;
                 break;
@@ -176,73 +190,113 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
                 umma::fence_after();
                 const uint32_t base = umma::smem_addr(ring + s * cp.stage);
                 const uint32_t wb = cp.resident ? umma::smem_addr(wsm) + uint32_t(k * cp.wstage) : base + uint32_t(cp.slab);
-                for (int t = 0; t < 27; ++t) {
-                    const int dz = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                    const uint64_t bd = umma::sdesc(wb + uint32_t(t * 2 * cout * 16), uint32_t(cout * 16), 128);
-                    const uint32_t sub = base + uint32_t(dz * 2 * cp.L * 16);
-                    for (int i = 0; i < T; ++i) {
-                        const uint32_t at = sub + uint32_t((i * 128 + int(P.sy) + 1 + dy * int(P.sy) + dx) * 16);
-                        umma::mma_bf16(acc + uint32_t(i * cout), umma::sdesc(at, uint32_t(cp.L * 16), 128), bd, idesc,
-                                       (k > 0 || t > 0) ? 1u : 0u);
-                    }
+                const uint64_t a0 = umma::sdesc(base, uint32_t(cp.L * 16), 128);
+                const uint64_t b0 = umma::sdesc(wb, uint32_t(cp.ncols * 16), 128);
+                for (int pr = 0; pr < 9; ++pr) {
+                    const int dz = pr / 3, dy = pr - 3 * dz;
+                    const uint64_t ad = a0 + uint64_t(dz * 2 * cp.L + dy * int(P.sy));
+                    const uint64_t bd = b0 + uint64_t(pr * 2 * cp.ncols);
+                    const uint32_t accumulate = (k > 0 || pr > 0) ? 1u : 0u;
+                    for (int i = 0; i < T; ++i)
+                        for (int sp = 0; sp < cp.nsplit; ++sp)
+                            umma::mma_bf16(acc + uint32_t(i * cp.ncols + sp * nn), ad + uint64_t(i * 126),
+                                           bd + uint64_t(sp * nn), idesc, accumulate);
                 }
                 umma::mma_commit(&empty[s]);
             }
             if (ok) umma::mma_commit(&tfull[buf]);
         }
     } else if (warp >= 2) {
-        // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 of every tile
-        const int quarter = warp & 3;
+        // epilogue: two groups of four warps take alternate work items (one
+        // accumulator buffer each; with a single buffer group 0 takes all).
+        // Warp w holds rows 32 (w % 4) .. + 31 of every tile.  Output row r
+        // (1..126) adds its own x tap 0 block, row r - 1's x tap -1 block and
+        // row r + 1's x tap +1 block; rows 0 and 127 only lend theirs.
+        const int grp = (warp - 2) >> 2, quarter = warp & 3, r = quarter * 32 + lane;
         const uint32_t trow = tmem + (uint32_t(quarter * 32) << 16);
+        const int barid = 1 + grp;
         int it = 0;
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
-            const int buf = it & 1;
-            if (!umma::mbar_wait(&tfull[buf], (it >> 1) & 1, kWait)) {
-                if (lane == 0) atomicExch(a.err, 1);
+            const int buf = cp.nbuf == 2 ? (it & 1) : 0, use = cp.nbuf == 2 ? (it >> 1) : it;
+            if ((cp.nbuf == 2 ? buf : 0) != grp) continue;
+            // one thread waits for the group, so that its four warps take the
+            // same path through the group's named barriers below
+            if ((warp & 3) == 2 && lane == 0) s_ok[grp] = umma::mbar_wait(&tfull[buf], use & 1, kWait) ? 1 : 0;
+            asm volatile("bar.sync %0, 128;" ::"r"(barid) : "memory");
+            if (!s_ok[grp]) {
+                if ((warp & 3) == 2 && lane == 0) atomicExch(a.err, 1);
                 break;
             }
             umma::fence_after();
             const int b = item / tpg;
             const long long q0 = P.guard + b * P.pg + P.sz + (long long)(item - b * tpg) * span;
             for (int i = 0; i < T; ++i) {
-                const long long q = q0 + i * 128 + quarter * 32 + lane;
+                const long long q = q0 + i * 126 - 1 + r;
                 const int rel = int(q - P.guard - b * P.pg);
                 const int zp = rel / int(P.sz), rem = rel - zp * int(P.sz);
                 const int yp = rem / int(P.sy), xp = rem - yp * int(P.sy);
-                const bool inside = zp >= 1 && zp <= nz && yp >= 1 && yp <= ny && xp >= 1 && xp <= nx;
+                const bool out = r >= 1 && r <= 126 && zp >= 1 && zp <= nz && yp >= 1 && yp <= ny && xp >= 1 &&
+                                 xp <= nx;
                 // the voxel's periodic copies (positions) and its unpadded index
                 const long long dxh = xp == 1 ? nx : (xp == nx ? -nx : 0);
                 const long long dzh = zp == 1 ? nz * P.sz : (zp == nz ? -nz * P.sz : 0);
                 const long long m = (((long long)b * nz + zp - 1) * ny + yp - 1) * nx + xp - 1;
+                const uint32_t col = trow + uint32_t(buf * cp.bufcols + i * cp.ncols);
                 for (int c = 0; c < cout; c += 16) {
-                    float r[16];
-                    umma::tmem_ld16(trow + uint32_t(buf * cp.bufcols + i * cout + c), r);  // warp-collective
-                    if (!inside) continue;
+                    uint32_t um[16], u0[16], up[16];
+                    umma::tmem_ld16_nowait(col + uint32_t(c), um);             // x tap -1
+                    umma::tmem_ld16_nowait(col + uint32_t(cout + c), u0);      // x tap 0
+                    umma::tmem_ld16_nowait(col + uint32_t(2 * cout + c), up);  // x tap +1
+                    umma::tmem_ld_wait();
+                    float (*xq)[2][16] = xch[grp];
+                    if (lane == 31)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) xq[quarter][0][e] = __uint_as_float(um[e]);
+                    if (lane == 0)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) xq[quarter][1][e] = __uint_as_float(up[e]);
+                    asm volatile("bar.sync %0, 128;" ::"r"(barid) : "memory");
+                    float v[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
-                        const float v = r[e] + (a.bias ? __ldg(a.bias + c + e) : 0.f);
-                        r[e] = a.relu ? fmaxf(v, 0.f) : v;
+                        float lo = __shfl_up_sync(0xffffffffu, __uint_as_float(um[e]), 1);
+                        float hi = __shfl_down_sync(0xffffffffu, __uint_as_float(up[e]), 1);
+                        if (lane == 0) lo = quarter > 0 ? xq[quarter - 1][0][e] : 0.f;
+                        if (lane == 31) hi = quarter < 3 ? xq[quarter + 1][1][e] : 0.f;
+                        v[e] = __uint_as_float(u0[e]) + lo + hi;
                     }
+                    asm volatile("bar.sync %0, 128;" ::"r"(barid) : "memory");
+                    if (!out) continue;
+                    if (a.bias) {
+                        const float4 *bb = reinterpret_cast<const float4 *>(a.bias + c);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float4 t4 = __ldg(bb + e);
+                            v[4 * e] += t4.x, v[4 * e + 1] += t4.y, v[4 * e + 2] += t4.z, v[4 * e + 3] += t4.w;
+                        }
+                    }
+                    if (a.relu)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] = fmaxf(v[e], 0.f);
                     if (a.out_f32) {
                         float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out) + m * cout + c);
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            o[e] = make_float4(r[4 * e], r[4 * e + 1], r[4 * e + 2], r[4 * e + 3]);
+                        for (int e = 0; e < 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
                     } else {
                         __align__(16) __nv_bfloat162 h[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) h[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
-                        const uint4 v0 = reinterpret_cast<const uint4 *>(h)[0];
-                        const uint4 v1 = reinterpret_cast<const uint4 *>(h)[1];
+                        for (int e = 0; e < 8; ++e) h[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                        const uint4 w0 = reinterpret_cast<const uint4 *>(h)[0];
+                        const uint4 w1 = reinterpret_cast<const uint4 *>(h)[1];
                         bf16 *o0 = static_cast<bf16 *>(a.out) + (long long)(c >> 3) * P.ptot * 8;
                         bf16 *o1 = o0 + P.ptot * 8;
                         const long long at[4] = {q, q + dxh, q + dzh, q + dxh + dzh};
-                        const bool use[4] = {true, dxh != 0, dzh != 0, dxh != 0 && dzh != 0};
+                        const bool use4[4] = {true, dxh != 0, dzh != 0, dxh != 0 && dzh != 0};
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (use[u]) {
-                                *reinterpret_cast<uint4 *>(o0 + at[u] * 8) = v0;
-                                *reinterpret_cast<uint4 *>(o1 + at[u] * 8) = v1;
+                            if (use4[u]) {
+                                *reinterpret_cast<uint4 *>(o0 + at[u] * 8) = w0;
+                                *reinterpret_cast<uint4 *>(o1 + at[u] * 8) = w1;
                             }
                     }
                 }
@@ -263,7 +317,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) wgrad_bulk_kernel(const __grid_co
     __shared__ __align__(8) uint64_t full[WSTAGES], empty[WSTAGES], done;
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cin = a.c0 + a.c1, cout = a.cout, g0 = a.c0 >> 3;
+    const int cin = a.c0 + a.c1, cout = a.cout, g0 = a.c0 >> 3, NS = a.stages;
     const int run = a.run, slot = run * 16;  // 8 channels x run positions
     const int abytes = 16 * slot, sbytes = abytes + (cout >> 3) * slot;
     uint32_t tcols = 32;
@@ -280,7 +334,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) wgrad_bulk_kernel(const __grid_co
 
     if (warp == 0) umma::tmem_alloc(&tslot, tcols);
     if (tid == 0) {
-        for (int s = 0; s < WSTAGES; ++s) {
+        for (int s = 0; s < NS; ++s) {
             umma::mbar_init(&full[s], 1);
             umma::mbar_init(&empty[s], 1);
         }
@@ -296,9 +350,9 @@ __global__ void __launch_bounds__(WTHREADS, 1) wgrad_bulk_kernel(const __grid_co
         // producer warp: one 4 KB run per slot, one slot per lane
         int c = 0;
         for (; c < nchunks; ++c) {
-            const int s = c % WSTAGES;
+            const int s = c % NS;
             int ok = 1;
-            if (lane == 0 && c >= WSTAGES && !umma::mbar_wait(&empty[s], ((c / WSTAGES) - 1) & 1, kWait)) ok = 0;
+            if (lane == 0 && c >= NS && !umma::mbar_wait(&empty[s], ((c / NS) - 1) & 1, kWait)) ok = 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 if (lane == 0) atomicExch(a.err, 1);
@@ -324,15 +378,15 @@ __global__ void __launch_bounds__(WTHREADS, 1) wgrad_bulk_kernel(const __grid_co
         }
         // before leaving: the copies of the last stages have landed (bounded)
         if (lane == 0) {
-            const int last = c < WSTAGES ? c : WSTAGES;
-            for (int u = c - last; u < c; ++u) umma::mbar_wait(&full[u % WSTAGES], (u / WSTAGES) & 1, kWait);
+            const int last = c < NS ? c : NS;
+            for (int u = c - last; u < c; ++u) umma::mbar_wait(&full[u % NS], (u / NS) & 1, kWait);
         }
     } else if (tid == 32) {
         const uint32_t idesc = umma::idesc_bf16(cout, true, true);
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
-            const int s = c % WSTAGES;
-            if (!umma::mbar_wait(&full[s], (c / WSTAGES) & 1, kWait)) {
+            const int s = c % NS;
+            if (!umma::mbar_wait(&full[s], (c / NS) & 1, kWait)) {
                 atomicExch(a.err, 1);
                 ok = false;
                 break;
@@ -382,7 +436,7 @@ __global__ void wgrad_bulk_reduce_kernel(const float *__restrict__ partial, int 
     dw[((long long)co * 27 + t) * cin + ci] = acc;
 }
 
-size_t wgrad_bulk_smem(int cout, int run) { return size_t(WSTAGES) * (16 + (cout >> 3)) * run * 16; }
+size_t wgrad_bulk_smem(int cout, int run, int stages) { return size_t(stages) * (16 + (cout >> 3)) * run * 16; }
 
 cudaError_t raise_smem_limit(const void *fn, size_t bytes, size_t &current)
 {
@@ -412,6 +466,8 @@ size_t conv3_bulk_smem(const VGrid &g, int cin, int cout, int tiles)
     return c.nstages >= 1 && c.tcols <= 512 ? size_t(c.smem) : ~size_t(0);
 }
 
+int conv3_bulk_buffers(const VGrid &g, int cin, int cout, int tiles) { return conv_plan(g, cin, cout, tiles).nbuf; }
+
 int conv3_bulk_stages(const VGrid &g, int cin, int cout, int tiles) { return conv_plan(g, cin, cout, tiles).nstages; }
 
 int wgrad_bulk_splits(const VGrid &g, int pps)
@@ -420,11 +476,15 @@ int wgrad_bulk_splits(const VGrid &g, int pps)
     return pps > 0 ? int((total + pps - 1) / pps) : 0;
 }
 
-int wgrad_bulk_run(int cout)
+// Two stages of the longest runs that fit: on GB300 fewer, larger copies beat
+// a deeper ring of the same bytes (measured: 256 x 2 stages 3.03 ms per U-Net
+// training step, 128 x 4 stages 4.02 ms, 128 x 3 stages 3.34 ms).
+void wgrad_bulk_config(int cout, int *run, int *stages)
 {
-    int run = WRUN;
-    while (run > 64 && wgrad_bulk_smem(cout, run) > size_t(kSmemBudget)) run >>= 1;
-    return run;
+    int r = WRUN;
+    while (r > 64 && wgrad_bulk_smem(cout, r, 2) > size_t(kSmemBudget)) r >>= 1;
+    *run = r;
+    *stages = 2;
 }
 
 int wgrad_bulk_pps(const VGrid &g, int row_tiles, int run)
@@ -442,8 +502,9 @@ cudaError_t launch_conv3_bulk(const ConvBulkArgs &a, cudaStream_t s)
 {
     const int cin = a.c0 + a.c1;
     if (a.c0 <= 0 || a.c0 % 16 || a.c1 < 0 || a.c1 % 16 || (a.c1 && !a.src1) || !a.src0 || !a.w || !a.out ||
-        a.cout <= 0 || a.cout % 16 || a.cout > 256 || a.tiles < 1 || a.tiles > 4 || a.g.lx < 1 || a.g.ly < 1 ||
-        a.g.lz < 1 || a.g.lx > 8 || a.g.nb < 1 || planar_of(a.g).ptot >= (1ll << 31))
+        a.cout <= 0 || a.cout % 16 || a.cout > 160 || a.tiles < 1 || a.tiles > 4 || a.g.lx < 1 || a.g.ly < 1 ||
+        a.g.lz < 1 || a.g.lx > 8 || a.g.nb < 1 || planar_of(a.g).ptot >= (1ll << 31) ||
+        (reinterpret_cast<uintptr_t>(a.bias) & 15))
         return cudaErrorInvalidValue;
     const size_t sm = conv3_bulk_smem(a.g, cin, a.cout, a.tiles);
     if (sm > size_t(kSmemBudget)) return cudaErrorInvalidValue;
@@ -451,7 +512,7 @@ cudaError_t launch_conv3_bulk(const ConvBulkArgs &a, cudaStream_t s)
     cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(conv3_bulk_kernel), sm, current);
     if (e != cudaSuccess) return e;
     const Planar P = planar_of(a.g);
-    const long long span = 128ll * a.tiles;
+    const long long span = 126ll * a.tiles;
     const long long items = ((1ll << a.g.lz) * P.sz + span - 1) / span * a.g.nb;
     const long long grid = items < sm_count() ? items : sm_count();
     conv3_bulk_kernel<<<unsigned(grid), CTHREADS, sm, s>>>(a);
@@ -463,12 +524,13 @@ cudaError_t launch_wgrad_bulk(const WgradBulkArgs &a, int nsplit, float *dw, cud
     const int cin = a.c0 + a.c1;
     if (a.c0 <= 0 || a.c0 % 16 || a.c1 < 0 || a.c1 % 16 || (a.c1 && !a.src1) || !a.src0 || !a.dyz || !dw ||
         !a.partial || a.cout <= 0 || a.cout % 16 || a.cout > 128 || a.run < 16 || a.run > WRUN || a.run % 16 ||
-        a.pps <= 0 || a.pps % a.run || wgrad_bulk_smem(a.cout, a.run) > size_t(kSmemBudget) ||
+        a.stages < 1 || a.stages > WSTAGES || a.pps <= 0 || a.pps % a.run ||
+        wgrad_bulk_smem(a.cout, a.run, a.stages) > size_t(kSmemBudget) ||
         a.rows_pad < 27 * cin || a.rows_pad % 128 || nsplit != wgrad_bulk_splits(a.g, a.pps) || a.g.lx < 1 ||
         a.g.ly < 1 || a.g.lz < 1 || a.g.lx > 8 || planar_of(a.g).ptot >= (1ll << 31))
         return cudaErrorInvalidValue;
     static size_t current = 0;
-    const size_t sm = wgrad_bulk_smem(a.cout, a.run);
+    const size_t sm = wgrad_bulk_smem(a.cout, a.run, a.stages);
     cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(wgrad_bulk_kernel), sm, current);
     if (e != cudaSuccess) return e;
     const dim3 grid(unsigned(a.rows_pad / 128), unsigned(nsplit));
