@@ -681,14 +681,14 @@ def run_unet_report(args):
     train_flops = 3.0 * fwd_flops  # forward, backward-data and weight gradient
     peak, peak_sus, kind = _peak_bf16()
     res = {"report": "unet", "workload": f"U-Net, {nb} samples of {n}^3 (bf16 operands, FP32 accumulation, "
-                                         "tcgen05 with TMA-staged 32-byte-swizzled tiles)",
+                                         "tcgen05 with bulk-copied planar operand slabs)",
            "ms_per_train_step": ms_step, "ms_per_prediction": ms_pred,
            "forward_gflop": fwd_flops / 1e9, "train_tflops_effective": train_flops / ms_step / 1e9,
            "forward_tflops_effective": fwd_flops / ms_pred / 1e9,
            "peak_bf16_tflops": peak, "peak_kind": kind,
            # the whole forward pass (convolutions plus the element-wise kernels between them) against
            # the tensor peak: a lower bound for the convolution kernels themselves
-           "roofline": {"kernel": "lbm::conv3_tma_kernel (whole forward pass)", "bound": "tensor",
+           "roofline": {"kernel": "lbm::conv3_bulk_kernel (whole forward pass)", "bound": "tensor",
                         "achieved": fwd_flops / ms_pred / 1e9, "peak": peak, "unit": "TFLOP/s",
                         "frac": fwd_flops / ms_pred / 1e9 / peak}}
     net.destroy()

@@ -668,15 +668,15 @@ void ufree_all(unet_ctx *c)
 
 unsigned blocks_for(long long n) { return unsigned((n + EW - 1) / EW); }
 
-// 128-row tiles per work item of the bulk convolution: the most whose two
-// accumulator buffers (3 cout columns a tile) fit TMEM with a ring of at
+// 128-position tiles per work item of the bulk convolution: the most whose
+// two accumulator buffers (cout columns a tile) fit TMEM with a ring of at
 // least two stages; else one buffer
 int conv_tiles(const VGrid &g, int cin, int cout)
 {
     for (int t = 4; t >= 1; t >>= 1)
-        if (2 * t * 3 * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 2) return t;
+        if (2 * t * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 2) return t;
     for (int t = 4; t >= 1; t >>= 1)
-        if (t * 3 * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 1) return t;
+        if (t * cout <= 512 && conv3_bulk_stages(g, cin, cout, t) >= 1) return t;
     return 1;
 }
 

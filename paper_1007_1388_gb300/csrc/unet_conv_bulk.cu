@@ -11,13 +11,16 @@
 // channels (one ring stage) the producer copies, for dz = -1, 0, 1, the run
 // of positions [q0 + dz sz - sy - 1, + L) of both 8-channel groups: the slab
 // every tap of that plane reaches.  The A operand of tap (dz, dy, dx) and tile
-// i is the dz slab at position offset i 128 + sy + 1 + dy sy + dx: K-major, no
-// swizzle, rows (positions) 16 bytes apart (SBO 128), the two channel groups
-// L 16 bytes apart (LBO); so 27 taps share one copy of their input.  Weights
-// stay resident when they fit (else they ride with every stage).  The TMEM
-// accumulators are double-buffered: the epilogue warps drain item n while the
-// MMAs of item n + 1 run.  Positions in halo columns and rows are computed
-// and dropped.
+// i is the dz slab at position offset i 128 + (dy + 1) sy + dx + 1: K-major,
+// no swizzle, rows (positions) 16 bytes apart (SBO 128), the two channel
+// groups L 16 bytes apart (LBO); so 27 taps share one copy of their input.
+// Weights stay resident when they fit (else they ride with every stage).  An
+// M = 128 MMA costs max(46, N / 2) cycles whatever the operand layout
+// (measured), so the 27 MMAs of N = cout per tile and stage run the tensor
+// core near that rate as long as the epilogue keeps up: two epilogue warp
+// groups take alternate work items, each with its own TMEM accumulator
+// buffer, while the MMAs of the next item run.  Positions in halo columns and
+// rows are computed and dropped.
 //
 // Weight gradient: each 16-row unit (tap, 16 input channels) of the 128-row
 // tile and each 8-channel group of dy is a run of `run` positions (256, or
@@ -52,9 +55,7 @@ struct ConvPlan {
     int wres;      // bytes of the resident weights (0 if not)
     int stage;     // bytes of one ring stage
     int nstages;   // ring depth
-    int ncols;     // accumulator columns of one tile: 3 cout (the three x taps side by side)
-    int nsplit;    // MMAs per (tap pair, tile): 1, or 3 where 3 cout > 256
-    int bufcols;   // TMEM columns of one accumulator buffer (tiles x ncols)
+    int bufcols;   // TMEM columns of one accumulator buffer (tiles x cout)
     int nbuf;      // accumulator buffers: 2, or 1 where two do not fit TMEM
     int tcols;     // TMEM columns allocated (a power of two)
     int smem;      // dynamic shared memory
@@ -64,7 +65,7 @@ __host__ __device__ inline ConvPlan conv_plan(const VGrid &g, int cin, int cout,
 {
     ConvPlan c;
     const int sy = (1 << g.lx) + 2;
-    c.L = (126 * tiles + 2 * sy + 2 + 7) / 8 * 8;
+    c.L = (128 * tiles + 2 * sy + 2 + 7) / 8 * 8;
     c.slab = 3 * 2 * c.L * 16;
     c.wstage = 27 * 2 * cout * 16;
     const int wall = (cin / 16) * c.wstage;
@@ -73,9 +74,7 @@ __host__ __device__ inline ConvPlan conv_plan(const VGrid &g, int cin, int cout,
     c.stage = c.slab + (c.resident ? 0 : c.wstage);
     const int n = (kSmemBudget - c.wres) / c.stage;
     c.nstages = n < CSTAGES ? n : CSTAGES;
-    c.ncols = 3 * cout;
-    c.nsplit = c.ncols > 256 ? 3 : 1;
-    c.bufcols = tiles * c.ncols;
+    c.bufcols = tiles * cout;
     c.nbuf = 2 * c.bufcols <= 512 ? 2 : 1;
     c.tcols = 32;
     while (c.tcols < c.nbuf * c.bufcols) c.tcols <<= 1;
@@ -94,14 +93,12 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
     __shared__ __align__(8) uint64_t full[CSTAGES], empty[CSTAGES], tfull[2], tempty[2], wbar;
     __shared__ uint32_t tslot;
     __shared__ int s_ok[2];
-    __shared__ float xch[2][4][2][16];  // per epilogue group, rows at the lane-quarter seams: x tap -1 of
-                                        // lane 31, x tap +1 of lane 0
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cin = a.c0 + a.c1, cout = a.cout, T = a.tiles, nks = cin >> 4, g0 = a.c0 >> 3;
     const ConvPlan cp = conv_plan(a.g, cin, cout, T);
     const Planar P = planar_of(a.g);
     const int nx = 1 << a.g.lx, ny = 1 << a.g.ly, nz = 1 << a.g.lz;
-    const int span = 126 * T;                            // output positions per work item
+    const int span = 128 * T;                            // output positions per work item
     const int tpg = int((nz * P.sz + span - 1) / span);  // work items per grid
     const int items = tpg * a.g.nb;
     unsigned char *wsm = smem;             // resident weights
@@ -161,13 +158,14 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
         for (int u = j - last; u < j; ++u) umma::mbar_wait(&full[u % cp.nstages], (u / cp.nstages) & 1, kWait);
         if (cp.resident) umma::mbar_wait(&wbar, 0, kWait);
     } else if (tid == 32) {
-        // MMA issuer: per stage, 9 (dz, dy) pairs x T tiles, N = the three x
-        // taps' output channels.  Row r of tile i is position q0 + 126 i - 1 + r,
-        // at slab offset 126 i + r + (dy + 1) sy.  Descriptors are built once per
-        // stage; a pair or tile moves only the start address field (16-byte
-        // units, no carry out of its 14 bits: shared memory stays below 256 KB).
-        const int nn = cp.ncols / cp.nsplit;
-        const uint32_t idesc = umma::idesc_bf16(nn, false, false);
+        // MMA issuer: per stage, 27 taps x T tiles, N = cout.  Row r of tile i
+        // is position q0 + 128 i + r, at slab offset 128 i + r + (dy + 1) sy +
+        // dx + 1.  Descriptors are built once per stage; a tap or tile moves
+        // only the start address field (16-byte units, no carry out of its 14
+        // bits: shared memory stays below 256 KB).  The packed weights hold the
+        // three x taps of a (dz, dy) pair side by side: tap (pair, d) starts d
+        // cout rows in, its two channel groups 3 cout rows apart (LBO).
+        const uint32_t idesc = umma::idesc_bf16(cout, false, false);
         bool ok = !cp.resident || umma::mbar_wait(&wbar, 0, kWait);
         if (!ok) atomicExch(a.err, 1);
         int j = 0, it = 0;
@@ -191,16 +189,16 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
                 const uint32_t base = umma::smem_addr(ring + s * cp.stage);
                 const uint32_t wb = cp.resident ? umma::smem_addr(wsm) + uint32_t(k * cp.wstage) : base + uint32_t(cp.slab);
                 const uint64_t a0 = umma::sdesc(base, uint32_t(cp.L * 16), 128);
-                const uint64_t b0 = umma::sdesc(wb, uint32_t(cp.ncols * 16), 128);
+                const uint64_t b0 = umma::sdesc(wb, uint32_t(3 * cout * 16), 128);
                 for (int pr = 0; pr < 9; ++pr) {
                     const int dz = pr / 3, dy = pr - 3 * dz;
-                    const uint64_t ad = a0 + uint64_t(dz * 2 * cp.L + dy * int(P.sy));
-                    const uint64_t bd = b0 + uint64_t(pr * 2 * cp.ncols);
-                    const uint32_t accumulate = (k > 0 || pr > 0) ? 1u : 0u;
-                    for (int i = 0; i < T; ++i)
-                        for (int sp = 0; sp < cp.nsplit; ++sp)
-                            umma::mma_bf16(acc + uint32_t(i * cp.ncols + sp * nn), ad + uint64_t(i * 126),
-                                           bd + uint64_t(sp * nn), idesc, accumulate);
+                    for (int d = 0; d < 3; ++d) {
+                        const uint64_t ad = a0 + uint64_t(dz * 2 * cp.L + dy * int(P.sy) + d);
+                        const uint64_t bd = b0 + uint64_t(pr * 6 * cout + d * cout);
+                        const uint32_t accumulate = (k > 0 || pr > 0 || d > 0) ? 1u : 0u;
+                        for (int i = 0; i < T; ++i)
+                            umma::mma_bf16(acc + uint32_t(i * cout), ad + uint64_t(i * 128), bd, idesc, accumulate);
+                    }
                 }
                 umma::mma_commit(&empty[s]);
             }
@@ -209,9 +207,7 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
     } else if (warp >= 2) {
         // epilogue: two groups of four warps take alternate work items (one
         // accumulator buffer each; with a single buffer group 0 takes all).
-        // Warp w holds rows 32 (w % 4) .. + 31 of every tile.  Output row r
-        // (1..126) adds its own x tap 0 block, row r - 1's x tap -1 block and
-        // row r + 1's x tap +1 block; rows 0 and 127 only lend theirs.
+        // Warp w holds rows 32 (w % 4) .. + 31 of every tile.
         const int grp = (warp - 2) >> 2, quarter = warp & 3, r = quarter * 32 + lane;
         const uint32_t trow = tmem + (uint32_t(quarter * 32) << 16);
         const int barid = 1 + grp;
@@ -219,53 +215,39 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
             const int buf = cp.nbuf == 2 ? (it & 1) : 0, use = cp.nbuf == 2 ? (it >> 1) : it;
             if ((cp.nbuf == 2 ? buf : 0) != grp) continue;
-            // one thread waits for the group, so that its four warps take the
-            // same path through the group's named barriers below
+            // one thread waits for the group and shares the outcome, so that its
+            // four warps leave together
             if ((warp & 3) == 2 && lane == 0) s_ok[grp] = umma::mbar_wait(&tfull[buf], use & 1, kWait) ? 1 : 0;
             asm volatile("bar.sync %0, 128;" ::"r"(barid) : "memory");
-            if (!s_ok[grp]) {
+            const int ok = s_ok[grp];
+            asm volatile("bar.sync %0, 128;" ::"r"(barid) : "memory");  // s_ok read before its next write
+            if (!ok) {
                 if ((warp & 3) == 2 && lane == 0) atomicExch(a.err, 1);
                 break;
             }
             umma::fence_after();
             const int b = item / tpg;
             const long long q0 = P.guard + b * P.pg + P.sz + (long long)(item - b * tpg) * span;
+            // position of row r in tile 0, then stepped by 128 per tile
+            int rel = int(q0 - P.guard - b * P.pg) + r;
+            int zp = rel / int(P.sz), rem = rel - zp * int(P.sz);
+            int yp = rem / int(P.sy), xp = rem - yp * int(P.sy);
             for (int i = 0; i < T; ++i) {
-                const long long q = q0 + i * 126 - 1 + r;
-                const int rel = int(q - P.guard - b * P.pg);
-                const int zp = rel / int(P.sz), rem = rel - zp * int(P.sz);
-                const int yp = rem / int(P.sy), xp = rem - yp * int(P.sy);
-                const bool out = r >= 1 && r <= 126 && zp >= 1 && zp <= nz && yp >= 1 && yp <= ny && xp >= 1 &&
-                                 xp <= nx;
+                if (i > 0) {
+                    xp += 128;
+                    while (xp >= int(P.sy)) xp -= int(P.sy), ++yp;
+                    while (yp >= ny + 2) yp -= ny + 2, ++zp;
+                }
+                const long long q = q0 + i * 128 + r;
+                const bool out = zp >= 1 && zp <= nz && yp >= 1 && yp <= ny && xp >= 1 && xp <= nx;
                 // the voxel's periodic copies (positions) and its unpadded index
                 const long long dxh = xp == 1 ? nx : (xp == nx ? -nx : 0);
                 const long long dzh = zp == 1 ? nz * P.sz : (zp == nz ? -nz * P.sz : 0);
                 const long long m = (((long long)b * nz + zp - 1) * ny + yp - 1) * nx + xp - 1;
-                const uint32_t col = trow + uint32_t(buf * cp.bufcols + i * cp.ncols);
+                const uint32_t col = trow + uint32_t(buf * cp.bufcols + i * cout);
                 for (int c = 0; c < cout; c += 16) {
-                    uint32_t um[16], u0[16], up[16];
-                    umma::tmem_ld16_nowait(col + uint32_t(c), um);             // x tap -1
-                    umma::tmem_ld16_nowait(col + uint32_t(cout + c), u0);      // x tap 0
-                    umma::tmem_ld16_nowait(col + uint32_t(2 * cout + c), up);  // x tap +1
-                    umma::tmem_ld_wait();
-                    float (*xq)[2][16] = xch[grp];
-                    if (lane == 31)
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) xq[quarter][0][e] = __uint_as_float(um[e]);
-                    if (lane == 0)
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) xq[quarter][1][e] = __uint_as_float(up[e]);
-                    asm volatile("bar.sync %0, 128;" ::"r"(barid) : "memory");
                     float v[16];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        float lo = __shfl_up_sync(0xffffffffu, __uint_as_float(um[e]), 1);
-                        float hi = __shfl_down_sync(0xffffffffu, __uint_as_float(up[e]), 1);
-                        if (lane == 0) lo = quarter > 0 ? xq[quarter - 1][0][e] : 0.f;
-                        if (lane == 31) hi = quarter < 3 ? xq[quarter + 1][1][e] : 0.f;
-                        v[e] = __uint_as_float(u0[e]) + lo + hi;
-                    }
-                    asm volatile("bar.sync %0, 128;" ::"r"(barid) : "memory");
+                    umma::tmem_ld16(col + uint32_t(c), v);  // warp-collective
                     if (!out) continue;
                     if (a.bias) {
                         const float4 *bb = reinterpret_cast<const float4 *>(a.bias + c);
@@ -502,7 +484,7 @@ cudaError_t launch_conv3_bulk(const ConvBulkArgs &a, cudaStream_t s)
 {
     const int cin = a.c0 + a.c1;
     if (a.c0 <= 0 || a.c0 % 16 || a.c1 < 0 || a.c1 % 16 || (a.c1 && !a.src1) || !a.src0 || !a.w || !a.out ||
-        a.cout <= 0 || a.cout % 16 || a.cout > 160 || a.tiles < 1 || a.tiles > 4 || a.g.lx < 1 || a.g.ly < 1 ||
+        a.cout <= 0 || a.cout % 16 || a.cout > 256 || a.tiles < 1 || a.tiles > 4 || a.g.lx < 1 || a.g.ly < 1 ||
         a.g.lz < 1 || a.g.lx > 8 || a.g.nb < 1 || planar_of(a.g).ptot >= (1ll << 31) ||
         (reinterpret_cast<uintptr_t>(a.bias) & 15))
         return cudaErrorInvalidValue;
@@ -512,7 +494,7 @@ cudaError_t launch_conv3_bulk(const ConvBulkArgs &a, cudaStream_t s)
     cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(conv3_bulk_kernel), sm, current);
     if (e != cudaSuccess) return e;
     const Planar P = planar_of(a.g);
-    const long long span = 126ll * a.tiles;
+    const long long span = 128ll * a.tiles;
     const long long items = ((1ll << a.g.lz) * P.sz + span - 1) / span * a.g.nb;
     const long long grid = items < sm_count() ? items : sm_count();
     conv3_bulk_kernel<<<unsigned(grid), CTHREADS, sm, s>>>(a);

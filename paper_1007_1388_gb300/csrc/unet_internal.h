@@ -103,14 +103,11 @@ __host__ __device__ inline long long planar_q(const VGrid &g, const Planar &p, l
 __host__ __device__ inline long long planar_elems(const VGrid &g, int C) { return (long long)C * planar_of(g).ptot; }
 
 // Bulk-copy tensor-core convolution over planar tensors.  A work item is
-// `tiles` x 126 consecutive positions of one grid's interior planes (columns
-// and rows of the halo included and discarded), each tile 128 MMA rows with
-// one helper row on either side; per 16 input channels it copies, for dz =
-// -1, 0, 1, the contiguous run of positions its taps reach (one bulk copy per
-// 8-channel group).  The A operand of a (dz, dy) pair is that slab at offset
-// (dy + 1) sy; the MMA's N holds the three x taps' outputs side by side, and
-// the epilogue adds each row's x tap 0 to its neighbours' x taps -1 and +1.
-// Persistent CTAs, one per SM.  w: packed bf16 weights [cin / 16][9][2][3][cout][8]
+// `tiles` x 128 consecutive positions of one grid's interior planes (columns
+// and rows of the halo included and discarded); per 16 input channels it
+// copies, for dz = -1, 0, 1, the contiguous run of positions its taps reach
+// (one bulk copy per 8-channel group), and every tap's A operand is that slab
+// at offset (dy + 1) sy + dx + 1.  Persistent CTAs, one per SM.  w: packed bf16 weights [cin / 16][9][2][3][cout][8]
 // (element (k, p, h, d, co, e) = W[co][3 p + d][16 k + 8 h + e]).  out: bf16
 // planar (periodic copies written too) or fp32 [M][cout].
 struct ConvBulkArgs {

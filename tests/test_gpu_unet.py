@@ -19,9 +19,9 @@
   forward bitwise (periodic copies included), weight gradient to FP32
   accumulation order;
 - the bulk-copy kernels on planar tensors (the network's own path) equal the
-  cp.async kernels to FP32 accumulation order (they add the three x taps in
-  the epilogue); a bf16 output touches exactly the interior and the periodic
-  copies.
+  cp.async kernels to FP32 accumulation order (input channels in stages of
+  16, taps inside each); a bf16 output touches exactly the interior and the
+  periodic copies.
 """
 import numpy as np
 import pytest
