@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 Q = 19
-FLUID, NOSLIP, MOVING = 0, 1, 2
+FLUID, NOSLIP, MOVING, PRESSURE = 0, 1, 2, 3
 BGK, TRT = 0, 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -56,6 +56,7 @@ class _Problem(ctypes.Structure):
         ("rho0", ctypes.c_double),
         ("force", ctypes.c_double * 3),
         ("wall_u", ctypes.c_double * 3),
+        ("rho_b", ctypes.c_double),
     ]
 
 
@@ -77,6 +78,7 @@ class Problem:
     rho0: float = 1.0
     force: tuple = (0.0, 0.0, 0.0)
     wall_u: tuple = (0.0, 0.0, 0.0)
+    rho_b: float | None = None  # density of PRESSURE boundaries; None = rho0
     _c: _Problem = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -90,6 +92,7 @@ class Problem:
         c.rho0 = float(self.rho0)
         c.force[:] = [float(v) for v in self.force]
         c.wall_u[:] = [float(v) for v in self.wall_u]
+        c.rho_b = float(self.rho0 if self.rho_b is None else self.rho_b)
         self._c = c
         if self.flags is not None:
             nx, ny, nz = self.dims

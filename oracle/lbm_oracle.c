@@ -40,7 +40,7 @@
 
 #define ORC_Q 19
 
-enum { ORC_FLUID = 0, ORC_NOSLIP = 1, ORC_MOVING = 2 };
+enum { ORC_FLUID = 0, ORC_NOSLIP = 1, ORC_MOVING = 2, ORC_PRESSURE = 3 };
 enum { ORC_BGK = 0, ORC_TRT = 1 };
 
 /* D3Q19 velocities: 0 rest, 1..6 the axis neighbours, 7..18 the twelve
@@ -78,7 +78,15 @@ typedef struct {
     double rho0;       /* reference density */
     double force[3];   /* body force density F */
     double wall_u[3];  /* velocity of every ORC_MOVING wall */
+    double rho_b;      /* density of every ORC_PRESSURE boundary */
 } orc_problem;
+
+/* Pressure boundary (not in the paper; its "arbitrary boundary conditions"
+ * are future work there): anti-bounce-back without the velocity correction.
+ * A population leaving the fluid towards an ORC_PRESSURE node returns as
+ * f_ibar = -f*_i + 2 w_i rho_b, which holds the density halfway between the
+ * fluid node and the boundary node at rho_b up to O(u^2).  In shifted
+ * variables (f~ = f - w rho0): f~_ibar = -f~*_i + 2 w_i (rho_b - rho0). */
 
 /* ------------------------------------------------------------------ */
 /* exported lattice and equilibrium, so that tests can pin them        */
@@ -215,6 +223,8 @@ void orc_step(const orc_problem *p, const uint8_t *flags, const double *src, dou
                     int kind = classify(p, flags, x - E[i][0], y - E[i][1], z - E[i][2], &s);
                     if (kind == ORC_FLUID) {
                         f[i] = src[i * N + s];
+                    } else if (kind == ORC_PRESSURE) {
+                        f[i] = -src[opposite(i) * N + c] + 2.0 * weight(i) * (p->rho_b - p->rho0);
                     } else {
                         double bb = src[opposite(i) * N + c];
                         if (kind == ORC_MOVING) {
@@ -271,6 +281,8 @@ void orc_step_cells(const orc_problem *p, const uint8_t *flags, const double *sr
             int kind = classify(p, flags, x - E[i][0], y - E[i][1], z - E[i][2], &s);
             if (kind == ORC_FLUID) {
                 f[i] = src[i * N + s];
+            } else if (kind == ORC_PRESSURE) {
+                f[i] = -src[opposite(i) * N + c] + 2.0 * weight(i) * (p->rho_b - p->rho0);
             } else {
                 double bb = src[opposite(i) * N + c];
                 if (kind == ORC_MOVING) {
@@ -426,6 +438,9 @@ void orc_push_step(const orc_problem *p, const uint8_t *flags, const double *src
                     int kind = push_target(p, flags, at, &t);
                     if (kind == ORC_FLUID) {
                         recv[i * N + t] = g;
+                    } else if (kind == ORC_PRESSURE) {
+                        /* anti-bounce-back: the reflected population is 2 w rho_b - g */
+                        recv[opposite(i) * N + c] = 2.0 * weight(i) * p->rho_b - g;
                     } else {
                         int k = opposite(i);
                         double ew = E[k][0] * p->wall_u[0] + E[k][1] * p->wall_u[1] +

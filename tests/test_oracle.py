@@ -276,6 +276,88 @@ def test_pull_step_matches_independent_push_step(orc, seed):
         f = a
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_pull_step_matches_push_step_with_pressure_boundaries(orc, seed):
+    """The same brute force with pressure cells and faces (anti-bounce-back,
+    random rho_b): the pull rule in shifted variables equals the push rule
+    2 w rho_b - f* written separately in unshifted ones."""
+    rng = np.random.default_rng(300 + seed)
+    dims = tuple(int(v) for v in rng.integers(3, 6, 3))
+    fl = _random_flags(rng, dims, 0.25)
+    fl[(fl != 0) & (rng.random(fl.shape) < 0.4)] = orc.PRESSURE
+    p = orc.Problem(dims=dims, tau=float(rng.uniform(0.55, 1.5)), flags=fl,
+                    periodic=tuple(int(v) for v in rng.integers(0, 2, 3)),
+                    face_bc=tuple(int(v) for v in rng.integers(1, 4, 6)),
+                    collision=int(seed % 2), magic=float(rng.uniform(0.05, 0.3)),
+                    force=tuple(rng.uniform(-1e-3, 1e-3, 3)),
+                    wall_u=tuple(rng.uniform(-0.05, 0.05, 3)), rho_b=float(rng.uniform(0.99, 1.01)))
+    assert (p.flags == orc.PRESSURE).any()
+    f = rng.uniform(-1e-2, 1e-2, (19,) + dims[::-1]) * (p.flags == 0)
+    for _ in range(3):
+        a = orc.step(p, f)
+        b = orc.push_step(p, f)
+        assert np.isfinite(b).all()
+        assert np.abs(a - b).max() < 1e-14
+        f = a
+
+
+def test_velocity_inlet_pressure_outlet_channel(orc):
+    """A velocity inlet (a moving-wall face at -x, Ladd bounce-back) and a
+    pressure outlet (anti-bounce-back at +x, rho_b = rho0) on a channel with
+    walls at -y/+y: the steady state carries the same mass flux through every
+    cross-section, develops the Poiseuille profile 6 U_mean y (H - y) / H^2 and
+    the density gradient -36 nu rho0 U_mean / H^2 (dp/dx = -12 mu U_mean / H^2,
+    p = rho / 3), and the density next to the outlet is rho_b up to half a
+    cell of that gradient."""
+    orc.set_threads(os.cpu_count() or 1)
+    nx, H, U, tau = 48, 12, 0.01, 0.8
+    nu = (tau - 0.5) / 3
+    p = orc.Problem(dims=(nx, H, 1), tau=tau, periodic=(0, 0, 1),
+                    face_bc=(orc.MOVING, orc.PRESSURE, 1, 1, 1, 1), wall_u=(U, 0, 0), rho_b=1.0)
+    f = orc.zeros(p)
+    prev = None
+    for _ in range(60):
+        f = orc.run(p, f, 500)
+        rho, u = orc.macroscopic(p, f)
+        if prev is not None and np.abs(u - prev).max() < 1e-12:
+            break
+        prev = u
+    orc.set_threads(1)
+    flux = u[0].sum(axis=(0, 1))  # per x, summed over y and z
+    assert np.abs(flux / flux.mean() - 1).max() < 1e-9
+    U_mean = flux.mean() / H
+    y = np.arange(H) + 0.5
+    prof = u[0, 0, :, nx // 2]
+    assert np.abs(prof - 6 * U_mean * y * (H - y) / H**2).max() < 1e-2 * prof.max()
+    grad = np.gradient(rho[0, H // 2, :])[nx // 3: 2 * nx // 3].mean()
+    want = -36 * nu * U_mean / H**2
+    assert abs(grad / want - 1) < 2e-2
+    # the rule omits the velocity correction 2 w rho0 (4.5 (e.u)^2 - 1.5 u^2):
+    # the density it holds is rho_b up to O(rho0 u^2)
+    assert abs(rho[0, H // 2, -1] - (1.0 - 0.5 * grad)) < 6.0 * (1.5 * U_mean) ** 2
+
+
+def test_pressure_boundary_rest_state_is_a_fixed_point(orc):
+    """At rest every term of the anti-bounce-back rule is exact: the state
+    f~ = w drho_b (uniform density rho_b, u = 0) stays put to roundoff with
+    pressure faces and pressure cells, which fixes the rule's sign and its
+    factor 2 (any other would drive the density away from rho_b)."""
+    rng = np.random.default_rng(8)
+    dims = (9, 7, 5)
+    fl = np.zeros(dims[::-1], np.uint8)
+    fl[(rng.random(fl.shape) < 0.1)] = orc.PRESSURE
+    rho_b = 1.004
+    p = orc.Problem(dims=dims, tau=0.7, flags=fl, periodic=(0, 0, 1), face_bc=(3, 3, 1, 3, 1, 1),
+                    collision=orc.TRT, rho_b=rho_b)
+    _, w, _ = orc.lattice()
+    f = (w[:, None, None, None] * (rho_b - 1.0)) * (fl == 0)
+    g = orc.run(p, f.copy(), 50)
+    assert np.abs(g - f).max() < 1e-16
+    # the wrong sign or factor would not hold it
+    rho, u = orc.macroscopic(p, g)
+    assert np.abs(rho[fl == 0] - rho_b).max() < 1e-15 and np.abs(u).max() < 1e-16
+
+
 def test_step_cells_and_macroscopic_agree_with_step(orc):
     rng = np.random.default_rng(21)
     dims = (6, 5, 7)
