@@ -63,8 +63,14 @@ typedef enum {
     LBM_ENUMERIC = -5   /* a NaN or Inf was found where the call checks for it */
 } lbm_status;
 
-/* Per-cell flag values (one uint8 per interior cell). */
-enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_MOVING = 2 };
+/* Per-cell flag values (one uint8 per interior cell).  LBM_PRESSURE (not in
+ * the paper, whose "arbitrary boundary conditions" are future work there): a
+ * pressure boundary; a population that would stream into it returns by
+ * anti-bounce-back, f~_ibar(x) = -f~*_i(x) + 2 w_i (rho_b - rho0), which
+ * holds the density rho_b halfway between x and the boundary node (up to the
+ * omitted O(rho0 u^2) velocity correction).  A velocity inlet is an
+ * LBM_MOVING face with wall_u the inlet velocity (Ladd bounce-back). */
+enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_MOVING = 2, LBM_PRESSURE = 3 };
 /* Collision operators: single relaxation time of Eq. (1), or two relaxation times. */
 enum { LBM_BGK = 0, LBM_TRT = 1 };
 /* PDF storage formats.  Arithmetic is FP32 for the first three and FP64 for
@@ -80,7 +86,8 @@ typedef struct {
     double wall_u[3];     /* velocity of every LBM_MOVING wall or cell; default 0 */
     int periodic[3];      /* 1 = periodic along x / y / z; default 0 */
     int face_bc[6];       /* wall kind beyond the -x,+x,-y,+y,-z,+z faces of a
-                             non-periodic axis: LBM_NOSLIP (default) or LBM_MOVING.
+                             non-periodic axis: LBM_NOSLIP (default), LBM_MOVING or
+                             LBM_PRESSURE.
                              Edge and corner cells of the wall shell shared by two
                              walls rest (LBM_NOSLIP). */
     int storage;          /* LBM_F32 (default), LBM_F16S, LBM_BF16S, LBM_F64 */
@@ -100,6 +107,7 @@ typedef struct {
                              LBM_KERNEL_TMA (LBM_EINVAL at create when not applicable) */
     int debug_flags;      /* 0; LBM_DEBUG_DROP_STAGE makes the TMA sweep skip one staged
                              load so its bounded waits expire (failure-path tests) */
+    double rho_b;         /* density of every LBM_PRESSURE boundary; 0 (default) = rho0 */
 } lbm_params;
 
 enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_REGISTER = 1, LBM_KERNEL_TMA = 2 };
@@ -116,7 +124,7 @@ void lbm_default_params(lbm_params *p);
  *   dims, block_dims : host int[3]; dims[a] must be a positive multiple of
  *                      block_dims[a] (else LBM_EINVAL).
  *   tau              : relaxation time, > 1/2 (else LBM_EINVAL); omega = 1/tau.
- *   flags            : host uint8[nx*ny*nz] with LBM_FLUID/NOSLIP/MOVING, x fastest,
+ *   flags            : host uint8[nx*ny*nz] with LBM_FLUID/NOSLIP/MOVING/PRESSURE, x fastest,
  *                      copied; NULL = all fluid.
  *   p                : host, may be NULL for defaults.
  *   out              : receives the context; NULL on failure.

@@ -309,7 +309,8 @@ int validate_params(const lbm_params &p)
     if (!(p.rho0 > 0) || !std::isfinite(p.rho0)) return 0;
     if (p.collision == LBM_TRT && !(p.magic > 0)) return 0;
     for (int f = 0; f < 6; ++f)
-        if (p.face_bc[f] != LBM_NOSLIP && p.face_bc[f] != LBM_MOVING) return 0;
+        if (p.face_bc[f] != LBM_NOSLIP && p.face_bc[f] != LBM_MOVING && p.face_bc[f] != LBM_PRESSURE) return 0;
+    if (!(p.rho_b >= 0) || !std::isfinite(p.rho_b)) return 0;  // 0 = rho0
     double s = p.storage_scale;
     if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_TMA) return 0;
     int e2 = 0;
@@ -337,9 +338,11 @@ std::vector<char> make_consts(const lbm_ctx *c)
         }
         cc.omega_p = T(wp);
         cc.omega_m = T(wm);
+        const double rho_b = p.rho_b > 0.0 ? p.rho_b : p.rho0;
         for (int q = 0; q < Q; ++q) {
             const double eu = ex(q) * p.wall_u[0] + ey(q) * p.wall_u[1] + ez(q) * p.wall_u[2];
             cc.bbw[q] = T(s * 6.0 * wq(q) * p.rho0 * eu);
+            cc.bbp[q] = T(s * 2.0 * wq(q) * (rho_b - p.rho0));
         }
         cc.inv_s = T(1.0 / s);
         cc.rho0 = T(p.rho0);
@@ -614,9 +617,9 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                 const long long cidx =
                                     ((long long)(z + 1) * b.py + (y + 1)) * b.pxf + (x + OXF);
                                 uint8_t v = classify(p, s.dims, s.flags, b.gx + x, b.gy + y, b.gz + z);
-                                if (v > F_MOVING)
-                                    return fail(c, LBM_EINVAL, "flag value %d is not LBM_FLUID/NOSLIP/MOVING",
-                                                int(v));
+                                if (v > F_PRESSURE)
+                                    return fail(c, LBM_EINVAL,
+                                                "flag value %d is not LBM_FLUID/NOSLIP/MOVING/PRESSURE", int(v));
                                 f[cidx] = v;
                             }
                     const long long pxy = (long long)b.pxf * b.py;
@@ -633,6 +636,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                         f[cidx - (ex(q) + ey(q) * (long long)b.pxf + ez(q) * pxy)] & F_KIND;
                                     if (nk) m |= 1u << q;
                                     if (nk == F_MOVING) m |= L_MOVING;
+                                    if (nk == F_PRESSURE) m |= L_PRESSURE;
                                 }
                                 if (m) {
                                     f[cidx] |= F_NEAR;

@@ -68,7 +68,7 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
     using S = typename Tr::S;
     if (MASK) {
         const uint32_t lm = __ldg(a.links + b.cell_base + cf);
-        const bool mv = (lm & L_MOVING) != 0;
+        const bool mv = (lm & (L_MOVING | L_PRESSURE)) != 0;
         v[0] = Tr::ld(src + c);
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
@@ -78,7 +78,8 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
             float w = Tr::ld(pa);
             if (mv && bq) {
                 const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                if ((nf & F_KIND) == F_MOVING) w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
+                w = wall_pull<float>(w, nf & F_KIND, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]),
+                                     UNIF ? a.kf.bbp[q] : __ldg(&cc->bbp[q]));
             }
             v[q] = w;
         }
@@ -87,9 +88,11 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
         for (int q = 0; q < Q; ++q) {
             const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
             if (nf & F_KIND) {
-                float w = Tr::ld(src + (opp(q) * G + c));
-                if ((nf & F_KIND) == F_MOVING) w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
-                v[q] = w;
+                const float g = Tr::ld(src + (opp(q) * G + c));
+                v[q] = (nf & F_KIND) == F_NOSLIP ? g
+                                                 : wall_pull<float>(g, nf & F_KIND,
+                                                                    UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]),
+                                                                    UNIF ? a.kf.bbp[q] : __ldg(&cc->bbp[q]));
             } else {
                 const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
                 v[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));

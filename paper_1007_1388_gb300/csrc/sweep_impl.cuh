@@ -109,10 +109,12 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                 const int n = c - (ex(q) + ey(q) * px + ez(q) * pxy);
                 const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                 if (nf & F_KIND) {
-                    T v = Tr::ld(src + (opp(q) * G + c));
-                    if ((nf & F_KIND) == F_MOVING)
-                        v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
-                    f[q] = v;
+                    const T g = Tr::ld(src + (opp(q) * G + c));
+                    f[q] = (nf & F_KIND) == F_NOSLIP
+                               ? g
+                               : wall_pull<T>(g, nf & F_KIND,
+                                              UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]),
+                                              UNIF ? param_consts<T>(a).bbp[q] : __ldg(&cc->bbp[q]));
                 } else {
                     const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
                     f[q] = Tr::ld(s + (q * G + n));
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
             }
         } else {
             const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
-            const bool mv = (lm & L_MOVING) != 0;
+            const bool mv = (lm & (L_MOVING | L_PRESSURE)) != 0;
             f[0] = Tr::ld(src + c);
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
@@ -131,8 +133,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                 T v = Tr::ld(pa);
                 if (mv && bq) {
                     const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                    if ((nf & F_KIND) == F_MOVING)
-                        v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
+                    v = wall_pull<T>(v, nf & F_KIND, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]),
+                                     UNIF ? param_consts<T>(a).bbp[q] : __ldg(&cc->bbp[q]));
                 }
                 f[q] = v;
             }

@@ -26,6 +26,7 @@ enum : uint8_t {
     F_FLUID = 0,
     F_NOSLIP = 1,
     F_MOVING = 2,
+    F_PRESSURE = 3,  // pressure boundary (anti-bounce-back to density rho_b)
     F_KIND = 3,   // mask of the kind bits
     F_NEAR = 4,   // fluid cell with at least one wall / solid neighbour
 };
@@ -33,8 +34,10 @@ enum : uint8_t {
 // Link mask of a fluid cell with F_NEAR set (one uint32 per flag cell, same
 // indexing as the flags): bit q (1..18) is set when the pull source x - e_q is
 // a wall or solid cell, so that g_q comes from half-way bounce-back; bit
-// L_MOVING when at least one of those sources is a moving wall.
+// L_MOVING when at least one of those sources is a moving wall, L_PRESSURE
+// when one is a pressure boundary.
 constexpr uint32_t L_MOVING = 1u << 31;
+constexpr uint32_t L_PRESSURE = 1u << 30;
 
 // Layout of a Block.  PDF planes store (ny+2)(nz+2) rows of px cells: the
 // interior x range [0, nx) padded only up to a 32-byte multiple, plus one ghost
@@ -84,6 +87,7 @@ struct CollideConsts {
     T omega_p, omega_m;
     T Fs[3];                  // s F
     T bbw[Q];                 // s * 6 w_q rho0 (e_q . u_wall)
+    T bbp[Q];                 // s * 2 w_q (rho_b - rho0): anti-bounce-back of pressure boundaries
     T inv_s, rho0;
     T zero;                   // 0
     T nc15, c45;              // -1.5 rho0s, 4.5 rho0s

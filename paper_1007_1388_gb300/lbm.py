@@ -18,7 +18,7 @@ import numpy as np
 
 Q = 19
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_ENUMERIC = 0, -1, -2, -3, -4, -5
-LBM_FLUID, LBM_NOSLIP, LBM_MOVING = 0, 1, 2
+LBM_FLUID, LBM_NOSLIP, LBM_MOVING, LBM_PRESSURE = 0, 1, 2, 3
 LBM_BGK, LBM_TRT = 0, 1
 LBM_F32, LBM_F16S, LBM_BF16S, LBM_F64 = 0, 1, 2, 3
 LBM_KERNEL_AUTO, LBM_KERNEL_REGISTER, LBM_KERNEL_TMA = 0, 1, 2
@@ -46,6 +46,7 @@ class lbm_params(ctypes.Structure):
         ("graph_steps", ctypes.c_int),
         ("kernel", ctypes.c_int),
         ("debug_flags", ctypes.c_int),
+        ("rho_b", ctypes.c_double),
     ]
 
 
