@@ -203,9 +203,9 @@ def run_gpu(args):
         return 0
 
     def make(storage=L.LBM_F32, coll=L.LBM_BGK, **extra):
-        p = L.make_params(collision=coll, force=(args.force, 0, 0), storage=storage,
-                          **W.channel_bc(), **extra)
-        return L.lbm_create((n, n, n), (b, b, b), TAU, None, p)
+        kw = dict(collision=coll, force=(args.force, 0, 0), storage=storage, **W.channel_bc())
+        kw.update(extra)
+        return L.lbm_create((n, n, n), (b, b, b), TAU, None, L.make_params(**kw))
 
     main_kw = {}
     if args.storage:
@@ -298,9 +298,13 @@ def run_gpu(args):
         for name, kw in [("trt_f32", dict(coll=L.LBM_TRT)),
                          ("bgk_f16s", dict(storage=L.LBM_F16S, storage_scale=256.0)),
                          ("bgk_bf16s", dict(storage=L.LBM_BF16S)),
-                         ("bgk_f64", dict(storage=L.LBM_F64))]:
+                         ("bgk_f64", dict(storage=L.LBM_F64)),
+                         # velocity inlet (moving-wall face) at -x, pressure outlet at +x
+                         ("bgk_inlet_outlet_f32", dict(periodic=(0, 0, 1), face_bc=(2, 3, 1, 1, 1, 1),
+                                                       wall_u=(0.01, 0, 0), force=(0, 0, 0), rho_b=1.0))]:
             c = make(**kw)
-            L.lbm_autotune(c, None)
+            if not args.no_autotune:
+                L.lbm_autotune(c, None)
             L.lbm_step(c, 5)
             L.lbm_profile_enable(c, True)
             L.lbm_profile_read(c)

@@ -55,14 +55,6 @@ __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
 
-// The value pulled across a wall link from the cell's own stored opposite
-// population g: half-way bounce-back (plus the moving-wall term), or
-// anti-bounce-back towards a pressure boundary.  kind = the source's flag kind.
-template <typename T>
-__device__ __forceinline__ T wall_pull(T g, uint8_t kind, T bbw, T bbp)
-{
-    return kind == 2 ? vadd(g, bbw) : (kind == 3 ? vsub(bbp, g) : g);
-}
 __device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ F2 vadd(F2 a, F2 b)

@@ -106,6 +106,7 @@ struct lbm_ctx {
     std::vector<char> active;     // per instance: swept (1) or frozen (0)
     int minb = 4;  // register budget of the sweep (resident CTAs per SM)
     std::vector<char> h_consts;  // host copy of the per-instance CollideConsts
+    bool has_pressure = false;   // some cell or wall of the Patch is a pressure boundary
     // kernel choice and the TMA sweep's launch state
     int kernel = LBM_KERNEL_REGISTER;
     TmaMaps maps{};
@@ -338,11 +339,9 @@ std::vector<char> make_consts(const lbm_ctx *c)
         }
         cc.omega_p = T(wp);
         cc.omega_m = T(wm);
-        const double rho_b = p.rho_b > 0.0 ? p.rho_b : p.rho0;
         for (int q = 0; q < Q; ++q) {
             const double eu = ex(q) * p.wall_u[0] + ey(q) * p.wall_u[1] + ez(q) * p.wall_u[2];
             cc.bbw[q] = T(s * 6.0 * wq(q) * p.rho0 * eu);
-            cc.bbp[q] = T(s * 2.0 * wq(q) * (rho_b - p.rho0));
         }
         cc.inv_s = T(1.0 / s);
         cc.rho0 = T(p.rho0);
@@ -620,6 +619,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                 if (v > F_PRESSURE)
                                     return fail(c, LBM_EINVAL,
                                                 "flag value %d is not LBM_FLUID/NOSLIP/MOVING/PRESSURE", int(v));
+                                if (v == F_PRESSURE) c->has_pressure = true;
                                 f[cidx] = v;
                             }
                     const long long pxy = (long long)b.pxf * b.py;
@@ -845,6 +845,13 @@ SweepArgs sweep_args(const lbm_ctx *c, int from)
     a.grid = c->grid;
     a.minb = c->minb;
     a.unif = c->ninst == 1 ? 1 : 0;
+    {
+        const double sc = (c->storage == LBM_F16S || c->storage == LBM_BF16S) ? c->p.storage_scale : 1.0;
+        const double rho_b = c->p.rho_b > 0.0 ? c->p.rho_b : c->p.rho0;
+        a.pbd = 2.0 * sc * (rho_b - c->p.rho0);
+        a.pbf = float(a.pbd);
+        a.pres = c->has_pressure ? 1 : 0;
+    }
     if (a.unif) {
         if (c->storage == LBM_F64)
             std::memcpy(&a.kd, c->h_consts.data(), sizeof(a.kd));

@@ -58,7 +58,7 @@ template <> struct Pair<2> {
 
 // The 19 pulled values of one cell next to a wall (half-way bounce-back),
 // from its link mask (MASK) or its neighbours' flags.
-template <int ST, bool MASK, bool UNIF>
+template <int ST, bool MASK, bool UNIF, bool PRES>
 __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, const BlockGeom &b,
                                           const CollideConsts<float> *cc, const typename Traits<ST>::S *src,
                                           const typename Traits<ST>::S *srcm, const typename Traits<ST>::S *srcp,
@@ -68,7 +68,7 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
     using S = typename Tr::S;
     if (MASK) {
         const uint32_t lm = __ldg(a.links + b.cell_base + cf);
-        const bool mv = (lm & (L_MOVING | L_PRESSURE)) != 0;
+        const bool mv = (lm & (PRES ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
         v[0] = Tr::ld(src + c);
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
@@ -78,8 +78,10 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
             float w = Tr::ld(pa);
             if (mv && bq) {
                 const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                w = wall_pull<float>(w, nf & F_KIND, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]),
-                                     UNIF ? a.kf.bbp[q] : __ldg(&cc->bbp[q]));
+                if ((nf & F_KIND) == F_MOVING)
+                    w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
+                else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                    w = vsub(vmul(float(wq(q)), a.pbf), w);
             }
             v[q] = w;
         }
@@ -88,11 +90,12 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
         for (int q = 0; q < Q; ++q) {
             const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
             if (nf & F_KIND) {
-                const float g = Tr::ld(src + (opp(q) * G + c));
-                v[q] = (nf & F_KIND) == F_NOSLIP ? g
-                                                 : wall_pull<float>(g, nf & F_KIND,
-                                                                    UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]),
-                                                                    UNIF ? a.kf.bbp[q] : __ldg(&cc->bbp[q]));
+                float w = Tr::ld(src + (opp(q) * G + c));
+                if ((nf & F_KIND) == F_MOVING)
+                    w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
+                else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                    w = vsub(vmul(float(wq(q)), a.pbf), w);
+                v[q] = w;
             } else {
                 const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
                 v[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
@@ -116,7 +119,7 @@ __device__ __forceinline__ void pull_plain(float (&v)[Q], const typename Traits<
     }
 }
 
-template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK>
+template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK, bool PRES>
 __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant__ SweepArgs a)
 {
     using Tr = Traits<ST>;
@@ -178,11 +181,11 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
             float v0[Q], v1[Q];
             const S *srcp0 = src, *srcm1 = src;  // the inner faces of the pair stay in the Block
             if (near0)
-                pull_near<ST, MASK, UNIF>(v0, a, b, cc, src, srcm0, srcp0, fl, c, cf, px, pxy, pxf, pxyf, G);
+                pull_near<ST, MASK, UNIF, PRES>(v0, a, b, cc, src, srcm0, srcp0, fl, c, cf, px, pxy, pxf, pxyf, G);
             else
                 pull_plain<ST>(v0, src, srcm0, srcp0, c, px, pxy, G);
             if (near1)
-                pull_near<ST, MASK, UNIF>(v1, a, b, cc, src, srcm1, srcp1, fl, c + 1, cf + 1, px, pxy, pxf, pxyf, G);
+                pull_near<ST, MASK, UNIF, PRES>(v1, a, b, cc, src, srcm1, srcp1, fl, c + 1, cf + 1, px, pxy, pxf, pxyf, G);
             else
                 pull_plain<ST>(v1, src, srcm1, srcp1, c + 1, px, pxy, G);
 #pragma unroll
@@ -207,20 +210,30 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
     }
 }
 
-template <int ST, int MINB, bool UNIF, bool MASK>
-void launch_sweep2_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+template <int ST, int MINB, bool UNIF, bool MASK, bool PRES>
+void launch_sweep2_pres(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
     if (a.collision == 0) {
         if (a.forced)
-            sweep2_kernel<ST, 0, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 0, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
         else
-            sweep2_kernel<ST, 0, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 0, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
     } else {
         if (a.forced)
-            sweep2_kernel<ST, 1, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 1, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
         else
-            sweep2_kernel<ST, 1, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 1, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
     }
+}
+
+// pressure boundaries: a separate instantiation (see launch_sweep_mask)
+template <int ST, int MINB, bool UNIF, bool MASK>
+void launch_sweep2_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (a.pres)
+        launch_sweep2_pres<ST, MINB, UNIF, MASK, true>(a, grid, block, s);
+    else
+        launch_sweep2_pres<ST, MINB, UNIF, MASK, false>(a, grid, block, s);
 }
 
 template <int ST, int MINB>

@@ -30,6 +30,20 @@ namespace lbm {
 // UNIF: a single instance whose collision constants are kernel parameters.
 // MASK: near-wall cells read precomputed link masks under a warp vote (porous
 // media, where near-wall and interior cells share warps).
+// 2 s (rho_b - rho0) of the pressure boundaries in the arithmetic type
+template <typename T>
+__device__ __forceinline__ T param_pb(const SweepArgs &a);
+template <>
+__device__ __forceinline__ float param_pb<float>(const SweepArgs &a)
+{
+    return a.pbf;
+}
+template <>
+__device__ __forceinline__ double param_pb<double>(const SweepArgs &a)
+{
+    return a.pbd;
+}
+
 template <typename T>
 __device__ __forceinline__ const CollideConsts<T> &param_consts(const SweepArgs &a);
 template <>
@@ -43,7 +57,7 @@ __device__ __forceinline__ const CollideConsts<double> &param_consts<double>(con
     return a.kd;
 }
 
-template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK>
+template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK, bool PRES>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     using Tr = Traits<ST>;
@@ -109,12 +123,12 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                 const int n = c - (ex(q) + ey(q) * px + ez(q) * pxy);
                 const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                 if (nf & F_KIND) {
-                    const T g = Tr::ld(src + (opp(q) * G + c));
-                    f[q] = (nf & F_KIND) == F_NOSLIP
-                               ? g
-                               : wall_pull<T>(g, nf & F_KIND,
-                                              UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]),
-                                              UNIF ? param_consts<T>(a).bbp[q] : __ldg(&cc->bbp[q]));
+                    T v = Tr::ld(src + (opp(q) * G + c));
+                    if ((nf & F_KIND) == F_MOVING)
+                        v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
+                    else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                        v = vsub(vmul(T(wq(q)), param_pb<T>(a)), v);
+                    f[q] = v;
                 } else {
                     const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
                     f[q] = Tr::ld(s + (q * G + n));
@@ -122,7 +136,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
             }
         } else {
             const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
-            const bool mv = (lm & (L_MOVING | L_PRESSURE)) != 0;
+            const bool mv = (lm & (PRES ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
             f[0] = Tr::ld(src + c);
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
@@ -133,8 +147,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                 T v = Tr::ld(pa);
                 if (mv && bq) {
                     const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                    v = wall_pull<T>(v, nf & F_KIND, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]),
-                                     UNIF ? param_consts<T>(a).bbp[q] : __ldg(&cc->bbp[q]));
+                    if ((nf & F_KIND) == F_MOVING)
+                        v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
+                    else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                        v = vsub(vmul(T(wq(q)), param_pb<T>(a)), v);
                 }
                 f[q] = v;
             }
@@ -148,20 +164,32 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
     }
 }
 
-template <int ST, int MINB, bool UNIF, bool MASK>
-void launch_sweep_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+template <int ST, int MINB, bool UNIF, bool MASK, bool PRES>
+void launch_sweep_pres(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
     if (a.collision == 0) {
         if (a.forced)
-            sweep_kernel<ST, 0, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 0, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
         else
-            sweep_kernel<ST, 0, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 0, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
     } else {
         if (a.forced)
-            sweep_kernel<ST, 1, true, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 1, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
         else
-            sweep_kernel<ST, 1, false, MINB, UNIF, MASK><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 1, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
     }
+}
+
+// Pressure boundaries are a separate instantiation, so that the kernels of
+// Patches without them keep the near-wall code they had (an extra branch
+// there costs the 16-bit sweeps their load batching).
+template <int ST, int MINB, bool UNIF, bool MASK>
+void launch_sweep_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (a.pres)
+        launch_sweep_pres<ST, MINB, UNIF, MASK, true>(a, grid, block, s);
+    else
+        launch_sweep_pres<ST, MINB, UNIF, MASK, false>(a, grid, block, s);
 }
 
 template <int ST, int MINB, bool UNIF>

@@ -345,10 +345,12 @@ __global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>:
                         if (!(own & F_NEAR)) continue;
                         const uint8_t nf = fl[cf + k - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                         if (nf & F_KIND) {
-                            const float g = Tr::ld(src + (opp(q) * G + c + k));
-                            v[k] = (nf & F_KIND) == F_NOSLIP
-                                       ? g
-                                       : wall_pull<float>(g, nf & F_KIND, ta.a.kf.bbw[q], ta.a.kf.bbp[q]);
+                            float w = Tr::ld(src + (opp(q) * G + c + k));
+                            if ((nf & F_KIND) == F_MOVING)
+                                w = vadd(w, ta.a.kf.bbw[q]);
+                            else if ((nf & F_KIND) == F_PRESSURE)
+                                w = vsub(vmul(float(wq(q)), ta.a.pbf), w);
+                            v[k] = w;
                         }
                     }
                     f[q] = f2_pack(v[0], v[1]);

@@ -87,7 +87,6 @@ struct CollideConsts {
     T omega_p, omega_m;
     T Fs[3];                  // s F
     T bbw[Q];                 // s * 6 w_q rho0 (e_q . u_wall)
-    T bbp[Q];                 // s * 2 w_q (rho_b - rho0): anti-bounce-back of pressure boundaries
     T inv_s, rho0;
     T zero;                   // 0
     T nc15, c45;              // -1.5 rho0s, 4.5 rho0s
@@ -131,6 +130,11 @@ struct SweepArgs {
                               // arithmetic) or kd (FP64) and reach the kernel as parameters
     CollideConsts<float> kf;
     CollideConsts<double> kd;
+    // pressure boundaries: 2 s (rho_b - rho0) (one value per context); the
+    // anti-bounce-back term of direction q is w_q times this
+    float pbf;
+    double pbd;
+    int pres;                 // 1: the Patch has pressure boundaries (kernels built for them)
 };
 
 }  // namespace lbm
