@@ -64,8 +64,8 @@ typedef enum {
 } lbm_status;
 
 /* Per-cell flag values (one uint8 per interior cell).  LBM_PRESSURE (not in
- * the paper, whose "arbitrary boundary conditions" are future work there): a
- * pressure boundary; a population that would stream into it returns by
+ * the paper, which leaves further boundary conditions on the GPU to future
+ * work, Sec. 6): a pressure boundary; a population that would stream into it returns by
  * anti-bounce-back, f~_ibar(x) = -f~*_i(x) + 2 w_i (rho_b - rho0), which
  * holds the density rho_b halfway between x and the boundary node (up to the
  * omitted O(rho0 u^2) velocity correction).  A velocity inlet is an

@@ -81,8 +81,9 @@ typedef struct {
     double rho_b;      /* density of every ORC_PRESSURE boundary */
 } orc_problem;
 
-/* Pressure boundary (not in the paper; its "arbitrary boundary conditions"
- * are future work there): anti-bounce-back without the velocity correction.
+/* Pressure boundary (not in the paper, which leaves further boundary
+ * conditions to future work, Sec. 6): anti-bounce-back without the velocity
+ * correction.
  * A population leaving the fluid towards an ORC_PRESSURE node returns as
  * f_ibar = -f*_i + 2 w_i rho_b, which holds the density halfway between the
  * fluid node and the boundary node at rho_b up to O(u^2).  In shifted
