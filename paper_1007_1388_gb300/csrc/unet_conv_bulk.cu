@@ -87,6 +87,7 @@ __device__ __forceinline__ const bf16 *group_base(const bf16 *s0, const bf16 *s1
     return grp < g0 ? s0 + (long long)grp * ptot * 8 : s1 + (long long)(grp - g0) * ptot * 8;
 }
 
+template <int T>
 __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_constant__ ConvBulkArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
     __shared__ uint32_t tslot;
     __shared__ int s_ok[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int cin = a.c0 + a.c1, cout = a.cout, T = a.tiles, nks = cin >> 4, g0 = a.c0 >> 3;
+    const int cin = a.c0 + a.c1, cout = a.cout, nks = cin >> 4, g0 = a.c0 >> 3;
     const ConvPlan cp = conv_plan(a.g, cin, cout, T);
     const Planar P = planar_of(a.g);
     const int nx = 1 << a.g.lx, ny = 1 << a.g.ly, nz = 1 << a.g.lz;
@@ -190,12 +191,15 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
                 const uint32_t wb = cp.resident ? umma::smem_addr(wsm) + uint32_t(k * cp.wstage) : base + uint32_t(cp.slab);
                 const uint64_t a0 = umma::sdesc(base, uint32_t(cp.L * 16), 128);
                 const uint64_t b0 = umma::sdesc(wb, uint32_t(3 * cout * 16), 128);
+#pragma unroll
                 for (int pr = 0; pr < 9; ++pr) {
                     const int dz = pr / 3, dy = pr - 3 * dz;
+#pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const uint64_t ad = a0 + uint64_t(dz * 2 * cp.L + dy * int(P.sy) + d);
                         const uint64_t bd = b0 + uint64_t(pr * 6 * cout + d * cout);
                         const uint32_t accumulate = (k > 0 || pr > 0 || d > 0) ? 1u : 0u;
+#pragma unroll
                         for (int i = 0; i < T; ++i)
                             umma::mma_bf16(acc + uint32_t(i * cout), ad + uint64_t(i * 128), bd, idesc, accumulate);
                     }
@@ -293,6 +297,7 @@ __global__ void __launch_bounds__(CTHREADS, 1) conv3_bulk_kernel(const __grid_co
     if (warp == 0) umma::tmem_dealloc(tmem, uint32_t(cp.tcols));
 }
 
+template <int RUN>
 __global__ void __launch_bounds__(WTHREADS, 1) wgrad_bulk_kernel(const __grid_constant__ WgradBulkArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) wgrad_bulk_kernel(const __grid_co
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cin = a.c0 + a.c1, cout = a.cout, g0 = a.c0 >> 3, NS = a.stages;
-    const int run = a.run, slot = run * 16;  // 8 channels x run positions
+    constexpr int run = RUN, slot = RUN * 16;  // 8 channels x run positions
     const int abytes = 16 * slot, sbytes = abytes + (cout >> 3) * slot;
     uint32_t tcols = 32;
     while (tcols < uint32_t(cout)) tcols <<= 1;
@@ -375,6 +380,7 @@ __global__ void __launch_bounds__(WTHREADS, 1) wgrad_bulk_kernel(const __grid_co
             }
             umma::fence_after();
             const uint32_t sa = umma::smem_addr(smem + s * sbytes), sb = sa + uint32_t(abytes);
+#pragma unroll
             for (int j = 0; j < run / 16; ++j)
                 umma::mma_bf16(tmem, umma::sdesc(sa + j * 256, 128, uint32_t(slot)),
                                umma::sdesc(sb + j * 256, 128, uint32_t(slot)), idesc, (c > 0 || j > 0) ? 1u : 0u);
@@ -490,14 +496,23 @@ cudaError_t launch_conv3_bulk(const ConvBulkArgs &a, cudaStream_t s)
         return cudaErrorInvalidValue;
     const size_t sm = conv3_bulk_smem(a.g, cin, a.cout, a.tiles);
     if (sm > size_t(kSmemBudget)) return cudaErrorInvalidValue;
-    static size_t current = 0;
-    cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(conv3_bulk_kernel), sm, current);
+    const void *fn = a.tiles == 4 ? reinterpret_cast<const void *>(conv3_bulk_kernel<4>)
+                     : a.tiles == 2 ? reinterpret_cast<const void *>(conv3_bulk_kernel<2>)
+                                    : reinterpret_cast<const void *>(conv3_bulk_kernel<1>);
+    if (a.tiles != 1 && a.tiles != 2 && a.tiles != 4) return cudaErrorInvalidValue;
+    static size_t current[3] = {0, 0, 0};
+    cudaError_t e = raise_smem_limit(fn, sm, current[a.tiles >> 1]);
     if (e != cudaSuccess) return e;
     const Planar P = planar_of(a.g);
     const long long span = 128ll * a.tiles;
     const long long items = ((1ll << a.g.lz) * P.sz + span - 1) / span * a.g.nb;
     const long long grid = items < sm_count() ? items : sm_count();
-    conv3_bulk_kernel<<<unsigned(grid), CTHREADS, sm, s>>>(a);
+    if (a.tiles == 4)
+        conv3_bulk_kernel<4><<<unsigned(grid), CTHREADS, sm, s>>>(a);
+    else if (a.tiles == 2)
+        conv3_bulk_kernel<2><<<unsigned(grid), CTHREADS, sm, s>>>(a);
+    else
+        conv3_bulk_kernel<1><<<unsigned(grid), CTHREADS, sm, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -511,12 +526,23 @@ cudaError_t launch_wgrad_bulk(const WgradBulkArgs &a, int nsplit, float *dw, cud
         a.rows_pad < 27 * cin || a.rows_pad % 128 || nsplit != wgrad_bulk_splits(a.g, a.pps) || a.g.lx < 1 ||
         a.g.ly < 1 || a.g.lz < 1 || a.g.lx > 8 || planar_of(a.g).ptot >= (1ll << 31))
         return cudaErrorInvalidValue;
-    static size_t current = 0;
+    if (a.run != 64 && a.run != 128 && a.run != 256) return cudaErrorInvalidValue;
+    const void *fn = a.run == 256 ? reinterpret_cast<const void *>(wgrad_bulk_kernel<256>)
+                     : a.run == 128 ? reinterpret_cast<const void *>(wgrad_bulk_kernel<128>)
+                                    : reinterpret_cast<const void *>(wgrad_bulk_kernel<64>);
+    static size_t current[3] = {0, 0, 0};
     const size_t sm = wgrad_bulk_smem(a.cout, a.run, a.stages);
-    cudaError_t e = raise_smem_limit(reinterpret_cast<const void *>(wgrad_bulk_kernel), sm, current);
+    cudaError_t e = raise_smem_limit(fn, sm, current[a.run == 256 ? 2 : (a.run == 128 ? 1 : 0)]);
     if (e != cudaSuccess) return e;
     const dim3 grid(unsigned(a.rows_pad / 128), unsigned(nsplit));
-    if (nsplit > 0) wgrad_bulk_kernel<<<grid, WTHREADS, sm, s>>>(a);
+    if (nsplit > 0) {
+        if (a.run == 256)
+            wgrad_bulk_kernel<256><<<grid, WTHREADS, sm, s>>>(a);
+        else if (a.run == 128)
+            wgrad_bulk_kernel<128><<<grid, WTHREADS, sm, s>>>(a);
+        else
+            wgrad_bulk_kernel<64><<<grid, WTHREADS, sm, s>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long n = 27ll * cin * a.cout;
