@@ -66,10 +66,12 @@ typedef enum {
 /* Per-cell flag values (one uint8 per interior cell).  LBM_PRESSURE (not in
  * the paper, which leaves further boundary conditions on the GPU to future
  * work, Sec. 6): a pressure boundary; a population that would stream into it returns by
- * anti-bounce-back, f~_ibar(x) = -f~*_i(x) + 2 w_i (rho_b - rho0), which
- * holds the density rho_b halfway between x and the boundary node (up to the
- * omitted O(rho0 u^2) velocity correction).  A velocity inlet is an
- * LBM_MOVING face with wall_u the inlet velocity (Ladd bounce-back). */
+ * anti-bounce-back with the velocity correction,
+ *   f~_ibar(x) = -f~*_i(x) + 2 w_i [(rho_b - rho0) + rho0 (4.5 (e_i.u_b)^2 - 1.5 u_b.u_b)],
+ * which holds the density rho_b halfway between x and the boundary node;
+ * u_b is the velocity of x's last collision, (sum_j e_j f~*_j(x) - F/2) / rho0
+ * from its stored populations.  A velocity inlet is an LBM_MOVING face with
+ * wall_u the inlet velocity (Ladd bounce-back). */
 enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_MOVING = 2, LBM_PRESSURE = 3 };
 /* Collision operators: single relaxation time of Eq. (1), or two relaxation times. */
 enum { LBM_BGK = 0, LBM_TRT = 1 };

@@ -82,12 +82,31 @@ typedef struct {
 } orc_problem;
 
 /* Pressure boundary (not in the paper, which leaves further boundary
- * conditions to future work, Sec. 6): anti-bounce-back without the velocity
- * correction.
- * A population leaving the fluid towards an ORC_PRESSURE node returns as
- * f_ibar = -f*_i + 2 w_i rho_b, which holds the density halfway between the
- * fluid node and the boundary node at rho_b up to O(u^2).  In shifted
- * variables (f~ = f - w rho0): f~_ibar = -f~*_i + 2 w_i (rho_b - rho0). */
+ * conditions to future work, Sec. 6): anti-bounce-back with the velocity
+ * correction.  A population leaving the fluid cell x towards an ORC_PRESSURE
+ * node returns as
+ *   f_ibar = -f*_i + 2 w_i [rho_b + rho0 (4.5 (e_i.u_b)^2 - 1.5 u_b^2)],
+ * twice the symmetric part of the equilibrium of Eq. (2) at (rho_b, u_b); it
+ * holds the density halfway between x and the boundary node at rho_b.  u_b
+ * is the velocity of cell x's last collision, read from its stored
+ * populations: rho0 u_b = sum_j e_j f~*_j(x) - F/2.  In shifted variables
+ * (f~ = f - w rho0): f~_ibar = -f~*_i + 2 w_i [(rho_b - rho0) + rho0 (...)]. */
+static void stored_velocity(const orc_problem *p, const double *src, long N, long c, double ub[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        double j = 0.0;
+        for (int q = 0; q < ORC_Q; ++q) j += E[q][a] * src[q * N + c];
+        ub[a] = (j - 0.5 * p->force[a]) / p->rho0;
+    }
+}
+
+/* the anti-bounce-back source of direction i for boundary velocity ub, shifted */
+static double abb_term(const orc_problem *p, int i, const double ub[3])
+{
+    double eu = E[i][0] * ub[0] + E[i][1] * ub[1] + E[i][2] * ub[2];
+    double usq = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+    return 2.0 * weight(i) * ((p->rho_b - p->rho0) + p->rho0 * (4.5 * eu * eu - 1.5 * usq));
+}
 
 /* ------------------------------------------------------------------ */
 /* exported lattice and equilibrium, so that tests can pin them        */
@@ -225,7 +244,9 @@ void orc_step(const orc_problem *p, const uint8_t *flags, const double *src, dou
                     if (kind == ORC_FLUID) {
                         f[i] = src[i * N + s];
                     } else if (kind == ORC_PRESSURE) {
-                        f[i] = -src[opposite(i) * N + c] + 2.0 * weight(i) * (p->rho_b - p->rho0);
+                        double ub[3];
+                        stored_velocity(p, src, N, c, ub);
+                        f[i] = -src[opposite(i) * N + c] + abb_term(p, i, ub);
                     } else {
                         double bb = src[opposite(i) * N + c];
                         if (kind == ORC_MOVING) {
@@ -283,7 +304,9 @@ void orc_step_cells(const orc_problem *p, const uint8_t *flags, const double *sr
             if (kind == ORC_FLUID) {
                 f[i] = src[i * N + s];
             } else if (kind == ORC_PRESSURE) {
-                f[i] = -src[opposite(i) * N + c] + 2.0 * weight(i) * (p->rho_b - p->rho0);
+                double ub[3];
+                stored_velocity(p, src, N, c, ub);
+                f[i] = -src[opposite(i) * N + c] + abb_term(p, i, ub);
             } else {
                 double bb = src[opposite(i) * N + c];
                 if (kind == ORC_MOVING) {
@@ -440,8 +463,21 @@ void orc_push_step(const orc_problem *p, const uint8_t *flags, const double *src
                     if (kind == ORC_FLUID) {
                         recv[i * N + t] = g;
                     } else if (kind == ORC_PRESSURE) {
-                        /* anti-bounce-back: the reflected population is 2 w rho_b - g */
-                        recv[opposite(i) * N + c] = 2.0 * weight(i) * p->rho_b - g;
+                        /* anti-bounce-back, unshifted: 2 w [rho_b + rho0 (4.5 (e.u)^2 - 1.5 u^2)] - g,
+                         * u the velocity this cell's stored populations carry */
+                        double jx = 0.0, jy = 0.0, jz = 0.0;
+                        for (int q = 0; q < ORC_Q; ++q) {
+                            double gq = src[q * N + c] + weight(q) * p->rho0;
+                            jx += E[q][0] * gq;
+                            jy += E[q][1] * gq;
+                            jz += E[q][2] * gq;
+                        }
+                        double ux = (jx - 0.5 * p->force[0]) / p->rho0, uy = (jy - 0.5 * p->force[1]) / p->rho0,
+                               uz = (jz - 0.5 * p->force[2]) / p->rho0;
+                        double eu = E[i][0] * ux + E[i][1] * uy + E[i][2] * uz;
+                        double usq = ux * ux + uy * uy + uz * uz;
+                        recv[opposite(i) * N + c] =
+                            2.0 * weight(i) * (p->rho_b + p->rho0 * (4.5 * eu * eu - 1.5 * usq)) - g;
                     } else {
                         int k = opposite(i);
                         double ew = E[k][0] * p->wall_u[0] + E[k][1] * p->wall_u[1] +

@@ -47,4 +47,77 @@ template <> struct Traits<3> {
     static __device__ __forceinline__ S from_t(T v) { return v; }
 };
 
+// ------------------------------------------------- pressure boundaries
+// Anti-bounce-back with the velocity correction, in scaled units: the value
+// pulled along e_q from a pressure node is
+//   g_q = w_q [pb + 9 s rho0 (e_q.u_b)^2 - 3 s rho0 u_b.u_b] - g*_opp(q)(x),
+// pb = 2 s (rho_b - rho0): twice the even part of the equilibrium (Eq. (2))
+// at (rho_b, u_b) minus the population that left x towards the node.  u_b is
+// the velocity of cell x's last collision, read back from its stored
+// populations: u_b = (sum_j e_j g*_j) ufac - uoff (the Guo half-force
+// removed from the post-collision momentum).  Every kernel goes through
+// these two functions, so all sweep variants round it identically.
+template <typename T>
+struct PresBC {
+    T P, ux, uy, uz, c9;  // P = pb - 3 s rho0 u_b.u_b, c9 = 9 s rho0
+};
+
+template <int ST, typename T>
+__device__ __forceinline__ PresBC<T> pres_setup(const typename Traits<ST>::S *src, int c, int G, T pb, T ufac,
+                                                T uox, T uoy, T uoz, T c45, T nc15)
+{
+    using Tr = Traits<ST>;
+    T jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const T g = Tr::ld(src + (q * G + c));
+        if (ex(q) > 0) jx = vadd(jx, g);
+        if (ex(q) < 0) jx = vsub(jx, g);
+        if (ey(q) > 0) jy = vadd(jy, g);
+        if (ey(q) < 0) jy = vsub(jy, g);
+        if (ez(q) > 0) jz = vadd(jz, g);
+        if (ez(q) < 0) jz = vsub(jz, g);
+    }
+    PresBC<T> r;
+    r.ux = vfma(jx, ufac, -uox);
+    r.uy = vfma(jy, ufac, -uoy);
+    r.uz = vfma(jz, ufac, -uoz);
+    const T usq = vfma(r.ux, r.ux, vfma(r.uy, r.uy, vmul(r.uz, r.uz)));
+    r.P = vfma(vadd(nc15, nc15), usq, pb);
+    r.c9 = vadd(c45, c45);
+    return r;
+}
+
+// g_q from the returning population g*_opp(q)(x); q is a constant after
+// the callers' loops are unrolled
+template <typename T>
+__device__ __forceinline__ T pres_pull(int q, const PresBC<T> &p, T g_opp)
+{
+    // e_q.u_b up to its sign (it enters squared): the first nonzero
+    // component of e_q taken positive, so q and opp(q) round alike
+    const int a = ex(q), b = ey(q), c = ez(q);
+    const int sg = a != 0 ? a : (b != 0 ? b : c);
+    T eu;
+    if (a != 0 && b != 0)
+        eu = b * sg > 0 ? vadd(p.ux, p.uy) : vsub(p.ux, p.uy);
+    else if (a != 0 && c != 0)
+        eu = c * sg > 0 ? vadd(p.ux, p.uz) : vsub(p.ux, p.uz);
+    else if (b != 0 && c != 0)
+        eu = c * sg > 0 ? vadd(p.uy, p.uz) : vsub(p.uy, p.uz);
+    else
+        eu = a != 0 ? p.ux : (b != 0 ? p.uy : p.uz);
+    return vsub(vmul(T(wq(q)), vfma(vmul(p.c9, eu), eu, p.P)), g_opp);
+}
+
+// the setup from the Patch's collision constants: kernel parameters for a
+// single instance (UNIF), else the instance's table entry
+template <int ST, bool UNIF, typename T>
+__device__ __forceinline__ PresBC<T> pres_cell(const CollideConsts<T> &kp, const CollideConsts<T> *kg, T pb,
+                                               const typename Traits<ST>::S *src, int c, int G)
+{
+    if (UNIF) return pres_setup<ST, T>(src, c, G, pb, kp.ufac, kp.uoff[0], kp.uoff[1], kp.uoff[2], kp.c45, kp.nc15);
+    return pres_setup<ST, T>(src, c, G, pb, __ldg(&kg->ufac), __ldg(&kg->uoff[0]), __ldg(&kg->uoff[1]),
+                             __ldg(&kg->uoff[2]), __ldg(&kg->c45), __ldg(&kg->nc15));
+}
+
 }  // namespace lbm

@@ -69,6 +69,8 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
     if (MASK) {
         const uint32_t lm = __ldg(a.links + b.cell_base + cf);
         const bool mv = (lm & (PRES ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
+        PresBC<float> pbc{};
+        if (PRES && (lm & L_PRESSURE)) pbc = pres_cell<ST, UNIF, float>(a.kf, cc, a.pbf, src, c, G);
         v[0] = Tr::ld(src + c);
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
@@ -81,11 +83,14 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
                 if ((nf & F_KIND) == F_MOVING)
                     w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
                 else if (PRES && (nf & F_KIND) == F_PRESSURE)
-                    w = vsub(vmul(float(wq(q)), a.pbf), w);
+                    w = pres_pull(q, pbc, w);
             }
             v[q] = w;
         }
     } else {
+        PresBC<float> pbc{};
+        if (PRES && (__ldg(a.links + b.cell_base + cf) & L_PRESSURE))
+            pbc = pres_cell<ST, UNIF, float>(a.kf, cc, a.pbf, src, c, G);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
@@ -94,7 +99,7 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
                 if ((nf & F_KIND) == F_MOVING)
                     w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
                 else if (PRES && (nf & F_KIND) == F_PRESSURE)
-                    w = vsub(vmul(float(wq(q)), a.pbf), w);
+                    w = pres_pull(q, pbc, w);
                 v[q] = w;
             } else {
                 const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);

@@ -30,7 +30,7 @@ namespace lbm {
 // UNIF: a single instance whose collision constants are kernel parameters.
 // MASK: near-wall cells read precomputed link masks under a warp vote (porous
 // media, where near-wall and interior cells share warps).
-// 2 s (rho_b - rho0) of the pressure boundaries in the arithmetic type
+// pb = 2 s (rho_b - rho0) of the pressure boundaries in the arithmetic type
 template <typename T>
 __device__ __forceinline__ T param_pb(const SweepArgs &a);
 template <>
@@ -118,6 +118,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                 f[q] = Tr::ld(s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
             }
         } else if (!MASK) {
+            PresBC<T> pbc{};
+            if (PRES && (__ldg(a.links + b.cell_base + cf) & L_PRESSURE))
+                pbc = pres_cell<ST, UNIF, T>(param_consts<T>(a), cc, param_pb<T>(a), src, c, G);
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const int n = c - (ex(q) + ey(q) * px + ez(q) * pxy);
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                     if ((nf & F_KIND) == F_MOVING)
                         v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
                     else if (PRES && (nf & F_KIND) == F_PRESSURE)
-                        v = vsub(vmul(T(wq(q)), param_pb<T>(a)), v);
+                        v = pres_pull(q, pbc, v);
                     f[q] = v;
                 } else {
                     const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
@@ -137,6 +140,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         } else {
             const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
             const bool mv = (lm & (PRES ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
+            PresBC<T> pbc{};
+            if (PRES && (lm & L_PRESSURE))
+                pbc = pres_cell<ST, UNIF, T>(param_consts<T>(a), cc, param_pb<T>(a), src, c, G);
             f[0] = Tr::ld(src + c);
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                     if ((nf & F_KIND) == F_MOVING)
                         v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
                     else if (PRES && (nf & F_KIND) == F_PRESSURE)
-                        v = vsub(vmul(T(wq(q)), param_pb<T>(a)), v);
+                        v = pres_pull(q, pbc, v);
                 }
                 f[q] = v;
             }

@@ -192,7 +192,7 @@ __device__ __forceinline__ void load_all(F2 (&f)[Q], const unsigned char *st, in
     if constexpr (q + 1 < Q) load_all<q + 1, ST, TX>(f, st, ty, x, hm, hp);
 }
 
-template <int ST, int COLL, bool FORCE, int TX>
+template <int ST, int COLL, bool FORCE, int TX, bool PRES>
 __global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>::MINB)
     sweep_tma_kernel(const __grid_constant__ TmaSweepArgs ta, const __grid_constant__ TmaMaps maps)
 {
@@ -335,6 +335,13 @@ __global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>:
             if ((fl0 | fl1) & F_NEAR) {
                 // half-way bounce-back, cell by cell, where the source is a wall or solid
                 const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
+                PresBC<float> pbc[2] = {};
+                if (PRES) {
+#pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        if (((k ? fl1 : fl0) & F_NEAR) && (__ldg(a.links + b.cell_base + cf + k) & L_PRESSURE))
+                            pbc[k] = pres_cell<ST, true, float>(a.kf, nullptr, a.pbf, src, c + k, G);
+                }
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     float v[2];
@@ -348,8 +355,8 @@ __global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>:
                             float w = Tr::ld(src + (opp(q) * G + c + k));
                             if ((nf & F_KIND) == F_MOVING)
                                 w = vadd(w, ta.a.kf.bbw[q]);
-                            else if ((nf & F_KIND) == F_PRESSURE)
-                                w = vsub(vmul(float(wq(q)), ta.a.pbf), w);
+                            else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                                w = pres_pull(q, pbc[k], w);
                             v[k] = w;
                         }
                     }
@@ -363,11 +370,11 @@ __global__ void __launch_bounds__(TmaLayout<ST, TX>::THREADS, TmaLayout<ST, TX>:
     }
 }
 
-template <int ST, int COLL, bool FORCE, int TX>
+template <int ST, int COLL, bool FORCE, int TX, bool PRES>
 cudaError_t launch_tma_inst(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s)
 {
     constexpr int smem = TmaLayout<ST, TX>::SMEM;
-    auto kern = sweep_tma_kernel<ST, COLL, FORCE, TX>;
+    auto kern = sweep_tma_kernel<ST, COLL, FORCE, TX, PRES>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -378,40 +385,49 @@ cudaError_t launch_tma_inst(const TmaSweepArgs &ta, const TmaMaps &maps, int gri
     return cudaGetLastError();
 }
 
-template <int ST, int COLL, bool FORCE, int TX>
+template <int ST, int COLL, bool FORCE, int TX, bool PRES>
 cudaError_t occupancy_tma_inst(int *n)
 {
     constexpr int smem = TmaLayout<ST, TX>::SMEM;
-    auto kern = sweep_tma_kernel<ST, COLL, FORCE, TX>;
+    auto kern = sweep_tma_kernel<ST, COLL, FORCE, TX, PRES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kern, TmaLayout<ST, TX>::THREADS, smem);
+}
+
+template <int ST, int COLL, bool FORCE, int TX, bool PRES>
+cudaError_t tma_inst(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s, int *occ)
+{
+    return occ ? occupancy_tma_inst<ST, COLL, FORCE, TX, PRES>(occ)
+               : launch_tma_inst<ST, COLL, FORCE, TX, PRES>(ta, maps, grid, s);
+}
+
+// pressure boundaries are a separate instantiation: their near-wall setup
+// would otherwise cost every TMA sweep registers
+template <int ST, int TX, bool PRES>
+cudaError_t tma_dispatch_pres(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s, int *occ)
+{
+    if (ta.a.collision == 0)
+        return ta.a.forced ? tma_inst<ST, 0, true, TX, PRES>(ta, maps, grid, s, occ)
+                           : tma_inst<ST, 0, false, TX, PRES>(ta, maps, grid, s, occ);
+    return ta.a.forced ? tma_inst<ST, 1, true, TX, PRES>(ta, maps, grid, s, occ)
+                       : tma_inst<ST, 1, false, TX, PRES>(ta, maps, grid, s, occ);
+}
+
+template <int ST, int TX>
+cudaError_t tma_dispatch(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s, int *occ)
+{
+    return ta.a.pres ? tma_dispatch_pres<ST, TX, true>(ta, maps, grid, s, occ)
+                     : tma_dispatch_pres<ST, TX, false>(ta, maps, grid, s, occ);
 }
 
 template <int ST>
 cudaError_t launch_sweep_tma_st(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s,
                                 int *occ)
 {
-    const int coll = ta.a.collision, forced = ta.a.forced;
-#define LBM_TMA_TX(TXV)                                                                              \
-    if (ta.nx == TXV) {                                                                             \
-        if (occ) {                                                                                  \
-            if (coll == 0)                                                                          \
-                return forced ? occupancy_tma_inst<ST, 0, true, TXV>(occ)                            \
-                              : occupancy_tma_inst<ST, 0, false, TXV>(occ);                          \
-            return forced ? occupancy_tma_inst<ST, 1, true, TXV>(occ)                                \
-                          : occupancy_tma_inst<ST, 1, false, TXV>(occ);                              \
-        }                                                                                           \
-        if (coll == 0)                                                                              \
-            return forced ? launch_tma_inst<ST, 0, true, TXV>(ta, maps, grid, s)                     \
-                          : launch_tma_inst<ST, 0, false, TXV>(ta, maps, grid, s);                   \
-        return forced ? launch_tma_inst<ST, 1, true, TXV>(ta, maps, grid, s)                         \
-                      : launch_tma_inst<ST, 1, false, TXV>(ta, maps, grid, s);                       \
-    }
-    LBM_TMA_TX(32)
-    LBM_TMA_TX(64)
-    LBM_TMA_TX(128)
-#undef LBM_TMA_TX
+    if (ta.nx == 32) return tma_dispatch<ST, 32>(ta, maps, grid, s, occ);
+    if (ta.nx == 64) return tma_dispatch<ST, 64>(ta, maps, grid, s, occ);
+    if (ta.nx == 128) return tma_dispatch<ST, 128>(ta, maps, grid, s, occ);
     return cudaErrorNotSupported;
 }
 

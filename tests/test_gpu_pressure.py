@@ -7,7 +7,9 @@
   thread, row tiles, runs, persistent grids, both near-wall strategies):
   bitwise equal, FP32 and shifted FP16;
 - a velocity-inlet / pressure-outlet channel split into Blocks: bitwise equal
-  to the single Block, and within 1e-5 of the oracle after 300 steps.
+  to the single Block, and within 1e-5 of the oracle after 300 steps;
+- a uniform flow through pressure faces and past pressure cells stays put
+  (the velocity correction makes it a fixed point of the rule).
 """
 import numpy as np
 import pytest
@@ -140,3 +142,24 @@ def test_inlet_outlet_channel_blocks_and_oracle(L):
     # the inlet drives the flow: mass enters and leaves through the x faces
     rho, u = oracle.macroscopic(p, ref)
     assert u[0].mean() > 1e-3
+
+
+@pytest.mark.parametrize("coll", [0, 1])
+def test_uniform_flow_through_pressure_boundaries_stays_put(L, coll):
+    rng = np.random.default_rng(9)
+    dims = (32, 12, 10)
+    flags = np.zeros(dims[::-1], np.uint8)
+    flags[rng.random(flags.shape) < 0.05] = 3
+    rho_b, u = 1.003, np.array([0.03, -0.02, 0.01])
+    e, w, _ = oracle.lattice()
+    eu = e @ u
+    feq = (w * ((rho_b - 1.0) + 3 * eu + 4.5 * eu**2 - 1.5 * u @ u)).astype(np.float32)
+    f0 = np.broadcast_to(feq[:, None, None, None], (19,) + dims[::-1]) * (flags == 0)
+    kw = dict(periodic=(0, 1, 1), face_bc=(3, 3, 1, 1, 1, 1), rho_b=rho_b, collision=coll)
+    ctx = L.lbm_create(dims, (16, 6, 10), 0.7, flags, L.make_params(**kw))
+    L.lbm_set_pdfs(ctx, f0)
+    L.lbm_step(ctx, 30)
+    got = _state(L, ctx, dims)
+    ctx.destroy()
+    # FP32 roundoff of the collision and the boundary term only
+    assert np.abs(got - f0).max() <= 2e-7
