@@ -110,9 +110,23 @@ typedef struct {
     int debug_flags;      /* 0; LBM_DEBUG_DROP_STAGE makes the TMA sweep skip one staged
                              load so its bounded waits expire (failure-path tests) */
     double rho_b;         /* density of every LBM_PRESSURE boundary; 0 (default) = rho0 */
+    int streaming;        /* LBM_STREAM_TWO_GRID (default): the pull of Sec. 3.2 from one
+                             PDF array into a second; LBM_STREAM_AA: one array updated in
+                             place (AA access pattern, half the PDF memory, the same bytes
+                             per cell update).  Steps alternate between a local step (each
+                             cell reads its own PDFs and writes them back into the opposite
+                             slots) and a step that pulls from and pushes to the neighbours;
+                             every even number of steps the array is in the natural layout
+                             and, with F32 storage, bitwise equal to the two-array state.
+                             At an odd time every query reads a gathered copy (a transient
+                             second array).  Single Patches only (not lbm_batch_create), the
+                             register sweep, one cell per thread; lbm_residual is not
+                             available (no previous state is kept: lbm_run_to_residual uses
+                             a velocity snapshot one step before each check instead). */
 } lbm_params;
 
 enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_REGISTER = 1, LBM_KERNEL_TMA = 2 };
+enum { LBM_STREAM_TWO_GRID = 0, LBM_STREAM_AA = 1 };
 enum { LBM_DEBUG_DROP_STAGE = 1 };
 
 typedef struct lbm_ctx lbm_ctx;
@@ -294,6 +308,8 @@ typedef struct {
                                  precomputed link masks under a warp vote */
     int pair;                 /* 1: the register sweep updates two neighbouring cells per
                                  thread (tile[0] then counts threads, each covering 2 cells) */
+    int streaming;            /* LBM_STREAM_TWO_GRID or LBM_STREAM_AA */
+    int aa_phase;             /* in place: 1 after an odd number of steps (swapped layout) */
 } lbm_info;
 int lbm_get_info(lbm_ctx *ctx, lbm_info *info);
 

@@ -107,6 +107,17 @@ struct lbm_ctx {
     int minb = 4;  // register budget of the sweep (resident CTAs per SM)
     std::vector<char> h_consts;  // host copy of the per-instance CollideConsts
     bool has_pressure = false;   // some cell or wall of the Patch is a pressure boundary
+    // in-place streaming (LBM_STREAM_AA): one PDF array; aa_phase 0 when it
+    // holds the state swapped in the cells' own slots (read through a slot
+    // remap), 1 after an odd number of steps, when it holds the state
+    // streamed (read back into a temporary array)
+    bool aa = false;
+    int aa_phase = 0;
+    size_t buf_bytes = 0;         // bytes of one PDF array
+    std::vector<XSlabF> aa_fwd;   // ghost rows <- neighbours' boundary rows, before the odd step
+    std::vector<XSlabF> aa_rev;   // neighbours' boundary rows <- ghost rows, after it
+    XSlabF *d_aa_fwd = nullptr;
+    XSlabF *d_aa_rev = nullptr;
     // kernel choice and the TMA sweep's launch state
     int kernel = LBM_KERNEL_REGISTER;
     TmaMaps maps{};
@@ -314,6 +325,7 @@ int validate_params(const lbm_params &p)
     if (!(p.rho_b >= 0) || !std::isfinite(p.rho_b)) return 0;  // 0 = rho0
     double s = p.storage_scale;
     if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_TMA) return 0;
+    if (p.streaming != LBM_STREAM_TWO_GRID && p.streaming != LBM_STREAM_AA) return 0;
     int e2 = 0;
     if (!(s > 0) || !std::isfinite(s) || std::frexp(s, &e2) != 0.5) return 0;  // power of two
     return 1;
@@ -550,6 +562,8 @@ int setup_tma(lbm_ctx *c)
     return LBM_OK;
 }
 
+cudaError_t enqueue_aa_prepare(const lbm_ctx *c);
+
 int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
 {
     const lbm_params &p = c->p;
@@ -558,6 +572,10 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     c->elem = p.storage == LBM_F32 ? 4 : (p.storage == LBM_F64 ? 8 : 2);
     c->forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
     for (int k = 0; k < c->ninst; ++k) c->iforce.insert(c->iforce.end(), p.force, p.force + 3);
+    c->aa = p.streaming == LBM_STREAM_AA;
+    if (c->aa && (c->ninst != 1 || p.kernel == LBM_KERNEL_TMA))
+        return fail(c, LBM_EINVAL, "in-place streaming (LBM_STREAM_AA) serves single Patches with the "
+                    "register sweep (not batches, not LBM_KERNEL_TMA)");
 
     if (p.stream) {
         c->stream = static_cast<cudaStream_t>(p.stream);
@@ -586,7 +604,10 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                     b.nx = s.bdims[0];
                     b.ny = s.bdims[1];
                     b.nz = s.bdims[2];
-                    b.px = round_up(b.nx, 32 / c->elem);
+                    // in place, two padding columns per row hold what the odd
+                    // step pushes through wall x faces (x = nx, and x = -1 as
+                    // the previous row's last column)
+                    b.px = round_up(b.nx + (c->aa ? 2 : 0), 32 / c->elem);
                     b.pxf = round_up(OXF + b.nx + 1, 16);
                     b.py = b.ny + 2;
                     b.G = plane_cells((long long)b.px * b.py * (b.nz + 2), c->elem);
@@ -720,9 +741,57 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                 const long long s0 = ((long long)(zs + 1) * bm.py + (ys + 1)) * bm.px;
                                 for (int q = 1; q < Q; ++q) {
                                     const int e[3] = {ex(q), ey(q), ez(q)};
-                                    bool into = true;
-                                    for (int a2 = 0; a2 < 3; ++a2)
+                                    bool into = true, out = true;
+                                    for (int a2 = 0; a2 < 3; ++a2) {
                                         if (n[a2] != 0 && e[a2] != -n[a2]) into = false;
+                                        if (n[a2] != 0 && e[a2] != n[a2]) out = false;
+                                    }
+                                    if (c->aa) {
+                                        // in place: the odd step reads and writes the directions
+                                        // leaving this Block through the face / edge
+                                        if (!out) continue;
+                                        // forward: into fluid ghost cells only (a wall or
+                                        // pressure node's slots hold what this Block's
+                                        // own cells stored there)
+                                        XSlabF fw{};
+                                        fw.len = bm.nx;
+                                        fw.rows = sl.rows;
+                                        fw.stride = sl.stride;
+                                        fw.dst = bm.pdf_base + (long long)q * bm.G + d0;
+                                        fw.src = bs.pdf_base + (long long)q * bs.G + s0;
+                                        fw.fstride = n1 != 0 && n2 == 0 ? (long long)bm.pxf * bm.py
+                                                     : (n2 != 0 && n1 == 0 ? bm.pxf : 0);
+                                        fw.fsrc = bm.cell_base + ((long long)(zg + 1) * bm.py + (yg + 1)) * bm.pxf + OXF;
+                                        c->aa_fwd.push_back(fw);
+                                        // reverse: only rows whose streaming cell (ghost - e_q)
+                                        // lies inside this Block along the slab's row axis
+                                        XSlabF rv{};
+                                        rv.len = bm.nx;
+                                        long long r0 = 0;  // first row
+                                        if (n1 != 0 && n2 == 0) {
+                                            r0 = std::max(0, e[2]);
+                                            rv.rows = bm.nz - std::abs(e[2]);
+                                            rv.stride = pxy;
+                                            rv.fstride = (long long)bm.pxf * bm.py;
+                                        } else if (n2 != 0 && n1 == 0) {
+                                            r0 = std::max(0, e[1]);
+                                            rv.rows = bm.ny - std::abs(e[1]);
+                                            rv.stride = bm.px;
+                                            rv.fstride = bm.pxf;
+                                        } else {
+                                            rv.rows = 1;
+                                        }
+                                        const long long roff = r0 * rv.stride;
+                                        rv.src = bm.pdf_base + (long long)q * bm.G + d0 + roff;
+                                        rv.dst = bs.pdf_base + (long long)q * bs.G + s0 + roff;
+                                        // flag of the streaming cell of element (row 0, x = 0)
+                                        const long long yw = (n1 != 0 ? yg : r0 * (n2 != 0)) - e[1];
+                                        const long long zw = (n2 != 0 ? zg : r0 * (n1 != 0)) - e[2];
+                                        rv.fsrc = bm.cell_base + ((zw + 1) * bm.py + (yw + 1)) * bm.pxf + OXF - e[0];
+                                        if (rv.rows > 0) c->aa_rev.push_back(rv);
+                                        c->exchange_pdfs += 2ll * sl.rows * bm.nx;
+                                        continue;
+                                    }
                                     if (!into) continue;
                                     sl.dst = bm.pdf_base + (long long)q * bm.G + d0;
                                     sl.src = bs.pdf_base + (long long)q * bs.G + s0;
@@ -738,15 +807,20 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
 
     // ---- device memory
     const size_t buf_bytes = size_t(pdf_base) * c->elem;
+    c->buf_bytes = buf_bytes;
     int rc;
     if ((rc = own(c, &c->buf[0], buf_bytes))) return rc;
-    if ((rc = own(c, &c->buf[1], buf_bytes))) return rc;
     CK(cudaMemsetAsync(c->buf[0], 0, buf_bytes, c->stream), "memset");
-    CK(cudaMemsetAsync(c->buf[1], 0, buf_bytes, c->stream), "memset");
+    if (!c->aa) {  // in place: one array
+        if ((rc = own(c, &c->buf[1], buf_bytes))) return rc;
+        CK(cudaMemsetAsync(c->buf[1], 0, buf_bytes, c->stream), "memset");
+    }
     if ((rc = upload(c, &c->d_flags, hflags))) return rc;
     if ((rc = upload(c, &c->d_links, hlinks))) return rc;
     if ((rc = upload(c, &c->d_blocks, c->blocks))) return rc;
     if ((rc = upload(c, &c->d_xslabs, c->xslabs))) return rc;
+    if ((rc = upload(c, &c->d_aa_fwd, c->aa_fwd))) return rc;
+    if ((rc = upload(c, &c->d_aa_rev, c->aa_rev))) return rc;
     std::vector<char> consts =
         c->storage == LBM_F64 ? make_consts<double>(c) : make_consts<float>(c);
     c->h_consts = consts;
@@ -777,7 +851,9 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
             w64 = w64 && (b.nx % 64 == 0);
             w32 = w32 && (b.nx % 32 == 0);
         }
-        if (even && w64) {
+        if (c->aa) {  // one cell per thread
+            if (!w32) flat = 256;
+        } else if (even && w64) {
             pair = 1;
             t[0] = 32;
             t[1] = 4;
@@ -794,17 +870,20 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                     "tile[0]*tile[1] <= 256", t[0], t[1]);
     if ((rc = set_sweep(c, t, flat, 0, pair))) return rc;
     // link masks pay where near-wall and interior cells share warps
-    c->mask = near_cells * 10 > c->fluid ? 1 : 0;
+    c->mask = !c->aa && near_cells * 10 > c->fluid ? 1 : 0;
     // the TMA sweep is set up wherever it applies (lbm_autotune may pick it);
     // it runs by default only when requested: the register sweep is faster
     // on GB300 for every workload measured so far
-    if (p.kernel != LBM_KERNEL_REGISTER && tma_applicable(c)) {
+    if (p.kernel != LBM_KERNEL_REGISTER && !c->aa && tma_applicable(c)) {
         if ((rc = setup_tma(c))) return rc;
         if (p.kernel == LBM_KERNEL_AUTO) c->kernel = LBM_KERNEL_REGISTER;
     } else if (p.kernel == LBM_KERNEL_TMA) {
         return fail(c, LBM_EINVAL, "the TMA sweep needs one Patch of equal Blocks 32, 64 or 128 "
                     "cells wide with rows divisible by 256/width, and F32/F16S/BF16S storage");
     }
+
+    // in place: the rest state's pressure links
+    CK(enqueue_aa_prepare(c), "prepare pressure links");
 
     // graph length: enough work per replay to hide launch overhead
     if (p.graph_steps < 0) {
@@ -876,6 +955,15 @@ FieldArgs field_args(const lbm_ctx *c)
     return a;
 }
 
+// Field arguments for a call that writes the state where it is: in place, an
+// even-time array (slots swapped).
+FieldArgs write_args(const lbm_ctx *c)
+{
+    FieldArgs a = field_args(c);
+    a.swap = c->aa ? 1 : 0;
+    return a;
+}
+
 cudaError_t enqueue_exchange(const lbm_ctx *c, int which)
 {
     ExchangeArgs x{};
@@ -921,9 +1009,45 @@ bool exchange_each_step(const lbm_ctx *c)
     return !c->xslabs.empty();
 }
 
-// One step from buffer `from` (communication step, then the work step).
+// In-place scheme: the forward exchange (before an odd step, and before a
+// gather), the reverse exchange (after an odd step), and the sweep itself.
+cudaError_t enqueue_aa_fwd(const lbm_ctx *c)
+{
+    return launch_exchange_flagged(c->d_aa_fwd, int(c->aa_fwd.size()), c->buf[0], c->elem, c->d_flags,
+                                   c->stream);
+}
+
+cudaError_t enqueue_aa_rev(const lbm_ctx *c)
+{
+    return launch_exchange_flagged(c->d_aa_rev, int(c->aa_rev.size()), c->buf[0], c->elem, c->d_flags,
+                                   c->stream);
+}
+
+cudaError_t enqueue_aa_sweep(const lbm_ctx *c, int mode, void *gather_dst = nullptr)
+{
+    SweepArgs a = sweep_args(c, 0);
+    a.src = c->buf[0];
+    a.dst = mode == 2 ? gather_dst : c->buf[0];
+    return launch_sweep_aa(a, mode, c->stream);
+}
+
+// One in-place step from phase ph: from an even time the forward exchange,
+// the pull-and-push step and the reverse exchange; from an odd time the
+// local step.
+cudaError_t enqueue_aa_step(const lbm_ctx *c, int ph)
+{
+    if (ph == 1) return enqueue_aa_sweep(c, 0);
+    cudaError_t e = enqueue_aa_fwd(c);
+    if (e == cudaSuccess) e = enqueue_aa_sweep(c, 1);
+    if (e == cudaSuccess) e = enqueue_aa_rev(c);
+    return e;
+}
+
+// One step from buffer `from` (communication step, then the work step); in
+// place, `from` is the phase.
 cudaError_t enqueue_step(const lbm_ctx *c, int from)
 {
+    if (c->aa) return enqueue_aa_step(c, from);
     if (exchange_each_step(c)) {
         cudaError_t e = enqueue_exchange(c, from);
         if (e != cudaSuccess) return e;
@@ -945,6 +1069,60 @@ int check_device_error(lbm_ctx *c)
                                                                 : "copies in flight at exit");
 }
 
+// In place, after the state was written at an even time: the values that
+// the next step pulls over pressure links (stored in the pressure nodes'
+// slots; the steps themselves keep them current).
+cudaError_t enqueue_aa_prepare(const lbm_ctx *c)
+{
+    if (!c->aa || !c->has_pressure) return cudaSuccess;
+    return enqueue_aa_sweep(c, 4);
+}
+
+// The odd-time state of the in-place scheme read back into the natural
+// layout of `dst` (S_q(x) at slot q).
+cudaError_t enqueue_aa_gather(const lbm_ctx *c, void *dst)
+{
+    cudaError_t e = cudaMemsetAsync(dst, 0, c->buf_bytes, c->stream);
+    if (e == cudaSuccess) e = enqueue_aa_sweep(c, 2, dst);
+    return e;
+}
+
+// The state for reading: the PDF array itself (with `fa.swap` set at an even
+// time of the in-place scheme), or, at an odd time, a copy in the natural
+// layout owned by `t`.
+int readable_state(lbm_ctx *c, std::unique_ptr<Temp> &t, const void **state, FieldArgs &fa)
+{
+    fa.swap = 0;
+    if (!c->aa || c->aa_phase == 0) {
+        *state = c->buf[c->cur];
+        fa.swap = c->aa ? 1 : 0;
+        return LBM_OK;
+    }
+    t.reset(new Temp(c, c->buf_bytes));
+    if (!t->p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes (the in-place state read back)", t->bytes);
+    CK(enqueue_aa_gather(c, t->p), "gather launch");
+    *state = t->p;
+    return LBM_OK;
+}
+
+// Brings the in-place array to an even-time layout (before a call that
+// changes the state where it is): read back, then stored swapped.
+int aa_normalize(lbm_ctx *c)
+{
+    if (!c->aa || c->aa_phase == 0) return LBM_OK;
+    Temp t(c, c->buf_bytes);
+    if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes (the in-place state read back)", t.bytes);
+    CK(enqueue_aa_gather(c, t.p), "gather launch");
+    SweepArgs a = sweep_args(c, 0);
+    a.src = t.p;
+    a.dst = c->buf[0];
+    CK(launch_sweep_aa(a, 3, c->stream), "store swapped");
+    CK(enqueue_aa_prepare(c), "prepare pressure links");
+    CK(cudaStreamSynchronize(c->stream), "normalize");
+    c->aa_phase = 0;
+    return LBM_OK;
+}
+
 int ensure_event(lbm_ctx *c, size_t idx)
 {
     while (c->ev.size() <= idx) {
@@ -958,6 +1136,29 @@ int ensure_event(lbm_ctx *c, size_t idx)
 int direct_steps(lbm_ctx *c, int n)
 {
     for (int s = 0; s < n; ++s) {
+        if (c->aa) {
+            const int ph = c->aa_phase;
+            if (c->profiling) {
+                // exchange interval: the forward exchange; the reverse
+                // exchange is timed with the sweep
+                size_t base = c->ev_used;
+                int rc = ensure_event(c, base + 2);
+                if (rc) return rc;
+                const bool has_x = ph == 0 && !c->aa_fwd.empty();
+                CK(cudaEventRecord(c->ev[base], c->stream), "cudaEventRecord");
+                if (has_x) CK(enqueue_aa_fwd(c), "exchange launch");
+                CK(cudaEventRecord(c->ev[base + 1], c->stream), "cudaEventRecord");
+                CK(enqueue_aa_sweep(c, ph == 0 ? 1 : 0), "sweep launch");
+                if (ph == 0) CK(enqueue_aa_rev(c), "exchange launch");
+                CK(cudaEventRecord(c->ev[base + 2], c->stream), "cudaEventRecord");
+                c->ev_has_x.push_back(has_x ? 1 : 0);
+                c->ev_used += 3;
+            } else {
+                CK(enqueue_aa_step(c, ph), "step launch");
+            }
+            c->aa_phase ^= 1;
+            continue;
+        }
         if (c->profiling) {
             size_t base = c->ev_used;
             int rc = ensure_event(c, base + 2);
@@ -1009,8 +1210,12 @@ int reduce(lbm_ctx *c, bool with_prev, std::vector<double> &out)
     int rc0 = check_device_error(c);
     if (rc0) return rc0;
     FieldArgs a = field_args(c);
-    CK(launch_reduce(a, c->buf[c->cur], with_prev ? c->buf[c->cur ^ 1] : nullptr, c->d_partial,
-                     c->d_inst_begin, c->ninst, c->d_red, c->stream),
+    std::unique_ptr<Temp> t;
+    const void *st = nullptr;
+    if (with_prev && c->aa) return fail(c, LBM_EINVAL, "in-place streaming keeps no previous state");
+    if ((rc0 = readable_state(c, t, &st, a))) return rc0;
+    CK(launch_reduce(a, st, with_prev ? c->buf[c->cur ^ 1] : nullptr, c->d_partial, c->d_inst_begin, c->ninst,
+                     c->d_red, c->stream),
        "reduce launch");
     out.assign(size_t(R_K) * c->ninst, 0.0);
     CK(cudaMemcpyAsync(out.data(), c->d_red, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
@@ -1160,6 +1365,10 @@ int lbm_step(lbm_ctx *c, int n)
         rc = direct_steps(c, n);
     } else {
         rc = LBM_OK;
+        if (c->aa && c->aa_phase == 1) {  // graphs start from the natural layout
+            rc = direct_steps(c, 1);
+            --n;
+        }
         while (n >= c->graph_steps && rc == LBM_OK) {
             rc = ensure_graph(c, c->cur);
             if (rc) break;
@@ -1182,7 +1391,13 @@ int lbm_synchronize(lbm_ctx *c)
 int lbm_macroscopic_device(lbm_ctx *c, float *rho, float *u)
 {
     if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_macroscopic_device: NULL argument");
-    CK(launch_macroscopic(field_args(c), c->buf[c->cur], rho, u, c->stream), "macroscopic launch");
+    std::unique_ptr<Temp> t;
+    const void *st = nullptr;
+    FieldArgs fa = field_args(c);
+    int rc = readable_state(c, t, &st, fa);
+    if (rc) return rc;
+    CK(launch_macroscopic(fa, st, rho, u, c->stream), "macroscopic launch");
+    if (t) CK(cudaStreamSynchronize(c->stream), "macroscopic");
     return LBM_OK;
 }
 
@@ -1207,8 +1422,12 @@ int lbm_get_pdfs(lbm_ctx *c, double *f)
     const size_t n = size_t(c->cells) * Q;
     Temp t(c, sizeof(double) * n);
     if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes", t.bytes);
-    CK(launch_get_pdfs(field_args(c), c->buf[c->cur], static_cast<double *>(t.p), c->stream),
-       "get_pdfs launch");
+    std::unique_ptr<Temp> g;
+    const void *st = nullptr;
+    FieldArgs fa = field_args(c);
+    int rc = readable_state(c, g, &st, fa);
+    if (rc) return rc;
+    CK(launch_get_pdfs(fa, st, static_cast<double *>(t.p), c->stream), "get_pdfs launch");
     CK(cudaMemcpyAsync(f, t.p, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "D2H pdfs");
     CK(cudaStreamSynchronize(c->stream), "lbm_get_pdfs");
     return check_device_error(c);
@@ -1221,18 +1440,22 @@ int lbm_set_pdfs(lbm_ctx *c, const double *f)
     Temp t(c, sizeof(double) * n);
     if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes", t.bytes);
     CK(cudaMemcpyAsync(t.p, f, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "H2D pdfs");
-    CK(launch_set_pdfs(field_args(c), c->buf[c->cur], static_cast<const double *>(t.p), c->stream),
+    CK(launch_set_pdfs(write_args(c), c->buf[c->cur], static_cast<const double *>(t.p), c->stream),
        "set_pdfs launch");
+    CK(enqueue_aa_prepare(c), "prepare pressure links");
     CK(cudaStreamSynchronize(c->stream), "lbm_set_pdfs");
     c->have_prev = false;
+    c->aa_phase = 0;
     return LBM_OK;
 }
 
 int lbm_init_equilibrium_device(lbm_ctx *c, const float *rho, const float *u)
 {
     if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_init_equilibrium_device: NULL argument");
-    CK(launch_init_equilibrium(field_args(c), c->buf[c->cur], rho, u, c->stream), "init launch");
+    CK(launch_init_equilibrium(write_args(c), c->buf[c->cur], rho, u, c->stream), "init launch");
+    CK(enqueue_aa_prepare(c), "prepare pressure links");
     c->have_prev = false;
+    c->aa_phase = 0;
     return LBM_OK;
 }
 
@@ -1284,6 +1507,9 @@ int lbm_invariants(lbm_ctx *c, double *mass, double mom[3], double *nonfinite, d
 int lbm_residual(lbm_ctx *c, double *res, double *per_instance)
 {
     if (!c || !res) return fail(c, LBM_EINVAL, "lbm_residual: NULL argument");
+    if (c->aa)
+        return fail(c, LBM_EINVAL, "lbm_residual: in-place streaming keeps no previous state (use "
+                    "lbm_snapshot_velocity and lbm_residual_vs_snapshot, or lbm_run_to_residual)");
     if (!c->have_prev)
         return fail(c, LBM_EINVAL, "lbm_residual: no step has been taken since the state was set");
     std::vector<double> r;
@@ -1313,10 +1539,21 @@ int lbm_run_to_residual(lbm_ctx *c, double tol, int check_every, long long max_s
     double r = INFINITY;
     while (done < max_steps) {
         const int n = int(std::min<long long>(check_every, max_steps - done));
-        int rc = lbm_step(c, n);
-        if (rc) return rc;
-        done += n;
-        rc = lbm_residual(c, &r, nullptr);
+        int rc;
+        if (c->aa) {
+            // the same one-step residual, against a velocity snapshot taken
+            // one step before the end of the interval
+            if (n > 1 && (rc = lbm_step(c, n - 1))) return rc;
+            if ((rc = lbm_snapshot_velocity(c))) return rc;
+            if ((rc = lbm_step(c, 1))) return rc;
+            done += n;
+            rc = lbm_residual_vs_snapshot(c, 1, &r, nullptr);
+        } else {
+            rc = lbm_step(c, n);
+            if (rc) return rc;
+            done += n;
+            rc = lbm_residual(c, &r, nullptr);
+        }
         if (rc) return rc;
         if (std::isnan(r)) {
             if (steps) *steps = done;
@@ -1333,7 +1570,10 @@ int lbm_run_to_residual(lbm_ctx *c, double tol, int check_every, long long max_s
 int lbm_impose_velocity_device(lbm_ctx *c, const float *u)
 {
     if (!c || !u) return fail(c, LBM_EINVAL, "lbm_impose_velocity_device: NULL argument");
-    CK(launch_impose_velocity(field_args(c), c->buf[c->cur], u, c->stream), "impose velocity");
+    int rc = aa_normalize(c);
+    if (rc) return rc;
+    CK(launch_impose_velocity(write_args(c), c->buf[c->cur], u, c->stream), "impose velocity");
+    CK(enqueue_aa_prepare(c), "prepare pressure links");
     c->have_prev = false;
     return LBM_OK;
 }
@@ -1356,7 +1596,13 @@ int lbm_snapshot_velocity(lbm_ctx *c)
         int rc = own(c, &c->d_snap, sizeof(float) * 4 * size_t(c->cells));
         if (rc) return rc;
     }
-    CK(launch_macroscopic(field_args(c), c->buf[c->cur], c->d_snap, c->d_snap + c->cells, c->stream), "snapshot");
+    std::unique_ptr<Temp> t;
+    const void *st = nullptr;
+    FieldArgs fa = field_args(c);
+    int rc = readable_state(c, t, &st, fa);
+    if (rc) return rc;
+    CK(launch_macroscopic(fa, st, c->d_snap, c->d_snap + c->cells, c->stream), "snapshot");
+    if (t) CK(cudaStreamSynchronize(c->stream), "snapshot");
     return LBM_OK;
 }
 
@@ -1367,7 +1613,11 @@ int lbm_residual_vs_snapshot(lbm_ctx *c, int steps_since, double *res, double *p
     int rc = check_device_error(c);
     if (rc) return rc;
     std::vector<double> r(size_t(R_K) * c->ninst, 0.0);
-    CK(launch_reduce_snap(field_args(c), c->buf[c->cur], c->d_snap + c->cells, c->d_partial, c->d_inst_begin,
+    std::unique_ptr<Temp> t;
+    const void *st = nullptr;
+    FieldArgs fa = field_args(c);
+    if ((rc = readable_state(c, t, &st, fa))) return rc;
+    CK(launch_reduce_snap(fa, st, c->d_snap + c->cells, c->d_partial, c->d_inst_begin,
                           c->ninst, c->d_red, c->stream),
        "snapshot residual");
     CK(cudaMemcpyAsync(r.data(), c->d_red, sizeof(double) * r.size(), cudaMemcpyDeviceToHost, c->stream), "D2H");
@@ -1411,6 +1661,9 @@ int lbm_run_to_residual_each(lbm_ctx *c, double tol, int check_every, int interv
     if (!c || check_every <= 0 || max_steps < 0 || !steps || (interval && (check_every & 1)))
         return fail(c, LBM_EINVAL, "lbm_run_to_residual_each: bad arguments (interval residuals need an "
                     "even check_every)");
+    if (c->aa)
+        return fail(c, LBM_EINVAL, "lbm_run_to_residual_each: in-place streaming serves single Patches "
+                    "(use lbm_run_to_residual)");
     const int K = c->ninst;
     std::vector<double> r(size_t(K), INFINITY);
     // PDF range of each instance (its Blocks are contiguous)
@@ -1484,6 +1737,8 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info)
     info->flat = c->kernel != LBM_KERNEL_TMA ? c->flat : 0;
     info->pair = c->kernel != LBM_KERNEL_TMA ? c->pair : 0;
     info->mask = c->kernel != LBM_KERNEL_TMA ? c->mask : 0;
+    info->streaming = c->aa ? LBM_STREAM_AA : LBM_STREAM_TWO_GRID;
+    info->aa_phase = c->aa_phase;
     info->sweep_ctas = c->kernel == LBM_KERNEL_TMA ? c->tma_grid
                        : c->grid > 0                ? c->grid
                                                     : int(c->stiles.size());
@@ -1539,6 +1794,9 @@ int check_cfg(lbm_ctx *c, const int *cd)
     if (cd[0] < 0 || cd[0] > 4) return fail(c, LBM_EINVAL, "sweep config: kind %d", cd[0]);
     if (cd[0] == 1 && !tma_ok)
         return fail(c, LBM_EINVAL, "sweep config: the TMA sweep does not apply to this context");
+    if (c->aa && (cd[0] == 1 || cd[0] >= 3 || cd[7] != 0))
+        return fail(c, LBM_EINVAL, "sweep config: in-place streaming takes row tiles or runs, one cell per "
+                    "thread, near-wall cells by lane (kinds 0 / 2, mask 0)");
     if (cd[0] >= 3) {
         bool even = c->storage != LBM_F64;
         for (const BlockGeom &b : c->blocks) even = even && (b.nx % 2 == 0);
@@ -1607,7 +1865,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
 {
     if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
     const bool tma_ok = c->kernel == LBM_KERNEL_TMA || (c->tma_grid > 0);
-    const std::string key = tune_key(c) + (tma_ok ? "|tma" : "");
+    const std::string key = tune_key(c) + (tma_ok ? "|tma" : "") + (c->aa ? "|aa" : "");
     // configuration: kind (0 register sweep over row tiles, 1 TMA sweep, 2
     // register sweep over runs of tx consecutive cells), tx, ty, tz, grid,
     // minb, zchunk, mask
@@ -1642,7 +1900,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int zc0 = c->tma_zchunk, m0 = c->mask;
-        bool pair_ok = c->storage != LBM_F64;
+        bool pair_ok = c->storage != LBM_F64 && !c->aa;
         for (const BlockGeom &b : c->blocks) pair_ok = pair_ok && (b.nx % 2 == 0);
         const int *st = c->sw_tile;
         std::vector<Cfg> cand;
@@ -1675,9 +1933,35 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");
+        // in place the timed steps change the state: it is saved here and
+        // restored after tuning (a transient second array)
+        std::unique_ptr<Temp> saved;
+        if (c->aa) {
+            int rc = aa_normalize(c);
+            if (rc) return rc;
+            saved.reset(new Temp(c, c->buf_bytes));
+            if (!saved->p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes (state saved while tuning)",
+                                      saved->bytes);
+            CK(cudaMemcpyAsync(saved->p, c->buf[0], c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream), "save");
+        }
         auto time_cfg = [&](const Cfg &cd, int reps, float *ms_out) -> int {
             int rc = apply(cd);
             if (rc) return rc;
+            if (c->aa) {  // pairs of steps: the local one and the odd one with its exchanges
+                CK(enqueue_aa_step(c, 0), "tune");
+                CK(enqueue_aa_step(c, 1), "tune");
+                CK(cudaEventRecord(e0, c->stream), "event");
+                for (int r = 0; r < reps; ++r) {
+                    CK(enqueue_aa_step(c, 0), "tune");
+                    CK(enqueue_aa_step(c, 1), "tune");
+                }
+                CK(cudaEventRecord(e1, c->stream), "event");
+                CK(cudaEventSynchronize(e1), "tune sync");
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+                *ms_out = ms / (2 * reps);
+                return LBM_OK;
+            }
             CK(enqueue_sweep(c, c->cur), "tune");
             CK(cudaEventRecord(e0, c->stream), "event");
             for (int r = 0; r < reps; ++r) CK(enqueue_sweep(c, c->cur), "tune");
@@ -1709,7 +1993,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         for (size_t k = 0; k < timed.size() && k < 4; ++k) {
             Cfg cd = timed[k].second;
             fin.push_back(cd);
-            if (cd[0] != 1) {
+            if (cd[0] != 1 && !c->aa) {
                 cd[7] ^= 1;
                 fin.push_back(cd);
             }
@@ -1726,6 +2010,11 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        if (saved) {
+            CK(cudaMemcpyAsync(c->buf[0], saved->p, c->buf_bytes, cudaMemcpyDeviceToDevice, c->stream),
+               "restore");
+            CK(cudaStreamSynchronize(c->stream), "restore");
+        }
         int rc = check_device_error(c);
         if (rc) return rc;
         if (cache_path) {

@@ -47,6 +47,34 @@ template <> struct Traits<3> {
     static __device__ __forceinline__ S from_t(T v) { return v; }
 };
 
+// kernel-parameter copies of the collision constants (a single instance)
+// pb = 2 s (rho_b - rho0) of the pressure boundaries in the arithmetic type
+template <typename T>
+__device__ __forceinline__ T param_pb(const SweepArgs &a);
+template <>
+__device__ __forceinline__ float param_pb<float>(const SweepArgs &a)
+{
+    return a.pbf;
+}
+template <>
+__device__ __forceinline__ double param_pb<double>(const SweepArgs &a)
+{
+    return a.pbd;
+}
+
+template <typename T>
+__device__ __forceinline__ const CollideConsts<T> &param_consts(const SweepArgs &a);
+template <>
+__device__ __forceinline__ const CollideConsts<float> &param_consts<float>(const SweepArgs &a)
+{
+    return a.kf;
+}
+template <>
+__device__ __forceinline__ const CollideConsts<double> &param_consts<double>(const SweepArgs &a)
+{
+    return a.kd;
+}
+
 // ------------------------------------------------- pressure boundaries
 // Anti-bounce-back with the velocity correction, in scaled units: the value
 // pulled along e_q from a pressure node is
@@ -62,22 +90,22 @@ struct PresBC {
     T P, ux, uy, uz, c9;  // P = pb - 3 s rho0 u_b.u_b, c9 = 9 s rho0
 };
 
-template <int ST, typename T>
-__device__ __forceinline__ PresBC<T> pres_setup(const typename Traits<ST>::S *src, int c, int G, T pb, T ufac,
-                                                T uox, T uoy, T uoz, T c45, T nc15)
+// one term of the momentum sum, in the order every caller uses (q = 1..18)
+template <typename T>
+__device__ __forceinline__ void pres_acc(int q, T g, T &jx, T &jy, T &jz)
 {
-    using Tr = Traits<ST>;
-    T jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        const T g = Tr::ld(src + (q * G + c));
-        if (ex(q) > 0) jx = vadd(jx, g);
-        if (ex(q) < 0) jx = vsub(jx, g);
-        if (ey(q) > 0) jy = vadd(jy, g);
-        if (ey(q) < 0) jy = vsub(jy, g);
-        if (ez(q) > 0) jz = vadd(jz, g);
-        if (ez(q) < 0) jz = vsub(jz, g);
-    }
+    if (ex(q) > 0) jx = vadd(jx, g);
+    if (ex(q) < 0) jx = vsub(jx, g);
+    if (ey(q) > 0) jy = vadd(jy, g);
+    if (ey(q) < 0) jy = vsub(jy, g);
+    if (ez(q) > 0) jz = vadd(jz, g);
+    if (ez(q) < 0) jz = vsub(jz, g);
+}
+
+template <typename T>
+__device__ __forceinline__ PresBC<T> pres_finish(T jx, T jy, T jz, T pb, T ufac, T uox, T uoy, T uoz, T c45,
+                                                 T nc15)
+{
     PresBC<T> r;
     r.ux = vfma(jx, ufac, -uox);
     r.uy = vfma(jy, ufac, -uoy);
@@ -86,6 +114,36 @@ __device__ __forceinline__ PresBC<T> pres_setup(const typename Traits<ST>::S *sr
     r.P = vfma(vadd(nc15, nc15), usq, pb);
     r.c9 = vadd(c45, c45);
     return r;
+}
+
+// From the stored populations of cell c: g*_q at src[q G + c], or, with SWAP
+// (the in-place scheme after its local step), at src[opp(q) G + c].
+template <int ST, typename T, bool SWAP = false>
+__device__ __forceinline__ PresBC<T> pres_setup(const typename Traits<ST>::S *src, int c, int G, T pb, T ufac,
+                                                T uox, T uoy, T uoz, T c45, T nc15)
+{
+    using Tr = Traits<ST>;
+    T jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        // the in-place scheme writes this array in the same launch: coherent loads there
+        const typename Tr::S *p = src + ((SWAP ? opp(q) : q) * G + c);
+        pres_acc(q, SWAP ? Tr::to_t(*p) : Tr::ld(p), jx, jy, jz);
+    }
+    return pres_finish(jx, jy, jz, pb, ufac, uox, uoy, uoz, c45, nc15);
+}
+
+// From post-collision values still in registers, rounded through the storage
+// format exactly as a later load would see them.
+template <int ST, typename T>
+__device__ __forceinline__ PresBC<T> pres_setup_regs(const T (&f)[Q], T pb, T ufac, T uox, T uoy, T uoz, T c45,
+                                                     T nc15)
+{
+    using Tr = Traits<ST>;
+    T jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) pres_acc(q, Tr::to_t(Tr::from_t(f[q])), jx, jy, jz);
+    return pres_finish(jx, jy, jz, pb, ufac, uox, uoy, uoz, c45, nc15);
 }
 
 // g_q from the returning population g*_opp(q)(x); q is a constant after
@@ -111,13 +169,15 @@ __device__ __forceinline__ T pres_pull(int q, const PresBC<T> &p, T g_opp)
 
 // the setup from the Patch's collision constants: kernel parameters for a
 // single instance (UNIF), else the instance's table entry
-template <int ST, bool UNIF, typename T>
+template <int ST, bool UNIF, typename T, bool SWAP = false>
 __device__ __forceinline__ PresBC<T> pres_cell(const CollideConsts<T> &kp, const CollideConsts<T> *kg, T pb,
                                                const typename Traits<ST>::S *src, int c, int G)
 {
-    if (UNIF) return pres_setup<ST, T>(src, c, G, pb, kp.ufac, kp.uoff[0], kp.uoff[1], kp.uoff[2], kp.c45, kp.nc15);
-    return pres_setup<ST, T>(src, c, G, pb, __ldg(&kg->ufac), __ldg(&kg->uoff[0]), __ldg(&kg->uoff[1]),
-                             __ldg(&kg->uoff[2]), __ldg(&kg->c45), __ldg(&kg->nc15));
+    if (UNIF)
+        return pres_setup<ST, T, SWAP>(src, c, G, pb, kp.ufac, kp.uoff[0], kp.uoff[1], kp.uoff[2], kp.c45,
+                                       kp.nc15);
+    return pres_setup<ST, T, SWAP>(src, c, G, pb, __ldg(&kg->ufac), __ldg(&kg->uoff[0]), __ldg(&kg->uoff[1]),
+                                   __ldg(&kg->uoff[2]), __ldg(&kg->c45), __ldg(&kg->nc15));
 }
 
 }  // namespace lbm

@@ -39,7 +39,43 @@ cudaError_t launch_exchange(const ExchangeArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The in-place scheme's exchanges, one element at a time where a flag is
+// fluid.  Forward (before the step from an even time): neighbours' boundary
+// rows into the ghost rows, where the ghost cell is fluid (a wall or pressure
+// node's slots hold what the Block's own cells stored there).  Reverse (after
+// it): what the step streamed into the ghost rows to the neighbours'
+// boundary rows, where the cell that streamed it is fluid (elsewhere the
+// destination holds a bounce-back value its own cell wrote).
+template <typename E>
+__global__ void __launch_bounds__(256) exchange_flagged_kernel(const XSlabF *slabs, E *buf, const uint8_t *flags)
+{
+    const XSlabF sl = slabs[blockIdx.x];
+    const int n = sl.rows * sl.len;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int r = k / sl.len, i = k - r * sl.len;
+        if (flags[sl.fsrc + (long long)r * sl.fstride + i] & F_KIND) continue;
+        const long long off = (long long)r * sl.stride + i;
+        buf[sl.dst + off] = buf[sl.src + off];
+    }
+}
+
+cudaError_t launch_exchange_flagged(const XSlabF *slabs, int nslabs, void *buf, int elem_bytes,
+                                    const uint8_t *flags, cudaStream_t s)
+{
+    if (nslabs == 0) return cudaSuccess;
+    if (elem_bytes == 2)
+        exchange_flagged_kernel<<<nslabs, 256, 0, s>>>(slabs, static_cast<uint16_t *>(buf), flags);
+    else if (elem_bytes == 4)
+        exchange_flagged_kernel<<<nslabs, 256, 0, s>>>(slabs, static_cast<uint32_t *>(buf), flags);
+    else
+        exchange_flagged_kernel<<<nslabs, 256, 0, s>>>(slabs, static_cast<unsigned long long *>(buf), flags);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- per-cell helpers
+// storage slot of direction q (swapped in the in-place scheme's even-time layout)
+__device__ __forceinline__ int slot(const FieldArgs &a, int q) { return a.swap ? opp(q) : q; }
+
 struct CellPos {
     const BlockGeom *b;
     int x, y, z;   // interior coordinates inside the block
@@ -107,7 +143,7 @@ __global__ void __launch_bounds__(256) macro_kernel(const __grid_constant__ Fiel
         T d = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const T gq = Tr::to_t(g[(long long)q * b.G]);
+            const T gq = Tr::to_t(g[(long long)slot(a, q) * b.G]);
             d += gq;
             jx += T(ex(q)) * gq;
             jy += T(ey(q)) * gq;
@@ -137,7 +173,7 @@ __global__ void __launch_bounds__(256) init_eq_kernel(const __grid_constant__ Fi
         S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
         if (a.flags[b.cell_base + p.cf] & F_KIND) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) g[(long long)q * b.G] = Tr::from_t(T(0));
+            for (int q = 0; q < Q; ++q) g[(long long)slot(a, q) * b.G] = Tr::from_t(T(0));
             return;
         }
         const float *r = rho + b.out_base;
@@ -150,7 +186,7 @@ __global__ void __launch_bounds__(256) init_eq_kernel(const __grid_constant__ Fi
         for (int q = 0; q < Q; ++q) {
             const T eu = T(ex(q)) * ux + T(ey(q)) * uy + T(ez(q)) * uz;
             const T feq = T(wq(q)) * (drho_s + P.rho0s * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
-            g[(long long)q * b.G] = Tr::from_t(feq);
+            g[(long long)slot(a, q) * b.G] = Tr::from_t(feq);
         }
     });
 }
@@ -178,7 +214,7 @@ __global__ void __launch_bounds__(256) impose_u_kernel(const __grid_constant__ F
         T jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            f[q] = Tr::to_t(g[(long long)q * b.G]);
+            f[q] = Tr::to_t(g[(long long)slot(a, q) * b.G]);
             jx += T(ex(q)) * f[q];
             jy += T(ey(q)) * f[q];
             jz += T(ez(q)) * f[q];
@@ -193,7 +229,7 @@ __global__ void __launch_bounds__(256) impose_u_kernel(const __grid_constant__ F
             const T et = T(ex(q)) * t0 + T(ey(q)) * t1 + T(ez(q)) * t2;
             const T d = T(wq(q)) * P.rho0s *
                         (T(3) * (et - en) + T(4.5) * (et * et - en * en) - T(1.5) * (tsq - nsq));
-            g[(long long)q * b.G] = Tr::from_t(f[q] + d);
+            g[(long long)slot(a, q) * b.G] = Tr::from_t(f[q] + d);
         }
     });
 }
@@ -216,7 +252,7 @@ __global__ void __launch_bounds__(256) get_pdfs_kernel(const __grid_constant__ F
         const S *g = static_cast<const S *>(buf) + b.pdf_base + p.c;
 #pragma unroll
         for (int q = 0; q < Q; ++q)
-            out[q * N + p.o] = solid ? 0.0 : double(Tr::to_t(g[(long long)q * b.G])) * inv_s;
+            out[q * N + p.o] = solid ? 0.0 : double(Tr::to_t(g[(long long)slot(a, q) * b.G])) * inv_s;
     });
 }
 
@@ -237,7 +273,7 @@ __global__ void __launch_bounds__(256) set_pdfs_kernel(const __grid_constant__ F
         S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
 #pragma unroll
         for (int q = 0; q < Q; ++q)
-            g[(long long)q * b.G] = Tr::from_t(solid ? T(0) : T(in[q * N + p.o] * s));
+            g[(long long)slot(a, q) * b.G] = Tr::from_t(solid ? T(0) : T(in[q * N + p.o] * s));
     });
 }
 
@@ -308,7 +344,7 @@ __global__ void __launch_bounds__(256) invariants_tiles_kernel(const __grid_cons
             double d = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const double v = double(Tr::to_t(g[(long long)q * b.G])) * inv_s;
+                const double v = double(Tr::to_t(g[(long long)slot(a, q) * b.G])) * inv_s;
                 d += v;
                 if (ex(q)) j[0] += ex(q) > 0 ? v : -v;
                 if (ey(q)) j[1] += ey(q) > 0 ? v : -v;
@@ -357,8 +393,8 @@ __global__ void __launch_bounds__(256) residual_tiles_kernel(const __grid_consta
             T j[3] = {T(0), T(0), T(0)}, dj[3] = {T(0), T(0), T(0)};
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                const T v = Tr::to_t(g[(long long)q * b.G]);
-                const T dv = v - Tr::to_t(h[(long long)q * b.G]);
+                const T v = Tr::to_t(g[(long long)slot(a, q) * b.G]);
+                const T dv = v - Tr::to_t(h[(long long)slot(a, q) * b.G]);
                 if (ex(q)) { j[0] += ex(q) > 0 ? v : -v; dj[0] += ex(q) > 0 ? dv : -dv; }
                 if (ey(q)) { j[1] += ey(q) > 0 ? v : -v; dj[1] += ey(q) > 0 ? dv : -dv; }
                 if (ez(q)) { j[2] += ez(q) > 0 ? v : -v; dj[2] += ez(q) > 0 ? dv : -dv; }
@@ -419,7 +455,7 @@ __global__ void __launch_bounds__(256) residual_snap_kernel(const __grid_constan
             T j[3] = {T(0), T(0), T(0)};
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                const T v = Tr::to_t(g[(long long)q * b.G]);
+                const T v = Tr::to_t(g[(long long)slot(a, q) * b.G]);
                 if (ex(q)) j[0] += ex(q) > 0 ? v : -v;
                 if (ey(q)) j[1] += ey(q) > 0 ? v : -v;
                 if (ez(q)) j[2] += ez(q) > 0 ? v : -v;
@@ -600,6 +636,20 @@ cudaError_t tma_occupancy(int storage, int tx, int collision, int forced, int *c
 }
 
 int tma_stages(int storage) { return storage == 0 ? 4 : 5; }
+
+// In-place sweep dispatch (kernels live in sweep_aa_*.cu).
+template <int ST> cudaError_t launch_sweep_aa_st(const SweepArgs &, int, cudaStream_t);
+
+cudaError_t launch_sweep_aa(const SweepArgs &a, int mode, cudaStream_t s)
+{
+    switch (a.storage) {
+    case 0: return launch_sweep_aa_st<0>(a, mode, s);
+    case 1: return launch_sweep_aa_st<1>(a, mode, s);
+    case 2: return launch_sweep_aa_st<2>(a, mode, s);
+    case 3: return launch_sweep_aa_st<3>(a, mode, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 // Sweep dispatch over the storage formats (kernels live in sweep_*.cu).
 template <int ST> cudaError_t launch_sweep_st(const SweepArgs &, cudaStream_t);

@@ -19,6 +19,15 @@ struct XSlab {
     long long stride;
     int rows, len;
 };
+// A slab of the in-place scheme's reverse exchange: element (r, i) moves
+// from src + r stride + i to dst + r stride + i when the flag at
+// fsrc + r fstride + i (the cell that streamed it) is fluid.
+struct XSlabF {
+    long long src, dst;
+    long long stride;
+    long long fsrc, fstride;
+    int rows, len;
+};
 
 // Sets the calling thread's message for lbm_last_error(NULL).
 void set_global_error(const char *msg);
@@ -71,6 +80,11 @@ struct ExchangeArgs {
     int elem_bytes;
 };
 cudaError_t launch_exchange(const ExchangeArgs &a, cudaStream_t s);
+cudaError_t launch_exchange_flagged(const XSlabF *slabs, int nslabs, void *buf, int elem_bytes,
+                                    const uint8_t *flags, cudaStream_t s);
+// In-place (AA-pattern) sweep: mode 0 even step, 1 odd step, 2 gather of an
+// odd-time state into the natural layout of a.dst.
+cudaError_t launch_sweep_aa(const SweepArgs &a, int mode, cudaStream_t s);
 
 struct FieldArgs {
     const Tile *tiles;
@@ -80,6 +94,8 @@ struct FieldArgs {
     const uint8_t *flags;
     int tx, ty, tz;
     int storage;
+    int swap;  // 1: direction q of a cell is stored in slot opp(q) (the in-place
+               // scheme at an even time)
 };
 // rho/u in the concatenated output layout (device pointers)
 cudaError_t launch_macroscopic(const FieldArgs &a, const void *buf, float *rho, float *u,

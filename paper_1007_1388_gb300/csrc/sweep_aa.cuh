@@ -1,0 +1,253 @@
+// The fused D3Q19 sweep in place, one PDF array (the AA access pattern of
+// Bailey et al., 2009): the same pull stream + bounce-back + collide of
+// Sec. 2.1 and Sec. 3.2, with the streaming split over two kinds of step so
+// that every thread reads and writes only locations no other thread touches
+// in the same launch.
+//
+// The state is the two-array sweep's: S_q(x), the populations of x after its
+// last collision.  Even times hold it swapped in the cell's own slots,
+// A[opp(q)][x] = S_q(x); odd times hold it streamed.
+//   from an even time (mode 1): f_q = A[opp(q)][x - e_q] = S_q(x - e_q), or,
+//     where x - e_q is not fluid, the bounce-back of A[q][x] = S_opp(q)(x)
+//     with the moving-wall or pressure term: exactly the two-array pull.
+//     Collide to S'.  Push: A[q][x + e_q] = S'_q(x) for every q (into the
+//     neighbour's slot when it is fluid, else into the wall or solid cell's
+//     own storage, kept only so that the state can be read back), and where
+//     x + e_q is not fluid also A[opp(q)][x] = the value that returns to x
+//     along e_opp(q) (S'_q plus the wall term).
+//   from an odd time (mode 0): f_q = A[q][x], collide, A[opp(q)][x] = f*_q.
+//     Local, except for pressure links, below.
+// A pressure link pulls along e_q from the pressure node P = x - e_q the
+// value -S_opp(q)(x) + w_q [...](u_b), whose boundary velocity u_b comes from
+// all of x's populations; in mode 1 those belong to the neighbours that pull
+// them.  So the step that produces S (mode 0, or mode 4 after the state was
+// written from the host) computes that value while S is in registers (or
+// x's own slots) and stores it in P's slot A[opp(q)][P], the address the
+// pull of mode 1 reads anyway (and x's push then overwrites).
+// Each location is read and then written by exactly one thread of a launch,
+// so no location is read after another thread wrote it.  Loads are plain
+// (coherent) loads: the array is written in the same launch.
+//
+// With FP32 storage every value is the same floating-point result as in the
+// two-array sweep (same pulled operands, same collision code), so the states
+// are bitwise equal at every step.  With 16-bit storage a bounce-back value
+// is rounded when mode 1 stores it, where the two-array sweep keeps it in
+// FP32 until the collision.
+//
+// Across Blocks: mode 1 reaches across x faces through the Blocks' xm_off /
+// xp_off like the two-array pull (and, beyond a wall face, into two padding
+// columns of every row); across y/z faces it reads and writes the ghost rows,
+// which a forward exchange fills before it and a reverse exchange drains
+// after it.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace lbm {
+
+// MODE: 0 step from an odd time, 1 step from an even time, 2 the state of
+// an odd time read back into the natural layout of a second array (a.dst:
+// S_q(x) at slot q), 3 a natural-layout state (a.src) stored swapped into
+// a.dst (an even-time array), 4 the pressure links' values of an even-time
+// state that was written from the host.
+template <int ST, int COLL, bool FORCE, int MINB, int MODE, bool PRES>
+__global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_constant__ SweepArgs a)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    using T = typename Tr::T;
+    const CollideConsts<T> &K = param_consts<T>(a);  // a single instance: kernel parameters
+    const CollKRef<T> KR{K};
+
+    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const Tile tile = a.tiles[t];
+        const BlockGeom &b = a.blocks[tile.block];
+        const int nx = b.nx, ny = b.ny;
+        int x, y, z;
+        if (a.flat) {
+            const int i = tile.x0 + int(threadIdx.x);
+            const int yz = i / nx;
+            x = i - yz * nx;
+            z = yz / ny;
+            y = yz - z * ny;
+        } else {
+            x = tile.x0 + int(threadIdx.x);
+            y = tile.y0 + int(threadIdx.y);
+            z = tile.z0 + int(blockIdx.y);
+        }
+        if (x >= nx || y >= ny || z >= b.nz) continue;
+        const int px = b.px, pxy = px * b.py;
+        const int pxf = b.pxf, pxyf = b.pxf * b.py;
+        const int G = int(b.G);
+        const int c = (z + 1) * pxy + (y + 1) * px + x;
+        const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
+        const uint8_t *fl = a.flags + b.cell_base;
+        const uint8_t flag = fl[cf];
+        if (flag & F_KIND) continue;  // solid and pressure cells are not updated
+        const S *R = static_cast<const S *>(a.src) + b.pdf_base;
+        S *W = static_cast<S *>(a.dst) + b.pdf_base;
+        // neighbours across the -x face (x = 0) and the +x face (x = nx - 1)
+        const long long xm = x == 0 ? b.xm_off : 0ll, xp = x == nx - 1 ? b.xp_off : 0ll;
+        T f[Q];
+
+        if (MODE == 0 || MODE == 3) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = Tr::to_t(R[q * G + c]);
+            if (MODE == 0) collide_v<COLL, FORCE>(f, KR);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) Tr::st(W + (opp(q) * G + c), f[q]);
+            if (MODE == 0 && PRES && (flag & F_NEAR)) {
+                const uint32_t lm = __ldg(a.links + b.cell_base + cf);
+                if (lm & L_PRESSURE) {
+                    const PresBC<T> pb = pres_setup_regs<ST, T>(f, param_pb<T>(a), K.ufac, K.uoff[0], K.uoff[1],
+                                                                K.uoff[2], K.c45, K.nc15);
+#pragma unroll
+                    for (int q = 1; q < Q; ++q) {
+                        if (!((lm >> q) & 1u)) continue;
+                        if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
+                        const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
+                        Tr::st(W + (o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))),
+                               pres_pull(q, pb, Tr::to_t(Tr::from_t(f[opp(q)]))));
+                    }
+                }
+            }
+            continue;
+        }
+        if (MODE == 4) {
+            if (!(flag & F_NEAR)) continue;
+            const uint32_t lm = __ldg(a.links + b.cell_base + cf);
+            if (!(lm & L_PRESSURE)) continue;
+            const PresBC<T> pb = pres_cell<ST, true, T, true>(K, nullptr, param_pb<T>(a), R, c, G);
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                if (!((lm >> q) & 1u)) continue;
+                if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
+                const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
+                Tr::st(W + (o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))),
+                       pres_pull(q, pb, Tr::to_t(R[q * G + c])));
+            }
+            continue;
+        }
+        if (MODE == 2) {  // S_q(x) was pushed to x + e_q
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
+                W[q * G + c] = R[o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))];
+            }
+            continue;
+        }
+
+        const bool near = flag & F_NEAR;
+        const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
+        if (!near) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
+                f[q] = Tr::to_t(R[o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
+                const S *pa = R + (o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
+                if ((lm >> q) & 1u) {
+                    const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+                    if (PRES && (nf & F_KIND) == F_PRESSURE) {
+                        f[q] = Tr::to_t(*pa);  // prepared by the step that produced S
+                    } else {
+                        T v = Tr::to_t(R[q * G + c]);  // S_opp(q)(x), stored swapped
+                        if ((nf & F_KIND) == F_MOVING) v = vadd(v, K.bbw[q]);
+                        f[q] = v;
+                    }
+                } else {
+                    f[q] = Tr::to_t(*pa);
+                }
+            }
+        }
+        collide_v<COLL, FORCE>(f, KR);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
+            Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
+        }
+        if (near) {
+            PresBC<T> pbw{};
+            if (PRES && (lm & L_PRESSURE))
+                pbw = pres_setup_regs<ST, T>(f, param_pb<T>(a), K.ufac, K.uoff[0], K.uoff[1], K.uoff[2], K.c45,
+                                             K.nc15);
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                if (!((lm >> opp(q)) & 1u)) continue;
+                // x + e_q is not fluid: S'_q comes back to x along e_opp(q)
+                T v = f[q];
+                const uint8_t nf = fl[cf + (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+                if ((nf & F_KIND) == F_MOVING)
+                    v = vadd(v, K.bbw[opp(q)]);
+                else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                    v = pres_pull(opp(q), pbw, Tr::to_t(Tr::from_t(v)));
+                Tr::st(W + (opp(q) * G + c), v);
+            }
+        }
+    }
+}
+
+template <int ST, int MINB, int MODE, bool PRES>
+void launch_aa_mode(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if constexpr (MODE >= 2) {  // no collision: one instantiation serves every operator
+        sweep_aa_kernel<ST, 0, false, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+    } else if (a.collision == 0) {
+        if (a.forced)
+            sweep_aa_kernel<ST, 0, true, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+        else
+            sweep_aa_kernel<ST, 0, false, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.forced)
+            sweep_aa_kernel<ST, 1, true, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+        else
+            sweep_aa_kernel<ST, 1, false, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+    }
+}
+
+template <int ST, int MINB>
+void launch_aa_minb(const SweepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (mode == 0)
+        a.pres ? launch_aa_mode<ST, MINB, 0, true>(a, grid, block, s)
+               : launch_aa_mode<ST, MINB, 0, false>(a, grid, block, s);
+    else if (mode == 1)
+        a.pres ? launch_aa_mode<ST, MINB, 1, true>(a, grid, block, s)
+               : launch_aa_mode<ST, MINB, 1, false>(a, grid, block, s);
+    else if (mode == 2)
+        launch_aa_mode<ST, MINB, 2, false>(a, grid, block, s);
+    else if (mode == 3)
+        launch_aa_mode<ST, MINB, 3, false>(a, grid, block, s);
+    else
+        launch_aa_mode<ST, MINB, 4, true>(a, grid, block, s);
+}
+
+// mode 0 step from an odd time, 1 from an even time (a.src == a.dst), 2 read
+// back an odd-time state, 3 store a natural-layout state swapped (a.src ->
+// a.dst), 4 prepare the pressure links of an even-time state (in place)
+template <int ST>
+cudaError_t launch_sweep_aa_st(const SweepArgs &a, int mode, cudaStream_t s)
+{
+    if ((a.tx * a.ty) % 32 != 0 || a.tx * a.ty > 256 || (a.flat && (a.ty != 1 || a.tz != 1)) || a.pair ||
+        !a.unif)
+        return cudaErrorInvalidConfiguration;
+    dim3 block(a.tx, a.ty, 1);
+    const unsigned gx = unsigned(a.grid > 0 ? a.grid : a.ntiles);
+    if (gx == 0) return cudaSuccess;
+    const dim3 grid(gx, unsigned(a.tz), 1);
+    if constexpr (ST == 3) {  // FP64 arithmetic needs the larger register budget
+        launch_aa_minb<ST, 2>(a, mode, grid, block, s);
+    } else {
+        if (a.minb == 4)
+            launch_aa_minb<ST, 4>(a, mode, grid, block, s);
+        else
+            launch_aa_minb<ST, 3>(a, mode, grid, block, s);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

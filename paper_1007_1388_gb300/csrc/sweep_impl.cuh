@@ -30,33 +30,6 @@ namespace lbm {
 // UNIF: a single instance whose collision constants are kernel parameters.
 // MASK: near-wall cells read precomputed link masks under a warp vote (porous
 // media, where near-wall and interior cells share warps).
-// pb = 2 s (rho_b - rho0) of the pressure boundaries in the arithmetic type
-template <typename T>
-__device__ __forceinline__ T param_pb(const SweepArgs &a);
-template <>
-__device__ __forceinline__ float param_pb<float>(const SweepArgs &a)
-{
-    return a.pbf;
-}
-template <>
-__device__ __forceinline__ double param_pb<double>(const SweepArgs &a)
-{
-    return a.pbd;
-}
-
-template <typename T>
-__device__ __forceinline__ const CollideConsts<T> &param_consts(const SweepArgs &a);
-template <>
-__device__ __forceinline__ const CollideConsts<float> &param_consts<float>(const SweepArgs &a)
-{
-    return a.kf;
-}
-template <>
-__device__ __forceinline__ const CollideConsts<double> &param_consts<double>(const SweepArgs &a)
-{
-    return a.kd;
-}
-
 template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK, bool PRES>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant__ SweepArgs a)
 {

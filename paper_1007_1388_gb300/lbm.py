@@ -22,6 +22,7 @@ LBM_FLUID, LBM_NOSLIP, LBM_MOVING, LBM_PRESSURE = 0, 1, 2, 3
 LBM_BGK, LBM_TRT = 0, 1
 LBM_F32, LBM_F16S, LBM_BF16S, LBM_F64 = 0, 1, 2, 3
 LBM_KERNEL_AUTO, LBM_KERNEL_REGISTER, LBM_KERNEL_TMA = 0, 1, 2
+LBM_STREAM_TWO_GRID, LBM_STREAM_AA = 0, 1
 LBM_DEBUG_DROP_STAGE = 1
 STORAGE_NAMES = {LBM_F32: "f32", LBM_F16S: "f16s", LBM_BF16S: "bf16s", LBM_F64: "f64"}
 BYTES_PER_PDF = {LBM_F32: 4, LBM_F16S: 2, LBM_BF16S: 2, LBM_F64: 8}
@@ -47,6 +48,7 @@ class lbm_params(ctypes.Structure):
         ("kernel", ctypes.c_int),
         ("debug_flags", ctypes.c_int),
         ("rho_b", ctypes.c_double),
+        ("streaming", ctypes.c_int),
     ]
 
 
@@ -69,6 +71,8 @@ class lbm_info(ctypes.Structure):
         ("flat", ctypes.c_int),
         ("mask", ctypes.c_int),
         ("pair", ctypes.c_int),
+        ("streaming", ctypes.c_int),
+        ("aa_phase", ctypes.c_int),
     ]
 
 
