@@ -217,6 +217,8 @@ def run_gpu(args):
         main_kw["coll"] = L.LBM_TRT
     if args.kernel:
         main_kw["kernel"] = {"auto": 0, "register": 1, "tma": 2}[args.kernel]
+    if args.streaming == "aa":
+        main_kw["streaming"] = L.LBM_STREAM_AA
     ctx = make(**main_kw)
     if not args.no_autotune:
         # pick kernel, tile and register budget by timing on this GPU (outside the timed region)
@@ -261,11 +263,16 @@ def run_gpu(args):
     st_main = main_kw.get("storage", 0)
     alg_bytes = BYTES_PER_LUP[st_main] * cells
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    traffic = _ncu_traffic("sweep_f32_channel256")
+    aa = args.streaming == "aa"
+    from paper_1007_1388_gb300 import build as _build
+
+    traffic = (_ncu_traffic("sweep_aa_f32_channel256", _build.AA_SOURCES) if aa
+               else _ncu_traffic("sweep_f32_channel256"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind,
-                "kernel": ("lbm::sweep_tma_kernel" if info.kernel == L.LBM_KERNEL_TMA
+                "kernel": ("lbm::sweep_aa_kernel" if aa
+                           else "lbm::sweep_tma_kernel" if info.kernel == L.LBM_KERNEL_TMA
                            else "lbm::sweep2_kernel" if info.pair else "lbm::sweep_kernel"),
                 "bytes_per_lup": BYTES_PER_LUP[st_main], "sweep_ms": sweep_ms,
                 "exchange_ms": xch_ms, "exchange_pdfs": info.exchange_pdfs}
@@ -301,7 +308,11 @@ def run_gpu(args):
                          ("bgk_f64", dict(storage=L.LBM_F64)),
                          # velocity inlet (moving-wall face) at -x, pressure outlet at +x
                          ("bgk_inlet_outlet_f32", dict(periodic=(0, 0, 1), face_bc=(2, 3, 1, 1, 1, 1),
-                                                       wall_u=(0.01, 0, 0), force=(0, 0, 0), rho_b=1.0))]:
+                                                       wall_u=(0.01, 0, 0), force=(0, 0, 0), rho_b=1.0)),
+                         # one PDF array updated in place (AA pattern)
+                         ("bgk_aa_f32", dict(streaming=L.LBM_STREAM_AA)),
+                         ("bgk_aa_f16s", dict(streaming=L.LBM_STREAM_AA, storage=L.LBM_F16S,
+                                              storage_scale=256.0))]:
             c = make(**kw)
             if not args.no_autotune:
                 L.lbm_autotune(c, None)
@@ -320,7 +331,9 @@ def run_gpu(args):
                 "mlups": cells * vsteps / (e0.elapsed_time(e1) * 1e-3) / 1e6,
                 "sweep_gbs": BYTES_PER_LUP[st] * cells / (sw * 1e-3) / 1e9,
                 "frac": BYTES_PER_LUP[st] * cells / (sw * 1e-3) / 1e9 / peak,
-                "bytes_per_lup": BYTES_PER_LUP[st]}
+                "bytes_per_lup": BYTES_PER_LUP[st],
+                "device_gb": L.lbm_get_info(c).device_bytes / 1e9,
+                "sweep_config": list(L.lbm_get_sweep_config(c))}
             c.destroy()
 
     batch = None
@@ -501,16 +514,24 @@ def run_sizes_report(args):
     L.use_torch_allocator()
     peak = _peaks()[0]
     rows = []
-    for n in args.sizes:
-        for per_axis in (1, 2, 4):
+    for n, per_axis, mode in [(n, pa, m) for n in args.sizes for m in args.size_streaming
+                              for pa in args.size_splits]:
+        if True:
             b = n // per_axis
-            p = L.make_params(force=(FORCE, 0, 0), **W.channel_bc())
+            streaming = L.LBM_STREAM_AA if mode == "aa" else L.LBM_STREAM_TWO_GRID
+            p = L.make_params(force=(FORCE, 0, 0), streaming=streaming, **W.channel_bc())
+            torch.cuda.empty_cache()
             try:
                 ctx = L.lbm_create((n,) * 3, (b,) * 3, TAU, None, p)
-            except L.LBMError as e:  # e.g. a Block beyond 32-bit plane offsets
-                rows.append({"n": n, "blocks": per_axis**3, "block": b, "refused": str(e)})
+            except L.LBMError as e:  # a Block beyond 32-bit plane offsets, or out of memory
+                rows.append({"n": n, "blocks": per_axis**3, "block": b, "streaming": mode, "refused": str(e)})
+                print(rows[-1], file=sys.stderr, flush=True)
                 continue
-            L.lbm_autotune(ctx, None)
+            tuned = True
+            try:
+                L.lbm_autotune(ctx, None)
+            except L.LBMError:  # in place, tuning needs a transient copy of the state
+                tuned = False
             steps = int(min(2000, max(50, 3e10 // n**3)))
             L.lbm_step(ctx, 10)
             torch.cuda.synchronize()
@@ -528,7 +549,8 @@ def run_sizes_report(args):
             sw = pr.sweep_ms / max(1, pr.sweep_launches)
             ex = pr.exchange_ms / 20
             m, _, nonfinite = L.lbm_invariants(ctx)
-            row = {"n": n, "blocks": per_axis**3, "block": b, "steps": steps,
+            row = {"n": n, "blocks": per_axis**3, "block": b, "streaming": mode, "autotuned": tuned,
+                   "device_gb": L.lbm_get_info(ctx).device_bytes / 1e9, "steps": steps,
                    "mlups": n**3 * steps / (ms * 1e-3) / 1e6,
                    "sweep_hbm_frac": BYTES_PER_LUP[0] * n**3 / (sw * 1e-3) / 1e9 / peak,
                    "exchange_share": ex / (ex + sw), "sweep_config": list(L.lbm_get_sweep_config(ctx)),
@@ -700,7 +722,7 @@ def run_unet_report(args):
     return 0
 
 
-def _ncu_traffic(name):
+def _ncu_traffic(name, sources=None):
     """DRAM bytes per launch from the committed ncu summary, if it is current."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
@@ -709,7 +731,7 @@ def _ncu_traffic(name):
         ent = d[name]
         from paper_1007_1388_gb300 import build
 
-        if ent.get("kernel_hash") != build.kernel_hash():
+        if ent.get("kernel_hash") != build.kernel_hash(*([sources] if sources else [])):
             return None
         return ent["dram_bytes_per_launch_full"]
     except Exception:
@@ -752,6 +774,12 @@ def main():
     ap.add_argument("--trt", action="store_true", help="TRT instead of BGK")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sweep configuration")
     ap.add_argument("--kernel", default="", help="auto | register | tma")
+    ap.add_argument("--streaming", default="two", choices=["two", "aa"],
+                    help="two PDF arrays (default) or one updated in place")
+    ap.add_argument("--size-streaming", nargs="+", default=["two"], choices=["two", "aa"],
+                    help="--report sizes: streaming modes to run")
+    ap.add_argument("--size-splits", type=int, nargs="+", default=[1, 2, 4],
+                    help="--report sizes: Blocks per axis")
     ap.add_argument("--force", type=float, default=FORCE, help="body force along x")
     args = ap.parse_args()
     if args.warmup < 3:

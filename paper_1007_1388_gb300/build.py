@@ -46,6 +46,7 @@ def _stale(target: str, deps) -> bool:
 SWEEP_SOURCES = ("sweep_impl.cuh", "sweep2_impl.cuh", "collide.cuh", "device_common.cuh", "sweep_types.h",
                  "sweep_f32.cu", "sweep2_f32.cu",
                  "sweep_f16s.cu", "sweep_bf16s.cu", "sweep_f64.cu")
+AA_SOURCES = ("sweep_aa.cuh", "collide.cuh", "device_common.cuh", "sweep_types.h", "sweep_aa_f32.cu")
 
 
 def kernel_hash(files=SWEEP_SOURCES) -> str:

@@ -604,10 +604,8 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                     b.nx = s.bdims[0];
                     b.ny = s.bdims[1];
                     b.nz = s.bdims[2];
-                    // in place, two padding columns per row hold what the odd
-                    // step pushes through wall x faces (x = nx, and x = -1 as
-                    // the previous row's last column)
-                    b.px = round_up(b.nx + (c->aa ? 2 : 0), 32 / c->elem);
+                    b.px = round_up(b.nx, 32 / c->elem);
+                    b.xw_base[0] = b.xw_base[1] = -1;
                     b.pxf = round_up(OXF + b.nx + 1, 16);
                     b.py = b.ny + 2;
                     b.G = plane_cells((long long)b.px * b.py * (b.nz + 2), c->elem);
@@ -692,6 +690,17 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                         }
                     }
                 }
+        // ---- in place: side storage beyond wall x faces
+        if (c->aa)
+            for (int bi = first_block; bi < int(c->blocks.size()); ++bi) {
+                BlockGeom &b = c->blocks[bi];
+                const long long rows = (long long)b.py * (b.nz + 2);
+                for (int side = 0; side < 2; ++side)
+                    if ((side == 0 ? b.xm_block : b.xp_block) < 0) {
+                        b.xw_base[side] = pdf_base;
+                        pdf_base += 5 * rows;
+                    }
+            }
         // ---- ghost exchange plan: faces and edges with a neighbour block
         for (int bz = 0; bz < nb[2]; ++bz)
             for (int by = 0; by < nb[1]; ++by)

@@ -35,15 +35,29 @@
 // FP32 until the collision.
 //
 // Across Blocks: mode 1 reaches across x faces through the Blocks' xm_off /
-// xp_off like the two-array pull (and, beyond a wall face, into two padding
-// columns of every row); across y/z faces it reads and writes the ghost rows,
-// which a forward exchange fills before it and a reverse exchange drains
-// after it.
+// xp_off like the two-array pull; beyond a wall x face (no x ghost columns)
+// the slots of the wall cells live in a small side array per face; across
+// y/z faces it reads and writes the ghost rows, which a forward exchange fills
+// before it and a reverse exchange drains after it.
 #pragma once
 
 #include "device_common.cuh"
 
 namespace lbm {
+
+// Element offset in the PDF buffer of slot q of the cell (x+dx, y+dy, z+dz)
+// next to cell (x, y, z) of Block b (c its index): the Block's own storage,
+// the x neighbour's, or, beyond a wall x face, the face's side array.
+__device__ __forceinline__ long long aa_slot(const BlockGeom &b, int q, int x, int y, int z, int c, int dx, int dy,
+                                             int dz, long long xm, long long xp, int px, int pxy, int G)
+{
+    const int side = dx < 0 && x == 0 ? 0 : (dx > 0 && x == b.nx - 1 ? 1 : -1);
+    if (side >= 0 && b.xw_base[side] >= 0)
+        return b.xw_base[side] + (long long)xdir_index(q) * ((long long)b.py * (b.nz + 2)) +
+               (long long)(z + dz + 1) * b.py + (y + dy + 1);
+    const long long o = dx > 0 ? xp : (dx < 0 ? xm : 0ll);
+    return b.pdf_base + o + ((long long)q * G + c + dx + dy * px + dz * pxy);
+}
 
 // MODE: 0 step from an odd time, 1 step from an even time, 2 the state of
 // an odd time read back into the natural layout of a second array (a.dst:
@@ -84,8 +98,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_consta
         const uint8_t *fl = a.flags + b.cell_base;
         const uint8_t flag = fl[cf];
         if (flag & F_KIND) continue;  // solid and pressure cells are not updated
-        const S *R = static_cast<const S *>(a.src) + b.pdf_base;
-        S *W = static_cast<S *>(a.dst) + b.pdf_base;
+        const S *R0 = static_cast<const S *>(a.src);
+        S *W0 = static_cast<S *>(a.dst);
+        const S *R = R0 + b.pdf_base;
+        S *W = W0 + b.pdf_base;
         // neighbours across the -x face (x = 0) and the +x face (x = nx - 1)
         const long long xm = x == 0 ? b.xm_off : 0ll, xp = x == nx - 1 ? b.xp_off : 0ll;
         T f[Q];
@@ -105,8 +121,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_consta
                     for (int q = 1; q < Q; ++q) {
                         if (!((lm >> q) & 1u)) continue;
                         if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
-                        const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
-                        Tr::st(W + (o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))),
+                        Tr::st(W0 + aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G),
                                pres_pull(q, pb, Tr::to_t(Tr::from_t(f[opp(q)]))));
                     }
                 }
@@ -122,18 +137,15 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_consta
             for (int q = 1; q < Q; ++q) {
                 if (!((lm >> q) & 1u)) continue;
                 if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
-                const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
-                Tr::st(W + (o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))),
+                Tr::st(W0 + aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G),
                        pres_pull(q, pb, Tr::to_t(R[q * G + c])));
             }
             continue;
         }
         if (MODE == 2) {  // S_q(x) was pushed to x + e_q
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
-                W[q * G + c] = R[o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))];
-            }
+            for (int q = 0; q < Q; ++q)
+                W[q * G + c] = R0[aa_slot(b, q, x, y, z, c, ex(q), ey(q), ez(q), xm, xp, px, pxy, G)];
             continue;
         }
 
@@ -148,37 +160,45 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_consta
         } else {
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
-                const S *pa = R + (o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy)));
                 if ((lm >> q) & 1u) {
                     const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                     if (PRES && (nf & F_KIND) == F_PRESSURE) {
-                        f[q] = Tr::to_t(*pa);  // prepared by the step that produced S
+                        // prepared by the step that produced S
+                        f[q] = Tr::to_t(
+                            R0[aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G)]);
                     } else {
                         T v = Tr::to_t(R[q * G + c]);  // S_opp(q)(x), stored swapped
                         if ((nf & F_KIND) == F_MOVING) v = vadd(v, K.bbw[q]);
                         f[q] = v;
                     }
                 } else {
-                    f[q] = Tr::to_t(*pa);
+                    const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
+                    f[q] = Tr::to_t(R[o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))]);
                 }
             }
         }
         collide_v<COLL, FORCE>(f, KR);
+        if (!near) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
-            Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
-        }
-        if (near) {
+            for (int q = 0; q < Q; ++q) {
+                const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
+                Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
+            }
+        } else {
             PresBC<T> pbw{};
             if (PRES && (lm & L_PRESSURE))
                 pbw = pres_setup_regs<ST, T>(f, param_pb<T>(a), K.ufac, K.uoff[0], K.uoff[1], K.uoff[2], K.c45,
                                              K.nc15);
 #pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                if (!((lm >> opp(q)) & 1u)) continue;
-                // x + e_q is not fluid: S'_q comes back to x along e_opp(q)
+            for (int q = 0; q < Q; ++q) {
+                if (!((lm >> opp(q)) & 1u)) {
+                    const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
+                    Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
+                    continue;
+                }
+                // x + e_q is not fluid: S'_q is kept in that cell's slot (to read
+                // the state back) and comes back to x along e_opp(q)
+                Tr::st(W0 + aa_slot(b, q, x, y, z, c, ex(q), ey(q), ez(q), xm, xp, px, pxy, G), f[q]);
                 T v = f[q];
                 const uint8_t nf = fl[cf + (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                 if ((nf & F_KIND) == F_MOVING)

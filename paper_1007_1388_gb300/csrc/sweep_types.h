@@ -68,7 +68,21 @@ struct BlockGeom {
     long long out_base;   // first cell of the instance in the concatenated output
     int NX, NY, NZ;       // instance size
     int pad_;
+    // in-place streaming: side storage of the slots of the cells just beyond
+    // a wall -x / +x face (what the pull-and-push step streams into the wall,
+    // and pressure nodes' prepared values); element offset in the PDF buffer
+    // of [5 directions with e_x = -1 / +1][py * (nz + 2) rows], -1 where the
+    // face has a neighbour Block (or two arrays are used)
+    long long xw_base[2];
 };
+
+// index 0..4 of direction q among the five with the same e_x (ascending q)
+__host__ __device__ constexpr int xdir_index(int q)
+{
+    int k = 0;
+    for (int r = 0; r < q; ++r) k += ex(r) == ex(q) ? 1 : 0;
+    return k;
+}
 
 // Collision constants of one instance in scaled units (scale s of the
 // storage; s = 1 for F32 / F64):
