@@ -57,6 +57,7 @@ class _Problem(ctypes.Structure):
         ("force", ctypes.c_double * 3),
         ("wall_u", ctypes.c_double * 3),
         ("rho_b", ctypes.c_double),
+        ("qw", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -79,6 +80,9 @@ class Problem:
     force: tuple = (0.0, 0.0, 0.0)
     wall_u: tuple = (0.0, 0.0, 0.0)
     rho_b: float | None = None  # density of PRESSURE boundaries; None = rho0
+    # curved walls: wall distances (19, nz, ny, nx) of the pulls whose source is a
+    # NOSLIP node (the wall at x - q e_i); None = half-way everywhere
+    qw: np.ndarray | None = None
     _c: _Problem = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -93,6 +97,10 @@ class Problem:
         c.force[:] = [float(v) for v in self.force]
         c.wall_u[:] = [float(v) for v in self.wall_u]
         c.rho_b = float(self.rho0 if self.rho_b is None else self.rho_b)
+        if self.qw is not None:
+            nx, ny, nz = self.dims
+            self.qw = np.ascontiguousarray(self.qw, dtype=np.float64).reshape(19, nz, ny, nx)
+            c.qw = self.qw.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self._c = c
         if self.flags is not None:
             nx, ny, nz = self.dims

@@ -79,7 +79,36 @@ typedef struct {
     double force[3];   /* body force density F */
     double wall_u[3];  /* velocity of every ORC_MOVING wall */
     double rho_b;      /* density of every ORC_PRESSURE boundary */
+    const double *qw;  /* curved walls: [19][N] wall distances, NULL = half-way everywhere */
 } orc_problem;
+
+static int classify(const orc_problem *p, const uint8_t *flags, int x, int y, int z, long *c);
+
+/* Curved resting walls (not in the paper, which leaves further boundary
+ * conditions to future work, Sec. 6): the linear interpolated bounce-back of
+ * Bouzidi, Firdaouss and Lallemand (2001).  For the pull of direction i at
+ * fluid cell x whose source x - e_i is an ORC_NOSLIP node, qw[i][x] = q in
+ * (0, 1] places the wall at x - q e_i (q = 1/2: half-way).  The value that
+ * returns to x along e_i is interpolated from post-collision populations
+ * moving towards the wall (direction ibar = opposite(i)):
+ *   q <  1/2: 2q f*_ibar(x) + (1 - 2q) f*_ibar(x + e_i)  (the fluid neighbour
+ *             on the far side; if it is not fluid, half-way bounce-back)
+ *   q >= 1/2: f*_ibar(x) / (2q) + (1 - 1/(2q)) f*_i(x)
+ * Both reduce to f*_ibar(x) at q = 1/2.  The weights sum to one, so the rule
+ * holds for the shifted f~ as it stands. */
+static double curved_pull(const orc_problem *p, const uint8_t *flags, const double *src, long N, long c,
+                          int x, int y, int z, int i)
+{
+    const int ib = opposite(i);
+    const double q = p->qw[i * N + c];
+    if (q < 0.5) {
+        long s = -1;
+        if (classify(p, flags, x + E[i][0], y + E[i][1], z + E[i][2], &s) != ORC_FLUID)
+            return src[ib * N + c];
+        return 2.0 * q * src[ib * N + c] + (1.0 - 2.0 * q) * src[ib * N + s];
+    }
+    return src[ib * N + c] / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * src[i * N + c];
+}
 
 /* Pressure boundary (not in the paper, which leaves further boundary
  * conditions to future work, Sec. 6): anti-bounce-back with the velocity
@@ -247,6 +276,8 @@ void orc_step(const orc_problem *p, const uint8_t *flags, const double *src, dou
                         double ub[3];
                         stored_velocity(p, src, N, c, ub);
                         f[i] = -src[opposite(i) * N + c] + abb_term(p, i, ub);
+                    } else if (kind == ORC_NOSLIP && p->qw) {
+                        f[i] = curved_pull(p, flags, src, N, c, x, y, z, i);
                     } else {
                         double bb = src[opposite(i) * N + c];
                         if (kind == ORC_MOVING) {
@@ -307,6 +338,8 @@ void orc_step_cells(const orc_problem *p, const uint8_t *flags, const double *sr
                 double ub[3];
                 stored_velocity(p, src, N, c, ub);
                 f[i] = -src[opposite(i) * N + c] + abb_term(p, i, ub);
+            } else if (kind == ORC_NOSLIP && p->qw) {
+                f[i] = curved_pull(p, flags, src, N, c, x, y, z, i);
             } else {
                 double bb = src[opposite(i) * N + c];
                 if (kind == ORC_MOVING) {
@@ -478,6 +511,23 @@ void orc_push_step(const orc_problem *p, const uint8_t *flags, const double *src
                         double usq = ux * ux + uy * uy + uz * uz;
                         recv[opposite(i) * N + c] =
                             2.0 * weight(i) * (p->rho_b + p->rho0 * (4.5 * eu * eu - 1.5 * usq)) - g;
+                    } else if (kind == ORC_NOSLIP && p->qw) {
+                        /* the wall sits at x + q e_i; the reflected population
+                         * (direction k) mixes g_i of x with g_i of the upstream
+                         * neighbour x - e_i (q < 1/2) or with g_k of x (q >= 1/2) */
+                        int k = opposite(i);
+                        double q = p->qw[k * N + c], r;
+                        if (q < 0.5) {
+                            int up[3] = {x - E[i][0], y - E[i][1], z - E[i][2]};
+                            long u = -1;
+                            if (push_target(p, flags, up, &u) == ORC_FLUID)
+                                r = 2.0 * q * g + (1.0 - 2.0 * q) * (src[i * N + u] + weight(i) * p->rho0);
+                            else
+                                r = g;
+                        } else {
+                            r = g / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * (src[k * N + c] + weight(k) * p->rho0);
+                        }
+                        recv[k * N + c] = r;
                     } else {
                         int k = opposite(i);
                         double ew = E[k][0] * p->wall_u[0] + E[k][1] * p->wall_u[1] +

@@ -15,6 +15,10 @@ index, or a transposed operand anywhere in the oracle fails at least one test:
                                    TRT == BGK when Lambda = (tau - 1/2)^2
 - forcing ........................ momentum grows by exactly F per cell and step,
                                    Poiseuille steady and start-up profiles
+- pressure boundary .............. push-vs-pull, rest and uniform-flow fixed points,
+                                   inlet/outlet channel (flux, profile, gradient)
+- curved walls ................... off-grid Poiseuille at second order, q = 1/2 is
+                                   half-way bounce-back, push-vs-pull brute force
 """
 import json
 import os
@@ -381,6 +385,91 @@ def test_pressure_boundary_rest_state_is_a_fixed_point(orc):
     # the wrong sign or factor would not hold it
     rho, u = orc.macroscopic(p, g)
     assert np.abs(rho[fl == 0] - rho_b).max() < 1e-15 and np.abs(u).max() < 1e-16
+
+
+# ------------------------------------------------------------ curved walls
+def _channel_qw(orc, H, db, dt):
+    """Wall distances of a y channel: the bottom wall db below row 0, the top
+    wall dt above row H-1, on every link that crosses them."""
+    e, _, _ = orc.lattice()
+    qw = np.full((19, 1, H, 1), 0.5)
+    for i in range(19):
+        if e[i, 1] == 1:
+            qw[i, 0, 0, 0] = db
+        if e[i, 1] == -1:
+            qw[i, 0, H - 1, 0] = dt
+    return qw
+
+
+def _poiseuille_error(orc, H, db, dt, coll, curved=True, tau=0.8, F=1e-6):
+    p = orc.Problem(dims=(1, H, 1), tau=tau, periodic=(1, 0, 1), collision=coll, force=(F, 0, 0),
+                    qw=_channel_qw(orc, H, db, dt) if curved else None)
+    f = orc.run(p, orc.zeros(p), 12 * H * H)
+    prev = None
+    for _ in range(50):
+        f = orc.run(p, f, 2000)
+        _, u = orc.macroscopic(p, f)
+        if prev is not None and np.abs(u - prev).max() < 1e-15:
+            break
+        prev = u
+    nu = (tau - 0.5) / 3
+    y = np.arange(H)
+    ua = F / (2 * nu) * (y + db) * (H - 1 + dt - y)  # walls at -db and H-1+dt
+    return np.abs(u[0, 0, :, 0] - ua).max() / ua.max()
+
+
+@pytest.mark.parametrize("coll", [0, 1])
+@pytest.mark.parametrize("db,dt", [(0.25, 0.25), (0.75, 0.75), (0.1, 0.9), (0.3, 0.6)])
+def test_curved_walls_poiseuille_off_grid_second_order(orc, coll, db, dt):
+    """Linear interpolated bounce-back (Bouzidi et al.) on a channel whose
+    walls sit db below the first and dt above the last fluid row: the steady
+    profile converges to the parabola between the true wall positions at
+    second order (error ratio ~4 from H = 8 to 16), and is several times
+    closer to it than half-way bounce-back, which puts the walls at 1/2."""
+    orc.set_threads(os.cpu_count() or 1)
+    e8 = _poiseuille_error(orc, 8, db, dt, coll)
+    e16 = _poiseuille_error(orc, 16, db, dt, coll)
+    half = _poiseuille_error(orc, 16, db, dt, coll, curved=False)
+    orc.set_threads(1)
+    assert e16 < 8e-3
+    assert 3.4 < e8 / e16 < 4.6
+    assert half > 3 * e16
+
+
+def test_curved_walls_at_one_half_are_half_way_bounce_back(orc):
+    """Every wall distance 1/2 reduces both interpolations to f*_ibar(x)."""
+    rng = np.random.default_rng(21)
+    dims = (6, 5, 4)
+    fl = _random_flags(rng, dims, 0.3)
+    fl[fl == 2] = 1
+    kw = dict(dims=dims, tau=0.7, flags=fl, periodic=(1, 0, 0), face_bc=(1,) * 6, collision=1,
+              force=(1e-4, 0, 0))
+    f = rng.uniform(-1e-2, 1e-2, (19,) + dims[::-1]) * (fl == 0)
+    a = orc.step(orc.Problem(**kw), f)
+    b = orc.step(orc.Problem(qw=np.full((19,) + dims[::-1], 0.5), **kw), f)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pull_step_matches_push_step_with_curved_walls(orc, seed):
+    """Random wall distances on every link into a resting wall or solid cell,
+    thin gaps included (where q < 1/2 falls back to half-way bounce-back): the
+    pull rule equals the push-and-reflect rule written separately."""
+    rng = np.random.default_rng(400 + seed)
+    dims = tuple(int(v) for v in rng.integers(3, 6, 3))
+    fl = _random_flags(rng, dims, 0.3)
+    qw = rng.uniform(0.05, 1.0, (19,) + dims[::-1])
+    p = orc.Problem(dims=dims, tau=float(rng.uniform(0.55, 1.5)), flags=fl,
+                    periodic=tuple(int(v) for v in rng.integers(0, 2, 3)),
+                    face_bc=tuple(int(v) for v in rng.integers(1, 3, 6)), collision=int(seed % 2),
+                    magic=float(rng.uniform(0.05, 0.3)), force=tuple(rng.uniform(-1e-3, 1e-3, 3)),
+                    wall_u=tuple(rng.uniform(-0.05, 0.05, 3)), qw=qw)
+    f = rng.uniform(-1e-2, 1e-2, (19,) + dims[::-1]) * (p.flags == 0)
+    for _ in range(3):
+        a = orc.step(p, f)
+        b = orc.push_step(p, f)
+        assert np.abs(a - b).max() < 1e-14
+        f = a
 
 
 def test_step_cells_and_macroscopic_agree_with_step(orc):
