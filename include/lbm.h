@@ -286,6 +286,30 @@ int lbm_residual_vs_snapshot(lbm_ctx *ctx, int steps_since, double *r, double *p
 int lbm_run_to_residual_each(lbm_ctx *ctx, double tol, int check_every, int interval, long long max_steps,
                              long long *steps, double *res);
 
+/*
+ * lbm_set_wall_distances - curved resting walls (not in the paper, which
+ * leaves further boundary conditions to future work, Sec. 6): linear
+ * interpolated bounce-back (Bouzidi, Firdaouss and Lallemand, 2001) on the
+ * listed links; every other wall link stays half-way bounce-back.
+ *   n      : number of links (0 clears all distances).
+ *   cells  : host int64[n], fluid cell of each link in the concatenated cell
+ *            numbering of lbm_get_pdfs (instance base + x + nx (y + ny z)).
+ *   dirs   : host int[n], the pull direction i (1..18) whose source x - e_i
+ *            is a resting wall (LBM_NOSLIP cell or face).
+ *   q      : host double[n] in (0, 1], the wall's position x - q e_i along the
+ *            link (1/2: half-way).  The pull becomes
+ *              q <  1/2: 2q f*_ibar(x) + (1 - 2q) f*_ibar(x + e_i)
+ *                        (half-way where x + e_i is not fluid)
+ *              q >= 1/2: f*_ibar(x) / (2q) + (1 - 1/(2q)) f*_i(x)
+ *            with ibar = opp(i) and f* the stored post-collision state.
+ * Replaces the previous set.  The sweeps that carry it are the register
+ * sweeps (a context on the TMA sweep switches to them).  LBM_EINVAL for an
+ * index, direction or distance out of range, a cell that is not fluid or a
+ * source that is not a resting wall (no distance is then set), and for
+ * in-place streaming.
+ */
+int lbm_set_wall_distances(lbm_ctx *ctx, long long n, const long long *cells, const int *dirs, const double *q);
+
 /* Sizes of a context. */
 typedef struct {
     long long cells;          /* interior cells over all Blocks / instances */

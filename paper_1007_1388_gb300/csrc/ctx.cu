@@ -22,6 +22,7 @@
 #include <new>
 #include <sstream>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -107,6 +108,11 @@ struct lbm_ctx {
     int minb = 4;  // register budget of the sweep (resident CTAs per SM)
     std::vector<char> h_consts;  // host copy of the per-instance CollideConsts
     bool has_pressure = false;   // some cell or wall of the Patch is a pressure boundary
+    // curved walls (lbm_set_wall_distances): link table and per-flag-cell rows
+    bool has_curved = false;
+    long long curved_links = 0;
+    int *d_curv_idx = nullptr;
+    void *d_curv_q = nullptr;
     // in-place streaming (LBM_STREAM_AA): one PDF array; aa_phase 0 when it
     // holds the state swapped in the cells' own slots (read through a slot
     // remap), 1 after an odd number of steps, when it holds the state
@@ -938,7 +944,9 @@ SweepArgs sweep_args(const lbm_ctx *c, int from)
         const double rho_b = c->p.rho_b > 0.0 ? c->p.rho_b : c->p.rho0;
         a.pbd = 2.0 * sc * (rho_b - c->p.rho0);
         a.pbf = float(a.pbd);
-        a.pres = c->has_pressure ? 1 : 0;
+        a.pres = (c->has_pressure ? 1 : 0) | (c->has_curved ? 2 : 0);
+        a.curv_idx = c->d_curv_idx;
+        a.curv_q = c->d_curv_q;
     }
     if (a.unif) {
         if (c->storage == LBM_F64)
@@ -1725,6 +1733,112 @@ int lbm_run_to_residual_each(lbm_ctx *c, double tol, int check_every, int interv
     c->active.clear();
     const int rc2 = set_sweep(c, c->sw_tile, c->flat, c->grid);
     return rc ? rc : rc2;
+}
+
+// Clears every curved-wall distance of the context.
+static int clear_wall_distances(lbm_ctx *c)
+{
+    if (c->has_curved) {
+        CK(launch_curved_setup(nullptr, nullptr, nullptr, 0, c->d_flags, c->d_links, c->stored, c->d_curv_idx,
+                               nullptr, c->stream),
+           "curved clear");
+        CK(cudaStreamSynchronize(c->stream), "curved clear");
+        invalidate_graphs(c);
+    }
+    c->has_curved = false;
+    c->curved_links = 0;
+    return LBM_OK;
+}
+
+int lbm_set_wall_distances(lbm_ctx *c, long long n, const long long *cells, const int *dirs, const double *q)
+{
+    if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
+    int rc0 = clear_wall_distances(c);  // a refused call leaves none set
+    if (rc0) return rc0;
+    if (n < 0 || (n > 0 && (!cells || !dirs || !q)))
+        return fail(c, LBM_EINVAL, "lbm_set_wall_distances: bad arguments");
+    if (c->aa) return fail(c, LBM_EINVAL, "lbm_set_wall_distances: in-place streaming takes no curved walls");
+    // each link: flag index of the fluid cell and of its pull source, table row
+    const size_t nl = static_cast<size_t>(n);
+    std::vector<long long> fidx(nl), sidx(nl);
+    std::vector<int> rows(nl);
+    std::unordered_map<long long, int> row_of;
+    std::vector<int> first(size_t(c->ninst), -1);
+    for (size_t bi = 0; bi < c->blocks.size(); ++bi)
+        if (first[size_t(c->blocks[bi].inst)] < 0) first[size_t(c->blocks[bi].inst)] = int(bi);
+    for (long long k = 0; k < n; ++k) {
+        const long long cell = cells[k];
+        const int d = dirs[k];
+        if (cell < 0 || cell >= c->cells || d < 1 || d >= Q || !(q[k] > 0.0 && q[k] <= 1.0))
+            return fail(c, LBM_EINVAL, "lbm_set_wall_distances: link %lld (cell %lld, direction %d, q %g) "
+                        "out of range", k, cell, d, q[k]);
+        const int inst = int(std::upper_bound(c->inst_out_base.begin(), c->inst_out_base.end(), cell) -
+                             c->inst_out_base.begin()) - 1;
+        const int *N = &c->idims[size_t(3 * inst)];
+        const long long local = cell - c->inst_out_base[size_t(inst)];
+        const int x = int(local % N[0]), y = int((local / N[0]) % N[1]), z = int(local / ((long long)N[0] * N[1]));
+        const BlockGeom &b0 = c->blocks[size_t(first[size_t(inst)])];
+        const int nbx = N[0] / b0.nx, nby = N[1] / b0.ny;
+        const BlockGeom &b = c->blocks[size_t(first[size_t(inst)] + ((z / b0.nz) * nby + y / b0.ny) * nbx + x / b0.nx)];
+        const long long pxyf = (long long)b.pxf * b.py;
+        const long long cf = (z % b.nz + 1) * pxyf + (long long)(y % b.ny + 1) * b.pxf + x % b.nx + OXF;
+        fidx[size_t(k)] = b.cell_base + cf;
+        sidx[size_t(k)] = b.cell_base + cf - (ex(d) + ey(d) * (long long)b.pxf + ez(d) * pxyf);
+        rows[size_t(k)] = row_of.emplace(fidx[size_t(k)], int(row_of.size())).first->second;
+    }
+    const size_t nrows = row_of.size();
+    const bool f64 = c->storage == LBM_F64;
+    const size_t tbytes = std::max<size_t>(nrows, 1) * 18 * (f64 ? 8 : 4);
+    std::vector<char> table(tbytes);
+    for (size_t r = 0; r < std::max<size_t>(nrows, 1) * 18; ++r) {
+        if (f64)
+            reinterpret_cast<double *>(table.data())[r] = 0.5;
+        else
+            reinterpret_cast<float *>(table.data())[r] = 0.5f;
+    }
+    for (long long k = 0; k < n; ++k) {
+        const size_t at = size_t(rows[size_t(k)]) * 18 + size_t(dirs[k] - 1);
+        if (f64)
+            reinterpret_cast<double *>(table.data())[at] = q[k];
+        else
+            reinterpret_cast<float *>(table.data())[at] = float(q[k]);
+    }
+    disown(c, c->d_curv_q);
+    c->d_curv_q = nullptr;
+    int rc;
+    if ((rc = upload(c, reinterpret_cast<char **>(&c->d_curv_q), table))) return rc;
+    if (!c->d_curv_idx && (rc = own(c, &c->d_curv_idx, sizeof(int) * size_t(std::max<long long>(c->stored, 1)))))
+        return rc;
+    CK(cudaMemsetAsync(c->d_curv_idx, 0xff, sizeof(int) * size_t(c->stored), c->stream), "memset");
+    Temp t(c, (sizeof(long long) * 2 + sizeof(int)) * size_t(std::max<long long>(n, 1)) + sizeof(int));
+    if (!t.p) return fail(c, LBM_ENOMEM, "temporary of %zu bytes", t.bytes);
+    long long *dfi = static_cast<long long *>(t.p), *dsi = dfi + n;
+    int *drows = reinterpret_cast<int *>(dsi + n), *dbad = drows + n;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(dfi, fidx.data(), sizeof(long long) * size_t(n), cudaMemcpyHostToDevice, c->stream), "H2D");
+        CK(cudaMemcpyAsync(dsi, sidx.data(), sizeof(long long) * size_t(n), cudaMemcpyHostToDevice, c->stream), "H2D");
+        CK(cudaMemcpyAsync(drows, rows.data(), sizeof(int) * size_t(n), cudaMemcpyHostToDevice, c->stream), "H2D");
+    }
+    CK(cudaMemsetAsync(dbad, 0, sizeof(int), c->stream), "memset");
+    CK(launch_curved_setup(dfi, dsi, drows, n, c->d_flags, c->d_links, c->stored, c->d_curv_idx, dbad, c->stream),
+       "curved setup");
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    CK(cudaStreamSynchronize(c->stream), "lbm_set_wall_distances");
+    invalidate_graphs(c);
+    if (bad) {
+        c->has_curved = true;  // bits may be set: clear them
+        if ((rc = clear_wall_distances(c))) return rc;
+        return fail(c, LBM_EINVAL, "lbm_set_wall_distances: %d link(s) do not start at a fluid cell or do not "
+                    "pull from a resting wall (LBM_NOSLIP); no distances set", bad);
+    }
+    c->has_curved = n > 0;
+    c->curved_links = n;
+    if (c->has_curved) {  // the TMA sweep has no curved links
+        c->kernel = LBM_KERNEL_REGISTER;
+        c->tma_grid = 0;
+    }
+    return LBM_OK;
 }
 
 int lbm_get_info(lbm_ctx *c, lbm_info *info)

@@ -167,6 +167,38 @@ __device__ __forceinline__ T pres_pull(int q, const PresBC<T> &p, T g_opp)
     return vsub(vmul(T(wq(q)), vfma(vmul(p.c9, eu), eu, p.P)), g_opp);
 }
 
+// ------------------------------------------------------- curved walls
+// Linear interpolated bounce-back (Bouzidi, Firdaouss and Lallemand, 2001) on
+// the pulled values f of a near-wall cell whose link mask has L_CURVED: the
+// pull of direction p from a resting wall node at distance q along -e_p
+// (table row `row`, q = 1/2 elsewhere) already holds the half-way value
+// S_opp(p)(x); it becomes
+//   q <  1/2: 2q S_opp(p)(x) + (1 - 2q) f_opp(p)   (f_opp(p) = S_opp(p)(x + e_p),
+//             the pull from the fluid neighbour beyond; half-way if x + e_p is
+//             not fluid)
+//   q >= 1/2: S_opp(p)(x) / (2q) + (1 - 1/(2q)) S_p(x)
+// Only wall pulls change, and f_opp(p) of the first case is a plain pull, so
+// the order of the directions does not matter.  `srcp` reads S_p(x).
+template <typename T, typename LoadOwn>
+__device__ __forceinline__ void curved_links(T (&f)[Q], uint32_t lm, const T *row, LoadOwn srcp)
+{
+#pragma unroll
+    for (int p = 1; p < Q; ++p) {
+        if (!((lm >> p) & 1u)) continue;
+        const T q = row[p - 1];
+        if (q == T(0.5)) continue;
+        const T bb = f[p];
+        if (q < T(0.5)) {
+            if ((lm >> opp(p)) & 1u) continue;
+            const T q2 = vadd(q, q);
+            f[p] = vfma(q2, bb, vmul(vsub(T(1), q2), f[opp(p)]));
+        } else {
+            const T h = T(1) / vadd(q, q);
+            f[p] = vfma(h, bb, vmul(vsub(T(1), h), srcp(p)));
+        }
+    }
+}
+
 // the setup from the Patch's collision constants: kernel parameters for a
 // single instance (UNIF), else the instance's table entry
 template <int ST, bool UNIF, typename T, bool SWAP = false>

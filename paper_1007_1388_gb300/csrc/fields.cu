@@ -1,6 +1,7 @@
 // Kernels around the sweep: the ghost-layer exchange between Blocks, the
 // moment (macroscopic) output, equilibrium initialisation, PDF conversion
 // for checkpoints, and the FP64 invariant / residual reductions.
+#include <algorithm>
 #include <cstdio>
 
 #include "device_common.cuh"
@@ -636,6 +637,42 @@ cudaError_t tma_occupancy(int storage, int tx, int collision, int forced, int *c
 }
 
 int tma_stages(int storage) { return storage == 0 ? 4 : 5; }
+
+// Curved walls: validate the listed links against the flags (fluid cell,
+// resting-wall source), then point each cell at its table row and mark its
+// link mask.  `bad` counts rejected links.
+__global__ void curved_setup_kernel(const long long *fidx, const long long *sidx, const int *rows, long long n,
+                                    const uint8_t *flags, uint32_t *links, int *idx, int *bad)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        if ((flags[fidx[k]] & F_KIND) != F_FLUID || (flags[sidx[k]] & F_KIND) != F_NOSLIP) {
+            atomicAdd(bad, 1);
+            continue;
+        }
+        idx[fidx[k]] = rows[k];
+        atomicOr(&links[fidx[k]], L_CURVED);
+    }
+}
+
+__global__ void clear_link_bit_kernel(uint32_t *links, long long n, uint32_t bit)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        links[k] &= ~bit;
+}
+
+cudaError_t launch_curved_setup(const long long *fidx, const long long *sidx, const int *rows, long long n,
+                                const uint8_t *flags, uint32_t *links, long long nlinks, int *idx, int *bad,
+                                cudaStream_t s)
+{
+    clear_link_bit_kernel<<<1024, 256, 0, s>>>(links, nlinks, L_CURVED);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n == 0) return e;
+    const long long g = std::min<long long>((n + 255) / 256, 4096);
+    curved_setup_kernel<<<unsigned(g), 256, 0, s>>>(fidx, sidx, rows, n, flags, links, idx, bad);
+    return cudaGetLastError();
+}
 
 // In-place sweep dispatch (kernels live in sweep_aa_*.cu).
 template <int ST> cudaError_t launch_sweep_aa_st(const SweepArgs &, int, cudaStream_t);

@@ -82,6 +82,12 @@ struct ExchangeArgs {
 cudaError_t launch_exchange(const ExchangeArgs &a, cudaStream_t s);
 cudaError_t launch_exchange_flagged(const XSlabF *slabs, int nslabs, void *buf, int elem_bytes,
                                     const uint8_t *flags, cudaStream_t s);
+// Curved walls: clears L_CURVED on all nlinks masks, then validates the n
+// links (flag index of the fluid cell, of its resting-wall source, table row)
+// and sets idx / L_CURVED; *bad counts links whose kinds do not fit.
+cudaError_t launch_curved_setup(const long long *fidx, const long long *sidx, const int *rows, long long n,
+                                const uint8_t *flags, uint32_t *links, long long nlinks, int *idx, int *bad,
+                                cudaStream_t s);
 // In-place (AA-pattern) sweep: mode 0 even step, 1 odd step, 2 gather of an
 // odd-time state into the natural layout of a.dst.
 cudaError_t launch_sweep_aa(const SweepArgs &a, int mode, cudaStream_t s);

@@ -58,7 +58,7 @@ template <> struct Pair<2> {
 
 // The 19 pulled values of one cell next to a wall (half-way bounce-back),
 // from its link mask (MASK) or its neighbours' flags.
-template <int ST, bool MASK, bool UNIF, bool PRES>
+template <int ST, bool MASK, bool UNIF, int XBC>
 __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, const BlockGeom &b,
                                           const CollideConsts<float> *cc, const typename Traits<ST>::S *src,
                                           const typename Traits<ST>::S *srcm, const typename Traits<ST>::S *srcp,
@@ -68,9 +68,9 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
     using S = typename Tr::S;
     if (MASK) {
         const uint32_t lm = __ldg(a.links + b.cell_base + cf);
-        const bool mv = (lm & (PRES ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
+        const bool mv = (lm & ((XBC & 1) ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
         PresBC<float> pbc{};
-        if (PRES && (lm & L_PRESSURE)) pbc = pres_cell<ST, UNIF, float>(a.kf, cc, a.pbf, src, c, G);
+        if ((XBC & 1) && (lm & L_PRESSURE)) pbc = pres_cell<ST, UNIF, float>(a.kf, cc, a.pbf, src, c, G);
         v[0] = Tr::ld(src + c);
 #pragma unroll
         for (int q = 1; q < Q; ++q) {
@@ -82,14 +82,14 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
                 const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                 if ((nf & F_KIND) == F_MOVING)
                     w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
-                else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                else if ((XBC & 1) && (nf & F_KIND) == F_PRESSURE)
                     w = pres_pull(q, pbc, w);
             }
             v[q] = w;
         }
     } else {
         PresBC<float> pbc{};
-        if (PRES && (__ldg(a.links + b.cell_base + cf) & L_PRESSURE))
+        if ((XBC & 1) && (__ldg(a.links + b.cell_base + cf) & L_PRESSURE))
             pbc = pres_cell<ST, UNIF, float>(a.kf, cc, a.pbf, src, c, G);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -98,7 +98,7 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
                 float w = Tr::ld(src + (opp(q) * G + c));
                 if ((nf & F_KIND) == F_MOVING)
                     w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
-                else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                else if ((XBC & 1) && (nf & F_KIND) == F_PRESSURE)
                     w = pres_pull(q, pbc, w);
                 v[q] = w;
             } else {
@@ -107,6 +107,18 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
             }
         }
     }
+}
+
+// curved walls of one near-wall cell (pressure-and-curved kernels only)
+template <int ST>
+__device__ __forceinline__ void pull_curved(float (&v)[Q], const SweepArgs &a, const BlockGeom &b,
+                                            const typename Traits<ST>::S *src, int c, int cf, int G)
+{
+    using Tr = Traits<ST>;
+    const uint32_t lm = __ldg(a.links + b.cell_base + cf);
+    if (lm & L_CURVED)
+        curved_links(v, lm, static_cast<const float *>(a.curv_q) + 18ll * __ldg(a.curv_idx + b.cell_base + cf),
+                     [&](int p) { return Tr::ld(src + (p * G + c)); });
 }
 
 // the plain pull of one cell (no wall among its sources)
@@ -124,7 +136,7 @@ __device__ __forceinline__ void pull_plain(float (&v)[Q], const typename Traits<
     }
 }
 
-template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK, bool PRES>
+template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK, int XBC>
 __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant__ SweepArgs a)
 {
     using Tr = Traits<ST>;
@@ -185,14 +197,18 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
         } else {
             float v0[Q], v1[Q];
             const S *srcp0 = src, *srcm1 = src;  // the inner faces of the pair stay in the Block
-            if (near0)
-                pull_near<ST, MASK, UNIF, PRES>(v0, a, b, cc, src, srcm0, srcp0, fl, c, cf, px, pxy, pxf, pxyf, G);
-            else
+            if (near0) {
+                pull_near<ST, MASK, UNIF, XBC>(v0, a, b, cc, src, srcm0, srcp0, fl, c, cf, px, pxy, pxf, pxyf, G);
+                if (XBC & 2) pull_curved<ST>(v0, a, b, src, c, cf, G);
+            } else {
                 pull_plain<ST>(v0, src, srcm0, srcp0, c, px, pxy, G);
-            if (near1)
-                pull_near<ST, MASK, UNIF, PRES>(v1, a, b, cc, src, srcm1, srcp1, fl, c + 1, cf + 1, px, pxy, pxf, pxyf, G);
-            else
+            }
+            if (near1) {
+                pull_near<ST, MASK, UNIF, XBC>(v1, a, b, cc, src, srcm1, srcp1, fl, c + 1, cf + 1, px, pxy, pxf, pxyf, G);
+                if (XBC & 2) pull_curved<ST>(v1, a, b, src, c + 1, cf + 1, G);
+            } else {
                 pull_plain<ST>(v1, src, srcm1, srcp1, c + 1, px, pxy, G);
+            }
 #pragma unroll
             for (int q = 0; q < Q; ++q) f[q] = f2_pack(v0[q], v1[q]);
         }
@@ -215,30 +231,32 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
     }
 }
 
-template <int ST, int MINB, bool UNIF, bool MASK, bool PRES>
+template <int ST, int MINB, bool UNIF, bool MASK, int XBC>
 void launch_sweep2_pres(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
     if (a.collision == 0) {
         if (a.forced)
-            sweep2_kernel<ST, 0, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 0, true, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
         else
-            sweep2_kernel<ST, 0, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 0, false, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
     } else {
         if (a.forced)
-            sweep2_kernel<ST, 1, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 1, true, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
         else
-            sweep2_kernel<ST, 1, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep2_kernel<ST, 1, false, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
     }
 }
 
-// pressure boundaries: a separate instantiation (see launch_sweep_mask)
+// pressure boundaries and curved walls: separate instantiations (see launch_sweep_mask)
 template <int ST, int MINB, bool UNIF, bool MASK>
 void launch_sweep2_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
-    if (a.pres)
-        launch_sweep2_pres<ST, MINB, UNIF, MASK, true>(a, grid, block, s);
-    else
-        launch_sweep2_pres<ST, MINB, UNIF, MASK, false>(a, grid, block, s);
+    switch (a.pres & 3) {
+    case 0: launch_sweep2_pres<ST, MINB, UNIF, MASK, 0>(a, grid, block, s); break;
+    case 1: launch_sweep2_pres<ST, MINB, UNIF, MASK, 1>(a, grid, block, s); break;
+    case 2: launch_sweep2_pres<ST, MINB, UNIF, MASK, 2>(a, grid, block, s); break;
+    default: launch_sweep2_pres<ST, MINB, UNIF, MASK, 3>(a, grid, block, s); break;
+    }
 }
 
 template <int ST, int MINB>

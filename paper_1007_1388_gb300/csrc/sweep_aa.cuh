@@ -233,10 +233,10 @@ template <int ST, int MINB>
 void launch_aa_minb(const SweepArgs &a, int mode, dim3 grid, dim3 block, cudaStream_t s)
 {
     if (mode == 0)
-        a.pres ? launch_aa_mode<ST, MINB, 0, true>(a, grid, block, s)
+        (a.pres & 1) ? launch_aa_mode<ST, MINB, 0, true>(a, grid, block, s)
                : launch_aa_mode<ST, MINB, 0, false>(a, grid, block, s);
     else if (mode == 1)
-        a.pres ? launch_aa_mode<ST, MINB, 1, true>(a, grid, block, s)
+        (a.pres & 1) ? launch_aa_mode<ST, MINB, 1, true>(a, grid, block, s)
                : launch_aa_mode<ST, MINB, 1, false>(a, grid, block, s);
     else if (mode == 2)
         launch_aa_mode<ST, MINB, 2, false>(a, grid, block, s);

@@ -30,7 +30,7 @@ namespace lbm {
 // UNIF: a single instance whose collision constants are kernel parameters.
 // MASK: near-wall cells read precomputed link masks under a warp vote (porous
 // media, where near-wall and interior cells share warps).
-template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK, bool PRES>
+template <int ST, int COLL, bool FORCE, int MINB, bool UNIF, bool MASK, int XBC>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant__ SweepArgs a)
 {
     using Tr = Traits<ST>;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
             }
         } else if (!MASK) {
             PresBC<T> pbc{};
-            if (PRES && (__ldg(a.links + b.cell_base + cf) & L_PRESSURE))
+            if ((XBC & 1) && (__ldg(a.links + b.cell_base + cf) & L_PRESSURE))
                 pbc = pres_cell<ST, UNIF, T>(param_consts<T>(a), cc, param_pb<T>(a), src, c, G);
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                     T v = Tr::ld(src + (opp(q) * G + c));
                     if ((nf & F_KIND) == F_MOVING)
                         v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
-                    else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                    else if ((XBC & 1) && (nf & F_KIND) == F_PRESSURE)
                         v = pres_pull(q, pbc, v);
                     f[q] = v;
                 } else {
@@ -112,9 +112,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
             }
         } else {
             const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
-            const bool mv = (lm & (PRES ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
+            const bool mv = (lm & ((XBC & 1) ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
             PresBC<T> pbc{};
-            if (PRES && (lm & L_PRESSURE))
+            if ((XBC & 1) && (lm & L_PRESSURE))
                 pbc = pres_cell<ST, UNIF, T>(param_consts<T>(a), cc, param_pb<T>(a), src, c, G);
             f[0] = Tr::ld(src + c);
 #pragma unroll
@@ -128,11 +128,18 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                     const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
                     if ((nf & F_KIND) == F_MOVING)
                         v = vadd(v, UNIF ? param_consts<T>(a).bbw[q] : __ldg(&cc->bbw[q]));
-                    else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                    else if ((XBC & 1) && (nf & F_KIND) == F_PRESSURE)
                         v = pres_pull(q, pbc, v);
                 }
                 f[q] = v;
             }
+        }
+        if ((XBC & 2) && near) {
+            const uint32_t lmc = __ldg(a.links + b.cell_base + cf);
+            if (lmc & L_CURVED)
+                curved_links(f, lmc,
+                             static_cast<const T *>(a.curv_q) + 18ll * __ldg(a.curv_idx + b.cell_base + cf),
+                             [&](int p) { return Tr::ld(src + (p * G + c)); });
         }
         if (UNIF)
             collide_v<COLL, FORCE>(f, KR);
@@ -143,32 +150,35 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
     }
 }
 
-template <int ST, int MINB, bool UNIF, bool MASK, bool PRES>
+template <int ST, int MINB, bool UNIF, bool MASK, int XBC>
 void launch_sweep_pres(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
     if (a.collision == 0) {
         if (a.forced)
-            sweep_kernel<ST, 0, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 0, true, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
         else
-            sweep_kernel<ST, 0, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 0, false, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
     } else {
         if (a.forced)
-            sweep_kernel<ST, 1, true, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 1, true, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
         else
-            sweep_kernel<ST, 1, false, MINB, UNIF, MASK, PRES><<<grid, block, 0, s>>>(a);
+            sweep_kernel<ST, 1, false, MINB, UNIF, MASK, XBC><<<grid, block, 0, s>>>(a);
     }
 }
 
-// Pressure boundaries are a separate instantiation, so that the kernels of
-// Patches without them keep the near-wall code they had (an extra branch
-// there costs the 16-bit sweeps their load batching).
+// Pressure boundaries (XBC bit 0) and curved walls (bit 1) are separate
+// instantiations, so that the kernels of Patches without them keep the
+// near-wall code they had (an extra branch there costs the 16-bit sweeps
+// their load batching; the curved-wall code costs registers).
 template <int ST, int MINB, bool UNIF, bool MASK>
 void launch_sweep_mask(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
-    if (a.pres)
-        launch_sweep_pres<ST, MINB, UNIF, MASK, true>(a, grid, block, s);
-    else
-        launch_sweep_pres<ST, MINB, UNIF, MASK, false>(a, grid, block, s);
+    switch (a.pres & 3) {
+    case 0: launch_sweep_pres<ST, MINB, UNIF, MASK, 0>(a, grid, block, s); break;
+    case 1: launch_sweep_pres<ST, MINB, UNIF, MASK, 1>(a, grid, block, s); break;
+    case 2: launch_sweep_pres<ST, MINB, UNIF, MASK, 2>(a, grid, block, s); break;
+    default: launch_sweep_pres<ST, MINB, UNIF, MASK, 3>(a, grid, block, s); break;
+    }
 }
 
 template <int ST, int MINB, bool UNIF>
@@ -199,12 +209,14 @@ cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
     const unsigned gx = unsigned(a.grid > 0 ? a.grid : a.ntiles);
     if (gx == 0) return cudaSuccess;
     const dim3 grid(gx, unsigned(a.tz), 1);
-    if (ST == 3)  // FP64 arithmetic needs the larger register budget
+    if constexpr (ST == 3) {  // FP64 arithmetic needs the larger register budget
         launch_sweep_minb<ST, 2>(a, grid, block, s);
-    else if (a.minb == 4)
-        launch_sweep_minb<ST, 4>(a, grid, block, s);
-    else
-        launch_sweep_minb<ST, 3>(a, grid, block, s);
+    } else {
+        if (a.minb == 4)
+            launch_sweep_minb<ST, 4>(a, grid, block, s);
+        else
+            launch_sweep_minb<ST, 3>(a, grid, block, s);
+    }
     return cudaGetLastError();
 }
 

@@ -417,7 +417,7 @@ cudaError_t tma_dispatch_pres(const TmaSweepArgs &ta, const TmaMaps &maps, int g
 template <int ST, int TX>
 cudaError_t tma_dispatch(const TmaSweepArgs &ta, const TmaMaps &maps, int grid, cudaStream_t s, int *occ)
 {
-    return ta.a.pres ? tma_dispatch_pres<ST, TX, true>(ta, maps, grid, s, occ)
+    return (ta.a.pres & 1) ? tma_dispatch_pres<ST, TX, true>(ta, maps, grid, s, occ)
                      : tma_dispatch_pres<ST, TX, false>(ta, maps, grid, s, occ);
 }
 

@@ -38,6 +38,9 @@ enum : uint8_t {
 // when one is a pressure boundary.
 constexpr uint32_t L_MOVING = 1u << 31;
 constexpr uint32_t L_PRESSURE = 1u << 30;
+// some pull of the cell crosses a curved resting wall (its distances are in
+// the curved-link table)
+constexpr uint32_t L_CURVED = 1u << 29;
 
 // Layout of a Block.  PDF planes store (ny+2)(nz+2) rows of px cells: the
 // interior x range [0, nx) padded only up to a 32-byte multiple, plus one ghost
@@ -148,7 +151,13 @@ struct SweepArgs {
     // anti-bounce-back term of direction q is w_q times this
     float pbf;
     double pbd;
-    int pres;                 // 1: the Patch has pressure boundaries (kernels built for them)
+    int pres;                 // bit 0: the Patch has pressure boundaries, bit 1: curved walls
+                              // (each selects kernels built for it)
+    // curved walls: per flag cell the row of the link table (-1: none), and
+    // the table, 18 wall distances per row (directions 1..18) in the
+    // arithmetic type; 1/2 on links that are half-way bounce-back
+    const int *curv_idx;
+    const void *curv_q;
 };
 
 }  // namespace lbm

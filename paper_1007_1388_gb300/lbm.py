@@ -119,6 +119,7 @@ SIGNATURES = {
     "lbm_autotune": ([_vp, ctypes.c_char_p, _P(ctypes.c_int)], _i),
     "lbm_get_sweep_config": ([_vp, _P(ctypes.c_int)], _i),
     "lbm_set_sweep_config": ([_vp, _P(ctypes.c_int)], _i),
+    "lbm_set_wall_distances": ([_vp, _ll, _vp, _vp, _vp], _i),
     "lbm_set_allocator": ([ALLOC_FN, FREE_FN, _vp], _i),
     "lbm_directions": ([_P(ctypes.c_int), _P(_d), _P(ctypes.c_int)], _i),
     "lbm_invariants_noalloc": ([_vp, _vp, _ll, _d, _P(_d), _vp, _vp], _i),
@@ -470,6 +471,17 @@ def lbm_get_sweep_config(ctx: Ctx):
 def lbm_set_sweep_config(ctx: Ctx, cfg):
     c = (ctypes.c_int * 8)(*[int(v) for v in cfg])
     _check(lib().lbm_set_sweep_config(ctx.ptr, c), ctx)
+
+
+def lbm_set_wall_distances(ctx: Ctx, cells, dirs, q):
+    """Curved resting walls on the listed links (cell index, pull direction
+    1..18 whose source is a resting wall, wall distance in (0, 1])."""
+    cells = np.ascontiguousarray(cells, dtype=np.int64).reshape(-1)
+    dirs = np.ascontiguousarray(dirs, dtype=np.int32).reshape(-1)
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    if not (cells.size == dirs.size == q.size):
+        raise ValueError("cells, dirs and q must have the same length")
+    _check(lib().lbm_set_wall_distances(ctx.ptr, cells.size, _ptr(cells), _ptr(dirs), _ptr(q)), ctx)
 
 
 def lbm_directions():
