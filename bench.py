@@ -312,8 +312,13 @@ def run_gpu(args):
                          # one PDF array updated in place (AA pattern)
                          ("bgk_aa_f32", dict(streaming=L.LBM_STREAM_AA)),
                          ("bgk_aa_f16s", dict(streaming=L.LBM_STREAM_AA, storage=L.LBM_F16S,
-                                              storage_scale=256.0))]:
+                                              storage_scale=256.0)),
+                         # every link into the -y / +y walls curved (walls 0.3 / 0.7 off the rows)
+                         ("bgk_curved_walls_f32", dict(curved=(0.3, 0.7)))]:
+            curved = kw.pop("curved", None)
             c = make(**kw)
+            if curved is not None:
+                L.lbm_set_wall_distances(c, *_wall_links(L, n, curved))
             if not args.no_autotune:
                 L.lbm_autotune(c, None)
             L.lbm_step(c, 5)
@@ -720,6 +725,25 @@ def run_unet_report(args):
     net.destroy()
     print(json.dumps(res))
     return 0
+
+
+def _wall_links(L, n, q):
+    """(cells, directions, distances) of every pull from the -y / +y walls of
+    an n^3 channel: the bottom wall q[0] below row 0, the top q[1] above row n-1."""
+    import numpy as np
+
+    e = L.lbm_directions()[0]
+    x, z = np.meshgrid(np.arange(n), np.arange(n))
+    cells, dirs, qs = [], [], []
+    for i in range(1, len(e)):
+        ey = int(e[i][1])
+        if ey == 0:
+            continue
+        y = 0 if ey == 1 else n - 1
+        cells.append((x + n * (y + n * z)).ravel())
+        dirs.append(np.full(n * n, i))
+        qs.append(np.full(n * n, q[0] if ey == 1 else q[1]))
+    return np.concatenate(cells), np.concatenate(dirs), np.concatenate(qs)
 
 
 def _ncu_traffic(name, sources=None):
