@@ -567,6 +567,69 @@ def run_sizes_report(args):
     return 0
 
 
+POROUS_WORKLOAD = ("D3Q19 channel through overlapping solid spheres (radii 2-6, periodic x/z, no-slip "
+                   "walls -y/+y), BGK tau=0.8, force 1e-6 along x, FP32; Block layout (64^3 Blocks) vs "
+                   "the fluid-cell list layout at each porosity")
+
+
+def run_porous_report(args):
+    """Block layout against the fluid-cell list layout on porous media of
+    several porosities: MFLUPS (fluid-cell updates per second), the sweep's
+    algorithmic bytes over its time against the measured HBM peak (153 B per
+    cell for Blocks, 224 B per fluid cell for the list), device memory.
+    Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1007_1388_gb300 import build
+
+    build.build()
+    import paper_1007_1388_gb300 as L
+    from paper_1007_1388_gb300 import workloads as W
+
+    L.use_torch_allocator()
+    peak = _peaks()[0]
+    n = args.porous_size
+    rows = []
+    for phi in args.porosities:
+        flags = W.overlapping_spheres(np.random.default_rng(4321), (n, n, n), phi)
+        nfl = int((flags == 0).sum())
+        for layout, name, bpu in ((L.LBM_LAYOUT_BLOCKS, "blocks", 153), (L.LBM_LAYOUT_SPARSE, "list", 224)):
+            torch.cuda.empty_cache()
+            p = L.make_params(force=(FORCE, 0, 0), layout=layout, **W.channel_bc())
+            ctx = L.lbm_create((n,) * 3, (64,) * 3, TAU, flags, p)
+            L.lbm_autotune(ctx, None)
+            steps = int(min(1000, max(50, 2e10 // n**3)))
+            L.lbm_step(ctx, 10)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            L.lbm_step(ctx, steps)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            L.lbm_profile_enable(ctx, True)
+            L.lbm_profile_read(ctx)
+            L.lbm_step(ctx, 20)
+            pr = L.lbm_profile_read(ctx)
+            L.lbm_profile_enable(ctx, False)
+            sw = pr.sweep_ms / max(1, pr.sweep_launches)
+            units = n**3 if layout == L.LBM_LAYOUT_BLOCKS else nfl
+            row = {"porosity": nfl / n**3, "layout": name, "steps": steps,
+                   "mflups": nfl * steps / (ms * 1e-3) / 1e6, "mlups": n**3 * steps / (ms * 1e-3) / 1e6,
+                   "sweep_ms": sw, "bytes_per_unit": bpu,
+                   "sweep_hbm_frac": bpu * units / (sw * 1e-3) / 1e9 / peak,
+                   "device_gb": L.lbm_get_info(ctx).device_bytes / 1e9,
+                   "sweep_config": list(L.lbm_get_sweep_config(ctx))}
+            ctx.destroy()
+            rows.append(row)
+            print(row, file=sys.stderr, flush=True)
+    print(json.dumps({"report": "porous", "workload": POROUS_WORKLOAD, "n": n, "peak_hbm_gbs": peak,
+                      "rows": rows}))
+    return 0
+
+
 WARMSTART_WORKLOAD = ("learned warm start: 64^3 channels (periodic x/z, walls -y/+y), sphere packings "
                       "(radius 2-6, porosity U[0.7, 0.9]), force U[5e-7, 5e-6] along x, BGK tau=0.8; "
                       "training seeds 0..N-1, held-out seeds 10000..; residual 1e-6 (change per step over "
@@ -773,7 +836,7 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
-    ap.add_argument("--report", default="", choices=["", "precision", "warmstart", "unet", "sizes"],
+    ap.add_argument("--report", default="", choices=["", "precision", "warmstart", "unet", "sizes", "porous"],
                     help="precision: storage-precision report on the 384^3 cavity; warmstart: the learned "
                          "warm start end to end (one JSON line each)")
     ap.add_argument("--ws-size", type=int, default=64)
@@ -804,6 +867,9 @@ def main():
                     help="--report sizes: streaming modes to run")
     ap.add_argument("--size-splits", type=int, nargs="+", default=[1, 2, 4],
                     help="--report sizes: Blocks per axis")
+    ap.add_argument("--porosities", type=float, nargs="+", default=[0.3, 0.5, 0.7, 0.9],
+                    help="--report porous: fluid fractions")
+    ap.add_argument("--porous-size", type=int, default=256, help="--report porous: cells per axis")
     ap.add_argument("--force", type=float, default=FORCE, help="body force along x")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -818,6 +884,8 @@ def main():
         return run_unet_report(args)
     if args.report == "sizes":
         return run_sizes_report(args)
+    if args.report == "porous":
+        return run_porous_report(args)
     return run_gpu(args)
 
 

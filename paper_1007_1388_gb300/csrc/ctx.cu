@@ -124,6 +124,12 @@ struct lbm_ctx {
     std::vector<XSlabF> aa_rev;   // neighbours' boundary rows <- ghost rows, after it
     XSlabF *d_aa_fwd = nullptr;
     XSlabF *d_aa_rev = nullptr;
+    // fluid-cell list layout (LBM_LAYOUT_SPARSE): list index per flag cell,
+    // neighbour table [19][nstride]
+    bool sparse = false;
+    long long nfluid = 0, nstride = 0;
+    int *d_sidx = nullptr;
+    int *d_nbr = nullptr;
     // kernel choice and the TMA sweep's launch state
     int kernel = LBM_KERNEL_REGISTER;
     TmaMaps maps{};
@@ -332,6 +338,7 @@ int validate_params(const lbm_params &p)
     double s = p.storage_scale;
     if (p.kernel < LBM_KERNEL_AUTO || p.kernel > LBM_KERNEL_TMA) return 0;
     if (p.streaming != LBM_STREAM_TWO_GRID && p.streaming != LBM_STREAM_AA) return 0;
+    if (p.layout != LBM_LAYOUT_BLOCKS && p.layout != LBM_LAYOUT_SPARSE) return 0;
     int e2 = 0;
     if (!(s > 0) || !std::isfinite(s) || std::frexp(s, &e2) != 0.5) return 0;  // power of two
     return 1;
@@ -579,6 +586,10 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     c->forced = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
     for (int k = 0; k < c->ninst; ++k) c->iforce.insert(c->iforce.end(), p.force, p.force + 3);
     c->aa = p.streaming == LBM_STREAM_AA;
+    c->sparse = p.layout == LBM_LAYOUT_SPARSE;
+    if (c->sparse && (c->ninst != 1 || c->aa || p.kernel == LBM_KERNEL_TMA))
+        return fail(c, LBM_EINVAL, "the fluid-cell list layout (LBM_LAYOUT_SPARSE) serves single Patches with "
+                    "two-array streaming (not batches, LBM_STREAM_AA or LBM_KERNEL_TMA)");
     if (c->aa && (c->ninst != 1 || p.kernel == LBM_KERNEL_TMA))
         return fail(c, LBM_EINVAL, "in-place streaming (LBM_STREAM_AA) serves single Patches with the "
                     "register sweep (not batches, not LBM_KERNEL_TMA)");
@@ -820,8 +831,60 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     c->cells = out_base;
     c->stored = cell_base;
 
+    // ---- fluid-cell list layout: numbering, neighbour table (periodic images
+    // and Block faces resolved here, so no exchange runs)
+    std::vector<int> hsidx, hnbr;
+    if (c->sparse) {
+        c->xslabs.clear();
+        c->exchange_pdfs = 0;
+        hsidx.assign(size_t(cell_base), -1);
+        long long nf = 0;
+        for (const BlockGeom &b : c->blocks)
+            for (int z = 0; z < b.nz; ++z)
+                for (int y = 0; y < b.ny; ++y)
+                    for (int x = 0; x < b.nx; ++x) {
+                        const long long cf = ((long long)(z + 1) * b.py + (y + 1)) * b.pxf + x + OXF;
+                        if ((hflags[size_t(b.cell_base + cf)] & F_KIND) == F_FLUID) hsidx[size_t(b.cell_base + cf)] = int(nf++);
+                    }
+        const long long stride = std::max<long long>(64, (nf + 63) / 64 * 64);
+        if ((long long)Q * stride >= (1ll << 31))
+            return fail(c, LBM_EINVAL, "fluid-cell list of %lld cells: 19 x cells must stay below 2^31", nf);
+        c->nfluid = nf;
+        c->nstride = stride;
+        hnbr.assign(size_t(Q * stride), -1);
+        const InstSpec &s0 = inst[0];
+        const int *N = s0.dims;
+        const int nb[3] = {N[0] / s0.bdims[0], N[1] / s0.bdims[1], N[2] / s0.bdims[2]};
+        for (const BlockGeom &b : c->blocks)
+            for (int z = 0; z < b.nz; ++z)
+                for (int y = 0; y < b.ny; ++y)
+                    for (int x = 0; x < b.nx; ++x) {
+                        const long long cf = ((long long)(z + 1) * b.py + (y + 1)) * b.pxf + x + OXF;
+                        const int k = hsidx[size_t(b.cell_base + cf)];
+                        if (k < 0) continue;
+                        int pres = 0;
+                        for (int q = 1; q < Q; ++q) {
+                            long long P[3] = {b.gx + x - ex(q), b.gy + y - ey(q), b.gz + z - ez(q)};
+                            const int kind = classify(p, N, s0.flags, P[0], P[1], P[2]) & F_KIND;
+                            int code = kind == F_MOVING ? -2 : (kind == F_PRESSURE ? -3 : -1);
+                            if (kind == F_PRESSURE) pres = 1;
+                            if (kind == F_FLUID) {
+                                for (int a2 = 0; a2 < 3; ++a2) P[a2] = ((P[a2] % N[a2]) + N[a2]) % N[a2];
+                                const int bd[3] = {s0.bdims[0], s0.bdims[1], s0.bdims[2]};
+                                const BlockGeom &n = c->blocks[size_t(((P[2] / bd[2]) * nb[1] + P[1] / bd[1]) * nb[0] +
+                                                                      P[0] / bd[0])];
+                                const long long ncf = ((P[2] % bd[2] + 1) * n.py + (P[1] % bd[1] + 1)) * n.pxf +
+                                                      P[0] % bd[0] + OXF;
+                                code = hsidx[size_t(n.cell_base + ncf)];
+                            }
+                            hnbr[size_t(q * stride + k)] = code;
+                        }
+                        hnbr[size_t(k)] = pres;
+                    }
+    }
+
     // ---- device memory
-    const size_t buf_bytes = size_t(pdf_base) * c->elem;
+    const size_t buf_bytes = (c->sparse ? size_t(Q * c->nstride) : size_t(pdf_base)) * c->elem;
     c->buf_bytes = buf_bytes;
     int rc;
     if ((rc = own(c, &c->buf[0], buf_bytes))) return rc;
@@ -836,6 +899,10 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     if ((rc = upload(c, &c->d_xslabs, c->xslabs))) return rc;
     if ((rc = upload(c, &c->d_aa_fwd, c->aa_fwd))) return rc;
     if ((rc = upload(c, &c->d_aa_rev, c->aa_rev))) return rc;
+    if (c->sparse) {
+        if ((rc = upload(c, &c->d_sidx, hsidx))) return rc;
+        if ((rc = upload(c, &c->d_nbr, hnbr))) return rc;
+    }
     std::vector<char> consts =
         c->storage == LBM_F64 ? make_consts<double>(c) : make_consts<float>(c);
     c->h_consts = consts;
@@ -947,6 +1014,9 @@ SweepArgs sweep_args(const lbm_ctx *c, int from)
         a.pres = (c->has_pressure ? 1 : 0) | (c->has_curved ? 2 : 0);
         a.curv_idx = c->d_curv_idx;
         a.curv_q = c->d_curv_q;
+        a.nbr = c->d_nbr;
+        a.nfluid = c->nfluid;
+        a.nstride = c->nstride;
     }
     if (a.unif) {
         if (c->storage == LBM_F64)
@@ -969,6 +1039,8 @@ FieldArgs field_args(const lbm_ctx *c)
     a.ty = c->tile[1];
     a.tz = c->tile[2];
     a.storage = c->storage;
+    a.sidx = c->sparse ? c->d_sidx : nullptr;
+    a.sstride = c->nstride;
     return a;
 }
 
@@ -999,6 +1071,7 @@ constexpr long long kWaitCycles = 2000000000ll;
 cudaError_t enqueue_sweep(const lbm_ctx *c, int from)
 {
     SweepArgs a = sweep_args(c, from);
+    if (c->sparse) return launch_sweep_sparse(a, c->stream);
     if (c->kernel != LBM_KERNEL_TMA) return launch_sweep(a, c->stream);
     const BlockGeom &b = c->blocks[0];
     TmaSweepArgs t{};
@@ -1757,7 +1830,9 @@ int lbm_set_wall_distances(lbm_ctx *c, long long n, const long long *cells, cons
     if (rc0) return rc0;
     if (n < 0 || (n > 0 && (!cells || !dirs || !q)))
         return fail(c, LBM_EINVAL, "lbm_set_wall_distances: bad arguments");
-    if (c->aa) return fail(c, LBM_EINVAL, "lbm_set_wall_distances: in-place streaming takes no curved walls");
+    if (c->aa || c->sparse)
+        return fail(c, LBM_EINVAL, "lbm_set_wall_distances: in-place streaming and the fluid-cell list take no "
+                    "curved walls");
     // each link: flag index of the fluid cell and of its pull source, table row
     const size_t nl = static_cast<size_t>(n);
     std::vector<long long> fidx(nl), sidx(nl);
@@ -1862,6 +1937,8 @@ int lbm_get_info(lbm_ctx *c, lbm_info *info)
     info->mask = c->kernel != LBM_KERNEL_TMA ? c->mask : 0;
     info->streaming = c->aa ? LBM_STREAM_AA : LBM_STREAM_TWO_GRID;
     info->aa_phase = c->aa_phase;
+    info->layout = c->sparse ? LBM_LAYOUT_SPARSE : LBM_LAYOUT_BLOCKS;
+    info->list_cells = c->nfluid;
     info->sweep_ctas = c->kernel == LBM_KERNEL_TMA ? c->tma_grid
                        : c->grid > 0                ? c->grid
                                                     : int(c->stiles.size());
@@ -1988,7 +2065,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
 {
     if (!c) return fail(c, LBM_EINVAL, "ctx is NULL");
     const bool tma_ok = c->kernel == LBM_KERNEL_TMA || (c->tma_grid > 0);
-    const std::string key = tune_key(c) + (tma_ok ? "|tma" : "") + (c->aa ? "|aa" : "");
+    const std::string key = tune_key(c) + (tma_ok ? "|tma" : "") + (c->aa ? "|aa" : "") + (c->sparse ? "|list" : "");
     // configuration: kind (0 register sweep over row tiles, 1 TMA sweep, 2
     // register sweep over runs of tx consecutive cells), tx, ty, tz, grid,
     // minb, zchunk, mask
@@ -2027,9 +2104,14 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         for (const BlockGeom &b : c->blocks) pair_ok = pair_ok && (b.nx % 2 == 0);
         const int *st = c->sw_tile;
         std::vector<Cfg> cand;
+        if (c->sparse) {  // the list sweep: register budget and grid only
+            for (int mb : {3, 4})
+                for (int m : {0, 4, 8, 16}) cand.push_back({0, st[0], st[1], st[2], m * sms, mb, zc0, 0});
+        }
         if (tma_ok)
             for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, st[0], st[1], st[2], 0, c->minb, zc, m0});
         for (int mb : {3, 4}) {
+            if (c->sparse) break;
             for (int tx : {32, 64, 128, 256}) {
                 if (tx > std::max(32, round_up(maxnx, 32))) continue;
                 for (int th : {128, 256}) {
@@ -2051,7 +2133,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
             }
         }
         // persistent grids over the default work list
-        for (int m : {4, 8, 16})
+        for (int m : {4, 8, 16}) if (!c->sparse)
             cand.push_back({kind0 == 1 ? 0 : kind0, st[0], st[1], st[2], m * sms, c->minb, zc0, m0});
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
@@ -2116,7 +2198,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         for (size_t k = 0; k < timed.size() && k < 4; ++k) {
             Cfg cd = timed[k].second;
             fin.push_back(cd);
-            if (cd[0] != 1 && !c->aa) {
+            if (cd[0] != 1 && !c->aa && !c->sparse) {
                 cd[7] ^= 1;
                 fin.push_back(cd);
             }

@@ -76,6 +76,16 @@ cudaError_t launch_exchange_flagged(const XSlabF *slabs, int nslabs, void *buf, 
 // ------------------------------------------------------- per-cell helpers
 // storage slot of direction q (swapped in the in-place scheme's even-time layout)
 __device__ __forceinline__ int slot(const FieldArgs &a, int q) { return a.swap ? opp(q) : q; }
+// offset of a cell's direction-0 PDF and the direction stride: the Block
+// layout, or the fluid-cell list (-1 for a solid cell there)
+__device__ __forceinline__ long long cell_off(const FieldArgs &a, const BlockGeom &b, int c, int cf)
+{
+    return a.sidx ? (long long)a.sidx[b.cell_base + cf] : b.pdf_base + c;
+}
+__device__ __forceinline__ long long pstride(const FieldArgs &a, const BlockGeom &b)
+{
+    return a.sidx ? a.sstride : b.G;
+}
 
 struct CellPos {
     const BlockGeom *b;
@@ -140,11 +150,11 @@ __global__ void __launch_bounds__(256) macro_kernel(const __grid_constant__ Fiel
             v[p.o] = v[N + p.o] = v[2 * N + p.o] = 0.f;
             return;
         }
-        const S *g = static_cast<const S *>(buf) + b.pdf_base + p.c;
+        const S *g = static_cast<const S *>(buf) + cell_off(a, b, p.c, p.cf);
         T d = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const T gq = Tr::to_t(g[(long long)slot(a, q) * b.G]);
+            const T gq = Tr::to_t(g[(long long)slot(a, q) * pstride(a, b)]);
             d += gq;
             jx += T(ex(q)) * gq;
             jy += T(ey(q)) * gq;
@@ -171,10 +181,11 @@ __global__ void __launch_bounds__(256) init_eq_kernel(const __grid_constant__ Fi
         const BlockGeom &b = *p.b;
         const CollideConsts<T> &P = cs[b.inst];
         const long long N = inst_cells(b);
-        S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
+        S *g = static_cast<S *>(buf) + cell_off(a, b, p.c, p.cf);
         if (a.flags[b.cell_base + p.cf] & F_KIND) {
+            if (a.sidx) return;  // the fluid-cell list stores no solid cells
 #pragma unroll
-            for (int q = 0; q < Q; ++q) g[(long long)slot(a, q) * b.G] = Tr::from_t(T(0));
+            for (int q = 0; q < Q; ++q) g[(long long)slot(a, q) * pstride(a, b)] = Tr::from_t(T(0));
             return;
         }
         const float *r = rho + b.out_base;
@@ -187,7 +198,7 @@ __global__ void __launch_bounds__(256) init_eq_kernel(const __grid_constant__ Fi
         for (int q = 0; q < Q; ++q) {
             const T eu = T(ex(q)) * ux + T(ey(q)) * uy + T(ez(q)) * uz;
             const T feq = T(wq(q)) * (drho_s + P.rho0s * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
-            g[(long long)slot(a, q) * b.G] = Tr::from_t(feq);
+            g[(long long)slot(a, q) * pstride(a, b)] = Tr::from_t(feq);
         }
     });
 }
@@ -210,12 +221,12 @@ __global__ void __launch_bounds__(256) impose_u_kernel(const __grid_constant__ F
         if (a.flags[b.cell_base + p.cf] & F_KIND) return;
         const CollideConsts<T> &P = cs[b.inst];
         const long long N = inst_cells(b);
-        S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
+        S *g = static_cast<S *>(buf) + cell_off(a, b, p.c, p.cf);
         T f[Q];
         T jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            f[q] = Tr::to_t(g[(long long)slot(a, q) * b.G]);
+            f[q] = Tr::to_t(g[(long long)slot(a, q) * pstride(a, b)]);
             jx += T(ex(q)) * f[q];
             jy += T(ey(q)) * f[q];
             jz += T(ez(q)) * f[q];
@@ -230,7 +241,7 @@ __global__ void __launch_bounds__(256) impose_u_kernel(const __grid_constant__ F
             const T et = T(ex(q)) * t0 + T(ey(q)) * t1 + T(ez(q)) * t2;
             const T d = T(wq(q)) * P.rho0s *
                         (T(3) * (et - en) + T(4.5) * (et * et - en * en) - T(1.5) * (tsq - nsq));
-            g[(long long)slot(a, q) * b.G] = Tr::from_t(f[q] + d);
+            g[(long long)slot(a, q) * pstride(a, b)] = Tr::from_t(f[q] + d);
         }
     });
 }
@@ -250,10 +261,10 @@ __global__ void __launch_bounds__(256) get_pdfs_kernel(const __grid_constant__ F
         const long long N = inst_cells(b);
         double *out = f + (long long)Q * b.out_base;
         const bool solid = a.flags[b.cell_base + p.cf] & F_KIND;
-        const S *g = static_cast<const S *>(buf) + b.pdf_base + p.c;
+        const S *g = static_cast<const S *>(buf) + cell_off(a, b, p.c, p.cf);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
-            out[q * N + p.o] = solid ? 0.0 : double(Tr::to_t(g[(long long)slot(a, q) * b.G])) * inv_s;
+            out[q * N + p.o] = solid ? 0.0 : double(Tr::to_t(g[(long long)slot(a, q) * pstride(a, b)])) * inv_s;
     });
 }
 
@@ -271,10 +282,11 @@ __global__ void __launch_bounds__(256) set_pdfs_kernel(const __grid_constant__ F
         const long long N = inst_cells(b);
         const double *in = f + (long long)Q * b.out_base;
         const bool solid = a.flags[b.cell_base + p.cf] & F_KIND;
-        S *g = static_cast<S *>(buf) + b.pdf_base + p.c;
+        if (solid && a.sidx) return;  // the fluid-cell list stores no solid cells
+        S *g = static_cast<S *>(buf) + cell_off(a, b, p.c, p.cf);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
-            g[(long long)slot(a, q) * b.G] = Tr::from_t(solid ? T(0) : T(in[q * N + p.o] * s));
+            g[(long long)slot(a, q) * pstride(a, b)] = Tr::from_t(solid ? T(0) : T(in[q * N + p.o] * s));
     });
 }
 
@@ -341,11 +353,11 @@ __global__ void __launch_bounds__(256) invariants_tiles_kernel(const __grid_cons
             const int c = (z + 1) * pxy + (y + 1) * b.px + x;
             const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
             if (a.flags[b.cell_base + cf] & F_KIND) continue;
-            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
+            const S *g = static_cast<const S *>(cur) + cell_off(a, b, c, cf);
             double d = 0.0, j[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const double v = double(Tr::to_t(g[(long long)slot(a, q) * b.G])) * inv_s;
+                const double v = double(Tr::to_t(g[(long long)slot(a, q) * pstride(a, b)])) * inv_s;
                 d += v;
                 if (ex(q)) j[0] += ex(q) > 0 ? v : -v;
                 if (ey(q)) j[1] += ey(q) > 0 ? v : -v;
@@ -389,13 +401,13 @@ __global__ void __launch_bounds__(256) residual_tiles_kernel(const __grid_consta
             const int c = (z + 1) * pxy + (y + 1) * b.px + x;
             const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
             if (a.flags[b.cell_base + cf] & F_KIND) continue;
-            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
-            const S *h = static_cast<const S *>(prev) + b.pdf_base + c;
+            const S *g = static_cast<const S *>(cur) + cell_off(a, b, c, cf);
+            const S *h = static_cast<const S *>(prev) + cell_off(a, b, c, cf);
             T j[3] = {T(0), T(0), T(0)}, dj[3] = {T(0), T(0), T(0)};
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                const T v = Tr::to_t(g[(long long)slot(a, q) * b.G]);
-                const T dv = v - Tr::to_t(h[(long long)slot(a, q) * b.G]);
+                const T v = Tr::to_t(g[(long long)slot(a, q) * pstride(a, b)]);
+                const T dv = v - Tr::to_t(h[(long long)slot(a, q) * pstride(a, b)]);
                 if (ex(q)) { j[0] += ex(q) > 0 ? v : -v; dj[0] += ex(q) > 0 ? dv : -dv; }
                 if (ey(q)) { j[1] += ey(q) > 0 ? v : -v; dj[1] += ey(q) > 0 ? dv : -dv; }
                 if (ez(q)) { j[2] += ez(q) > 0 ? v : -v; dj[2] += ez(q) > 0 ? dv : -dv; }
@@ -452,11 +464,11 @@ __global__ void __launch_bounds__(256) residual_snap_kernel(const __grid_constan
             const int cf = (z + 1) * pxyf + (y + 1) * b.pxf + x + OXF;
             if (a.flags[b.cell_base + cf] & F_KIND) continue;
             const long long o = ((long long)(b.gz + z) * b.NY + (b.gy + y)) * b.NX + (b.gx + x);
-            const S *g = static_cast<const S *>(cur) + b.pdf_base + c;
+            const S *g = static_cast<const S *>(cur) + cell_off(a, b, c, cf);
             T j[3] = {T(0), T(0), T(0)};
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
-                const T v = Tr::to_t(g[(long long)slot(a, q) * b.G]);
+                const T v = Tr::to_t(g[(long long)slot(a, q) * pstride(a, b)]);
                 if (ex(q)) j[0] += ex(q) > 0 ? v : -v;
                 if (ey(q)) j[1] += ey(q) > 0 ? v : -v;
                 if (ez(q)) j[2] += ez(q) > 0 ? v : -v;

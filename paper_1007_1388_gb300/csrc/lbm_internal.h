@@ -88,6 +88,8 @@ cudaError_t launch_exchange_flagged(const XSlabF *slabs, int nslabs, void *buf, 
 cudaError_t launch_curved_setup(const long long *fidx, const long long *sidx, const int *rows, long long n,
                                 const uint8_t *flags, uint32_t *links, long long nlinks, int *idx, int *bad,
                                 cudaStream_t s);
+// The sweep over the fluid-cell list (sweep_sparse.cu).
+cudaError_t launch_sweep_sparse(const SweepArgs &a, cudaStream_t s);
 // In-place (AA-pattern) sweep: mode 0 even step, 1 odd step, 2 gather of an
 // odd-time state into the natural layout of a.dst.
 cudaError_t launch_sweep_aa(const SweepArgs &a, int mode, cudaStream_t s);
@@ -102,6 +104,8 @@ struct FieldArgs {
     int storage;
     int swap;  // 1: direction q of a cell is stored in slot opp(q) (the in-place
                // scheme at an even time)
+    const int *sidx;     // fluid-cell list layout: list index per flag cell (-1 solid), else NULL
+    long long sstride;   // its direction stride
 };
 // rho/u in the concatenated output layout (device pointers)
 cudaError_t launch_macroscopic(const FieldArgs &a, const void *buf, float *rho, float *u,

@@ -158,6 +158,12 @@ struct SweepArgs {
     // arithmetic type; 1/2 on links that are half-way bounce-back
     const int *curv_idx;
     const void *curv_q;
+    // fluid-cell list layout: neighbour table [19][nstride] (row 0: bit 0 =
+    // the cell has a pressure link; rows 1..18: the pull source's list index,
+    // or -1 resting wall, -2 moving wall, -3 pressure node), fluid cells, and
+    // the stride of the PDF and neighbour rows
+    const int *nbr;
+    long long nfluid, nstride;
 };
 
 }  // namespace lbm

@@ -23,6 +23,7 @@ LBM_BGK, LBM_TRT = 0, 1
 LBM_F32, LBM_F16S, LBM_BF16S, LBM_F64 = 0, 1, 2, 3
 LBM_KERNEL_AUTO, LBM_KERNEL_REGISTER, LBM_KERNEL_TMA = 0, 1, 2
 LBM_STREAM_TWO_GRID, LBM_STREAM_AA = 0, 1
+LBM_LAYOUT_BLOCKS, LBM_LAYOUT_SPARSE = 0, 1
 LBM_DEBUG_DROP_STAGE = 1
 STORAGE_NAMES = {LBM_F32: "f32", LBM_F16S: "f16s", LBM_BF16S: "bf16s", LBM_F64: "f64"}
 BYTES_PER_PDF = {LBM_F32: 4, LBM_F16S: 2, LBM_BF16S: 2, LBM_F64: 8}
@@ -49,6 +50,7 @@ class lbm_params(ctypes.Structure):
         ("debug_flags", ctypes.c_int),
         ("rho_b", ctypes.c_double),
         ("streaming", ctypes.c_int),
+        ("layout", ctypes.c_int),
     ]
 
 
@@ -73,6 +75,8 @@ class lbm_info(ctypes.Structure):
         ("pair", ctypes.c_int),
         ("streaming", ctypes.c_int),
         ("aa_phase", ctypes.c_int),
+        ("layout", ctypes.c_int),
+        ("list_cells", ctypes.c_longlong),
     ]
 
 

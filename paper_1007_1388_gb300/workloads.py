@@ -9,6 +9,7 @@ channel / porous-media cases of the benchmark configurations):
   cavity(n)            n^3 lid-driven cavity, lid = +y face moving along x
   channel(dims)        periodic x and z, resting walls at -y/+y (Poiseuille)
   sphere_packing(...)  random non-overlapping spheres in a channel
+  overlapping_spheres(...) random overlapping spheres (any porosity)
   batch_instances(...) many uneven channels with sphere packings and tau
   channel_samples(...) the learned warm start's samples: n^3 sphere-packed
                        channels with porosity and driving force per seed
@@ -95,6 +96,35 @@ def sphere_packing(rng: np.random.Generator, dims, porosity, rmin=2, rmax=6, max
         sub[inside] = NOSLIP
         flags[np.ix_(zs, ys, xs)] = sub
     return flags
+
+
+def overlapping_spheres(rng: np.random.Generator, dims, porosity, rmin=2, rmax=6):
+    """Solid spheres that may overlap (a Boolean model of a porous medium),
+    periodic in x and z, added in batches until the fluid fraction is at most
+    `porosity`; any fluid fraction down to zero is reachable, unlike the
+    non-overlapping packing.  Integer radii uniform in [rmin, rmax]."""
+    nx, ny, nz = dims
+    solid = np.zeros((nz, ny, nx), bool)
+    mean_vol = np.mean([4.0 / 3.0 * np.pi * r**3 for r in range(rmin, rmax + 1)])
+    while (~solid).mean() > porosity:
+        # enough spheres to close about half the remaining gap
+        k = max(1, int(0.5 * ((~solid).mean() - porosity) * nx * ny * nz / mean_vol))
+        for _ in range(k):
+            r = int(rng.integers(rmin, rmax + 1))
+            c = rng.uniform([0, 0, 0], [nx, ny, nz])
+            xs = np.arange(int(np.floor(c[0] - r - 1)), int(np.ceil(c[0] + r + 1)) + 1) % nx
+            zs = np.arange(int(np.floor(c[2] - r - 1)), int(np.ceil(c[2] + r + 1)) + 1) % nz
+            ys = np.arange(max(0, int(np.floor(c[1] - r - 1))), min(ny, int(np.ceil(c[1] + r + 1)) + 1))
+            xs, zs = np.unique(xs), np.unique(zs)
+            dx = np.abs(xs + 0.5 - c[0])
+            dx = np.minimum(dx, nx - dx)
+            dz = np.abs(zs + 0.5 - c[2])
+            dz = np.minimum(dz, nz - dz)
+            dy = ys + 0.5 - c[1]
+            inside = (dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2) <= r * r
+            sub = solid[np.ix_(zs, ys, xs)]
+            solid[np.ix_(zs, ys, xs)] = sub | inside
+    return np.where(solid, NOSLIP, FLUID).astype(np.uint8)
 
 
 def batch_instances(seed=1234, n=256, lo=16, hi=96, tau_lo=0.55, tau_hi=1.2,

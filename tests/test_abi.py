@@ -106,7 +106,7 @@ def test_create_rejects_bad_geometry_before_touching_the_gpu(L, dims, bdims, tau
 
 @pytest.mark.parametrize("field,value", [
     ("collision", 7), ("storage", 9), ("rho0", 0.0), ("storage_scale", 3.0),
-    ("storage_scale", -2.0), ("streaming", 2),
+    ("storage_scale", -2.0), ("streaming", 2), ("layout", 2),
 ])
 def test_create_rejects_bad_params(L, field, value):
     p = L.lbm_default_params()
@@ -139,6 +139,20 @@ def test_in_place_streaming_rejects_batches_and_the_tma_sweep(L):
     p.stream = 1
     with pytest.raises(L.LBMError) as ei:
         L.lbm_create((64, 8, 8), (64, 8, 8), 0.7, None, p)
+    assert ei.value.code == L.LBM_EINVAL
+
+
+def test_fluid_list_layout_rejects_batches_in_place_and_tma(L):
+    for extra in (dict(streaming=L.LBM_STREAM_AA), dict(kernel=L.LBM_KERNEL_TMA)):
+        p = L.make_params(layout=L.LBM_LAYOUT_SPARSE, **extra)
+        p.stream = 1  # never used: the checks come first
+        with pytest.raises(L.LBMError) as ei:
+            L.lbm_create((64, 8, 8), (64, 8, 8), 0.7, None, p)
+        assert ei.value.code == L.LBM_EINVAL and "fluid-cell list" in L.lbm_last_error()
+    p = L.make_params(layout=L.LBM_LAYOUT_SPARSE)
+    p.stream = 1
+    with pytest.raises(L.LBMError) as ei:
+        L.lbm_batch_create([(8, 8, 8), (8, 8, 8)], [0.7, 0.8], None, p)
     assert ei.value.code == L.LBM_EINVAL
 
 
