@@ -171,3 +171,31 @@ def test_sweep_config_validation(L):
             L.lbm_set_sweep_config(ctx, bad)
         assert L.lbm_get_sweep_config(ctx) == before
     ctx.destroy()
+
+
+def test_graph_direct_and_profiled_steps_agree(L):
+    """Multi-Block steps through graph replay, direct launches and the
+    profiled path (events around the exchange and the sweep) agree bitwise,
+    and the profile counts one exchange and one sweep per step."""
+    import numpy as np
+
+    from paper_1007_1388_gb300 import workloads as W
+
+    dims, bd = (64, 32, 32), (32, 16, 16)
+    rng = np.random.default_rng(12)
+    flags = W.random_flags(rng, dims, 0.1)
+    f0 = W.random_pdfs(rng, dims, 1e-2, flags)
+    kw = dict(periodic=(1, 1, 1), force=(1e-5, 0, 0), collision=1)
+    outs = []
+    for graph_steps, prof in ((0, False), (-1, False), (-1, True)):
+        ctx = L.lbm_create(dims, bd, 0.8, flags, L.make_params(graph_steps=graph_steps, **kw))
+        L.lbm_set_pdfs(ctx, f0)
+        L.lbm_profile_enable(ctx, prof)
+        L.lbm_step(ctx, 33)
+        if prof:
+            pr = L.lbm_profile_read(ctx)
+            assert pr.sweep_launches == 33 and pr.exchange_launches == 33
+            assert pr.sweep_ms > 0 and pr.exchange_ms > 0
+        outs.append(L.lbm_get_pdfs(ctx))
+        ctx.destroy()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
