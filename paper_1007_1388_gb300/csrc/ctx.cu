@@ -933,7 +933,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
             w64 = w64 && (b.nx % 64 == 0);
             w32 = w32 && (b.nx % 32 == 0);
         }
-        if (c->aa) {  // one cell per thread
+        if (c->aa) {  // in place: one cell per thread (two spill at these register budgets)
             if (!w32) flat = 256;
         } else if (even && w64) {
             pair = 1;
@@ -1994,9 +1994,9 @@ int check_cfg(lbm_ctx *c, const int *cd)
     if (cd[0] < 0 || cd[0] > 4) return fail(c, LBM_EINVAL, "sweep config: kind %d", cd[0]);
     if (cd[0] == 1 && !tma_ok)
         return fail(c, LBM_EINVAL, "sweep config: the TMA sweep does not apply to this context");
-    if (c->aa && (cd[0] == 1 || cd[0] >= 3 || cd[7] != 0))
-        return fail(c, LBM_EINVAL, "sweep config: in-place streaming takes row tiles or runs, one cell per "
-                    "thread, near-wall cells by lane (kinds 0 / 2, mask 0)");
+    if (c->aa && (cd[0] == 1 || cd[7] != 0))
+        return fail(c, LBM_EINVAL, "sweep config: in-place streaming takes the register sweep with near-wall "
+                    "cells by lane (kinds 0, 2, 3, 4; mask 0)");
     if (cd[0] >= 3) {
         bool even = c->storage != LBM_F64;
         for (const BlockGeom &b : c->blocks) even = even && (b.nx % 2 == 0);
@@ -2100,7 +2100,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int zc0 = c->tma_zchunk, m0 = c->mask;
-        bool pair_ok = c->storage != LBM_F64 && !c->aa;
+        bool pair_ok = c->storage != LBM_F64;
         for (const BlockGeom &b : c->blocks) pair_ok = pair_ok && (b.nx % 2 == 0);
         const int *st = c->sw_tile;
         std::vector<Cfg> cand;

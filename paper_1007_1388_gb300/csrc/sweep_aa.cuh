@@ -42,6 +42,7 @@
 #pragma once
 
 #include "device_common.cuh"
+#include "sweep2_impl.cuh"  // Pair<ST>::st2
 
 namespace lbm {
 
@@ -64,15 +65,142 @@ __device__ __forceinline__ long long aa_slot(const BlockGeom &b, int q, int x, i
 // S_q(x) at slot q), 3 a natural-layout state (a.src) stored swapped into
 // a.dst (an even-time array), 4 the pressure links' values of an even-time
 // state that was written from the host.
-template <int ST, int COLL, bool FORCE, int MINB, int MODE, bool PRES>
-__global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_constant__ SweepArgs a)
+//
+// aa_cell: one cell (x, y, z) of Block b in the given mode; the whole work of
+// the one-cell kernel, and of the two-cell kernel for cells that touch a wall
+// or solid cell.
+template <int ST, int COLL, bool FORCE, int MODE, bool PRES>
+__device__ __forceinline__ void aa_cell(const SweepArgs &a, const BlockGeom &b, int x, int y, int z)
 {
     using Tr = Traits<ST>;
     using S = typename Tr::S;
     using T = typename Tr::T;
     const CollideConsts<T> &K = param_consts<T>(a);  // a single instance: kernel parameters
     const CollKRef<T> KR{K};
+    const int nx = b.nx;
+    const int px = b.px, pxy = px * b.py;
+    const int pxf = b.pxf, pxyf = b.pxf * b.py;
+    const int G = int(b.G);
+    const int c = (z + 1) * pxy + (y + 1) * px + x;
+    const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
+    const uint8_t *fl = a.flags + b.cell_base;
+    const uint8_t flag = fl[cf];
+    if (flag & F_KIND) return;  // solid and pressure cells are not updated
+    const S *R0 = static_cast<const S *>(a.src);
+    S *W0 = static_cast<S *>(a.dst);
+    const S *R = R0 + b.pdf_base;
+    S *W = W0 + b.pdf_base;
+    // neighbours across the -x face (x = 0) and the +x face (x = nx - 1)
+    const long long xm = x == 0 ? b.xm_off : 0ll, xp = x == nx - 1 ? b.xp_off : 0ll;
+    T f[Q];
 
+    if (MODE == 0 || MODE == 3) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) f[q] = Tr::to_t(R[q * G + c]);
+        if (MODE == 0) collide_v<COLL, FORCE>(f, KR);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) Tr::st(W + (opp(q) * G + c), f[q]);
+        if (MODE == 0 && PRES && (flag & F_NEAR)) {
+            const uint32_t lm = __ldg(a.links + b.cell_base + cf);
+            if (lm & L_PRESSURE) {
+                const PresBC<T> pb = pres_setup_regs<ST, T>(f, param_pb<T>(a), K.ufac, K.uoff[0], K.uoff[1],
+                                                            K.uoff[2], K.c45, K.nc15);
+#pragma unroll
+                for (int q = 1; q < Q; ++q) {
+                    if (!((lm >> q) & 1u)) continue;
+                    if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
+                    Tr::st(W0 + aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G),
+                           pres_pull(q, pb, Tr::to_t(Tr::from_t(f[opp(q)]))));
+                }
+            }
+        }
+        return;
+    }
+    if (MODE == 4) {
+        if (!(flag & F_NEAR)) return;
+        const uint32_t lm = __ldg(a.links + b.cell_base + cf);
+        if (!(lm & L_PRESSURE)) return;
+        const PresBC<T> pb = pres_cell<ST, true, T, true>(K, nullptr, param_pb<T>(a), R, c, G);
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+            if (!((lm >> q) & 1u)) continue;
+            if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
+            Tr::st(W0 + aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G),
+                   pres_pull(q, pb, Tr::to_t(R[q * G + c])));
+        }
+        return;
+    }
+    if (MODE == 2) {  // S_q(x) was pushed to x + e_q
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            W[q * G + c] = R0[aa_slot(b, q, x, y, z, c, ex(q), ey(q), ez(q), xm, xp, px, pxy, G)];
+        return;
+    }
+
+    const bool near = flag & F_NEAR;
+    const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
+    if (!near) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
+            f[q] = Tr::to_t(R[o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if ((lm >> q) & 1u) {
+                const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+                if (PRES && (nf & F_KIND) == F_PRESSURE) {
+                    // prepared by the step that produced S
+                    f[q] = Tr::to_t(
+                        R0[aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G)]);
+                } else {
+                    T v = Tr::to_t(R[q * G + c]);  // S_opp(q)(x), stored swapped
+                    if ((nf & F_KIND) == F_MOVING) v = vadd(v, K.bbw[q]);
+                    f[q] = v;
+                }
+            } else {
+                const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
+                f[q] = Tr::to_t(R[o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))]);
+            }
+        }
+    }
+    collide_v<COLL, FORCE>(f, KR);
+    if (!near) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
+            Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
+        }
+    } else {
+        PresBC<T> pbw{};
+        if (PRES && (lm & L_PRESSURE))
+            pbw = pres_setup_regs<ST, T>(f, param_pb<T>(a), K.ufac, K.uoff[0], K.uoff[1], K.uoff[2], K.c45,
+                                         K.nc15);
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (!((lm >> opp(q)) & 1u)) {
+                const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
+                Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
+                continue;
+            }
+            // x + e_q is not fluid: S'_q is kept in that cell's slot (to read
+            // the state back) and comes back to x along e_opp(q)
+            Tr::st(W0 + aa_slot(b, q, x, y, z, c, ex(q), ey(q), ez(q), xm, xp, px, pxy, G), f[q]);
+            T v = f[q];
+            const uint8_t nf = fl[cf + (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+            if ((nf & F_KIND) == F_MOVING)
+                v = vadd(v, K.bbw[opp(q)]);
+            else if (PRES && (nf & F_KIND) == F_PRESSURE)
+                v = pres_pull(opp(q), pbw, Tr::to_t(Tr::from_t(v)));
+            Tr::st(W + (opp(q) * G + c), v);
+        }
+    }
+}
+
+template <int ST, int COLL, bool FORCE, int MINB, int MODE, bool PRES>
+__global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_constant__ SweepArgs a)
+{
     for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const Tile tile = a.tiles[t];
         const BlockGeom &b = a.blocks[tile.block];
@@ -90,122 +218,114 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_consta
             z = tile.z0 + int(blockIdx.y);
         }
         if (x >= nx || y >= ny || z >= b.nz) continue;
-        const int px = b.px, pxy = px * b.py;
+        aa_cell<ST, COLL, FORCE, MODE, PRES>(a, b, x, y, z);
+    }
+}
+
+// Two cells (x even, x + 1) per thread.  A pair of fluid cells with no wall
+// or solid cell among their neighbours takes the vector path in modes 0 and
+// 1: the 9 directions with e_x = 0 move both cells' values with one aligned
+// vector load or store, the other 10 with two scalar accesses, and the
+// collision runs on the packed FP32x2 lane type (bitwise equal to the scalar
+// one).  Every other pair, and every pair in modes 2..4, goes cell by cell
+// through aa_cell.  Loads are plain (coherent): the array is written in the
+// same launch.
+template <int ST>
+__device__ __forceinline__ F2 aa_ld2(const typename Traits<ST>::S *p);
+template <>
+__device__ __forceinline__ F2 aa_ld2<0>(const float *p)
+{
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return f2_pack(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ F2 aa_ld2<1>(const __half *p)
+{
+    const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+    return f2_pack(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ F2 aa_ld2<2>(const __nv_bfloat16 *p)
+{
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    return f2_pack(v.x, v.y);
+}
+
+template <int ST, int COLL, bool FORCE, int MINB, int MODE, bool PRES>
+__global__ void __launch_bounds__(256, MINB) sweep_aa2_kernel(const __grid_constant__ SweepArgs a)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    const CollKRef<float> KR{a.kf};
+    for (long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const Tile tile = a.tiles[t];
+        const BlockGeom &b = a.blocks[tile.block];
+        const int nx = b.nx, ny = b.ny;
+        int x, y, z;  // the first (even) cell of the pair; nx is even
+        if (a.flat) {
+            const int i = tile.x0 + 2 * int(threadIdx.x);
+            const int yz = i / nx;
+            x = i - yz * nx;
+            z = yz / ny;
+            y = yz - z * ny;
+        } else {
+            x = tile.x0 + 2 * int(threadIdx.x);
+            y = tile.y0 + int(threadIdx.y);
+            z = tile.z0 + int(blockIdx.y);
+        }
+        if (x >= nx || y >= ny || z >= b.nz) continue;
         const int pxf = b.pxf, pxyf = b.pxf * b.py;
-        const int G = int(b.G);
-        const int c = (z + 1) * pxy + (y + 1) * px + x;
         const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
         const uint8_t *fl = a.flags + b.cell_base;
-        const uint8_t flag = fl[cf];
-        if (flag & F_KIND) continue;  // solid and pressure cells are not updated
-        const S *R0 = static_cast<const S *>(a.src);
-        S *W0 = static_cast<S *>(a.dst);
-        const S *R = R0 + b.pdf_base;
-        S *W = W0 + b.pdf_base;
-        // neighbours across the -x face (x = 0) and the +x face (x = nx - 1)
-        const long long xm = x == 0 ? b.xm_off : 0ll, xp = x == nx - 1 ? b.xp_off : 0ll;
-        T f[Q];
-
-        if (MODE == 0 || MODE == 3) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q) f[q] = Tr::to_t(R[q * G + c]);
-            if (MODE == 0) collide_v<COLL, FORCE>(f, KR);
-#pragma unroll
-            for (int q = 0; q < Q; ++q) Tr::st(W + (opp(q) * G + c), f[q]);
-            if (MODE == 0 && PRES && (flag & F_NEAR)) {
-                const uint32_t lm = __ldg(a.links + b.cell_base + cf);
-                if (lm & L_PRESSURE) {
-                    const PresBC<T> pb = pres_setup_regs<ST, T>(f, param_pb<T>(a), K.ufac, K.uoff[0], K.uoff[1],
-                                                                K.uoff[2], K.c45, K.nc15);
-#pragma unroll
-                    for (int q = 1; q < Q; ++q) {
-                        if (!((lm >> q) & 1u)) continue;
-                        if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
-                        Tr::st(W0 + aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G),
-                               pres_pull(q, pb, Tr::to_t(Tr::from_t(f[opp(q)]))));
-                    }
-                }
-            }
+        const uint8_t fl0 = fl[cf], fl1 = fl[cf + 1];
+        if (MODE >= 2 || ((fl0 | fl1) & (F_KIND | F_NEAR))) {
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k)  // one copy of the cell code
+                if (!((k ? fl1 : fl0) & F_KIND)) aa_cell<ST, COLL, FORCE, MODE, PRES>(a, b, x + k, y, z);
             continue;
         }
-        if (MODE == 4) {
-            if (!(flag & F_NEAR)) continue;
-            const uint32_t lm = __ldg(a.links + b.cell_base + cf);
-            if (!(lm & L_PRESSURE)) continue;
-            const PresBC<T> pb = pres_cell<ST, true, T, true>(K, nullptr, param_pb<T>(a), R, c, G);
+        const int px = b.px, pxy = px * b.py;
+        const int G = int(b.G);
+        const int c = (z + 1) * pxy + (y + 1) * px + x;
+        const S *R = static_cast<const S *>(a.src) + b.pdf_base;
+        S *W = static_cast<S *>(a.dst) + b.pdf_base;
+        // cell x reaches across the -x face at x = 0, cell x + 1 across the +x face at x + 1 = nx - 1
+        const long long xm0 = x == 0 ? b.xm_off : 0ll, xp1 = x + 2 == nx ? b.xp_off : 0ll;
+        F2 f[Q];
+        if (MODE == 0) {
 #pragma unroll
-            for (int q = 1; q < Q; ++q) {
-                if (!((lm >> q) & 1u)) continue;
-                if ((fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)] & F_KIND) != F_PRESSURE) continue;
-                Tr::st(W0 + aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G),
-                       pres_pull(q, pb, Tr::to_t(R[q * G + c])));
-            }
+            for (int q = 0; q < Q; ++q) f[q] = aa_ld2<ST>(R + (q * G + c));
+            collide_v<COLL, FORCE>(f, KR);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) Pair<ST>::st2(W + (opp(q) * G + c), f[q]);
             continue;
         }
-        if (MODE == 2) {  // S_q(x) was pushed to x + e_q
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
-                W[q * G + c] = R0[aa_slot(b, q, x, y, z, c, ex(q), ey(q), ez(q), xm, xp, px, pxy, G)];
-            continue;
-        }
-
-        const bool near = flag & F_NEAR;
-        const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
-        if (!near) {
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
-                f[q] = Tr::to_t(R[o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))]);
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                if ((lm >> q) & 1u) {
-                    const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                    if (PRES && (nf & F_KIND) == F_PRESSURE) {
-                        // prepared by the step that produced S
-                        f[q] = Tr::to_t(
-                            R0[aa_slot(b, opp(q), x, y, z, c, -ex(q), -ey(q), -ez(q), xm, xp, px, pxy, G)]);
-                    } else {
-                        T v = Tr::to_t(R[q * G + c]);  // S_opp(q)(x), stored swapped
-                        if ((nf & F_KIND) == F_MOVING) v = vadd(v, K.bbw[q]);
-                        f[q] = v;
-                    }
-                } else {
-                    const long long o = ex(q) > 0 ? xm : (ex(q) < 0 ? xp : 0ll);
-                    f[q] = Tr::to_t(R[o + (opp(q) * G + c - (ex(q) + ey(q) * px + ez(q) * pxy))]);
-                }
-            }
+        for (int q = 0; q < Q; ++q) {  // pull from x - e_q: A[opp(q)][x - e_q]
+            const long long a0 = opp(q) * G + c - (ey(q) * px + ez(q) * pxy);
+            if (ex(q) == 0)
+                f[q] = aa_ld2<ST>(R + a0);
+            else if (ex(q) > 0)
+                f[q] = f2_pack(Tr::to_t(R[xm0 + a0 - 1]), Tr::to_t(R[a0]));
+            else
+                f[q] = f2_pack(Tr::to_t(R[a0 + 1]), Tr::to_t(R[xp1 + a0 + 2]));
         }
         collide_v<COLL, FORCE>(f, KR);
-        if (!near) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
-                Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
-            }
-        } else {
-            PresBC<T> pbw{};
-            if (PRES && (lm & L_PRESSURE))
-                pbw = pres_setup_regs<ST, T>(f, param_pb<T>(a), K.ufac, K.uoff[0], K.uoff[1], K.uoff[2], K.c45,
-                                             K.nc15);
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                if (!((lm >> opp(q)) & 1u)) {
-                    const long long o = ex(q) > 0 ? xp : (ex(q) < 0 ? xm : 0ll);
-                    Tr::st(W + (o + (q * G + c + (ex(q) + ey(q) * px + ez(q) * pxy))), f[q]);
-                    continue;
+        for (int q = 0; q < Q; ++q) {  // push to x + e_q: A[q][x + e_q]
+            const long long b0 = q * G + c + (ey(q) * px + ez(q) * pxy);
+            if (ex(q) == 0) {
+                Pair<ST>::st2(W + b0, f[q]);
+            } else {
+                float lo, hi;
+                f2_unpack(f[q], lo, hi);
+                if (ex(q) > 0) {
+                    Tr::st(W + (b0 + 1), lo);
+                    Tr::st(W + (xp1 + b0 + 2), hi);
+                } else {
+                    Tr::st(W + (xm0 + b0 - 1), lo);
+                    Tr::st(W + b0, hi);
                 }
-                // x + e_q is not fluid: S'_q is kept in that cell's slot (to read
-                // the state back) and comes back to x along e_opp(q)
-                Tr::st(W0 + aa_slot(b, q, x, y, z, c, ex(q), ey(q), ez(q), xm, xp, px, pxy, G), f[q]);
-                T v = f[q];
-                const uint8_t nf = fl[cf + (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                if ((nf & F_KIND) == F_MOVING)
-                    v = vadd(v, K.bbw[opp(q)]);
-                else if (PRES && (nf & F_KIND) == F_PRESSURE)
-                    v = pres_pull(opp(q), pbw, Tr::to_t(Tr::from_t(v)));
-                Tr::st(W + (opp(q) * G + c), v);
             }
         }
     }
@@ -214,6 +334,24 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_consta
 template <int ST, int MINB, int MODE, bool PRES>
 void launch_aa_mode(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
 {
+    if constexpr (ST != 3) {  // two cells per thread: FP32 and 16-bit storage
+        if (a.pair) {
+            if constexpr (MODE >= 2) {
+                sweep_aa2_kernel<ST, 0, false, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+            } else if (a.collision == 0) {
+                if (a.forced)
+                    sweep_aa2_kernel<ST, 0, true, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+                else
+                    sweep_aa2_kernel<ST, 0, false, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+            } else {
+                if (a.forced)
+                    sweep_aa2_kernel<ST, 1, true, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+                else
+                    sweep_aa2_kernel<ST, 1, false, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
+            }
+            return;
+        }
+    }
     if constexpr (MODE >= 2) {  // no collision: one instantiation serves every operator
         sweep_aa_kernel<ST, 0, false, MINB, MODE, PRES><<<grid, block, 0, s>>>(a);
     } else if (a.collision == 0) {
@@ -252,8 +390,8 @@ void launch_aa_minb(const SweepArgs &a, int mode, dim3 grid, dim3 block, cudaStr
 template <int ST>
 cudaError_t launch_sweep_aa_st(const SweepArgs &a, int mode, cudaStream_t s)
 {
-    if ((a.tx * a.ty) % 32 != 0 || a.tx * a.ty > 256 || (a.flat && (a.ty != 1 || a.tz != 1)) || a.pair ||
-        !a.unif)
+    if ((a.tx * a.ty) % 32 != 0 || a.tx * a.ty > 256 || (a.flat && (a.ty != 1 || a.tz != 1)) || !a.unif ||
+        (a.pair && ST == 3))
         return cudaErrorInvalidConfiguration;
     dim3 block(a.tx, a.ty, 1);
     const unsigned gx = unsigned(a.grid > 0 ? a.grid : a.ntiles);
