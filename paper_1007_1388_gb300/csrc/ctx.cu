@@ -787,7 +787,8 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                         fw.src = bs.pdf_base + (long long)q * bs.G + s0;
                                         fw.fstride = n1 != 0 && n2 == 0 ? (long long)bm.pxf * bm.py
                                                      : (n2 != 0 && n1 == 0 ? bm.pxf : 0);
-                                        fw.fsrc = bm.cell_base + ((long long)(zg + 1) * bm.py + (yg + 1)) * bm.pxf + OXF;
+                                        fw.fsrc = bm.cell_base +
+                                                  ((long long)(zg + 1) * bm.py + (yg + 1)) * bm.pxf + OXF;
                                         c->aa_fwd.push_back(fw);
                                         // reverse: only rows whose streaming cell (ghost - e_q)
                                         // lies inside this Block along the slab's row axis
@@ -844,7 +845,8 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                 for (int y = 0; y < b.ny; ++y)
                     for (int x = 0; x < b.nx; ++x) {
                         const long long cf = ((long long)(z + 1) * b.py + (y + 1)) * b.pxf + x + OXF;
-                        if ((hflags[size_t(b.cell_base + cf)] & F_KIND) == F_FLUID) hsidx[size_t(b.cell_base + cf)] = int(nf++);
+                        const size_t at = size_t(b.cell_base + cf);
+                        if ((hflags[at] & F_KIND) == F_FLUID) hsidx[at] = int(nf++);
                     }
         const long long stride = std::max<long long>(64, (nf + 63) / 64 * 64);
         if ((long long)Q * stride >= (1ll << 31))

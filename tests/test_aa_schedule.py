@@ -168,7 +168,8 @@ def build(dims, bd, periodic, face_bc, flags, elem=8):
                                 out = all(not (n[a] != 0 and e[a] != n[a]) for a in range(3))
                                 if not out:
                                     continue
-                                ffst = bm.pxf * bm.py if (n1 != 0 and n2 == 0) else (bm.pxf if (n2 != 0 and n1 == 0) else 0)
+                                ffst = (bm.pxf * bm.py if (n1 != 0 and n2 == 0)
+                                        else (bm.pxf if (n2 != 0 and n1 == 0) else 0))
                                 fwd.append(dict(dst=bm.pdf_base + q * bm.G + d0, src=bs.pdf_base + q * bs.G + s0,
                                                 rows=rows, stride=stride, len=bm.nx,
                                                 fsrc=bm.cell_base + ((zg + 1) * bm.py + (yg + 1)) * bm.pxf + OXF,
@@ -338,9 +339,12 @@ def run(dims, bd, periodic, face_bc, flags, steps, tau=0.8, wall_u=(0.03, -0.01,
                 pxyf = b.pxf * b.py
                 for x, y, z, c, cf in cells(b):
                     tid += 1
-                    if PAIR and x % 2 == 1 and (b.flags[cf - 1] | (4 if b.near[cf - 1] else 0) | b.flags[cf] | (4 if b.near[cf] else 0)) == 0:
+                    def plain(i):  # fluid with no wall or solid neighbour
+                        return b.flags[i] == 0 and not b.near[i]
+
+                    if PAIR and x % 2 == 1 and plain(cf - 1) and plain(cf):
                         continue  # done by the pair of x - 1
-                    if PAIR and x % 2 == 0 and x + 1 < b.nx and (b.flags[cf] | b.flags[cf + 1]) == 0 and not b.near[cf] and not b.near[cf + 1]:
+                    if PAIR and x % 2 == 0 and x + 1 < b.nx and plain(cf) and plain(cf + 1):
                         R = b.pdf_base
                         xm0 = b.xm_off if x == 0 else 0
                         xp1 = b.xp_off if x + 2 == b.nx else 0
