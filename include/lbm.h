@@ -368,8 +368,10 @@ int lbm_profile_read(lbm_ctx *ctx, lbm_profile *out);
  * lbm_autotune - times each candidate sweep configuration (row tiles, runs
  * of consecutive cells, persistent grids, register budgets, the TMA sweep
  * where it applies) on the context's own data (sweeps from the current state
- * into the scratch buffer, which leaves the simulation state unchanged) and
- * keeps the fastest.  cache_path (may be
+ * into the scratch buffer, which leaves the simulation state unchanged; in
+ * place, pairs of steps with the state saved before and restored after, so
+ * that it needs a transient second array and fails with LBM_ENOMEM where
+ * that does not fit) and keeps the fastest.  cache_path (may be
  * NULL) names a JSON-lines file: a matching entry is reused instead of
  * timing, a new result is appended.  best (may be NULL) receives the tile.
  */
@@ -387,8 +389,11 @@ int lbm_autotune(lbm_ctx *ctx, const char *cache_path, int best[3]);
  * persistent launch (0 = one per work item); minb = 3 or 4 resident CTAs per
  * SM the register budget allows (FP64 storage always uses 2); mask = 1 treats
  * near-wall cells through precomputed link masks under a warp vote.  Every
- * configuration gives bitwise identical results.  LBM_EINVAL for an invalid
- * or inapplicable configuration (the context is then unchanged).
+ * configuration gives bitwise identical results.  In-place streaming takes
+ * kinds 0, 2, 3 and 4 with mask 0 (its tuning saves and restores the state
+ * around the timed steps, a transient second array); the fluid-cell list
+ * uses only grid and minb.  LBM_EINVAL for an invalid or inapplicable
+ * configuration (the context is then unchanged).
  */
 int lbm_get_sweep_config(lbm_ctx *ctx, int cfg[8]);
 int lbm_set_sweep_config(lbm_ctx *ctx, const int cfg[8]);
