@@ -40,6 +40,23 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _max_over_ranks(x, ws, device):
+    """The largest x over all ranks: the slowest replica sets the job's time."""
+    if ws == 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_value(ws, cells, steps, ms_max):
+    """Whole-job throughput in MLUPS: each of ws replicas updated `cells`
+    cells `steps` times, the job taking ms_max milliseconds."""
+    return ws * cells * steps / (ms_max * 1e-3) / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -242,12 +259,8 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     prof = L.lbm_profile_read(ctx)
     L.lbm_profile_enable(ctx, False)
-    ms_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = _max_over_ranks(ms, ws, "cuda")
+    value = _job_value(ws, cells, args.steps, ms_max)
 
     # ---- graph-replay timing of the same step (information)
     barrier()
