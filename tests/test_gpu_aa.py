@@ -202,3 +202,26 @@ def test_graphs_writes_at_odd_times_residual_loop_and_autotune(L):
     assert np.array_equal(L.lbm_get_pdfs(two), L.lbm_get_pdfs(aa))
     for c in (two, aa, nog):
         c.destroy()
+
+
+@pytest.mark.parametrize("cfg", [(0, 64, 2, 2, 0, 4, 8, 0), (2, 256, 1, 1, 0, 3, 8, 0),
+                                 (3, 32, 4, 1, 0, 3, 8, 0), (4, 128, 1, 1, 608, 4, 8, 0)])
+def test_every_sweep_configuration_gives_the_same_steps(L, cfg):
+    """One and two cells per thread, row tiles and runs, a persistent grid:
+    the in-place steps stay bitwise equal to the two-array sweep."""
+    dims, bd, periodic, face_bc = GEOMS[0]
+    rng = np.random.default_rng(808)
+    flags = _flags(rng, dims, 0.12, pressure=True)
+    kw = _kw(rng, 1, periodic, face_bc)
+    two, aa = _pair(L, dims, bd, 0.9, flags, kw)
+    L.lbm_set_sweep_config(aa, cfg)
+    assert tuple(L.lbm_get_sweep_config(aa)) == cfg
+    f0 = W.random_pdfs(rng, dims, 1e-2, flags)
+    L.lbm_set_pdfs(two, f0)
+    L.lbm_set_pdfs(aa, f0)
+    for n in (1, 4, 7):
+        L.lbm_step(two, n)
+        L.lbm_step(aa, n)
+        assert np.array_equal(L.lbm_get_pdfs(two), L.lbm_get_pdfs(aa)), n
+    two.destroy()
+    aa.destroy()
