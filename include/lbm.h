@@ -290,7 +290,9 @@ int lbm_residual_vs_snapshot(lbm_ctx *ctx, int steps_since, double *r, double *p
  * work shrinks as instances converge.  steps[k] receives the steps after
  * which instance k first met tol (a multiple of check_every), or -1; res[k]
  * (res may be NULL) its residual then, or its last residual.  Afterwards the
- * context sweeps every instance again.  LBM_ENUMERIC if a residual is NaN.
+ * context sweeps every instance again.  LBM_ENUMERIC if a residual is NaN;
+ * LBM_EINVAL for in-place streaming and the fluid-cell list (single Patches:
+ * lbm_run_to_residual).
  */
 int lbm_run_to_residual_each(lbm_ctx *ctx, double tol, int check_every, int interval, long long max_steps,
                              long long *steps, double *res);

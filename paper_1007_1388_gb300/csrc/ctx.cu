@@ -1753,9 +1753,9 @@ int lbm_run_to_residual_each(lbm_ctx *c, double tol, int check_every, int interv
     if (!c || check_every <= 0 || max_steps < 0 || !steps || (interval && (check_every & 1)))
         return fail(c, LBM_EINVAL, "lbm_run_to_residual_each: bad arguments (interval residuals need an "
                     "even check_every)");
-    if (c->aa)
-        return fail(c, LBM_EINVAL, "lbm_run_to_residual_each: in-place streaming serves single Patches "
-                    "(use lbm_run_to_residual)");
+    if (c->aa || c->sparse)
+        return fail(c, LBM_EINVAL, "lbm_run_to_residual_each: in-place streaming and the fluid-cell list "
+                    "serve single Patches (use lbm_run_to_residual)");
     const int K = c->ninst;
     std::vector<double> r(size_t(K), INFINITY);
     // PDF range of each instance (its Blocks are contiguous)
