@@ -134,6 +134,7 @@ def lib():
             "orc_init_equilibrium": ([pp, u8, d, d, d], None),
             "orc_invariants": ([pp, u8, d, d, d], None),
             "orc_residual": ([pp, u8, d, d], ctypes.c_double),
+            "orc_interval_residual": ([pp, u8, d, d, ctypes.c_int], ctypes.c_double),
             "orc_push_step": ([pp, u8, d, d], None),
         }
         for name, (args, res) in sig.items():
@@ -257,7 +258,32 @@ def invariants(p: Problem, f):
 
 
 def residual(p: Problem, prev, cur) -> float:
+    """One-step velocity residual ||u_n - u_{n-1}|| / ||u_n|| (fluid cells)."""
     return float(lib().orc_residual(ctypes.byref(p._c), _fp(p), _dp(_f64(prev)), _dp(_f64(cur))))
+
+
+def interval_residual(p: Problem, prev, cur, k: int) -> float:
+    """Change per step over k steps, ||u_n - u_{n-k}|| / (k ||u_n||), from the
+    stored states k steps apart (the criterion for sphere-packed channels)."""
+    return float(lib().orc_interval_residual(ctypes.byref(p._c), _fp(p), _dp(_f64(prev)),
+                                             _dp(_f64(cur)), int(k)))
+
+
+def run_to_interval_residual(p: Problem, f, tol: float, k: int, max_steps: int):
+    """Steps f in chunks of k until the interval residual over the last chunk
+    is below tol.  Returns (steps, residual of the last chunk, state); steps
+    is -1 when max_steps passed first.  The stopping rule: the first multiple
+    of k at which r < tol."""
+    f = _f64(f).copy()
+    done, r = 0, float("inf")
+    while done < max_steps:
+        g = run(p, f, k)
+        done += k
+        r = interval_residual(p, f, g, k)
+        f = g
+        if r < tol:
+            return done, r, f
+    return -1, r, f
 
 
 if __name__ == "__main__":  # pragma: no cover

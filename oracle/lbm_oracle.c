@@ -441,6 +441,20 @@ double orc_residual(const orc_problem *p, const uint8_t *flags, const double *pr
     return sqrt(num) / sqrt(den);
 }
 
+/* Change per step over an interval of k steps, the convergence criterion
+ * taken for sphere-packed channels (not in the paper; the one-step residual
+ * above stalls there on an undamped period-2 mode of the scheme):
+ *   r = ||u_n - u_{n-k}||_2 / (k ||u_n||_2)   over fluid cells,
+ * from the stored states of steps n-k (prev) and n (cur).  It is the one-step
+ * residual's quotient of norms, now between states k steps apart, divided
+ * by k.  Returns 0 when both norms vanish. */
+double orc_interval_residual(const orc_problem *p, const uint8_t *flags, const double *prev,
+                             const double *cur, int k)
+{
+    if (k <= 0) return NAN;
+    return orc_residual(p, flags, prev, cur) / (double)k;
+}
+
 /* ------------------------------------------------------------------ */
 /* An independently written push-form step on UNSHIFTED populations,
  * used only to pin orc_step by brute force on tiny grids.  The stored

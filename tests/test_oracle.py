@@ -19,6 +19,10 @@ index, or a transposed operand anywhere in the oracle fails at least one test:
                                    inlet/outlet channel (flux, profile, gradient)
 - curved walls ................... off-grid Poiseuille at second order, q = 1/2 is
                                    half-way bounce-back, push-vs-pull brute force
+- residuals ...................... closed values; uniform forced flow from rest
+                                   (u_n = (n - 1/2) F exactly, so r = 1/(n - 1/2)
+                                   and the stopping step in closed form); the
+                                   period-2 mode cancels over an even interval
 """
 import json
 import os
@@ -502,6 +506,47 @@ def test_residual_definition(orc):
     assert abs(orc.residual(p, a / 2, a) - 0.5) < 1e-15
 
 
+def test_interval_residual_closed_values(orc):
+    """r_k = ||u_n - u_{n-k}|| / (k ||u_n||): zero for equal states, exactly
+    1/k from a state at rest, 1/(2k) from half the velocity."""
+    rng = np.random.default_rng(41)
+    dims = (5, 4, 3)
+    p = orc.Problem(dims=dims, tau=0.7, periodic=(1, 1, 1))
+    a = rng.uniform(-1e-2, 1e-2, (19,) + dims[::-1])
+    z = np.zeros_like(a)
+    for k in (1, 2, 50):
+        assert orc.interval_residual(p, a, a, k) == 0.0
+        assert orc.interval_residual(p, z, z, k) == 0.0
+        assert abs(orc.interval_residual(p, z, a, k) - 1.0 / k) < 1e-15
+        assert abs(orc.interval_residual(p, a / 2, a, k) - 0.5 / k) < 1e-15
+
+
+def test_interval_residual_of_uniform_forced_flow(orc):
+    """A fully periodic box driven from rest by a uniform force moves as a
+    plug.  Its stored momentum grows by exactly F per cell and step, and the
+    velocity that step n's collision used (the reported one) carries half of
+    that step's force: u_n = (n - 1/2) F.  So the change per step over k
+    steps is r = |k F| / (k |u_n|) = 1/(n - 1/2) whatever F and k, and the
+    first multiple of k with r < tol follows in closed form.  A dropped
+    half-force shift gives 1/n and stops one check earlier below; a dropped
+    division by k gives k/(n - 1/2)."""
+    dims = (4, 3, 5)
+    F = (2e-5, -1e-5, 3e-5)
+    for coll in (orc.BGK, orc.TRT):
+        p = orc.Problem(dims=dims, tau=0.9, periodic=(1, 1, 1), force=F, collision=coll)
+        f = orc.zeros(p)
+        g = orc.run(p, f, 30)
+        h = orc.run(p, g, 10)
+        assert abs(orc.interval_residual(p, g, h, 10) - 1.0 / 39.5) < 1e-10
+        assert abs(orc.interval_residual(p, f, h, 40) - 1.0 / 39.5) < 1e-10
+        # 1/(n - 1/2) < 1/79.75 first at n = 81 -> the check at 90 (80 if the
+        # half-force shift were dropped)
+        steps, r, _ = orc.run_to_interval_residual(p, f, 1.0 / 79.75, 10, 1000)
+        assert steps == 90 and abs(r - 1.0 / 89.5) < 1e-10, (steps, r)
+        steps, r, _ = orc.run_to_interval_residual(p, f, 1.0 / 79.75, 10, 80)
+        assert steps == -1 and abs(r - 1.0 / 79.5) < 1e-10
+
+
 def test_threaded_step_is_identical(orc):
     """The OpenMP split over z planes changes no result bit."""
     from paper_1007_1388_gb300 import workloads as W
@@ -543,5 +588,10 @@ def test_staggered_mode_stalls_the_one_step_residual(orc):
             one = orc.residual(p, f, g)
             two = orc.residual(p, f, h)
             assert one > 1e-5 and two < 1e-12, (coll, one, two)
+            # the change per step over an even interval cancels the mode;
+            # over an odd one it does not
+            assert orc.interval_residual(p, f, h, 2) < 1e-12
+            k3 = orc.step(p, h)
+            assert orc.interval_residual(p, f, k3, 3) > 1e-6
     finally:
         orc.set_threads(1)
