@@ -1,0 +1,176 @@
+"""The interval residual against the FP64 oracle.
+
+The convergence criterion of sphere-packed channels is the change per step
+over an even interval of k steps, r = ||u_n - u_{n-k}|| / (k ||u_n||) over
+fluid cells (the one-step residual stalls there on an undamped period-2
+mode).  Checked here:
+
+- lbm_residual_vs_snapshot on a batch of uneven sphere-packed channels, per
+  instance and for a single-instance context, against
+  oracle.interval_residual of the same pair of states (the FP32 states the
+  GPU holds, read back exactly).  The GPU forms each cell's velocity, the
+  float32 snapshot and their difference in FP32 and accumulates the norms in
+  FP64, so the difference carries a few FP32 roundings of |u| (2^-24 each):
+  |r - r_oracle| <= 1e-5 r_oracle + 2.5e-7 / k, i.e. 1e-5 relative while the
+  change over the interval is large, and four roundings of |u| spread over
+  the k steps once it is small;
+- the step at which lbm_run_to_residual_each(interval=1) stops each instance
+  against the oracle's own FP64 run to the same tolerance: equal, or one
+  check apart only where the oracle's residual at the earlier check lies
+  within the trajectory bound of tol;
+- the residual sequence of one instance stepped check by check on the GPU
+  against the oracle's sequence along its own FP64 trajectory, at every
+  check up to convergence.  Trajectory bound: |r - r_oracle| <= 2e-3 r_oracle
+  + 1e-6 / k.  Every FP32 step rounds each stored PDF (2^-24 relative), so
+  over a check interval the two velocity fields drift apart by about
+  sqrt(k) such roundings of |u| (~4e-7 |u| at k = 50), i.e. ~1e-8 in r.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1007_1388_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def bound_same_states(ref, k):
+    """Same pair of states: FP32 velocity formation."""
+    return 1e-5 * ref + 2.5e-7 / k
+
+
+def bound_trajectory(ref, k):
+    """Own trajectories: FP32 vs FP64 states."""
+    return 2e-3 * ref + 1e-6 / k
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1007_1388_gb300 import build
+
+    build.build()
+    import paper_1007_1388_gb300 as L
+
+    L.use_torch_allocator()
+    oracle.build()
+    import os
+
+    oracle.set_threads(os.cpu_count() or 1)
+    return L
+
+
+def _instances():
+    """Four uneven sphere-packed channels (periodic x/z, walls at -y/+y)."""
+    rng = np.random.default_rng(2024)
+    out = []
+    for dims, tau, por, F in [((16, 16, 16), 0.8, 0.8, 2e-6), ((20, 18, 24), 0.7, 0.85, 1e-6),
+                              ((24, 16, 20), 1.0, 0.75, 4e-6), ((18, 22, 16), 0.9, 0.9, 3e-6)]:
+        out.append((dims, tau, W.sphere_packing(rng, dims, por), F))
+    return out
+
+
+def _problem(dims, tau, flags, F):
+    return oracle.Problem(dims=dims, tau=tau, flags=flags, force=(F, 0, 0), **W.channel_bc())
+
+
+def _batch(L, inst):
+    ctx = L.lbm_batch_create([d for d, _, _, _ in inst], [t for _, t, _, _ in inst],
+                             [f for _, _, f, _ in inst], L.make_params(**W.channel_bc()))
+    L.lbm_set_forces(ctx, [[F, 0.0, 0.0] for _, _, _, F in inst])
+    return ctx
+
+
+def _split(f, inst):
+    out, off = [], 0
+    for dims, _, _, _ in inst:
+        nx, ny, nz = dims
+        n = nx * ny * nz
+        out.append(f[off:off + 19 * n].reshape(19, nz, ny, nx))
+        off += 19 * n
+    return out
+
+
+@pytest.mark.parametrize("start,k", [(20, 2), (150, 50), (400, 50)])
+def test_residual_vs_snapshot_matches_oracle_on_the_same_states(L, start, k):
+    inst = _instances()
+    ctx = _batch(L, inst)
+    L.lbm_step(ctx, start)
+    f0 = _split(L.lbm_get_pdfs(ctx), inst)
+    L.lbm_snapshot_velocity(ctx)
+    L.lbm_step(ctx, k)
+    f1 = _split(L.lbm_get_pdfs(ctx), inst)
+    r, per = L.lbm_residual_vs_snapshot(ctx, k, per_instance=True)
+    ctx.destroy()
+    for j, (dims, tau, flags, F) in enumerate(inst):
+        ref = oracle.interval_residual(_problem(dims, tau, flags, F), f0[j], f1[j], k)
+        print(f"start {start} k {k} instance {j}: GPU {per[j]:.6e} oracle {ref:.6e} "
+              f"rel {abs(per[j] - ref) / ref:.2e}")
+        assert ref > 0 and abs(per[j] - ref) <= bound_same_states(ref, k), (j, per[j], ref)
+    # the whole batch's value lies between its instances' values
+    assert min(per) <= r <= max(per)
+    # a single-instance context: the total is the instance's value
+    dims, tau, flags, F = inst[1]
+    c = L.lbm_create(dims, dims, tau, flags, L.make_params(force=(F, 0, 0), **W.channel_bc()))
+    L.lbm_step(c, start)
+    g0 = L.lbm_get_pdfs(c).reshape(19, dims[2], dims[1], dims[0])
+    L.lbm_snapshot_velocity(c)
+    L.lbm_step(c, k)
+    g1 = L.lbm_get_pdfs(c).reshape(19, dims[2], dims[1], dims[0])
+    r1 = L.lbm_residual_vs_snapshot(c, k)
+    c.destroy()
+    ref = oracle.interval_residual(_problem(dims, tau, flags, F), g0, g1, k)
+    assert abs(r1 - ref) <= bound_same_states(ref, k)
+
+
+def test_stopping_step_matches_oracle(L):
+    tol, every = 1e-6, 50
+    inst = _instances()
+    ctx = _batch(L, inst)
+    steps, res = L.lbm_run_to_residual_each(ctx, tol, every, 20000, interval=True)
+    ctx.destroy()
+    for j, (dims, tau, flags, F) in enumerate(inst):
+        p = _problem(dims, tau, flags, F)
+        # the oracle's own run, keeping every check's residual
+        f = oracle.zeros(p)
+        seq, s_o = [], -1
+        for c in range(1, 20000 // every + 1):
+            g = oracle.run(p, f, every)
+            seq.append(oracle.interval_residual(p, f, g, every))
+            f = g
+            if seq[-1] < tol:
+                s_o = c * every
+                break
+        assert s_o > 0 and steps[j] > 0, (j, s_o, steps[j])
+        if steps[j] != s_o:
+            # only a check whose residual sits at the tolerance may differ
+            assert abs(int(steps[j]) - s_o) == every, (j, steps[j], s_o)
+            c = min(int(steps[j]), s_o) // every - 1
+            assert abs(seq[c] - tol) <= bound_trajectory(tol, every), (j, seq[c])
+        print(f"instance {j} {dims}: GPU stops at {steps[j]}, oracle at {s_o} "
+              f"(residuals {res[j]:.4e} / {seq[-1]:.4e})")
+
+
+def test_residual_sequence_follows_oracle(L):
+    every = 50
+    dims, tau, flags, F = _instances()[2]
+    c = L.lbm_create(dims, dims, tau, flags, L.make_params(force=(F, 0, 0), **W.channel_bc()))
+    p = _problem(dims, tau, flags, F)
+    f = oracle.zeros(p)
+    L.lbm_snapshot_velocity(c)
+    ref = 1.0
+    for check in range(40):
+        L.lbm_step(c, every)
+        r = L.lbm_residual_vs_snapshot(c, every)
+        L.lbm_snapshot_velocity(c)
+        g = oracle.run(p, f, every)
+        ref = oracle.interval_residual(p, f, g, every)
+        f = g
+        print(f"check {check}: GPU {r:.6e} oracle {ref:.6e} rel {abs(r - ref) / ref:.2e}")
+        assert abs(r - ref) <= bound_trajectory(ref, every), (check, r, ref)
+        if ref < 1e-6:
+            break
+    assert ref < 1e-6
+    c.destroy()
