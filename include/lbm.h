@@ -414,9 +414,10 @@ int lbm_directions(int *e, double *w, int *opp);
 /*
  * lbm_invariants_noalloc - the FP64 sums of lbm_invariants for callers that
  * cannot allocate device memory.  The paper has no counterpart; it exists for
- * callers that run where cudaMalloc is not allowed or not safe (while another
- * component captures a CUDA graph, inside a framework's allocator callback,
- * or when a caching allocator already holds all device memory).
+ * callers that run where cudaMalloc is not allowed or not safe: inside a
+ * framework's allocator callback (a new allocation would re-enter it), or
+ * when a caching allocator already holds all device memory (cudaMalloc
+ * fails).
  *   f       : device, float[19*n_cells], shifted PDFs, direction-major
  *             (f[q*n_cells + c]); caller-owned.
  *   flags   : device, uint8[n_cells] (LBM_FLUID = 0 is summed), or NULL = all fluid.

@@ -97,7 +97,10 @@ const char *unet_last_error(const unet_ctx *ctx);
 /*
  * Layer-level entry points on caller-owned device buffers (bf16 =
  * __nv_bfloat16 bits), for tests and for users composing their own networks.
- * Grid: nb grids of 2^lz x 2^ly x 2^lx voxels.
+ * Grid: nb grids of 2^lz x 2^ly x 2^lx voxels.  Each call takes its scratch
+ * (the kernels' error word, weight-gradient partial sums) from the allocator
+ * installed with lbm_set_allocator (cudaMalloc when none is), gives it back
+ * before returning, and synchronises its stream.
  *
  * unet_conv3 - out[m][co] = act(bias[co] + sum_t sum_ci in[m + off_t][ci] w[co][t][ci])
  * with in = [src0, src1] (channels c0 + c1, multiples of 16; c1 may be 0 and

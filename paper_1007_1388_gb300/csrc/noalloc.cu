@@ -1,13 +1,14 @@
 // lbm_invariants_noalloc: the FP64 invariant reduction for callers that
 // cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc (or any allocating routine): code that
-// runs while another component is capturing a CUDA graph, code called back
-// from inside a framework's own allocator, or processes whose device memory
-// a caching allocator has already reserved in full.  For them this entry
-// point computes the same sums as lbm_invariants, but on a plain array the
-// caller owns, and keeps its per-tile partial sums in a fixed file-scope
-// device array instead of allocated scratch.  It allocates nothing.
+// Some callers cannot call cudaMalloc (or any allocating routine): code
+// called back from inside a framework's own allocator, where a new
+// allocation would re-enter it, or processes whose device memory a caching
+// allocator has already reserved in full, where cudaMalloc fails.  For them
+// this entry point computes the same sums as lbm_invariants, but on a plain
+// array the caller owns, and keeps its per-tile partial sums in a fixed
+// file-scope device array instead of allocated scratch.  It allocates
+// nothing.
 #include <mutex>
 
 #include "device_common.cuh"

@@ -1100,6 +1100,40 @@ int unet_adam_step(unet_ctx *c, float lr, float b1, float b2, float eps)
     return LBM_OK;
 }
 
+// Scratch of one layer-API call (error word, weight-gradient partials):
+// taken from the allocator installed with lbm_set_allocator (the caller's
+// caching allocator) when there is one, else from cudaMalloc, and given back
+// when the call returns (after its stream has been synchronised).
+struct LayerScratch {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void *stream = nullptr;
+    lbm_alloc_fn al = nullptr;
+    lbm_free_fn rl = nullptr;
+    void *user = nullptr;
+
+    LayerScratch(size_t n, void *s) : bytes(n), stream(s)
+    {
+        current_allocator(&al, &rl, &user);
+        if (al) {
+            p = al(bytes, stream, user);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    ~LayerScratch()
+    {
+        if (!p) return;
+        if (rl)
+            rl(p, bytes, stream, user);
+        else if (!al)
+            cudaFree(p);
+    }
+    LayerScratch(const LayerScratch &) = delete;
+    LayerScratch &operator=(const LayerScratch &) = delete;
+};
+
 int unet_conv3(const void *src0, int c0, int up0, const void *src1, int c1, const void *w, const float *bias,
                void *out, int out_f32, int relu, int cout, int nb, int lz, int ly, int lx, void *stream)
 {
@@ -1118,8 +1152,9 @@ int unet_conv3(const void *src0, int c0, int up0, const void *src1, int c1, cons
     a.out_f32 = out_f32 ? 1 : 0;
     a.relu = relu ? 1 : 0;
     a.g = VGrid{nb, lz, ly, lx};
-    int *err = nullptr;
-    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return ufail(nullptr, LBM_ENOMEM, "unet_conv3: error word");
+    LayerScratch scratch(256, stream);
+    if (!scratch.p) return ufail(nullptr, LBM_ENOMEM, "unet_conv3: error word");
+    int *err = static_cast<int *>(scratch.p);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(err, 0, sizeof(int), s);
     a.err = err;
@@ -1127,7 +1162,6 @@ int unet_conv3(const void *src0, int c0, int up0, const void *src1, int c1, cons
     int h = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaFree(err);
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3: invalid channels or pointers");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3: a bounded wait timed out");
@@ -1152,19 +1186,10 @@ int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1
     a.vps = wgrad_vps(g.voxels(), a.rows_pad / 128);
     a.g = g;
     const int nsplit = wgrad_splits(g, a.vps);
-    void *(*al)(size_t, void *, void *) = nullptr;
-    void (*rl)(void *, size_t, void *, void *) = nullptr;
-    void *user = nullptr;
-    current_allocator(&al, &rl, &user);
     const size_t bytes = size_t(nsplit) * a.rows_pad * cout * sizeof(float) + 256;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    void *ws = nullptr;
-    if (al) {
-        ws = al(bytes, stream, user);
-    } else if (cudaMalloc(&ws, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        ws = nullptr;
-    }
+    LayerScratch scratch(bytes, stream);
+    void *ws = scratch.p;
     if (!ws) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_wgrad: workspace of %zu bytes", bytes);
     a.partial = static_cast<float *>(ws);
     a.err = reinterpret_cast<int *>(static_cast<char *>(ws) + bytes - 256);
@@ -1173,10 +1198,6 @@ int unet_conv3_wgrad(const void *src0, int c0, int up0, const void *src1, int c1
     int h = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (rl)
-        rl(ws, bytes, stream, user);
-    else if (!al)
-        cudaFree(ws);
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_wgrad: invalid channels");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_wgrad: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_wgrad: a bounded wait timed out");
@@ -1203,8 +1224,9 @@ int unet_conv3_halo(const void *src0, int c0, const void *src1, int c1, const vo
     a.out_f32 = out_f32 ? 1 : 0;
     a.relu = relu ? 1 : 0;
     a.g = g;
-    int *err = nullptr;
-    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_halo: error word");
+    LayerScratch scratch(256, stream);
+    if (!scratch.p) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_halo: error word");
+    int *err = static_cast<int *>(scratch.p);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(err, 0, sizeof(int), s);
     a.err = err;
@@ -1212,7 +1234,6 @@ int unet_conv3_halo(const void *src0, int c0, const void *src1, int c1, const vo
     int h = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaFree(err);
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo: invalid channels or grid");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_halo: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_halo: a bounded wait timed out");
@@ -1239,19 +1260,10 @@ int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, co
     a.vps = wgrad_vps(g.voxels(), a.rows_pad / 128);
     a.g = g;
     const int nsplit = wgrad_splits(g, a.vps);
-    void *(*al)(size_t, void *, void *) = nullptr;
-    void (*rl)(void *, size_t, void *, void *) = nullptr;
-    void *user = nullptr;
-    current_allocator(&al, &rl, &user);
     const size_t bytes = size_t(nsplit) * a.rows_pad * cout * sizeof(float) + 256;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    void *ws = nullptr;
-    if (al) {
-        ws = al(bytes, stream, user);
-    } else if (cudaMalloc(&ws, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        ws = nullptr;
-    }
+    LayerScratch scratch(bytes, stream);
+    void *ws = scratch.p;
     if (!ws) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_halo_wgrad: workspace of %zu bytes", bytes);
     a.partial = static_cast<float *>(ws);
     a.err = reinterpret_cast<int *>(static_cast<char *>(ws) + bytes - 256);
@@ -1260,10 +1272,6 @@ int unet_conv3_halo_wgrad(const void *src0, int c0, const void *src1, int c1, co
     int h = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (rl)
-        rl(ws, bytes, stream, user);
-    else if (!al)
-        cudaFree(ws);
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_halo_wgrad: invalid channels");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_halo_wgrad: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_halo_wgrad: a bounded wait timed out");
@@ -1297,8 +1305,9 @@ int unet_conv3_planar(const void *src0, int c0, const void *src1, int c1, const 
     a.relu = relu ? 1 : 0;
     a.tiles = cout > 0 ? conv_tiles(g, c0 + c1, cout) : 1;
     a.g = g;
-    int *err = nullptr;
-    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_planar: error word");
+    LayerScratch scratch(256, stream);
+    if (!scratch.p) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_planar: error word");
+    int *err = static_cast<int *>(scratch.p);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaMemsetAsync(err, 0, sizeof(int), s);
     a.err = err;
@@ -1306,7 +1315,6 @@ int unet_conv3_planar(const void *src0, int c0, const void *src1, int c1, const 
     int h = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaFree(err);
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_planar: invalid channels or grid");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_planar: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_planar: a bounded wait timed out");
@@ -1334,19 +1342,10 @@ int unet_conv3_planar_wgrad(const void *src0, int c0, const void *src1, int c1, 
     a.pps = wgrad_bulk_pps(g, a.rows_pad / 128, a.run);
     a.g = g;
     const int nsplit = wgrad_bulk_splits(g, a.pps);
-    void *(*al)(size_t, void *, void *) = nullptr;
-    void (*rl)(void *, size_t, void *, void *) = nullptr;
-    void *user = nullptr;
-    current_allocator(&al, &rl, &user);
     const size_t bytes = size_t(nsplit) * a.rows_pad * cout * sizeof(float) + 256;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    void *ws = nullptr;
-    if (al) {
-        ws = al(bytes, stream, user);
-    } else if (cudaMalloc(&ws, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        ws = nullptr;
-    }
+    LayerScratch scratch(bytes, stream);
+    void *ws = scratch.p;
     if (!ws) return ufail(nullptr, LBM_ENOMEM, "unet_conv3_planar_wgrad: workspace of %zu bytes", bytes);
     a.partial = static_cast<float *>(ws);
     a.err = reinterpret_cast<int *>(static_cast<char *>(ws) + bytes - 256);
@@ -1355,10 +1354,6 @@ int unet_conv3_planar_wgrad(const void *src0, int c0, const void *src1, int c1, 
     int h = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&h, a.err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (rl)
-        rl(ws, bytes, stream, user);
-    else if (!al)
-        cudaFree(ws);
     if (e == cudaErrorInvalidValue) return ufail(nullptr, LBM_EINVAL, "unet_conv3_planar_wgrad: invalid channels");
     if (e != cudaSuccess) return ufail(nullptr, LBM_ECUDA, "unet_conv3_planar_wgrad: %s", cudaGetErrorString(e));
     if (h) return ufail(nullptr, LBM_ETIMEOUT, "unet_conv3_planar_wgrad: a bounded wait timed out");

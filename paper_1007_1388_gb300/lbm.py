@@ -496,19 +496,55 @@ def lbm_directions():
     return np.array(e[:]).reshape(Q, 3), np.array(w[:]), np.array(o[:])
 
 
+def _noalloc_tensor(name, t, dtype, numel):
+    """Checks one tensor argument of lbm_invariants_noalloc before its address
+    reaches the kernels: dtype, element count and contiguity."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
 def lbm_invariants_noalloc(f, flags, n_cells: int, rho0: float, force, out, stream=None):
     """Allocation-free FP64 invariants of a caller-owned device PDF array.
 
     f: CUDA float32 tensor of 19*n_cells (direction-major); flags: CUDA uint8
-    tensor of n_cells or None; out: CUDA float64 tensor of 5; stream: a
-    torch.cuda.Stream (default: the current stream).  Enqueues only.
+    tensor of n_cells or None; out: CUDA float64 tensor of 5; all on one
+    device.  stream: a torch.cuda.Stream on that device (default: its current
+    stream).  Enqueues only; the call is made with that device current.
+    Raises ValueError before any device work for a wrong dtype, size,
+    layout or device.
     """
     import torch
 
-    s = stream if stream is not None else torch.cuda.current_stream()
+    n_cells = int(n_cells)
+    if n_cells <= 0:
+        raise ValueError("n_cells must be positive")
+    ts = [_noalloc_tensor("f", f, torch.float32, Q * n_cells), _noalloc_tensor("out", out, torch.float64, 5)]
+    if flags is not None:
+        ts.append(_noalloc_tensor("flags", flags, torch.uint8, n_cells))
+    for t in ts:
+        if t.device.type != "cuda":
+            raise ValueError("f, flags and out must be CUDA tensors")
+    dev = f.device
+    if any(t.device != dev for t in ts):
+        raise ValueError("f, flags and out must be on the same device")
+    if stream is not None and stream.device != dev:
+        raise ValueError("stream must belong to the device of f")
+    if len(force) != 3:
+        raise ValueError("force must have 3 components")
     F = (ctypes.c_double * 3)(*[float(v) for v in force])
-    _check(lib().lbm_invariants_noalloc(_ptr(f), _ptr(flags), int(n_cells), float(rho0), F,
-                                        _ptr(out), s.cuda_stream))
+    with torch.cuda.device(dev):
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        _check(lib().lbm_invariants_noalloc(_ptr(f), _ptr(flags), n_cells, float(rho0), F,
+                                            _ptr(out), s.cuda_stream))
 
 
 def lbm_last_error(ctx: Ctx | None = None) -> str:

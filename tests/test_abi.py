@@ -171,3 +171,31 @@ def test_product_path_has_no_oracle_or_cpu_fallback():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "lbm_oracle" not in text, fn
+
+
+def test_noalloc_binding_checks_arguments_before_the_call(L):
+    """lbm_invariants_noalloc's binding refuses a wrong dtype, size, layout or
+    device with ValueError before any address reaches the library (checked
+    here with CPU tensors: the device check comes last, so the earlier
+    checks are reached)."""
+    torch = pytest.importorskip("torch")
+    n = 100
+    f = torch.zeros(19 * n, dtype=torch.float32)
+    out = torch.zeros(5, dtype=torch.float64)
+    flags = torch.zeros(n, dtype=torch.uint8)
+    cases = [
+        (f.double(), flags, n, out, "float32"),
+        (f[:-1], flags, n, out, "elements"),
+        (f, flags, n + 1, out, "elements"),
+        (f, flags, n, torch.zeros(4, dtype=torch.float64), "elements"),
+        (f, flags, n, out.float(), "float64"),
+        (f, flags[:-1], n, out, "elements"),
+        (f, flags.to(torch.int32), n, out, "uint8"),
+        (torch.zeros(2 * 19 * n, dtype=torch.float32)[::2], flags, n, out, "contiguous"),
+        (f, flags, 0, out, "positive"),
+        (f, flags, n, out, "CUDA"),
+        (f.numpy(), flags, n, out, "torch tensor"),
+    ]
+    for ff, fl, nc, oo, what in cases:
+        with pytest.raises(ValueError, match=what):
+            L.lbm_invariants_noalloc(ff, fl, nc, 1.0, (0.0, 0.0, 0.0), oo)

@@ -1,10 +1,10 @@
 """The allocation-free invariant reduction (lbm_invariants_noalloc).
 
-Some callers cannot allocate device memory (they run while another
-component captures a CUDA graph, inside a framework's allocator callback, or
-after a caching allocator has reserved the whole device).  This entry point
-gives them the FP64 invariants using a fixed device array instead of scratch
-allocations.  Here its output is checked against lbm_invariants of the same
+Some callers cannot allocate device memory: code called back from inside a
+framework's allocator (a new allocation would re-enter it), or processes
+whose device memory a caching allocator has reserved in full (cudaMalloc
+fails).  This entry point gives them the FP64 invariants using a fixed
+device array instead of scratch allocations.  Here its output is checked against lbm_invariants of the same
 state on two calls in a row (the second on a different state, so stale
 partial sums from the first call would show), with the tolerances of the
 other reduction tests.  The file sorts last so that a stop at the first
@@ -73,7 +73,15 @@ def test_noalloc_all_fluid_and_limit(L):
     v = float(np.float32(1e-3))  # the value the FP32 array holds
     assert abs(got[0] - n * (1.0 + v)) <= 1e-9
     assert abs(got[2] - n * v) <= 1e-9 and got[1] == 0.0 and got[3] == 0.0
-    with pytest.raises(L.LBMError) as ei:
-        L.lbm_invariants_noalloc(f, None, 67108864 + 1, 1.0, (0, 0, 0), out)
-    assert ei.value.code == L.LBM_EINVAL
+    # beyond the scratch array's size the C entry point refuses before any
+    # launch (called directly: the binding would refuse the small f first)
+    import ctypes
+
+    F = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    rc = L.lib().lbm_invariants_noalloc(f.data_ptr(), None, 67108864 + 1, 1.0, F, out.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream)
+    assert rc == L.LBM_EINVAL
     assert "scratch limit" in L.lbm_last_error()
+    # the binding checks sizes against the tensors
+    with pytest.raises(ValueError):
+        L.lbm_invariants_noalloc(f, None, n + 1, 1.0, (0.0, 0.0, 0.0), out)
