@@ -358,6 +358,14 @@ def run_gpu(args):
     if not args.skip_batch:
         batch = _batch_variants(args, L, W, barrier, torch)
 
+    log = (lambda m: print(m, file=sys.stderr, flush=True)) if rank == 0 else None
+    ttr = None
+    if not args.skip_ttr:
+        ttr = _time_to_residual(args, L, W, torch, log)
+    precision = None
+    if not args.skip_precision:
+        precision = _precision(L, W, torch, args.report_size, args.precision_steps, args.report_block, log)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         cores = os.cpu_count() or 1
@@ -381,7 +389,7 @@ def run_gpu(args):
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(prof.sweep_launches + prof.exchange_launches),
                "clocks": clk.summary(), "graph_mlups": graph_mlups, "variants": variants,
-               "batch": batch}
+               "batch": batch, "time_to_residual": ttr, "precision": precision}
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -459,28 +467,16 @@ def _batch_variants(args, L, W, barrier, torch):
 PRECISION_WORKLOAD = "D3Q19 lid-driven cavity 384^3, lid 0.05 along x on +y, BGK tau=0.55, 5000 steps"
 
 
-def run_precision_report(args):
-    """Storage precision at full size: u and rho of FP32, shifted FP16 (scale
-    256 and 1) and BF16 storage against FP64 storage of the same cavity, with
-    the MLUPS of each.  Prints one JSON line."""
-    import numpy as np
-    import torch
-
-    torch.cuda.set_device(0)
-    from paper_1007_1388_gb300 import build
-
-    build.build()
-    import paper_1007_1388_gb300 as L
-    from paper_1007_1388_gb300 import workloads as W
-
-    L.use_torch_allocator()
-    n, steps, b = args.report_size, args.report_steps, args.report_block
+def _precision(L, W, torch, n, steps, b, log=None):
+    """u and rho of FP32, shifted FP16 (scale 256 and 1) and BF16 storage
+    against FP64 storage of the same lid-driven cavity after `steps` steps,
+    and the MLUPS of each (autotuned, CUDA events)."""
     cases = [("f64", L.LBM_F64, 1.0), ("f32", L.LBM_F32, 1.0), ("f16s_scale256", L.LBM_F16S, 256.0),
              ("f16s_scale1", L.LBM_F16S, 1.0), ("bf16s", L.LBM_BF16S, 1.0)]
-    out = {"report": "precision", "workload": PRECISION_WORKLOAD.replace("384", str(n), 1)
-           .replace("5000", str(steps)), "block": b}
+    out = {"workload": PRECISION_WORKLOAD.replace("384", str(n), 1).replace("5000", str(steps)), "block": b}
     ref = None
     for name, st, scale in cases:
+        torch.cuda.empty_cache()
         p = L.make_params(wall_u=(0.05, 0, 0), storage=st, storage_scale=scale, **W.cavity_bc())
         ctx = L.lbm_create((n,) * 3, (b,) * 3, 0.55, None, p)
         L.lbm_autotune(ctx, None)
@@ -492,10 +488,12 @@ def run_precision_report(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         m, _, nonfinite = L.lbm_invariants(ctx)
-        rho, u = L.lbm_macroscopic(ctx)
+        rho = torch.empty(n**3, dtype=torch.float32, device="cuda")
+        u = torch.empty(3 * n**3, dtype=torch.float32, device="cuda")
+        L.lbm_macroscopic_device(ctx, rho, u)
+        L.lbm_synchronize(ctx)
         ctx.destroy()
-        rho = torch.from_numpy(rho).cuda().double()
-        u = torch.from_numpy(u).cuda().double()
+        rho, u = rho.double(), u.double()
         row = {"mlups": n**3 * steps / (ms * 1e-3) / 1e6, "mass": m, "nonfinite": nonfinite}
         if ref is None:
             ref = (rho, u)
@@ -505,10 +503,153 @@ def run_precision_report(args):
             row.update(u_max_err=float(du.abs().max()), u_rms_err=float(du.square().mean().sqrt()),
                        rho_max_err=float(dr.abs().max()), rho_rms_err=float(dr.square().mean().sqrt()))
         out[name] = row
-        print(name, row, file=sys.stderr, flush=True)
+        if log:
+            log(f"{name} {row}")
         del rho, u
+    del ref
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_precision_report(args):
+    """Storage precision at full size (one JSON line): see _precision."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1007_1388_gb300 import build
+
+    build.build()
+    import paper_1007_1388_gb300 as L
+    from paper_1007_1388_gb300 import workloads as W
+
+    L.use_torch_allocator()
+    out = _precision(L, W, torch, args.report_size, args.report_steps, args.report_block,
+                     log=lambda m: print(m, file=sys.stderr, flush=True))
+    out["report"] = "precision"
     print(json.dumps(out))
     return 0
+
+
+TTR_WORKLOAD = ("held-out sphere-packed channels 64^3 (seeds 10000.., periodic x/z, walls -y/+y, spheres of "
+                "radius 2-6, porosity U[0.7, 0.9], force U[5e-7, 5e-6] along x), BGK tau=0.8; residual 1e-6 = "
+                "change per step over 50-step checks, per instance")
+
+
+def _solve_separate(L, W, WS, flags, forces, n, tol, every, max_steps):
+    """The same channels as one context each (own stream), stepped
+    interleaved: every live context takes a velocity snapshot and `every`
+    steps, then each is checked.  Returns (steps per instance, seconds)."""
+    import numpy as np
+    import torch
+
+    K = len(flags)
+    ctxs = [L.lbm_create((n, n, n), (n, n, n), WS.TAU, f, L.make_params(force=(F, 0, 0), **W.channel_bc()))
+            for f, F in zip(flags, forces)]
+    steps = np.full(K, -1, np.int64)
+    live, done = list(range(K)), 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while live and done < max_steps:
+        for k in live:
+            L.lbm_snapshot_velocity(ctxs[k])
+            L.lbm_step(ctxs[k], every)
+        done += every
+        nxt = []
+        for k in live:
+            if L.lbm_residual_vs_snapshot(ctxs[k], every) < tol:
+                steps[k] = done
+            else:
+                nxt.append(k)
+        live = nxt
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    for c in ctxs:
+        c.destroy()
+    return steps, sec
+
+
+def _time_to_residual(args, L, W, torch, log=None):
+    """Time to residual 1e-6 on held-out sphere-packed channels: FP32 from
+    rest (one batch context; and one context per channel), shifted-FP16
+    storage handed over to FP32 at residual 1e-5, the learned warm start
+    (network trained in this run), and both combined.  Wall seconds from the
+    initial state to every instance converged (host-timed, checks included);
+    final velocity error against the FP32 solution from rest."""
+    import numpy as np
+    from paper_1007_1388_gb300 import unet, warmstart as WS
+
+    n, K, tol, every = args.ttr_size, args.ttr_eval, 1e-6, 50
+    V = n ** 3
+    t0 = time.perf_counter()
+    samples = W.channel_samples(list(range(args.ttr_train)) + list(range(10000, 10000 + K)), n)
+    ev = samples[args.ttr_train:]
+    flags = [f for f, _ in ev]
+    forces = [F for _, F in ev]
+    out = {"workload": TTR_WORKLOAD.replace("64^3", f"{n}^3"), "instances": K, "tol": tol, "check_every": every,
+           "geometry_seconds": time.perf_counter() - t0}
+    u_ref = None
+
+    def row(steps, sec, u=None):
+        ok = steps[steps >= 0]
+        r = {"steps_mean": float(ok.mean()) if ok.size else None,
+             "steps_median": float(np.median(ok)) if ok.size else None,
+             "steps_max": int(ok.max()) if ok.size else None, "unconverged": int((steps < 0).sum()),
+             "wall_s": sec}
+        if u is not None:
+            e = [float((u[3 * V * k:3 * V * (k + 1)] - u_ref[3 * V * k:3 * V * (k + 1)]).norm()
+                       / u_ref[3 * V * k:3 * V * (k + 1)].norm()) for k in range(K)]
+            r["u_rel_err_mean"], r["u_rel_err_max"] = float(np.mean(e)), float(np.max(e))
+        if "f32_batched" in out:
+            r["speedup_wall"] = out["f32_batched"]["wall_s"] / sec
+            r["speedup_steps"] = out["f32_batched"]["steps_mean"] / r["steps_mean"] if ok.size else None
+        if log:
+            log(f"time to residual: {r}")
+        return r
+
+    ctx, st, _, sec = WS.solve(flags, forces, n, tol, every)
+    _, u_ref = WS.fields(ctx, K, n)
+    ctx.destroy()
+    out["f32_batched"] = row(st, sec)
+    st, sec = _solve_separate(L, W, WS, flags, forces, n, tol, every, 20000)
+    out["f32_separate_contexts"] = row(st, sec)
+    ctx, st, s16, _, sec = WS.solve_handover(flags, forces, n, tol, 1e-5, every)
+    _, u = WS.fields(ctx, K, n)
+    ctx.destroy()
+    out["f16s_then_f32"] = row(st, sec, u)
+    out["f16s_then_f32"]["steps_16bit_mean"] = float(s16.mean())
+    out["f16s_then_f32"]["switch_tol"] = 1e-5
+    # the learned warm start: training set solved and network trained here
+    t1 = time.perf_counter()
+    train = WS.make_dataset(None, n, chunk=250, tol=tol, samples=samples[:args.ttr_train])
+    net = unet.UNet(n, 4, seed=1)
+    losses = WS.train(net, train, epochs=args.ttr_epochs, lr=2e-3, lr_final=2e-5)
+    torch.cuda.synchronize()
+    out["network"] = {"train_channels": args.ttr_train, "epochs": args.ttr_epochs,
+                      "train_set_solve_seconds": train.solve_seconds,
+                      "train_seconds": time.perf_counter() - t1 - train.solve_seconds,
+                      "loss_last": float(np.mean(losses[-50:]))}
+    solid = torch.from_numpy(np.concatenate([f.reshape(-1) for f in flags])).cuda()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    init = WS.predict(net, solid, forces, n, train.s_rho, train.s_u)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t2
+    e = [float((init[1][3 * V * k:3 * V * (k + 1)] - u_ref[3 * V * k:3 * V * (k + 1)]).norm()
+               / u_ref[3 * V * k:3 * V * (k + 1)].norm()) for k in range(K)]
+    out["network"].update(inference_seconds=t_inf, prediction_u_rel_err_mean=float(np.mean(e)))
+    ctx, st, _, sec = WS.solve(flags, forces, n, tol, every, init=init)
+    _, u = WS.fields(ctx, K, n)
+    ctx.destroy()
+    out["warm_start_f32"] = row(st, sec + t_inf, u)
+    ctx, st, s16, _, sec = WS.solve_handover(flags, forces, n, tol, 1e-5, every, init=init)
+    _, u = WS.fields(ctx, K, n)
+    ctx.destroy()
+    out["warm_start_f16s_then_f32"] = row(st, sec + t_inf, u)
+    out["warm_start_f16s_then_f32"]["steps_16bit_mean"] = float(s16.mean())
+    net.destroy()
+    del train, init, u, u_ref, solid
+    torch.cuda.empty_cache()
+    return out
 
 
 SIZES_WORKLOAD = ("D3Q19 channel (periodic x/z, no-slip walls -y/+y), BGK tau=0.8, force 1e-6 along x, FP32; "
@@ -849,6 +990,14 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-ttr", action="store_true", help="skip the time-to-residual block")
+    ap.add_argument("--skip-precision", action="store_true", help="skip the storage-precision block")
+    ap.add_argument("--precision-steps", type=int, default=2000,
+                    help="steps of the precision block in the default run (--report precision: --report-steps)")
+    ap.add_argument("--ttr-size", type=int, default=64)
+    ap.add_argument("--ttr-eval", type=int, default=48, help="held-out channels of the time-to-residual block")
+    ap.add_argument("--ttr-train", type=int, default=1000, help="training channels of its warm start")
+    ap.add_argument("--ttr-epochs", type=int, default=30)
     ap.add_argument("--report", default="", choices=["", "precision", "warmstart", "unet", "sizes", "porous"],
                     help="precision: storage-precision report on the 384^3 cavity; warmstart: the learned "
                          "warm start end to end (one JSON line each)")

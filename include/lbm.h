@@ -210,6 +210,17 @@ int lbm_get_pdfs(lbm_ctx *ctx, double *f);
 int lbm_set_pdfs(lbm_ctx *ctx, const double *f);
 
 /*
+ * lbm_get_pdfs_device / lbm_set_pdfs_device - the same on a caller-owned
+ * device double[19*N] in the same layout, enqueued on the context stream
+ * (no host copy).  A state read from one context can be set into another of
+ * the same geometry and a different storage format: the hand-over from
+ * shifted 16-bit to FP32 storage is exact (every 16-bit value divided by a
+ * power-of-two scale is an FP32 value).
+ */
+int lbm_get_pdfs_device(lbm_ctx *ctx, double *f);
+int lbm_set_pdfs_device(lbm_ctx *ctx, const double *f);
+
+/*
  * lbm_init_equilibrium - sets every fluid cell to f~eq(rho - rho0, u) of
  * Eq. (2) (warm start from given fields).  rho: float[N], u: float[3*N].
  */

@@ -1541,6 +1541,30 @@ int lbm_set_pdfs(lbm_ctx *c, const double *f)
     return LBM_OK;
 }
 
+int lbm_get_pdfs_device(lbm_ctx *c, double *f)
+{
+    if (!c || !f) return fail(c, LBM_EINVAL, "lbm_get_pdfs_device: NULL argument");
+    std::unique_ptr<Temp> g;
+    const void *st = nullptr;
+    FieldArgs fa = field_args(c);
+    int rc = readable_state(c, g, &st, fa);
+    if (rc) return rc;
+    CK(launch_get_pdfs(fa, st, f, c->stream), "get_pdfs launch");
+    // an odd-time in-place state was read back into a transient array
+    if (g) CK(cudaStreamSynchronize(c->stream), "lbm_get_pdfs_device");
+    return LBM_OK;
+}
+
+int lbm_set_pdfs_device(lbm_ctx *c, const double *f)
+{
+    if (!c || !f) return fail(c, LBM_EINVAL, "lbm_set_pdfs_device: NULL argument");
+    CK(launch_set_pdfs(write_args(c), c->buf[c->cur], f, c->stream), "set_pdfs launch");
+    CK(enqueue_aa_prepare(c), "prepare pressure links");
+    c->have_prev = false;
+    c->aa_phase = 0;
+    return LBM_OK;
+}
+
 int lbm_init_equilibrium_device(lbm_ctx *c, const float *rho, const float *u)
 {
     if (!c || !rho || !u) return fail(c, LBM_EINVAL, "lbm_init_equilibrium_device: NULL argument");

@@ -106,6 +106,8 @@ SIGNATURES = {
     "lbm_macroscopic_device": ([_vp, _vp, _vp], _i),
     "lbm_get_pdfs": ([_vp, _vp], _i),
     "lbm_set_pdfs": ([_vp, _vp], _i),
+    "lbm_get_pdfs_device": ([_vp, _vp], _i),
+    "lbm_set_pdfs_device": ([_vp, _vp], _i),
     "lbm_init_equilibrium": ([_vp, _vp, _vp], _i),
     "lbm_init_equilibrium_device": ([_vp, _vp, _vp], _i),
     "lbm_invariants": ([_vp, _P(_d), _P(_d), _P(_d), _vp], _i),
@@ -361,6 +363,26 @@ def lbm_set_pdfs(ctx: Ctx, f):
     f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
     assert f.size == Q * ctx.cells
     _check(lib().lbm_set_pdfs(ctx.ptr, _ptr(f)), ctx)
+
+
+def _device_pdfs(ctx: Ctx, f):
+    """Checks a device PDF buffer: a contiguous CUDA float64 tensor of 19 N."""
+    import torch
+
+    if not (isinstance(f, torch.Tensor) and f.dtype == torch.float64 and f.is_cuda and f.is_contiguous()
+            and f.numel() == Q * ctx.cells):
+        raise ValueError(f"f must be a contiguous CUDA float64 tensor of {Q * ctx.cells} values")
+    return f
+
+
+def lbm_get_pdfs_device(ctx: Ctx, f):
+    """Enqueues the state's shifted PDFs into the CUDA float64 tensor f (19 N)."""
+    _check(lib().lbm_get_pdfs_device(ctx.ptr, _ptr(_device_pdfs(ctx, f))), ctx)
+
+
+def lbm_set_pdfs_device(ctx: Ctx, f):
+    """Enqueues setting the state from the CUDA float64 tensor f (19 N)."""
+    _check(lib().lbm_set_pdfs_device(ctx.ptr, _ptr(_device_pdfs(ctx, f))), ctx)
 
 
 def lbm_init_equilibrium(ctx: Ctx, rho, u):

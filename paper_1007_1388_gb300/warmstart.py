@@ -20,9 +20,11 @@ divided by the force F_k and by a velocity scale s_u (and s_rho = s_u / 3 for
 the density): the mean fluid velocity per unit force over the first solved
 chunk, from the library's FP64 per-instance momentum sums, which makes the
 targets of order one.  The network's force input is F_k / F_REF.  A
-prediction is smoothed (unet_smooth_fields) before it becomes the initial
-equilibrium: its short-wavelength error slows the solver more than its
-smooth error.
+prediction is smoothed once (unet_smooth_fields) before it becomes the
+initial equilibrium: its short-wavelength error slows the solver more than
+its smooth error.  Measured on held-out 32^3 and 64^3 channels, one pass and
+a plain equilibrium start need the fewest steps; more passes, or a consistent
+start (lbm_init_consistent_device, whose relaxation steps count), need more.
 """
 from __future__ import annotations
 
@@ -39,7 +41,7 @@ RHO0 = 1.0
 F_REF = 5e-6
 
 
-SMOOTH_PASSES = 4
+SMOOTH_PASSES = 1
 
 
 def mean_velocity_per_force(ctx, forces):
@@ -58,10 +60,7 @@ def solve(flags, forces, n: int, tol: float = 1e-6, check_every: int = 50, max_s
     steps are counted).  Returns (ctx, steps per instance, residuals, seconds)."""
     import torch
 
-    K = len(flags)
-    p = L.make_params(storage=storage, storage_scale=256.0 if storage == L.LBM_F16S else 1.0, **W.channel_bc())
-    ctx = L.lbm_batch_create([(n, n, n)] * K, [TAU] * K, [np.asarray(f, np.uint8) for f in flags], p)
-    L.lbm_set_forces(ctx, np.stack([np.asarray(forces, np.float64), np.zeros(K), np.zeros(K)], axis=1))
+    ctx = batch_context(flags, forces, n, storage)
     t0 = time.perf_counter()
     if init is not None:
         torch.cuda.synchronize()
@@ -75,6 +74,51 @@ def solve(flags, forces, n: int, tol: float = 1e-6, check_every: int = 50, max_s
     if init is not None and consistent > 0:
         steps = np.where(steps >= 0, steps + consistent, steps)
     return ctx, steps, res, time.perf_counter() - t0
+
+
+def batch_context(flags, forces, n: int, storage: int = L.LBM_F32):
+    """One batch context of len(flags) n^3 channels with per-instance forces."""
+    K = len(flags)
+    p = L.make_params(storage=storage, storage_scale=256.0 if storage == L.LBM_F16S else 1.0, **W.channel_bc())
+    ctx = L.lbm_batch_create([(n, n, n)] * K, [TAU] * K, [np.asarray(f, np.uint8) for f in flags], p)
+    L.lbm_set_forces(ctx, np.stack([np.asarray(forces, np.float64), np.zeros(K), np.zeros(K)], axis=1))
+    return ctx
+
+
+def solve_handover(flags, forces, n: int, tol: float = 1e-6, switch_tol: float = 1e-5, check_every: int = 50,
+                   max_steps_16: int = 20_000, max_steps: int = 200_000, init=None):
+    """Shifted-FP16 storage until each instance's residual is below
+    switch_tol, then the exact state handed over to FP32 storage
+    (lbm_get_pdfs_device / lbm_set_pdfs_device) and iterated to tol.  FP16
+    storage follows the FP32 residual down to ~1e-5 and stalls near 2e-6 (its
+    rounding noise), so the hand-over keeps FP16's bandwidth for most of the
+    steps and FP32's accuracy for the result.  init as in solve (equilibrium
+    start).  Both contexts are created before the clock starts.  Returns
+    (FP32 ctx, total steps per instance, 16-bit steps, residuals, seconds)."""
+    import torch
+
+    K, V = len(flags), n ** 3
+    c16 = batch_context(flags, forces, n, L.LBM_F16S)
+    c32 = batch_context(flags, forces, n, L.LBM_F32)
+    f = torch.empty(19 * K * V, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if init is not None:
+        L.lbm_init_equilibrium_device(c16, init[0], init[1])
+    L.lbm_synchronize(c16)
+    s16, _ = L.lbm_run_to_residual_each(c16, switch_tol, check_every, max_steps_16, interval=True)
+    s16 = np.where(s16 >= 0, s16, max_steps_16)
+    L.lbm_get_pdfs_device(c16, f)
+    L.lbm_synchronize(c16)
+    L.lbm_set_pdfs_device(c32, f)
+    L.lbm_synchronize(c32)
+    s32, res = L.lbm_run_to_residual_each(c32, tol, check_every, max_steps, interval=True)
+    L.lbm_synchronize(c32)
+    sec = time.perf_counter() - t0
+    c16.destroy()
+    del f
+    steps = np.where(s32 >= 0, s16 + s32, -1)
+    return c32, steps, s16, res, sec
 
 
 def fields(ctx, K: int, n: int):
