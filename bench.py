@@ -252,10 +252,12 @@ def run_gpu(args):
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(dev) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")  # a range for profilers (ncu --nvtx)
         e0.record(stream)
         L.lbm_step(ctx, args.steps)
         e1.record(stream)
         barrier()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     prof = L.lbm_profile_read(ctx)
     L.lbm_profile_enable(ctx, False)
@@ -606,7 +608,9 @@ def _time_to_residual(args, L, W, torch, log=None):
             log(f"time to residual: {r}")
         return r
 
+    torch.cuda.nvtx.range_push("ttr_f32_batched")  # a range for profilers (ncu --nvtx)
     ctx, st, _, sec = WS.solve(flags, forces, n, tol, every)
+    torch.cuda.nvtx.range_pop()
     _, u_ref = WS.fields(ctx, K, n)
     ctx.destroy()
     out["f32_batched"] = row(st, sec)
