@@ -925,12 +925,12 @@ int lbm_run_to_residual_each(lbm_ctx *c, double tol, int check_every, int interv
             }
         }
         if (rc) break;
-        if (changed && remaining > 0 && (rc = set_sweep(c, c->sw_tile, c->flat, c->grid))) break;
+        if (changed && remaining > 0 && (rc = set_sweep(c, c->sw_tile, c->flat, c->grid, c->pair))) break;
     }
     for (int k = 0; k < K; ++k)
         if (steps[k] < 0 && res) res[k] = r[size_t(k)];
     c->active.clear();
-    const int rc2 = set_sweep(c, c->sw_tile, c->flat, c->grid);
+    const int rc2 = set_sweep(c, c->sw_tile, c->flat, c->grid, c->pair);
     return rc ? rc : rc2;
 }
 

@@ -204,7 +204,7 @@ template <typename T>
 std::vector<char> make_consts(const lbm_ctx *c);
 void invalidate_graphs(lbm_ctx *c);
 int set_tiles(lbm_ctx *c, const int t[3]);
-int set_sweep(lbm_ctx *c, const int t[3], int flat, int grid, int pair = 0);
+int set_sweep(lbm_ctx *c, const int t[3], int flat, int grid, int pair);
 bool tma_applicable(const lbm_ctx *c);
 int setup_tma(lbm_ctx *c);
 int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst);
