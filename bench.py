@@ -409,7 +409,10 @@ BATCH_FORCE = 1e-5
 def _batch_variants(args, L, W, barrier, torch):
     """Batched launch over 256 uneven instances (one sweep launch per step, CUDA
     graph, autotuned tiling) against the same instances as 256 separate
-    contexts on concurrent streams, FP32 and shifted-FP16 storage."""
+    contexts on concurrent streams, FP32 and shifted-FP16 storage; and the
+    time to residual 1e-6 of every instance, batched against separate."""
+    import numpy as np
+
     inst = W.batch_instances(seed=1234, n=args.batch_instances)
     dims = [d for d, _, _ in inst]
     taus = [t for _, t, _ in inst]
@@ -447,6 +450,25 @@ def _batch_variants(args, L, W, barrier, torch):
         res["launches_per_step"] = (pr.sweep_launches + pr.exchange_launches) / 20
         ctx.destroy()
         out[name] = res
+        if name == "f32" and not args.skip_ttr and not args.batch_no_separate:
+            # time to residual 1e-6 (change per step over 50-step checks) of every
+            # instance from rest: one batch context against one context per instance
+            tt = {"tol": 1e-6, "check_every": 50, "max_steps": 30000}
+            ctx = L.lbm_batch_create(dims, taus, flags, p)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, _ = L.lbm_run_to_residual_each(ctx, 1e-6, 50, 30000, interval=True)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            ctx.destroy()
+            ok = st[st >= 0]
+            tt["batched"] = {"wall_s": sec, "steps_mean": float(ok.mean()) if ok.size else None,
+                             "steps_max": int(ok.max()) if ok.size else None, "unconverged": int((st < 0).sum())}
+            ctxs = [L.lbm_create(d, d, t, f, p) for d, t, f in inst]
+            st2, sec2 = _solve_contexts(L, ctxs, 1e-6, 50, 30000)
+            tt["separate_contexts"] = {"wall_s": sec2, "steps_equal": bool(np.array_equal(st, st2))}
+            tt["batched_over_separate"] = sec2 / sec
+            res["time_to_residual"] = tt
         if args.batch_no_separate:
             continue
         # the same instances, one context (and stream) each
@@ -541,12 +563,19 @@ def _solve_separate(L, W, WS, flags, forces, n, tol, every, max_steps):
     """The same channels as one context each (own stream), stepped
     interleaved: every live context takes a velocity snapshot and `every`
     steps, then each is checked.  Returns (steps per instance, seconds)."""
+    ctxs = [L.lbm_create((n, n, n), (n, n, n), WS.TAU, f, L.make_params(force=(F, 0, 0), **W.channel_bc()))
+            for f, F in zip(flags, forces)]
+    return _solve_contexts(L, ctxs, tol, every, max_steps)
+
+
+def _solve_contexts(L, ctxs, tol, every, max_steps):
+    """Steps single-instance contexts (own streams) interleaved until each
+    one's change per step over `every` steps is below tol; destroys them.
+    Returns (steps per context, -1 where not reached; seconds)."""
     import numpy as np
     import torch
 
-    K = len(flags)
-    ctxs = [L.lbm_create((n, n, n), (n, n, n), WS.TAU, f, L.make_params(force=(F, 0, 0), **W.channel_bc()))
-            for f, F in zip(flags, forces)]
+    K = len(ctxs)
     steps = np.full(K, -1, np.int64)
     live, done = list(range(K)), 0
     torch.cuda.synchronize()
