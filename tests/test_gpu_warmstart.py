@@ -71,14 +71,14 @@ def test_run_to_residual_each_freezes_exactly(env):
     p = L.make_params(**W.channel_bc())
     ctx = L.lbm_batch_create([(n, n, n)] * 4, [0.8] * 4, [f for f, _ in samples], p)
     L.lbm_set_forces(ctx, [[F, 0, 0] for F in forces])
-    cfg = L.lbm_get_sweep_config(ctx)
-    assert cfg[0] == L.SWEEP_RUNS2  # two cells per thread (even Block widths, not a multiple of 64)
+    cfg = (L.SWEEP_RUNS2, 128, 1, 1, 0, 4, 8, 1)  # two cells per thread, link masks
+    L.lbm_set_sweep_config(ctx, cfg)
     steps, res = L.lbm_run_to_residual_each(ctx, tol, every, 40000, interval=True)
     assert np.all(steps > 0) and np.all(steps % every == 0) and np.all(res < tol), (steps, res)
     fb = L.lbm_get_pdfs(ctx)
     # the context sweeps every instance again afterwards, with the same sweep configuration
     assert L.lbm_get_info(ctx).tiles > 0
-    assert L.lbm_get_sweep_config(ctx) == cfg
+    assert tuple(L.lbm_get_sweep_config(ctx)) == cfg
     ctx.destroy()
     V = n ** 3
     for k, ((fl, F), s) in enumerate(zip(samples, steps)):
