@@ -174,3 +174,33 @@ def test_residual_sequence_follows_oracle(L):
             break
     assert ref < 1e-6
     c.destroy()
+
+
+def test_stopping_step_at_the_warm_start_size(L):
+    """One 64^3 warm-start channel (seed 10000, the first held-out seed of the
+    time-to-residual benchmark; porosity and force drawn from its seed): the
+    step at which the batched solver's interval residual (50-step checks)
+    first falls below 1e-6 equals the oracle's, or lies one check from it
+    where the oracle's residual sits at the tolerance."""
+    tol, every, n = 1e-6, 50, 64
+    fl, F = W.channel_sample(10000, n)
+    ctx = L.lbm_batch_create([(n, n, n)], [0.8], [fl], L.make_params(**W.channel_bc()))
+    L.lbm_set_forces(ctx, [[F, 0.0, 0.0]])
+    steps, res = L.lbm_run_to_residual_each(ctx, tol, every, 20000, interval=True)
+    ctx.destroy()
+    p = _problem((n, n, n), 0.8, fl, F)
+    f = oracle.zeros(p)
+    seq, s_o = [], -1
+    for c in range(1, 20000 // every + 1):
+        g = oracle.run(p, f, every)
+        seq.append(oracle.interval_residual(p, f, g, every))
+        f = g
+        if seq[-1] < tol:
+            s_o = c * every
+            break
+    print(f"64^3 channel: GPU stops at {steps[0]} (r = {res[0]:.4e}), oracle at {s_o} (r = {seq[-1]:.4e})")
+    assert s_o > 0 and steps[0] > 0
+    if steps[0] != s_o:
+        assert abs(int(steps[0]) - s_o) == every
+        c = min(int(steps[0]), s_o) // every - 1
+        assert abs(seq[c] - tol) <= bound_trajectory(tol, every), seq[c]
