@@ -400,7 +400,10 @@ int lbm_autotune(lbm_ctx *ctx, const char *cache_path, int best[3]);
  * and 2 with two neighbouring cells per thread (tx threads cover 2 tx cells;
  * even Block widths, FP32 / F16S / BF16S storage); grid = CTAs of a
  * persistent launch (0 = one per work item); minb = 3 or 4 resident CTAs per
- * SM the register budget allows (FP64 storage always uses 2); mask = 1 treats
+ * SM the register budget allows (FP64 storage always uses 2), or 5 (48
+ * registers) for the one-cell register sweep (kinds 0 and 2) of two-array
+ * Block layouts, whose Patches with pressure boundaries or curved walls run
+ * the budget-4 kernels instead; mask = 1 treats
  * near-wall cells through precomputed link masks under a warp vote.  Every
  * configuration gives bitwise identical results.  In-place streaming takes
  * kinds 0, 2, 3 and 4 with mask 0 (its tuning saves and restores the state

@@ -661,6 +661,7 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
     if ((rc = set_tiles(c, td))) return rc;
     int t[3] = {p.tile[0], p.tile[1], p.tile[2]};
     int flat = 0, pair = 0;
+    bool budget5 = false;
     if (t[0] <= 0 || t[1] <= 0 || t[2] <= 0) {
         for (int a = 0; a < 3; ++a) t[a] = td[a];
         // Two cells per thread wherever the Block widths are even (FP32 and
@@ -682,6 +683,12 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
             if (!w32) flat = 256;
         } else if (porous) {
             flat = 128;
+            // FP32 PDFs leave the one-cell sweep room for a 48-register budget
+            // (five 256-thread CTAs per SM): measured 0.415 against 0.439 ms per
+            // sweep on 48 sphere-packed 64^3 channels, 1.65 against 1.69 ms on
+            // 256 of them; 16-bit storage needs its conversion registers and
+            // stays at budget 4 (0.445 against 0.363 ms)
+            budget5 = c->storage == LBM_F32 && !c->sparse;
         } else if (even && w64) {
             pair = 1;
             t[0] = 32;
@@ -710,6 +717,8 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
         return fail(c, LBM_EINVAL, "the TMA sweep needs one Patch of equal Blocks 32, 64 or 128 "
                     "cells wide with rows divisible by 256/width, and F32/F16S/BF16S storage");
     }
+
+    if (budget5 && c->kernel == LBM_KERNEL_REGISTER) c->minb = 5;
 
     // in place: the rest state's pressure links
     CK(enqueue_aa_prepare(c), "prepare pressure links");

@@ -59,7 +59,10 @@ int check_cfg(lbm_ctx *c, const int *cd)
         return fail(c, LBM_EINVAL, "sweep config: tile %dx%dx%d", cd[1], cd[2], cd[3]);
     if (cd[0] == 1 && (cd[6] <= 0 || cd[6] > 1024)) return fail(c, LBM_EINVAL, "sweep config: zchunk %d", cd[6]);
     if (cd[4] < 0) return fail(c, LBM_EINVAL, "sweep config: grid %d", cd[4]);
-    if (cd[5] != 3 && cd[5] != 4) return fail(c, LBM_EINVAL, "sweep config: minb %d (3 or 4)", cd[5]);
+    if (cd[5] != 3 && cd[5] != 4 && cd[5] != 5) return fail(c, LBM_EINVAL, "sweep config: minb %d (3, 4 or 5)", cd[5]);
+    if (cd[5] == 5 && ((cd[0] != 0 && cd[0] != 2) || c->aa || c->sparse || c->storage == LBM_F64))
+        return fail(c, LBM_EINVAL, "sweep config: minb 5 applies to the one-cell register sweep (kinds 0 and 2) "
+                    "of two-array Block layouts with FP32 / F16S / BF16S storage");
     if (cd[7] != 0 && cd[7] != 1) return fail(c, LBM_EINVAL, "sweep config: mask %d", cd[7]);
     return LBM_OK;
 }
@@ -159,7 +162,7 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
                 for (int m : {0, 4, 8, 16}) cand.push_back({0, st[0], st[1], st[2], m * sms, mb, zc0, 0});
         }
         if (tma_ok)
-            for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, st[0], st[1], st[2], 0, c->minb, zc, m0});
+            for (int zc : {2, 4, 8, 16, 32}) cand.push_back({1, st[0], st[1], st[2], 0, std::min(c->minb, 4), zc, m0});
         for (int mb : {3, 4}) {
             if (c->sparse) break;
             for (int tx : {32, 64, 128, 256}) {
@@ -170,6 +173,11 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
                 }
             }
             for (int th : {128, 256}) cand.push_back({2, th, 1, 1, 0, mb, zc0, m0});
+            if (mb == 4 && !c->aa && c->storage != LBM_F64) {  // 48 registers, one cell per thread
+                for (int th : {128, 256}) cand.push_back({2, th, 1, 1, 0, 5, zc0, m0});
+                for (int tx : {32, 64})
+                    if (tx <= std::max(32, round_up(maxnx, 32))) cand.push_back({0, tx, 128 / tx, 2, 0, 5, zc0, m0});
+            }
             if (pair_ok) {
                 // two cells per thread: row tiles of 2 tx cells, runs of 2 th cells
                 for (int tx : {32, 64}) {
@@ -184,7 +192,9 @@ int lbm_autotune(lbm_ctx *c, const char *cache_path, int best_out[3])
         }
         // persistent grids over the default work list
         for (int m : {4, 8, 16})
-            if (!c->sparse) cand.push_back({kind0 == 1 ? 0 : kind0, st[0], st[1], st[2], m * sms, c->minb, zc0, m0});
+            if (!c->sparse)
+                cand.push_back({kind0 == 1 ? 0 : kind0, st[0], st[1], st[2], m * sms,
+                                kind0 == 0 || kind0 == 2 ? c->minb : std::min(c->minb, 4), zc0, m0});
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "event");
         CK(cudaEventCreate(&e1), "event");

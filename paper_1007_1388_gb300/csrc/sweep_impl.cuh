@@ -199,6 +199,18 @@ void launch_sweep_minb(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s
         launch_sweep_unif<ST, MINB, false>(a, grid, block, s);
 }
 
+// Register budget 5 (48 registers, five 256-thread CTAs per SM): only the
+// kernels without pressure boundaries or curved walls are built with it; a
+// Patch that has either runs the budget-4 kernels.
+template <int ST, bool UNIF>
+void launch_sweep_minb5(const SweepArgs &a, dim3 grid, dim3 block, cudaStream_t s)
+{
+    if (a.mask)
+        launch_sweep_pres<ST, 5, UNIF, true, 0>(a, grid, block, s);
+    else
+        launch_sweep_pres<ST, 5, UNIF, false, 0>(a, grid, block, s);
+}
+
 template <int ST>
 cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
 {
@@ -212,10 +224,16 @@ cudaError_t launch_sweep_st(const SweepArgs &a, cudaStream_t s)
     if constexpr (ST == 3) {  // FP64 arithmetic needs the larger register budget
         launch_sweep_minb<ST, 2>(a, grid, block, s);
     } else {
-        if (a.minb == 4)
+        if (a.minb == 5 && (a.pres & 3) == 0) {
+            if (a.unif)
+                launch_sweep_minb5<ST, true>(a, grid, block, s);
+            else
+                launch_sweep_minb5<ST, false>(a, grid, block, s);
+        } else if (a.minb >= 4) {
             launch_sweep_minb<ST, 4>(a, grid, block, s);
-        else
+        } else {
             launch_sweep_minb<ST, 3>(a, grid, block, s);
+        }
     }
     return cudaGetLastError();
 }

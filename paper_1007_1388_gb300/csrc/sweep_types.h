@@ -142,7 +142,7 @@ struct SweepArgs {
     int forced;               // any instance has a nonzero force
     int storage;              // LBM_F32 .. LBM_F64
     int grid;                 // CTAs to launch (<= ntiles; persistent loop when smaller)
-    int minb;                 // register budget: 3 or 4 resident 256-thread CTAs per SM
+    int minb;                 // register budget: 3, 4 or 5 resident 256-thread CTAs per SM
     int unif;                 // 1: a single instance, whose constants are kf (FP32
                               // arithmetic) or kd (FP64) and reach the kernel as parameters
     CollideConsts<float> kf;

@@ -169,7 +169,9 @@ def test_sweep_variants_bitwise_with_curved_walls(L, storage):
     R, U, R2, U2 = L.SWEEP_ROWS, L.SWEEP_RUNS, L.SWEEP_ROWS2, L.SWEEP_RUNS2
     configs = [(R, 32, 4, 1, 0, 4, 8, 0), (R, 32, 8, 2, 0, 3, 8, 1), (U, 256, 1, 1, 0, 4, 8, 0),
                (U, 128, 1, 1, 304, 3, 8, 1), (R2, 32, 4, 1, 0, 3, 8, 0), (R2, 32, 8, 2, 0, 4, 8, 1),
-               (U2, 128, 1, 1, 0, 3, 8, 1), (U2, 256, 1, 1, 304, 4, 8, 0)]
+               (U2, 128, 1, 1, 0, 3, 8, 1), (U2, 256, 1, 1, 304, 4, 8, 0),
+               # the 48-register budget falls back to the budget-4 kernels here
+               (U, 128, 1, 1, 0, 5, 8, 1)]
     outs = []
     for cfg in configs:
         ctx = L.lbm_create(dims, bd, 0.7, flags, L.make_params(kernel=L.LBM_KERNEL_REGISTER, **kw))

@@ -93,13 +93,14 @@ def test_tma_sweep_bounded_wait_reports_timeout(L):
 
 # -------------------------------------------------- register sweep variants
 def _configs(L, bx):
-    """Row tiles, runs of consecutive cells, persistent grids, both register
-    budgets and both near-wall strategies."""
+    """Row tiles, runs of consecutive cells, persistent grids, the register
+    budgets (64, 80 and, one cell per thread, 48 registers) and both near-wall
+    strategies."""
     R, U, R2, U2 = L.SWEEP_ROWS, L.SWEEP_RUNS, L.SWEEP_ROWS2, L.SWEEP_RUNS2
     out = [(R, 32, 4, 1, 0, 4, 8, 0), (R, 32, 8, 2, 0, 3, 8, 1), (U, 256, 1, 1, 0, 4, 8, 0),
            (U, 128, 1, 1, 0, 3, 8, 1), (U, 256, 1, 1, 304, 4, 8, 1), (R, 32, 4, 2, 152, 3, 8, 0),
            (R2, 32, 4, 1, 0, 3, 8, 0), (R2, 32, 8, 2, 0, 4, 8, 1), (U2, 128, 1, 1, 0, 3, 8, 1),
-           (U2, 256, 1, 1, 304, 4, 8, 0)]
+           (U2, 256, 1, 1, 304, 4, 8, 0), (U, 128, 1, 1, 0, 5, 8, 1), (R, 32, 4, 2, 0, 5, 8, 0)]
     if bx >= 64:
         out.append((R, 64, 4, 4, 0, 4, 8, 1))
     return out
@@ -130,6 +131,8 @@ def test_sweep_variants_bitwise_single_patch(L, storage):
         # the default for even Blocks that are not a multiple of 64 wide: runs, two cells per
         # thread; one cell per thread where near-wall cells are many (link masks)
         assert info.flat == 128 and info.pair == (0 if info.mask else 1)
+        # FP32 one-cell runs take the 48-register budget, 16-bit storage 64 registers
+        assert L.lbm_get_sweep_config(ctx)[5] == (5 if info.mask and storage == 0 else 4)
         ref = _run_cfg(L, ctx, f0, 17, None)
         for cfg in _configs(L, bd[0]):
             got = _run_cfg(L, ctx, f0, 17, cfg)
@@ -166,7 +169,8 @@ def test_sweep_config_validation(L):
     ctx = L.lbm_create((40, 16, 8), (40, 16, 8), 0.7, None, L.make_params())
     before = L.lbm_get_sweep_config(ctx)
     for bad in [(5, 32, 4, 1, 0, 4, 8, 0), (0, 48, 4, 1, 0, 4, 8, 0), (0, 32, 16, 1, 0, 4, 8, 0),
-                (2, 100, 1, 1, 0, 4, 8, 0), (0, 32, 4, 1, -1, 4, 8, 0), (0, 32, 4, 1, 0, 5, 8, 0),
+                (2, 100, 1, 1, 0, 4, 8, 0), (0, 32, 4, 1, -1, 4, 8, 0), (0, 32, 4, 1, 0, 6, 8, 0),
+                (3, 32, 4, 1, 0, 5, 8, 0),
                 (0, 32, 4, 1, 0, 4, 8, 2), (1, 32, 4, 1, 0, 4, 8, 0)]:
         with pytest.raises(L.LBMError):
             L.lbm_set_sweep_config(ctx, bad)
