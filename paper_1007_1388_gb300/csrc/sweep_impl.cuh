@@ -7,8 +7,15 @@
 // cell it applies half-way bounce-back (Sec. 2.1) with the momentum-
 // consistent sign, g_q = src_opp(q)[x] + s 6 w_q rho0 (e_q . u_wall).  It
 // then collides (Eq. (1), BGK or TRT, Guo forcing; collide.cuh) and stores
-// dst_q[x].  Solid cells are skipped.  Across x faces the pull reads the
-// neighbouring Block's boundary column directly; the y/z ghost rows were
+// dst_q[x].  Solid cells are not updated.  With FP32 storage those that share
+// a 32-byte sector of a PDF plane with fluid cells (F_FILL) store the rest
+// state, 0, and the last cells of a row zero its padding (F_PAD), so that every
+// sector the sweep writes is written whole: a partly written sector makes the
+// memory system read the old sector first (measured in sphere packings as
+// DRAM reads well above the pulled bytes; a solid cell's PDFs are never read,
+// and the interface reports them as 0).  The 16-bit sweeps, bound by
+// instruction latency rather than bytes, ran slower with these stores.  Across x faces the
+// pull reads the neighbouring Block's boundary column directly; the y/z ghost rows were
 // filled by the exchange, so every Block runs the same instruction sequence
 // (multi-Block runs are bitwise equal to single-Block runs).
 //
@@ -82,9 +89,18 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         // Otherwise each lane branches on its own near-wall bit (no cost where
         // near-wall cells fill whole warps, as along plane walls).
         const bool take_mask = MASK ? __any_sync(0xffffffffu, near) : near;
-        if (flag & F_KIND) continue;  // solid cells (and lanes outside the Block) are not updated
+        // solid cells (and lanes outside the Block) are not updated, but (FP32,
+        // Patches without pressure boundaries or curved walls, whose kernels
+        // keep their registers for those) cells sharing a stored sector with
+        // fluid cells join the warp's stores with the rest state
+        constexpr bool FILL = ST == 0 && XBC == 0;
+        const bool fill = FILL && (flag & F_FILL);
+        if ((flag & F_KIND) && !fill) continue;
         T f[Q];
-        if (!take_mask) {
+        if (fill) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = T(0);
+        } else if (!take_mask) {
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
@@ -141,12 +157,19 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                              static_cast<const T *>(a.curv_q) + 18ll * __ldg(a.curv_idx + b.cell_base + cf),
                              [&](int p) { return Tr::ld(src + (p * G + c)); });
         }
-        if (UNIF)
-            collide_v<COLL, FORCE>(f, KR);
-        else
-            collide_v<COLL, FORCE>(f, KP);
+        if (!fill) {
+            if (UNIF)
+                collide_v<COLL, FORCE>(f, KR);
+            else
+                collide_v<COLL, FORCE>(f, KP);
+        }
 #pragma unroll
         for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c), f[q]);
+        if (FILL && (flag & F_PAD)) {  // padding element nx + j of the row, j = nx - 1 - x
+            const int d = 2 * (flag >> F_PAD_SHIFT) + 1;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) Tr::st(dst + (q * G + c + d), T(0));
+        }
     }
 }
 
