@@ -102,7 +102,14 @@ SweepArgs sweep_args(const lbm_ctx *c, int from)
     a.storage = c->storage;
     a.grid = c->grid;
     a.minb = c->minb;
-    a.unif = c->ninst == 1 ? 1 : 0;
+    // A single instance's collision constants reach the kernel as parameters,
+    // except in the one-cell 16-bit sweep with link masks, which measured
+    // faster reading them from global memory (one sphere-packed 256x256x128
+    // channel, F16S: 0.244 against 0.304 ms per sweep; FP32 and the two-cell
+    // sweeps are faster with parameters)
+    const bool narrow = c->storage == LBM_F16S || c->storage == LBM_BF16S;
+    const bool onecell = c->kernel == LBM_KERNEL_REGISTER && !c->aa && !c->sparse && !c->pair;
+    a.unif = c->ninst == 1 && !(narrow && onecell && c->mask) ? 1 : 0;
     {
         const double sc = (c->storage == LBM_F16S || c->storage == LBM_BF16S) ? c->p.storage_scale : 1.0;
         const double rho_b = c->p.rho_b > 0.0 ? c->p.rho_b : c->p.rho0;

@@ -56,6 +56,38 @@ template <> struct Pair<2> {
     }
 };
 
+// The 19 pulled values of one cell from its link mask lm (bit q: the pull
+// source x - e_q is a wall, so g_q comes from half-way bounce-back; lm = 0
+// gives the plain pull).
+template <int ST, bool UNIF, int XBC>
+__device__ __forceinline__ void pull_mask(float (&v)[Q], uint32_t lm, const SweepArgs &a,
+                                          const CollideConsts<float> *cc, const typename Traits<ST>::S *src,
+                                          const typename Traits<ST>::S *srcm, const typename Traits<ST>::S *srcp,
+                                          const uint8_t *fl, int c, int cf, int px, int pxy, int pxf, int pxyf, int G)
+{
+    using Tr = Traits<ST>;
+    using S = typename Tr::S;
+    const bool mv = (lm & ((XBC & 1) ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
+    PresBC<float> pbc{};
+    if ((XBC & 1) && (lm & L_PRESSURE)) pbc = pres_cell<ST, UNIF, float>(a.kf, cc, a.pbf, src, c, G);
+    v[0] = Tr::ld(src + c);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const bool bq = (lm >> q) & 1u;
+        const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
+        const S *pa = bq ? src + (opp(q) * G + c) : s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy));
+        float w = Tr::ld(pa);
+        if (mv && bq) {
+            const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
+            if ((nf & F_KIND) == F_MOVING)
+                w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
+            else if ((XBC & 1) && (nf & F_KIND) == F_PRESSURE)
+                w = pres_pull(q, pbc, w);
+        }
+        v[q] = w;
+    }
+}
+
 // The 19 pulled values of one cell next to a wall (half-way bounce-back),
 // from its link mask (MASK) or its neighbours' flags.
 template <int ST, bool MASK, bool UNIF, int XBC>
@@ -67,26 +99,8 @@ __device__ __forceinline__ void pull_near(float (&v)[Q], const SweepArgs &a, con
     using Tr = Traits<ST>;
     using S = typename Tr::S;
     if (MASK) {
-        const uint32_t lm = __ldg(a.links + b.cell_base + cf);
-        const bool mv = (lm & ((XBC & 1) ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
-        PresBC<float> pbc{};
-        if ((XBC & 1) && (lm & L_PRESSURE)) pbc = pres_cell<ST, UNIF, float>(a.kf, cc, a.pbf, src, c, G);
-        v[0] = Tr::ld(src + c);
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-            const bool bq = (lm >> q) & 1u;
-            const S *s = ex(q) > 0 ? srcm : (ex(q) < 0 ? srcp : src);
-            const S *pa = bq ? src + (opp(q) * G + c) : s + (q * G + c - (ex(q) + ey(q) * px + ez(q) * pxy));
-            float w = Tr::ld(pa);
-            if (mv && bq) {
-                const uint8_t nf = fl[cf - (ex(q) + ey(q) * pxf + ez(q) * pxyf)];
-                if ((nf & F_KIND) == F_MOVING)
-                    w = vadd(w, UNIF ? a.kf.bbw[q] : __ldg(&cc->bbw[q]));
-                else if ((XBC & 1) && (nf & F_KIND) == F_PRESSURE)
-                    w = pres_pull(q, pbc, w);
-            }
-            v[q] = w;
-        }
+        pull_mask<ST, UNIF, XBC>(v, __ldg(a.links + b.cell_base + cf), a, cc, src, srcm, srcp, fl, c, cf, px, pxy,
+                                 pxf, pxyf, G);
     } else {
         PresBC<float> pbc{};
         if ((XBC & 1) && (__ldg(a.links + b.cell_base + cf) & L_PRESSURE))
@@ -194,6 +208,21 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
                 else
                     f[q] = f2_pack(Tr::ld(src + (a0 + 1)), Tr::ld(srcp1 + (a0 + 2)));
             }
+        } else if (MASK) {
+            // one path for the whole warp: each cell's link mask (0 without a
+            // wall neighbour) picks the pulled or the bounced PDF per direction,
+            // so that lanes whose cells differ do not run both pulls
+            float v0[Q], v1[Q];
+            const uint32_t lm0 = near0 ? __ldg(a.links + b.cell_base + cf) : 0u;
+            const uint32_t lm1 = near1 ? __ldg(a.links + b.cell_base + cf + 1) : 0u;
+            pull_mask<ST, UNIF, XBC>(v0, lm0, a, cc, src, srcm0, src, fl, c, cf, px, pxy, pxf, pxyf, G);
+            pull_mask<ST, UNIF, XBC>(v1, lm1, a, cc, src, src, srcp1, fl, c + 1, cf + 1, px, pxy, pxf, pxyf, G);
+            if (XBC & 2) {
+                if (near0) pull_curved<ST>(v0, a, b, src, c, cf, G);
+                if (near1) pull_curved<ST>(v1, a, b, src, c + 1, cf + 1, G);
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) f[q] = f2_pack(v0[q], v1[q]);
         } else {
             float v0[Q], v1[Q];
             const S *srcp0 = src, *srcm1 = src;  // the inner faces of the pair stay in the Block
