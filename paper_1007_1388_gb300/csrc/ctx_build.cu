@@ -360,6 +360,8 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                     b.ny = s.bdims[1];
                     b.nz = s.bdims[2];
                     b.px = round_up(b.nx, 32 / c->elem);
+                    div_magic(uint32_t(b.nx), &b.mnx, &b.snx);
+                    div_magic(uint32_t(b.ny), &b.mny, &b.sny);
                     b.xw_base[0] = b.xw_base[1] = -1;
                     b.pxf = round_up(OXF + b.nx + 1, 16);
                     b.py = b.ny + 2;

@@ -164,9 +164,9 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
         int x, y, z;  // x: the first (even) cell of the pair
         if (a.flat) {
             const int i = tile.x0 + 2 * int(threadIdx.x);
-            const int yz = i / nx;
+            const int yz = quot(i, b.mnx, b.snx);  // i / nx
             x = i - yz * nx;
-            z = yz / ny;
+            z = quot(yz, b.mny, b.sny);  // yz / ny
             y = yz - z * ny;
         } else {
             x = tile.x0 + 2 * int(threadIdx.x);

@@ -208,9 +208,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa_kernel(const __grid_consta
         int x, y, z;
         if (a.flat) {
             const int i = tile.x0 + int(threadIdx.x);
-            const int yz = i / nx;
+            const int yz = quot(i, b.mnx, b.snx);  // i / nx
             x = i - yz * nx;
-            z = yz / ny;
+            z = quot(yz, b.mny, b.sny);  // yz / ny
             y = yz - z * ny;
         } else {
             x = tile.x0 + int(threadIdx.x);
@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa2_kernel(const __grid_const
         int x, y, z;  // the first (even) cell of the pair; nx is even
         if (a.flat) {
             const int i = tile.x0 + 2 * int(threadIdx.x);
-            const int yz = i / nx;
+            const int yz = quot(i, b.mnx, b.snx);  // i / nx
             x = i - yz * nx;
-            z = yz / ny;
+            z = quot(yz, b.mny, b.sny);  // yz / ny
             y = yz - z * ny;
         } else {
             x = tile.x0 + 2 * int(threadIdx.x);

@@ -53,9 +53,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         if (a.flat) {
             // a run of consecutive cells of the Block, (z, y, x) order
             const int i = tile.x0 + int(threadIdx.x);
-            const int yz = i / nx;
+            const int yz = quot(i, b.mnx, b.snx);  // i / nx
             x = i - yz * nx;
-            z = yz / ny;
+            z = quot(yz, b.mny, b.sny);  // yz / ny
             y = yz - z * ny;
         } else {
             x = tile.x0 + int(threadIdx.x);

@@ -74,6 +74,9 @@ struct BlockGeom {
     long long out_base;   // first cell of the instance in the concatenated output
     int NX, NY, NZ;       // instance size
     int pad_;
+    // n / nx and n / ny for 0 <= n < 2^31 as (n * m) >> sh (div_magic, quot)
+    uint32_t mnx, mny;
+    int snx, sny;
     // in-place streaming: side storage of the slots of the cells just beyond
     // a wall -x / +x face (what the pull-and-push step streams into the wall,
     // and pressure nodes' prepared values); element offset in the PDF buffer
@@ -81,6 +84,23 @@ struct BlockGeom {
     // face has a neighbour Block (or two arrays are used)
     long long xw_base[2];
 };
+
+// Division by a run-time divisor d >= 1 as a multiply and a shift (the
+// multiply-shift method of Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994): with 2^s >= d and
+// m = ceil(2^(31+s) / d) < 2^32, floor(n m / 2^(31+s)) = floor(n / d) for every
+// 0 <= n < 2^31, because n m / 2^(31+s) exceeds n / d by less than 2^-s <= 1/d.
+inline void div_magic(uint32_t d, uint32_t *m, int *sh)
+{
+    int s = 0;
+    while ((1ull << s) < d) ++s;
+    *m = uint32_t(((1ull << (31 + s)) + d - 1) / d);
+    *sh = 31 + s;
+}
+__host__ __device__ __forceinline__ int quot(int n, uint32_t m, int sh)
+{
+    return int((unsigned long long)(unsigned)n * m >> sh);
+}
 
 // index 0..4 of direction q among the five with the same e_x (ascending q)
 __host__ __device__ constexpr int xdir_index(int q)
