@@ -192,6 +192,10 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
         const int c = (z + 1) * pxy + (y + 1) * px + x;
         const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
         const uint8_t fl0 = inside ? fl[cf] : uint8_t(F_NOSLIP), fl1 = inside ? fl[cf + 1] : uint8_t(F_NOSLIP);
+        // MASK: both link masks (0 without a wall neighbour; cf is even) are
+        // loaded beside the flags, so that the pulls wait for one round trip
+        uint2 lmask = make_uint2(0u, 0u);
+        if (MASK && inside) lmask = __ldg(reinterpret_cast<const uint2 *>(a.links + b.cell_base + cf));
         const bool solid0 = fl0 & F_KIND, solid1 = fl1 & F_KIND;
         const bool near0 = !solid0 && (fl0 & F_NEAR), near1 = !solid1 && (fl1 & F_NEAR);
         const bool take_near = MASK ? __any_sync(0xffffffffu, near0 || near1) : (near0 || near1);
@@ -213,8 +217,8 @@ __global__ void __launch_bounds__(256, MINB) sweep2_kernel(const __grid_constant
             // wall neighbour) picks the pulled or the bounced PDF per direction,
             // so that lanes whose cells differ do not run both pulls
             float v0[Q], v1[Q];
-            const uint32_t lm0 = near0 ? __ldg(a.links + b.cell_base + cf) : 0u;
-            const uint32_t lm1 = near1 ? __ldg(a.links + b.cell_base + cf + 1) : 0u;
+            const uint32_t lm0 = near0 ? lmask.x : 0u;
+            const uint32_t lm1 = near1 ? lmask.y : 0u;
             pull_mask<ST, UNIF, XBC>(v0, lm0, a, cc, src, srcm0, src, fl, c, cf, px, pxy, pxf, pxyf, G);
             pull_mask<ST, UNIF, XBC>(v1, lm1, a, cc, src, src, srcp1, fl, c + 1, cf + 1, px, pxy, pxf, pxyf, G);
             if (XBC & 2) {

@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         const int c = (z + 1) * pxy + (y + 1) * px + x;
         const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
         const uint8_t flag = inside ? fl[cf] : uint8_t(F_NOSLIP);
+        // MASK: the link mask (0 for cells without a wall neighbour) is loaded
+        // beside the flag, not after it, so that the pulls wait for one round
+        // trip to memory instead of two
+        const uint32_t lmask = MASK && inside ? __ldg(a.links + b.cell_base + cf) : 0u;
         const bool near = !(flag & F_KIND) && (flag & F_NEAR);
         // MASK: warps without a near-wall lane take the plain pull; the others
         // take one branch-free path in which each direction loads either the
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
                 }
             }
         } else {
-            const uint32_t lm = near ? __ldg(a.links + b.cell_base + cf) : 0u;
+            const uint32_t lm = near ? lmask : 0u;
             const bool mv = (lm & ((XBC & 1) ? (L_MOVING | L_PRESSURE) : L_MOVING)) != 0;
             PresBC<T> pbc{};
             if ((XBC & 1) && (lm & L_PRESSURE))
