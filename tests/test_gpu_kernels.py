@@ -204,3 +204,26 @@ def test_graph_direct_and_profiled_steps_agree(L):
         outs.append(L.lbm_get_pdfs(ctx))
         ctx.destroy()
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_two_cell_16bit_open_rows_bitwise(L, storage):
+    """16-bit storage without obstacles, where whole warps take the two-cell
+    sweep's vector path (one aligned pair load for the directions with
+    e_x = 0, two 2-byte loads for the others): equal to the one-cell sweep bit
+    for bit for row tiles narrower and wider than a warp, runs that wrap rows
+    inside a warp, Blocks across x faces (periodic and a wall), moving walls."""
+    R, U2, R2 = L.SWEEP_ROWS, L.SWEEP_RUNS2, L.SWEEP_ROWS2
+    rng = np.random.default_rng(90 + storage)
+    for dims, bd, periodic in [((128, 24, 20), (64, 12, 10), (1, 0, 1)), ((96, 16, 12), (48, 16, 6), (0, 0, 1)),
+                               ((40, 18, 14), (20, 9, 14), (1, 1, 0))]:
+        f0 = W.random_pdfs(rng, dims, 1e-2)
+        kw = dict(force=(2e-5, -1e-5, 1e-5), wall_u=(0.03, 0, 0.01), periodic=periodic,
+                  face_bc=(1, 1, 2, 1, 1, 1), storage=storage, storage_scale=(256.0 if storage == 1 else 1.0))
+        ctx = L.lbm_create(dims, bd, 0.7, None, L.make_params(**kw))
+        ref = _run_cfg(L, ctx, f0, 9, (R, 32, 4, 1, 0, 4, 8, 0))
+        for cfg in [(R2, 32, 4, 1, 0, 4, 8, 0), (R2, 32, 8, 2, 0, 3, 8, 0), (U2, 128, 1, 1, 0, 4, 8, 0),
+                    (U2, 256, 1, 1, 304, 3, 8, 0), (R2, 32, 2, 1, 0, 4, 8, 1), (U2, 64, 1, 1, 0, 4, 8, 1)]:
+            got = _run_cfg(L, ctx, f0, 9, cfg)
+            assert np.array_equal(got, ref), (dims, cfg, float(np.abs(got - ref).max()))
+        ctx.destroy()
