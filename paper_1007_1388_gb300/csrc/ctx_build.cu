@@ -420,12 +420,12 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                     ++near_cells;
                                 }
                             }
-                    // FP32: no-slip cells that share a 32-byte PDF sector with a
-                    // fluid cell store the rest state (0) in the one-cell sweep, and
-                    // the last px - nx cells of a row zero the row's padding, so that
-                    // every sector the sweep writes is complete (a partly written
-                    // sector costs the memory system a read of the old sector)
-                    if (c->storage == LBM_F32) {
+                    // FP32 and 16-bit: no-slip cells that share a 32-byte PDF sector
+                    // with a fluid cell store the rest state (0) in the one-cell sweep,
+                    // and (FP32) the last cells of a row zero its padding, so that every
+                    // sector the sweep writes is complete (a partly written sector
+                    // costs the memory system a read of the old sector)
+                    if (c->storage != LBM_F64) {
                         const int per = 32 / c->elem, k = b.px - b.nx;
                         for (int z = 0; z < b.nz; ++z)
                             for (int y = 0; y < b.ny; ++y) {
@@ -438,9 +438,10 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                     for (int x = x0; x < x1; ++x)
                                         if ((f[row + x] & F_KIND) == F_NOSLIP) f[row + x] |= F_FILL;
                                 }
-                                // padding element nx + j is zeroed by cell nx - 1 - j, when
-                                // all of those cells are stored
-                                bool tail = k > 0 && k <= b.nx;
+                                // FP32: padding element nx + j is zeroed by cell nx - 1 - j,
+                                // when all of those cells are stored (the 16-bit sweeps ran
+                                // slower with padding stores in their kernels)
+                                bool tail = c->storage == LBM_F32 && k > 0 && k <= b.nx;
                                 for (int x = b.nx - k; tail && x < b.nx; ++x)
                                     tail = (f[row + x] & F_KIND) == F_FLUID || (f[row + x] & F_FILL);
                                 if (tail)

@@ -7,14 +7,13 @@
 // cell it applies half-way bounce-back (Sec. 2.1) with the momentum-
 // consistent sign, g_q = src_opp(q)[x] + s 6 w_q rho0 (e_q . u_wall).  It
 // then collides (Eq. (1), BGK or TRT, Guo forcing; collide.cuh) and stores
-// dst_q[x].  Solid cells are not updated.  With FP32 storage those that share
-// a 32-byte sector of a PDF plane with fluid cells (F_FILL) store the rest
-// state, 0, and the last cells of a row zero its padding (F_PAD), so that every
-// sector the sweep writes is written whole: a partly written sector makes the
-// memory system read the old sector first (measured in sphere packings as
-// DRAM reads well above the pulled bytes; a solid cell's PDFs are never read,
-// and the interface reports them as 0).  The 16-bit sweeps, bound by
-// instruction latency rather than bytes, ran slower with these stores.  Across x faces the
+// dst_q[x].  Solid cells are not updated.  With FP32 and 16-bit storage those
+// that share a 32-byte sector of a PDF plane with fluid cells (F_FILL) store
+// the rest state, 0, and (FP32) the last cells of a row zero its padding
+// (F_PAD), so that every sector the sweep writes is written whole: a partly written sector
+// makes the memory system read the old sector first (measured in sphere
+// packings as DRAM reads well above the pulled bytes; a solid cell's PDFs are
+// never read, and the interface reports them as 0).  Across x faces the
 // pull reads the neighbouring Block's boundary column directly; the y/z ghost rows were
 // filled by the exchange, so every Block runs the same instruction sequence
 // (multi-Block runs are bitwise equal to single-Block runs).
@@ -93,11 +92,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const __grid_constant_
         // Otherwise each lane branches on its own near-wall bit (no cost where
         // near-wall cells fill whole warps, as along plane walls).
         const bool take_mask = MASK ? __any_sync(0xffffffffu, near) : near;
-        // solid cells (and lanes outside the Block) are not updated, but (FP32,
-        // Patches without pressure boundaries or curved walls, whose kernels
-        // keep their registers for those) cells sharing a stored sector with
-        // fluid cells join the warp's stores with the rest state
-        constexpr bool FILL = ST == 0 && XBC == 0;
+        // solid cells (and lanes outside the Block) are not updated, but (FP32
+        // and 16-bit, Patches without pressure boundaries or curved walls, whose
+        // kernels keep their registers for those) cells sharing a stored sector
+        // with fluid cells join the warp's stores with the rest state
+        constexpr bool FILL = ST <= 2 && XBC == 0;
         const bool fill = FILL && (flag & F_FILL);
         if ((flag & F_KIND) && !fill) continue;
         T f[Q];

@@ -29,7 +29,7 @@ enum : uint8_t {
     F_PRESSURE = 3,  // pressure boundary (anti-bounce-back to density rho_b)
     F_KIND = 3,   // mask of the kind bits
     F_NEAR = 4,   // fluid cell with at least one wall / solid neighbour
-    F_FILL = 8,   // FP32: interior no-slip cell sharing a 32-byte PDF sector with a fluid cell
+    F_FILL = 8,   // FP32/16-bit: interior no-slip cell sharing a 32-byte PDF sector with a fluid cell
     F_PAD = 16,   // FP32: cell nx - 1 - j of a row (j in the bits above) also zeroes padding element nx + j
 };
 constexpr int F_PAD_SHIFT = 5;  // j < 8: a row of 32-byte sectors has at most 7 FP32 padding elements
