@@ -240,9 +240,10 @@ def test_device_pdfs_hand_over_exactly(env):
 
 
 def test_f16s_hand_over_reaches_the_fp32_solution(env):
-    """Shifted-FP16 storage to residual 1e-5, then FP32 to 1e-6: every
-    instance converges, and the final velocity agrees with the FP32 solution
-    from rest within 1e-3 (relative L2; FP16 storage alone stalls near 2e-6)."""
+    """Shifted-FP16 storage to residual 1e-4 (the default hand-over), then
+    FP32 to 1e-6: every instance converges, and the final velocity agrees
+    with the FP32 solution from rest within 1e-3 (relative L2; FP16 storage
+    alone stalls near 2e-6)."""
     torch, L, _, WS, W = env
     n, tol = 24, 1e-6
     V = n ** 3
@@ -251,7 +252,7 @@ def test_f16s_hand_over_reaches_the_fp32_solution(env):
     forces = [F for _, F in samples]
     ctx_r, steps_r, _, _ = WS.solve(flags, forces, n, tol)
     _, u_r = WS.fields(ctx_r, len(flags), n)
-    ctx_h, steps_h, s16, _, _ = WS.solve_handover(flags, forces, n, tol, 1e-5)
+    ctx_h, steps_h, s16, _, _ = WS.solve_handover(flags, forces, n, tol)
     _, u_h = WS.fields(ctx_h, len(flags), n)
     print("steps from rest", steps_r.tolist(), "hand-over", steps_h.tolist(), "16-bit", s16.tolist())
     assert np.all(steps_h > 0) and np.all(s16 > 0) and np.all(s16 < steps_h)
