@@ -277,13 +277,6 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa2_kernel(const __grid_const
         const int pxf = b.pxf, pxyf = b.pxf * b.py;
         const int cf = (z + 1) * pxyf + (y + 1) * pxf + x + OXF;
         const uint8_t *fl = a.flags + b.cell_base;
-        const uint8_t fl0 = fl[cf], fl1 = fl[cf + 1];
-        if (MODE >= 2 || ((fl0 | fl1) & (F_KIND | F_NEAR))) {
-#pragma unroll 1
-            for (int k = 0; k < 2; ++k)  // one copy of the cell code
-                if (!((k ? fl1 : fl0) & F_KIND)) aa_cell<ST, COLL, FORCE, MODE, PRES>(a, b, x + k, y, z);
-            continue;
-        }
         const int px = b.px, pxy = px * b.py;
         const int G = int(b.G);
         const int c = (z + 1) * pxy + (y + 1) * px + x;
@@ -291,24 +284,38 @@ __global__ void __launch_bounds__(256, MINB) sweep_aa2_kernel(const __grid_const
         S *W = static_cast<S *>(a.dst) + b.pdf_base;
         // cell x reaches across the -x face at x = 0, cell x + 1 across the +x face at x + 1 = nx - 1
         const long long xm0 = x == 0 ? b.xm_off : 0ll, xp1 = x + 2 == nx ? b.xp_off : 0ll;
+        // modes 0 and 1: the pair's values are loaded before its flags arrive, so
+        // that the loads do not wait for them (every slot read is a stored slot
+        // of the Block or of its x neighbour); a pair that touches a wall or a
+        // solid cell drops them and goes through the cell code
         F2 f[Q];
         if (MODE == 0) {
 #pragma unroll
             for (int q = 0; q < Q; ++q) f[q] = aa_ld2<ST>(R + (q * G + c));
+        } else if (MODE == 1) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {  // pull from x - e_q: A[opp(q)][x - e_q]
+                const long long a0 = opp(q) * G + c - (ey(q) * px + ez(q) * pxy);
+                if (ex(q) == 0)
+                    f[q] = aa_ld2<ST>(R + a0);
+                else if (ex(q) > 0)
+                    f[q] = f2_pack(Tr::to_t(R[xm0 + a0 - 1]), Tr::to_t(R[a0]));
+                else
+                    f[q] = f2_pack(Tr::to_t(R[a0 + 1]), Tr::to_t(R[xp1 + a0 + 2]));
+            }
+        }
+        const uint8_t fl0 = fl[cf], fl1 = fl[cf + 1];
+        if (MODE >= 2 || ((fl0 | fl1) & (F_KIND | F_NEAR))) {
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k)  // one copy of the cell code
+                if (!((k ? fl1 : fl0) & F_KIND)) aa_cell<ST, COLL, FORCE, MODE, PRES>(a, b, x + k, y, z);
+            continue;
+        }
+        if (MODE == 0) {
             collide_v<COLL, FORCE>(f, KR);
 #pragma unroll
             for (int q = 0; q < Q; ++q) Pair<ST>::st2(W + (opp(q) * G + c), f[q]);
             continue;
-        }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {  // pull from x - e_q: A[opp(q)][x - e_q]
-            const long long a0 = opp(q) * G + c - (ey(q) * px + ez(q) * pxy);
-            if (ex(q) == 0)
-                f[q] = aa_ld2<ST>(R + a0);
-            else if (ex(q) > 0)
-                f[q] = f2_pack(Tr::to_t(R[xm0 + a0 - 1]), Tr::to_t(R[a0]));
-            else
-                f[q] = f2_pack(Tr::to_t(R[a0 + 1]), Tr::to_t(R[xp1 + a0 + 2]));
         }
         collide_v<COLL, FORCE>(f, KR);
 #pragma unroll
