@@ -4,6 +4,7 @@
 // place), the fluid-cell list's numbering and neighbour table, the sweep's
 // work lists and the TMA sweep's tensor maps.
 #include "ctx_internal.h"
+#include "sector_fill.h"
 
 using namespace lbm;
 
@@ -421,34 +422,14 @@ int build_context(lbm_ctx *c, const std::vector<InstSpec> &inst)
                                 }
                             }
                     // FP32 and 16-bit: no-slip cells that share a 32-byte PDF sector
-                    // with a fluid cell store the rest state (0) in the one-cell sweep,
-                    // and (FP32) the last cells of a row zero its padding, so that every
+                    // with a fluid cell store the rest state in the one-cell sweep, and
+                    // (FP32) the last cells of a row zero its padding, so that every
                     // sector the sweep writes is complete (a partly written sector
-                    // costs the memory system a read of the old sector)
-                    if (c->storage != LBM_F64) {
-                        const int per = 32 / c->elem, k = b.px - b.nx;
-                        for (int z = 0; z < b.nz; ++z)
-                            for (int y = 0; y < b.ny; ++y) {
-                                const long long row = (z + 1) * pxy + (long long)(y + 1) * b.pxf + OXF;
-                                for (int x0 = 0; x0 < b.nx; x0 += per) {
-                                    const int x1 = std::min(b.nx, x0 + per);
-                                    bool fluid = false;
-                                    for (int x = x0; x < x1; ++x) fluid = fluid || (f[row + x] & F_KIND) == F_FLUID;
-                                    if (!fluid) continue;
-                                    for (int x = x0; x < x1; ++x)
-                                        if ((f[row + x] & F_KIND) == F_NOSLIP) f[row + x] |= F_FILL;
-                                }
-                                // FP32: padding element nx + j is zeroed by cell nx - 1 - j,
-                                // when all of those cells are stored (the 16-bit sweeps ran
-                                // slower with padding stores in their kernels)
-                                bool tail = c->storage == LBM_F32 && k > 0 && k <= b.nx;
-                                for (int x = b.nx - k; tail && x < b.nx; ++x)
-                                    tail = (f[row + x] & F_KIND) == F_FLUID || (f[row + x] & F_FILL);
-                                if (tail)
-                                    for (int x = b.nx - k; x < b.nx; ++x)
-                                        f[row + x] |= uint8_t(F_PAD | ((b.nx - 1 - x) << F_PAD_SHIFT));
-                            }
-                    }
+                    // costs the memory system a read of the old sector; the 16-bit
+                    // sweeps ran slower with padding stores in their kernels)
+                    if (c->storage != LBM_F64)
+                        mark_sector_fills(f.data(), b.nx, b.ny, b.nz, b.px, b.py, b.pxf, c->elem,
+                                          c->storage == LBM_F32);
                     hflags.insert(hflags.end(), f.begin(), f.end());
                     hlinks.insert(hlinks.end(), lk.begin(), lk.end());
                     c->blocks.push_back(b);
